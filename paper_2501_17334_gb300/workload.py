@@ -1,0 +1,200 @@
+"""Seeded synthetic inputs for Pauli quantum state tomography.
+
+This module only *makes data*: the measurement operators, a ground-truth
+state, and the multinomial counts an experiment would have recorded
+(Step 1 of the method, Sec. III "Steps").  It holds none of the sampler's
+arithmetic -- no parameterisation, likelihood, proposal or pooling -- so both
+the FP64 oracle and the CUDA path can consume its output as plain data.
+
+Conventions (the paper is silent on them, Sec. IV uses "all possible Pauli
+measurement combinations"):
+
+* basis index ``k = sum_q s_q 3**(Q-1-q)`` with ``s = 0, 1, 2`` for X, Y, Z and
+  qubit 0 the most significant factor of the Kronecker product;
+* outcome index ``l = sum_q b_q 2**(Q-1-q)`` with ``b = 0`` the +1 eigenvalue;
+* POVM element ``Lambda_kl`` is row ``k*D + l`` of a ``[K*D, D, D]`` array.
+
+Workloads follow the five benchmark configurations (1 to 5 qubits); the seed of
+the truth is ``1000 + c``, of the counts ``2000 + c`` and of the chains
+``3000 + c`` for configuration ``c``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+# single-qubit eigenvectors, index [setting][outcome] ; setting 0=X, 1=Y, 2=Z
+_S2 = 1.0 / math.sqrt(2.0)
+_EIGVEC = np.array(
+    [
+        [[_S2, _S2], [_S2, -_S2]],            # X+ , X-
+        [[_S2, 1j * _S2], [_S2, -1j * _S2]],  # Y+ , Y-
+        [[1.0, 0.0], [0.0, 1.0]],             # Z+ , Z-
+    ],
+    dtype=np.complex128,
+)
+
+
+def pauli_vectors(num_qubits: int) -> np.ndarray:
+    """Measurement vectors ``phi_kl`` (``Lambda_kl = |phi_kl><phi_kl|``), shape ``[K*D, D]``."""
+    q = int(num_qubits)
+    if q < 1:
+        raise ValueError("num_qubits must be >= 1")
+    d = 1 << q
+    k_count = 3 ** q
+    out = np.empty((k_count * d, d), dtype=np.complex128)
+    for k in range(k_count):
+        settings = [(k // 3 ** (q - 1 - i)) % 3 for i in range(q)]
+        for l in range(d):
+            bits = [(l >> (q - 1 - i)) & 1 for i in range(q)]
+            v = np.array([1.0 + 0j])
+            for s, b in zip(settings, bits):
+                v = np.kron(v, _EIGVEC[s, b])
+            out[k * d + l] = v
+    return out
+
+
+def pauli_povms(num_qubits: int):
+    """All ``3**Q`` Pauli-basis POVMs as real and imaginary ``[K*D, D, D]`` float64 arrays."""
+    phi = pauli_vectors(num_qubits)
+    lam = phi[:, :, None] * phi[:, None, :].conj()
+    return np.ascontiguousarray(lam.real), np.ascontiguousarray(lam.imag)
+
+
+def ginibre_state(dim: int, rank: int, rng: np.random.Generator) -> np.ndarray:
+    """``G G^dagger / Tr`` with ``G`` a ``dim x rank`` standard complex Gaussian matrix."""
+    g = rng.standard_normal((dim, rank)) + 1j * rng.standard_normal((dim, rank))
+    rho = g @ g.conj().T
+    return rho / np.trace(rho).real
+
+
+def haar_pure_state(dim: int, rng: np.random.Generator) -> np.ndarray:
+    """``|psi><psi|`` for a normalised complex Gaussian vector (Haar-random pure state)."""
+    psi = rng.standard_normal(dim) + 1j * rng.standard_normal(dim)
+    psi /= np.linalg.norm(psi)
+    return np.outer(psi, psi.conj())
+
+
+def depolarise(rho: np.ndarray, weight: float) -> np.ndarray:
+    """``(1 - weight) rho + weight I/D``."""
+    d = rho.shape[0]
+    return (1.0 - weight) * rho + weight * np.eye(d) / d
+
+
+def sample_counts(truth: np.ndarray, num_qubits: int, shots_per_basis, rng: np.random.Generator) -> np.ndarray:
+    """Multinomial outcome counts ``c_kl`` (int32, length ``K*D``) of ``shots_per_basis`` draws per basis.
+
+    Outcome probabilities follow the Born rule ``<phi_kl| truth |phi_kl>``.
+    """
+    phi = pauli_vectors(num_qubits)
+    d = 1 << num_qubits
+    k_count = 3 ** num_qubits
+    born = np.einsum("ia,ab,ib->i", phi.conj(), truth, phi).real
+    born = np.clip(born, 0.0, None).reshape(k_count, d)
+    shots = np.broadcast_to(np.asarray(shots_per_basis, dtype=np.int64), (k_count,))
+    counts = np.empty((k_count, d), dtype=np.int64)
+    for k in range(k_count):
+        pk = born[k] / born[k].sum()
+        counts[k] = rng.multinomial(int(shots[k]), pk)
+    return counts.reshape(-1).astype(np.int32)
+
+
+@dataclasses.dataclass
+class Problem:
+    """One tomography problem: inputs for both the oracle and the CUDA sampler."""
+
+    num_qubits: int
+    povm_re: np.ndarray
+    povm_im: np.ndarray
+    counts: np.ndarray
+    truth: np.ndarray
+    num_chains: int
+    num_steps: int
+    beta0: float
+    seed: int
+    name: str = ""
+
+    @property
+    def dim(self) -> int:
+        return 1 << self.num_qubits
+
+    @property
+    def num_povms(self) -> int:
+        return 3 ** self.num_qubits
+
+
+def make_problem(
+    num_qubits: int,
+    truth: np.ndarray,
+    shots_per_basis,
+    num_chains: int,
+    num_steps: int,
+    beta0: float,
+    data_seed: int,
+    chain_seed: int,
+    name: str = "",
+) -> Problem:
+    povm_re, povm_im = pauli_povms(num_qubits)
+    counts = sample_counts(truth, num_qubits, shots_per_basis, np.random.default_rng(data_seed))
+    return Problem(num_qubits, povm_re, povm_im, counts, truth, int(num_chains), int(num_steps),
+                   float(beta0), int(chain_seed), name)
+
+
+def config_problem(index: int, num_chains: Optional[int] = None, num_steps: Optional[int] = None) -> Problem:
+    """Benchmark configuration ``index`` (1..4) with optional chain/step overrides.
+
+    1: 1 qubit, Ginibre 2x2 truth, 1000 shots/basis, 64 chains x 2000 steps, beta0 0.1.
+    2: 2 qubits, Ginibre truth mixed with I/D at weight 0.1, 1000 shots, 4096 x 5000, beta0 0.05.
+    3: 3 qubits, rank-2 Ginibre mixed at 0.05, 2000 shots, 16384 x 2000, beta0 0.1 (the
+       paper's initial beta, Algorithm 2, since the configuration names none).
+    4: 4 qubits, Haar pure state depolarised at 0.02, 1000 shots, 65536 x 1000, beta0 0.02.
+    """
+    rng = np.random.default_rng(1000 + index)
+    if index == 1:
+        q, truth, shots, r, s, b = 1, ginibre_state(2, 2, rng), 1000, 64, 2000, 0.1
+    elif index == 2:
+        q, truth, shots, r, s, b = 2, depolarise(ginibre_state(4, 4, rng), 0.1), 1000, 4096, 5000, 0.05
+    elif index == 3:
+        q, truth, shots, r, s, b = 3, depolarise(ginibre_state(8, 2, rng), 0.05), 2000, 16384, 2000, 0.1
+    elif index == 4:
+        q, truth, shots, r, s, b = 4, depolarise(haar_pure_state(16, rng), 0.02), 1000, 65536, 1000, 0.02
+    else:
+        raise ValueError("configuration index must be 1..4 (use heterogeneous_batch for 5)")
+    if num_chains is not None:
+        r = num_chains
+    if num_steps is not None:
+        s = num_steps
+    return make_problem(q, truth, shots, r, s, b, 2000 + index, 3000 + index, name=f"config{index}")
+
+
+def heterogeneous_batch(num_problems: int = 64, seed: int = 1005, max_qubits: int = 5,
+                        chain_scale: float = 1.0) -> List[Problem]:
+    """Batch of independent problems of uneven size (configuration 5).
+
+    Qubits uniform in 1..max_qubits, shots per basis uniform in 500..4000, Ginibre truth of
+    rank uniform in 1..D, chain counts log-uniform in [256, 32768] (times ``chain_scale``).
+    """
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(num_problems):
+        q = int(rng.integers(1, max_qubits + 1))
+        d = 1 << q
+        rank = int(rng.integers(1, d + 1))
+        truth = ginibre_state(d, rank, rng)
+        shots = int(rng.integers(500, 4001))
+        chains = int(round(math.exp(rng.uniform(math.log(256), math.log(32768))) * chain_scale))
+        chains = max(1, chains)
+        probs.append(make_problem(q, truth, shots, chains, 1000, 0.05,
+                                  int(rng.integers(1 << 31)), int(rng.integers(1 << 31)),
+                                  name=f"batch{i}"))
+    return probs
+
+
+def latent_batch(num: int, num_qubits: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Standard-normal latent vectors ``x`` of length ``4 D^2`` (float64, ``[num, 4D^2]``)."""
+    d = 1 << num_qubits
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal((num, 4 * d * d))
