@@ -1,0 +1,237 @@
+/*
+ * qst.h -- C ABI of the GB300 (sm_103a) pooled-chain pCN sampler for Bayesian
+ * quantum state tomography (Nguyen, Law, Lukens, arXiv:2501.17334).
+ *
+ * The library runs R independent, non-communicating preconditioned
+ * Crank-Nicolson Metropolis-Hastings chains per tomography problem (Sec. I and
+ * Algorithm 2), each over the Bures parameterisation rho(x) of Algorithm 1, with
+ * the multinomial likelihood of Eq. likelihood, and pools every chain's kept
+ * states into the posterior mean of Eq. BME2 plus the autocorrelation
+ * diagnostics of Eq. ACFrho and Eq. IACT.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a qst_status; no C++ exception crosses the ABI.
+ *     qst_last_error() gives a human-readable message for the last failure
+ *     on the calling thread.
+ *   - "host" pointers are CPU memory owned by the caller; "device" pointers are
+ *     CUDA global memory on the handle's device, owned by the caller.
+ *   - Work is enqueued on the caller's CUDA stream given at creation; calls that
+ *     return host data synchronise that stream first.
+ *   - Device-side trouble (a non-finite initial log-likelihood, an exhausted
+ *     wait, a failed bounds check) sets bits of a device status word; the next
+ *     synchronising call reports it as QST_ERR_NUMERIC or QST_ERR_TIMEOUT.
+ *   - Latent vectors x in R^{4 D^2} are stored [Re G | Im G | Re H | Im H] with
+ *     each D x D block column-major (Algorithm 1 steps 2-3).
+ *   - The packed density matrix vec_h(rho) in R^{D^2} has, at row-major
+ *     position (i, j): Re rho_ii on the diagonal, Re rho_ij above it (i < j),
+ *     Im rho_ij below it (i > j).
+ */
+#ifndef QST_H
+#define QST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QST_OK = 0,
+    QST_ERR_INVALID_ARG = 1, /* rejected input; nothing was allocated or enqueued */
+    QST_ERR_CUDA = 2,        /* a CUDA runtime/driver call failed */
+    QST_ERR_OOM = 3,         /* workspace too small or allocation failed */
+    QST_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    QST_ERR_NUMERIC = 5,     /* non-finite values where finite ones were required */
+    QST_ERR_STATE = 6,       /* call not valid in the handle's current state */
+    QST_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} qst_status;
+
+/* Arithmetic of the projector contraction p = vec_h(rho) . P (Sec. II, p_kl = Tr Lambda_kl rho). */
+typedef enum {
+    QST_PREC_FP32 = 0,  /* plain FP32 SIMT contraction */
+    QST_PREC_BF16X3 = 1 /* tcgen05 tensor cores: rho split into three bf16 terms against the
+                           exactly-representable Pauli projector matrix, FP32 accumulation */
+} qst_precision;
+
+/* One tomography problem (Sec. III Steps 1-4).  All pointers are host memory,
+ * read during qst_create only. */
+typedef struct {
+    int32_t num_qubits;     /* Q, 1..4 (D = 2^Q) */
+    int32_t num_povms;      /* K, the number of measurement settings (3^Q for Pauli) */
+    const int32_t *counts;  /* [K*D] outcome counts c_kl >= 0, setting-major */
+    const double *povm_re;  /* [K*D][D][D] row-major real parts of Lambda_kl */
+    const double *povm_im;  /* [K*D][D][D] imaginary parts */
+    int64_t num_chains;     /* R >= 1 */
+    int64_t chain_offset;   /* global id of chain 0 (disjoint ranges shard one run) */
+    uint64_t seed;          /* Philox4x32-10 key */
+    double beta0;           /* this problem's initial beta (Algorithm 2 l.1); 0 = the config's beta0 */
+} qst_problem_desc;
+
+/* Sampler settings (Algorithm 2 and Sec. IV); qst_default_config fills the paper's values. */
+typedef struct {
+    double beta0;           /* initial pCN step beta (Algorithm 2 l.1: 0.1) */
+    int32_t adapt_interval; /* M_A (Sec. III: 500); 0 keeps beta fixed */
+    double acc_lo, acc_hi;  /* acceptance window [0.2, 0.6] (Algorithm 2 l.14, l.17) */
+    double adapt_factor;    /* 1.1 (Algorithm 2 l.15, l.18) */
+    double beta_max;        /* 1.0: clamp keeping sqrt(1 - beta^2) real (the paper is silent) */
+    int32_t thin;           /* T: keep every T-th state (Algorithm 2 l.22) */
+    int32_t burn_in;        /* pool only steps j > burn_in (the paper uses none: 0) */
+    int32_t diag_chains;    /* chains per problem whose kept states are stored for the ACF */
+    int32_t traj_capacity;  /* kept states stored per diagnostic chain (Sec. IV: N = 2^10) */
+    int32_t acf_lmax;       /* l_max of Eq. ACFrho / Eq. IACT (Fig. 2: 200) */
+    int32_t trace_steps;    /* record the accept flag and log L(y') of the first trace_steps steps */
+    int32_t precision;      /* qst_precision */
+    int32_t qr_passes;      /* modified Gram-Schmidt passes computing U of Algorithm 1 l.4-5: 1, or 2
+                               (default) re-orthogonalising once, which cuts U's FP32 error ~10x */
+    int32_t reserved[3];    /* zero */
+} qst_sampler_cfg;
+
+/* Diagnostics of one problem (Sec. IV). */
+typedef struct {
+    int64_t steps_done;      /* steps j taken so far */
+    int64_t num_pooled;      /* N R: samples in the pooled mean */
+    int64_t num_kept;        /* N: kept states per chain */
+    double accept_rate;      /* accepted / proposed, over all chains and steps */
+    double beta_min, beta_mean, beta_max;
+    int64_t num_nonfinite;   /* chains whose current log L is not finite */
+    int32_t diag_chains;     /* chains whose tau was computed (0 if N <= l_max) */
+    int32_t acf_lmax;
+    double tau_mean;         /* mean over diagnostic chains of tau (Eq. IACT) */
+    double tau_max;
+    double n_eff;            /* N R / tau_mean (Sec. IV) */
+    uint32_t device_status;  /* raw status bits */
+    uint32_t reserved;
+} qst_diag;
+
+typedef struct qst_handle qst_handle;
+
+/* Kernel kinds for the profiling counters. */
+typedef enum {
+    QST_KERNEL_PROPOSE = 0,  /* Philox, pCN proposal, Algorithm 1, packing */
+    QST_KERNEL_PROJECT = 1,  /* projector contraction + log-likelihood epilogue */
+    QST_KERNEL_ACCEPT = 2,   /* accept test, adaptation, write-back, pooling, trajectories */
+    QST_KERNEL_DIAG = 3,     /* ACF / IACT and pooled-mean reductions */
+    QST_KERNEL_KINDS = 4
+} qst_kernel_kind;
+
+/* ---- status and configuration -------------------------------------------------------- */
+
+const char *qst_status_string(qst_status status);
+/* Message of the last failing call on this thread ("" if none). */
+const char *qst_last_error(void);
+/* Fills cfg with the paper's settings: beta0 0.1, M_A 500, window [0.2, 0.6], factor 1.1,
+ * beta_max 1, T 1, no burn-in, 256 diagnostic chains, capacity 1024, l_max 200, FP32,
+ * two Gram-Schmidt passes. */
+void qst_default_config(qst_sampler_cfg *cfg);
+
+/* ---- lifecycle ---------------------------------------------------------------------- */
+
+/* Device bytes qst_create needs for these problems and settings.
+ * Errors: QST_ERR_INVALID_ARG for an invalid problem or setting (see qst_create). */
+qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_problems,
+                              const qst_sampler_cfg *cfg, size_t *bytes);
+
+/* Validates the problems (Sec. III Step 1: counts >= 0; each Lambda_kl Hermitian and
+ * sum_l Lambda_kl = I to 1e-12; Q in 1..4; R >= 1; T >= 1; 0 < beta0 <= beta_max <= 1 for the
+ * config's and every problem's own beta0 (0 meaning the config's);
+ * for QST_PREC_BF16X3 every packed projector entry exactly representable in bf16),
+ * packs the projectors, uploads everything into the workspace and enqueues the chains'
+ * initial states y^0 ~ N(0, I) with rho(y^0) and log L(y^0) (Algorithm 2 l.1).
+ * d_workspace: device memory of at least qst_workspace_size bytes, 256-byte aligned,
+ * owned by the caller and kept alive until qst_destroy; NULL makes the library
+ * allocate (and later free) it itself.  cuda_stream: a cudaStream_t (NULL = default).
+ * The problem descriptions are copied; the caller may free them on return. */
+qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, const qst_sampler_cfg *cfg,
+                      void *d_workspace, size_t workspace_bytes, void *cuda_stream, qst_handle **out);
+
+/* Enqueues num_steps steps j -> j+1 of Algorithm 2 for every chain of every problem
+ * (proposal, Algorithm 1, likelihood, accept, adaptation, thinning and pooling).
+ * Asynchronous on the handle's stream; resumable (step numbering continues).
+ * Errors: QST_ERR_INVALID_ARG if num_steps < 0. */
+qst_status qst_run_chains(qst_handle *h, int64_t num_steps);
+
+/* Pooled posterior mean rho^{N,R} of Eq. BME2 / Step 6 for one problem, as row-major
+ * host arrays rho_re[D*D], rho_im[D*D] (caller-owned), and the sample count N R.
+ * Synchronises the stream.  Errors: QST_ERR_STATE if nothing has been pooled yet. */
+qst_status qst_posterior_mean(qst_handle *h, int32_t problem, double *rho_re, double *rho_im,
+                              int64_t *num_pooled);
+
+/* Diagnostics of one problem (Sec. IV): acceptance, beta statistics, the chain-averaged
+ * ACF c[0..l_max] of Eq. ACFrho into acf (host, l_max+1 doubles, may be NULL) and the
+ * per-chain IACT tau of Eq. IACT into tau (host, diag_chains doubles, may be NULL).
+ * Synchronises the stream. */
+qst_status qst_diagnostics(qst_handle *h, int32_t problem, qst_diag *out, double *acf, double *tau);
+
+/* Waits for the handle's work and reports device status bits. */
+qst_status qst_synchronize(qst_handle *h);
+
+/* Releases the handle (and the workspace if the library allocated it). */
+void qst_destroy(qst_handle *h);
+
+/* ---- state access, checkpoint, restore ----------------------------------------------- */
+
+/* Copies the current chain states of one problem to host arrays (each may be NULL):
+ * y [R][4 D^2] float, logl [R] double, beta [R] double, accepts [R] int64 (accepted
+ * proposals so far).  Synchronises. */
+qst_status qst_get_state(qst_handle *h, int32_t problem, float *y, double *logl, double *beta,
+                         int64_t *accepts);
+
+/* Accept flags [trace_steps][R] (uint8) and log L(y') [trace_steps][R] of the first
+ * cfg.trace_steps steps (host, each may be NULL).  Synchronises. */
+qst_status qst_get_trace(qst_handle *h, int32_t problem, uint8_t *accept, double *logl_prop);
+
+/* Size of, writing of and reading of a host checkpoint of every chain state, pooled sum,
+ * trajectory and step counter.  Philox streams are counter-based, so a restored handle
+ * continues bit-identically.  qst_restore needs a handle created with the same problems
+ * and settings.  Both synchronise. */
+qst_status qst_checkpoint_size(qst_handle *h, size_t *bytes);
+qst_status qst_checkpoint(qst_handle *h, void *buffer, size_t bytes);
+qst_status qst_restore(qst_handle *h, const void *buffer, size_t bytes);
+
+/* ---- stateless evaluation ---------------------------------------------------------------- */
+
+/* For n latent vectors x (device, [n][4 D^2] float), computes rho(x) of Algorithm 1 as
+ * packed vec_h (device [n][D^2] float, may be NULL), the outcome probabilities
+ * p_kl = Tr Lambda_kl rho (device [n][K D] float, may be NULL) and log L(x) of
+ * Eq. likelihood (device [n] double, may be NULL), with the handle's precision.
+ * Uses the problem's proposal buffers as scratch: call it between qst_run_chains calls,
+ * not concurrently with them.  Errors: QST_ERR_INVALID_ARG if n < 0 or n > R. */
+qst_status qst_evaluate(qst_handle *h, int32_t problem, const float *x, int64_t n, float *rho, float *p,
+                        double *logl);
+
+/* ---- profiling ---------------------------------------------------------------------------- */
+
+/* Enables (1) or disables (0) CUDA-event timing of every kernel launch on the stream. */
+qst_status qst_set_profiling(qst_handle *h, int32_t enabled);
+/* Total device milliseconds and launch count of one kernel kind since the last reset
+ * (synchronises); reset != 0 zeroes the counters afterwards. */
+qst_status qst_kernel_time(qst_handle *h, int32_t kind, int32_t reset, double *total_ms, int64_t *launches);
+/* Kernel launches the handle has enqueued since creation. */
+int64_t qst_launch_count(const qst_handle *h);
+
+/* ---- test hooks ---------------------------------------------------------------------------- */
+
+/* Raw Philox4x32-10 words: for chains chain0..chain0+nchains-1 and blocks
+ * block0..block0+nblocks-1 of the stream (seed, step, tag), writes
+ * out[((c - chain0) * nblocks + (b - block0)) * 4 + w] (device uint32).
+ * Counter = (block, step, chain, tag), key = (seed low, seed high). */
+qst_status qst_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uint32_t chain0, int64_t nchains,
+                             uint32_t block0, int32_t nblocks, uint32_t *out, void *cuda_stream);
+
+/* Packs the POVM elements into the real [D^2][K D] matrix P with p = vec_h(rho) . P:
+ * P[(i,i), kl] = Re Lambda_ii, P[(i,j), kl] = 2 Re Lambda_ij (i < j), 2 Im Lambda_ij (i > j).
+ * Host-only.  P_out: host [D^2][K D] float. */
+qst_status qst_pack_projectors(int32_t num_qubits, int32_t num_povms, const double *povm_re,
+                               const double *povm_im, float *P_out);
+
+/* Fault injection: sets the current latent state of one chain to NaN, so every later
+ * proposal has a non-finite log-likelihood and is rejected; the chain keeps (and keeps
+ * pooling) its last valid rho.  Device-side only, asynchronous. */
+qst_status qst_inject_nan(qst_handle *h, int32_t problem, int64_t chain);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QST_H */

@@ -1,0 +1,250 @@
+// Accept / reject, step-size adaptation, thinning and pooling (Algorithm 2 l.6-24,
+// Eq. BME2), the diagnostics reductions (Eq. ACFrho, Eq. IACT) and small test hooks.
+#include "qst_internal.cuh"
+
+namespace qst {
+namespace {
+
+constexpr int kChainsPerCta = 128;
+constexpr int kThreads = 256;
+
+struct AcceptArgs {
+    ProblemView p;
+    SamplerParams sp;
+    int mode;          // MODE_INIT or MODE_STEP
+    uint32_t step;     // j
+    int kept;          // j is a kept step (j % T == 0 and j > burn_in)
+    int64_t kept_idx;  // index of this kept state (0-based) in the trajectories
+};
+
+// One CTA owns chains [128 b, 128 b + 128) and pool slot b.
+__global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
+    const ProblemView &p = a.p;
+    __shared__ uint8_t flag[kChainsPerCta];
+    __shared__ float inv_tr[kChainsPerCta];
+    __shared__ float part[kThreads];
+    const int tid = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * kChainsPerCta;
+    const int nc = (int)min((int64_t)kChainsPerCta, p.R - c0);
+
+    // ---- phase 1: one thread per chain -------------------------------------------------
+    if (tid < kChainsPerCta) {
+        uint8_t acc = 0;
+        float itr = 0.0f;
+        if (tid < nc) {
+            const int64_t c = c0 + tid;
+            // log L(y') = C0 + sum_{c>0} c log(q invf) - N log t: q = vec_h(rho) . P for the
+            // stored FP32 rho, t its exact trace, p = q / t
+            const double tr = p.trace_prop[c];
+            itr = (float)(1.0 / tr);
+            double logl_prop = p.C0 - p.Ntot * log(tr);
+            for (int g = 0; g < p.ngroups; ++g) logl_prop += p.logl_part[(int64_t)g * p.R + c];
+            if (a.mode == MODE_INIT) {
+                acc = 1;
+                p.logl_cur[c] = logl_prop;
+                p.cur[c] ^= 1;
+            } else {
+                // l.6-7: alpha ~ U(0,1), accept iff log alpha < log L(y') - log L(y)
+                const uint32_t chain_id = (uint32_t)(p.chain_offset + c);
+                const uint4 w = Philox::block(make_uint4(0u, a.step, chain_id, TAG_ALPHA),
+                                              (uint32_t)(p.seed & 0xffffffffu), (uint32_t)(p.seed >> 32));
+                const double alpha = ((double)(w.x >> 9) + 0.5) * 0x1p-23;
+                const double log_alpha = log(alpha);
+                const double logl_cur = p.logl_cur[c];
+                acc = (log_alpha < logl_prop - logl_cur) ? 1 : 0;
+                int32_t win = p.acc_win[c];
+                if (acc) {
+                    p.logl_cur[c] = logl_prop;
+                    p.cur[c] ^= 1;
+                    win += 1;
+                    p.acc_total[c] += 1;
+                }
+                if (p.trace_steps > 0 && a.step >= 1 && a.step <= (uint32_t)p.trace_steps) {
+                    const int64_t t = (int64_t)(a.step - 1) * p.R + c;
+                    p.trace_acc[t] = acc;
+                    p.trace_logl[t] = logl_prop;
+                }
+                // l.13-21: every M_A steps rescale beta by the window's acceptance rate
+                if (a.sp.adapt_interval > 0 && a.step % (uint32_t)a.sp.adapt_interval == 0) {
+                    const double rate = (double)win / (double)a.sp.adapt_interval;
+                    double beta = p.beta[c];
+                    if (rate > a.sp.acc_hi) beta = a.sp.adapt_factor * beta;
+                    if (rate < a.sp.acc_lo) beta = beta / a.sp.adapt_factor;
+                    if (beta > a.sp.beta_max) beta = a.sp.beta_max;
+                    p.beta[c] = beta;
+                    win = 0;
+                }
+                p.acc_win[c] = win;
+            }
+        }
+        flag[tid] = acc;
+        inv_tr[tid] = itr;
+    }
+    __syncthreads();
+
+    // ---- phase 2: rho write-back, pooling of the current state, trajectories ------------
+    // Threads cover the packed entries; with fewer entries than threads, several thread
+    // groups split the chains and combine through shared memory.
+    const int d = p.d;
+    const int width = d < kThreads ? d : kThreads;
+    const int ngrp = kThreads / width;
+    const int e_local = tid % width, grp = tid / width;
+    const bool pool_now = (a.mode == MODE_STEP) && a.kept;
+    for (int e0 = 0; e0 < d; e0 += width) {
+        const int e = e0 + e_local;
+        float sum = 0.0f;
+        if (grp < ngrp) {
+            for (int k = grp; k < nc; k += ngrp) {
+                const int64_t c = c0 + k;
+                float v;
+                if (flag[k]) {
+                    v = p.rho_prop[c * p.d_pad + e] * inv_tr[k];
+                    p.rho_cur[c * p.d_pad + e] = v;
+                } else {
+                    v = pool_now ? p.rho_cur[c * p.d_pad + e] : 0.0f;
+                }
+                sum += v;
+                if (pool_now && c < p.n_diag && a.kept_idx < p.traj_cap)
+                    p.traj[((int64_t)c * p.traj_cap + a.kept_idx) * d + e] = v;
+            }
+        }
+        if (pool_now) {
+            part[tid] = sum;
+            __syncthreads();
+            if (grp == 0) {
+                float tot = 0.0f;
+                for (int q = 0; q < ngrp; ++q) tot += part[q * width + e_local];
+                p.pool[(int64_t)blockIdx.x * d + e] += (double)tot;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Sums the pool slots in slot order (deterministic) -> out[d].
+__global__ void pool_reduce_kernel(const double *pool, int n_slots, int d, double *out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < n_slots; ++b) s += pool[(int64_t)b * d + e];
+        out[e] = s;
+    }
+}
+
+// Eq. ACFrho for one diagnostic chain per CTA: c~[l] = sum_{n < N - lmax} sum_e w_e
+// (x_n,e - m_e)(x_{n+l},e - m_e) with w_e = 1 on the diagonal and 2 off it (each packed
+// off-diagonal entry stands for the (i,j) and (j,i) terms of Eq. ACFa).  Products in
+// FP32 summed over chunks of 32 samples, chunks accumulated in FP64.
+__global__ void acf_kernel(const float *traj, int traj_cap, int d, int D, int n_kept, int lmax, double *out) {
+    extern __shared__ float sh[];  // mean[d]
+    __shared__ double red[kThreads];
+    const float *x = traj + (int64_t)blockIdx.x * traj_cap * d;
+    for (int e = threadIdx.x; e < d; e += blockDim.x) {
+        double s = 0.0;
+        for (int n = 0; n < n_kept; ++n) s += x[(int64_t)n * d + e];
+        sh[e] = (float)(s / n_kept);
+    }
+    __syncthreads();
+    const int m = n_kept - lmax;
+    for (int l = 0; l <= lmax; ++l) {
+        double acc = 0.0;
+        for (int e = threadIdx.x; e < d; e += blockDim.x) {
+            const float mu = sh[e];
+            const float w = ((e / D) == (e % D)) ? 1.0f : 2.0f;
+            float chunk = 0.0f;
+            for (int n = 0; n < m; ++n) {
+                chunk = __fmaf_rn(x[(int64_t)n * d + e] - mu, x[(int64_t)(n + l) * d + e] - mu, chunk);
+                if ((n & 31) == 31) {
+                    acc += (double)(w * chunk);
+                    chunk = 0.0f;
+                }
+            }
+            acc += (double)(w * chunk);
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[(int64_t)blockIdx.x * (lmax + 1) + l] = red[0];
+        __syncthreads();
+    }
+}
+
+// log L = C0 - N log t + sum over column groups, for stateless evaluation.
+__global__ void logl_combine_kernel(const double *part, const double *trace, int ngroups, int64_t rows, double C0,
+                                    double Ntot, double *out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double v = C0 - Ntot * log(trace[r]);
+    for (int g = 0; g < ngroups; ++g) v += part[(int64_t)g * rows + r];
+    out[r] = v;
+}
+
+__global__ void philox_blocks_kernel(uint64_t seed, uint32_t step, uint32_t tag, uint32_t chain0, int64_t nchains,
+                                     uint32_t block0, int32_t nblocks, uint32_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nchains * nblocks) return;
+    const uint32_t c = chain0 + (uint32_t)(i / nblocks);
+    const uint32_t b = block0 + (uint32_t)(i % nblocks);
+    const uint4 w = Philox::block(make_uint4(b, step, c, tag), (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    reinterpret_cast<uint4 *>(out)[i] = w;
+}
+
+__global__ void inject_nan_kernel(float *y, const uint8_t *cur, int64_t R, int nx, int64_t chain) {
+    const int b = cur[chain];
+    for (int e = threadIdx.x; e < nx; e += blockDim.x) y[((int64_t)b * R + chain) * nx + e] = __int_as_float(0x7fc00000);
+}
+
+}  // namespace
+
+cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mode, uint32_t step, bool kept,
+                          int64_t kept_idx, uint32_t *status, cudaStream_t s) {
+    (void)status;
+    AcceptArgs a;
+    a.p = p;
+    a.sp = sp;
+    a.mode = mode;
+    a.step = step;
+    a.kept = kept ? 1 : 0;
+    a.kept_idx = kept_idx;
+    const int64_t blocks = (p.R + kChainsPerCta - 1) / kChainsPerCta;
+    accept_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int accept_slots(int64_t R) { return (int)((R + kChainsPerCta - 1) / kChainsPerCta); }
+
+cudaError_t launch_pool_reduce(const ProblemView &p, double *out, cudaStream_t s) {
+    pool_reduce_kernel<<<(p.d + 255) / 256, 256, 0, s>>>(p.pool, p.n_slots, p.d, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acf(const ProblemView &p, int n_kept, int lmax, double *acf_raw, cudaStream_t s) {
+    if (p.n_diag <= 0 || n_kept <= lmax) return cudaSuccess;
+    acf_kernel<<<p.n_diag, kThreads, sizeof(float) * p.d, s>>>(p.traj, p.traj_cap, p.d, p.D, n_kept, lmax, acf_raw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_logl_combine(const ProblemView &p, int64_t rows, double *out, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    logl_combine_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(p.logl_part, p.trace_prop, p.ngroups, rows, p.C0,
+                                                                         p.Ntot, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uint32_t chain0, int64_t nchains,
+                                 uint32_t block0, int32_t nblocks, uint32_t *out, cudaStream_t s) {
+    const int64_t total = nchains * nblocks;
+    if (total <= 0) return cudaSuccess;
+    philox_blocks_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(seed, step, tag, chain0, nchains, block0,
+                                                                          nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_nan(const ProblemView &p, int64_t chain, cudaStream_t s) {
+    inject_nan_kernel<<<1, 256, 0, s>>>(p.y, p.cur, p.R, p.nx, chain);
+    return cudaGetLastError();
+}
+
+}  // namespace qst

@@ -1,0 +1,838 @@
+// Host side of the C ABI declared in include/qst.h: validation, projector packing,
+// workspace layout, the step loop, read-back, checkpointing and profiling.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/qst.h"
+#include "qst_internal.cuh"
+
+using namespace qst;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+qst_status fail(qst_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+qst_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(QST_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(QST_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define QST_CUDA(call, what)                      \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Packs Lambda (row-major [KD][D][D]) into P[(i,j)][m] with stride ld (see qst.h).
+void pack_projectors(int D, int KD, const double *re, const double *im, double *P, int ld) {
+    for (int m = 0; m < KD; ++m) {
+        const double *lr = re + (size_t)m * D * D;
+        const double *li = im + (size_t)m * D * D;
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                double v;
+                if (i == j) v = lr[i * D + i];
+                else if (i < j) v = 2.0 * lr[i * D + j];
+                else v = 2.0 * li[i * D + j];
+                P[(size_t)(i * D + j) * ld + m] = v;
+            }
+    }
+}
+
+bool bf16_exact(double v) {
+    const float f = (float)v;
+    if ((double)f != v) return false;
+    return __bfloat162float(__float2bfloat16_rn(f)) == f;
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-problem host record and workspace layout
+// ------------------------------------------------------------------------------------------
+struct Layout {
+    size_t P32, Pbf, cnt, invf, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, acc_win,
+        acc_total, pool, traj, trace_acc, trace_logl, red, acf, logl_eval, end;
+};
+
+struct HostProblem {
+    ProblemView v{};
+    int Q = 0, K = 0, KDmax = 0;
+    double beta0 = 0.0;
+    Layout off{};
+    std::vector<float> P32;
+    std::vector<__nv_bfloat16> Pbf;
+    std::vector<float> cnt, invf;
+    TcPlan *tc = nullptr;
+};
+
+struct Plan {
+    std::vector<HostProblem> probs;
+    size_t status_off = 0;  // device status word
+    size_t bytes = 0;       // total workspace bytes
+};
+
+qst_status validate_cfg(const qst_sampler_cfg *cfg) {
+    if (!cfg) return fail(QST_ERR_INVALID_ARG, "cfg is NULL");
+    if (!(cfg->beta0 > 0.0) || !(cfg->beta_max <= 1.0) || !(cfg->beta0 <= cfg->beta_max))
+        return fail(QST_ERR_INVALID_ARG, "need 0 < beta0 <= beta_max <= 1 (beta0=%g, beta_max=%g)", cfg->beta0,
+                    cfg->beta_max);
+    if (cfg->adapt_interval < 0) return fail(QST_ERR_INVALID_ARG, "adapt_interval must be >= 0");
+    if (!(cfg->adapt_factor > 0.0)) return fail(QST_ERR_INVALID_ARG, "adapt_factor must be > 0");
+    if (!(cfg->acc_lo <= cfg->acc_hi)) return fail(QST_ERR_INVALID_ARG, "need acc_lo <= acc_hi");
+    if (cfg->thin < 1) return fail(QST_ERR_INVALID_ARG, "thin (T) must be >= 1");
+    if (cfg->burn_in < 0) return fail(QST_ERR_INVALID_ARG, "burn_in must be >= 0");
+    if (cfg->diag_chains < 0 || cfg->traj_capacity < 0 || cfg->acf_lmax < 0 || cfg->trace_steps < 0)
+        return fail(QST_ERR_INVALID_ARG, "diagnostic sizes must be >= 0");
+    if (cfg->precision != QST_PREC_FP32 && cfg->precision != QST_PREC_BF16X3)
+        return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
+    if (cfg->qr_passes != 1 && cfg->qr_passes != 2)
+        return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1 or 2");
+    return QST_OK;
+}
+
+qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sampler_cfg *cfg) {
+    if (d.num_qubits < 1 || d.num_qubits > 4)
+        return fail(d.num_qubits == 5 ? QST_ERR_UNSUPPORTED : QST_ERR_INVALID_ARG,
+                    "problem %d: num_qubits %d outside 1..4", idx, d.num_qubits);
+    if (d.num_povms < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_povms must be >= 1", idx);
+    if (!d.counts || !d.povm_re || !d.povm_im) return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
+    if (d.num_chains < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_chains must be >= 1", idx);
+    if (d.chain_offset < 0 || d.chain_offset + d.num_chains > (int64_t(1) << 32))
+        return fail(QST_ERR_INVALID_ARG, "problem %d: chain ids must fit 32 bits", idx);
+    if (!(d.beta0 >= 0.0) || d.beta0 > 1.0)
+        return fail(QST_ERR_INVALID_ARG, "problem %d: beta0 %g outside [0, 1] (0 = the config's)", idx, d.beta0);
+    if (d.beta0 > cfg->beta_max)
+        return fail(QST_ERR_INVALID_ARG, "problem %d: beta0 %g above beta_max %g", idx, d.beta0, cfg->beta_max);
+    const int D = 1 << d.num_qubits, KD = d.num_povms * D;
+    for (int m = 0; m < KD; ++m)
+        if (d.counts[m] < 0) return fail(QST_ERR_INVALID_ARG, "problem %d: negative count at %d", idx, m);
+    // Hermitian elements, completeness per setting
+    for (int m = 0; m < KD; ++m) {
+        const double *re = d.povm_re + (size_t)m * D * D, *im = d.povm_im + (size_t)m * D * D;
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                if (!std::isfinite(re[i * D + j]) || !std::isfinite(im[i * D + j]))
+                    return fail(QST_ERR_INVALID_ARG, "problem %d: non-finite POVM entry", idx);
+                if (std::fabs(re[i * D + j] - re[j * D + i]) > 1e-12 || std::fabs(im[i * D + j] + im[j * D + i]) > 1e-12)
+                    return fail(QST_ERR_INVALID_ARG, "problem %d: POVM element %d is not Hermitian", idx, m);
+            }
+    }
+    for (int k = 0; k < d.num_povms; ++k)
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                double sr = 0.0, si = 0.0;
+                for (int l = 0; l < D; ++l) {
+                    sr += d.povm_re[((size_t)(k * D + l) * D + i) * D + j];
+                    si += d.povm_im[((size_t)(k * D + l) * D + i) * D + j];
+                }
+                if (std::fabs(sr - (i == j ? 1.0 : 0.0)) > 1e-12 || std::fabs(si) > 1e-12)
+                    return fail(QST_ERR_INVALID_ARG, "problem %d: setting %d does not sum to the identity", idx, k);
+            }
+    return QST_OK;
+}
+
+qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler_cfg *cfg, Plan &plan) {
+    if (!probs || n < 1) return fail(QST_ERR_INVALID_ARG, "need at least one problem");
+    qst_status st = validate_cfg(cfg);
+    if (st != QST_OK) return st;
+    plan.probs.clear();
+    plan.probs.resize(n);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    for (int i = 0; i < n; ++i) {
+        const qst_problem_desc &d = probs[i];
+        st = validate_problem(d, i, cfg);
+        if (st != QST_OK) return st;
+        HostProblem &hp = plan.probs[i];
+        ProblemView &v = hp.v;
+        hp.Q = d.num_qubits;
+        hp.K = d.num_povms;
+        v.D = 1 << d.num_qubits;
+        v.d = v.D * v.D;
+        v.nx = 4 * v.d;
+        v.KD = d.num_povms * v.D;
+        v.d_pad = round_up(v.d, 64);
+        v.KD_pad = round_up(v.KD, 128);
+        v.R = d.num_chains;
+        v.chain_offset = d.chain_offset;
+        v.seed = d.seed;
+        hp.beta0 = d.beta0 > 0.0 ? d.beta0 : cfg->beta0;
+        const bool tc = cfg->precision == QST_PREC_BF16X3;
+        if (tc) {
+            const int nt = tc_column_tile(v.KD);
+            if (nt <= 0) return fail(QST_ERR_UNSUPPORTED, "problem %d: no tensor-core column tile for %d projectors", i, v.KD);
+            v.KD_tc = round_up(v.KD, nt);
+        } else {
+            v.KD_tc = 0;
+        }
+        hp.KDmax = std::max(v.KD_pad, v.KD_tc);
+        // packed projectors
+        std::vector<double> P((size_t)v.d * v.KD);
+        pack_projectors(v.D, v.KD, d.povm_re, d.povm_im, P.data(), v.KD);
+        hp.P32.assign((size_t)v.d_pad * v.KD_pad, 0.0f);
+        for (int r = 0; r < v.d; ++r)
+            for (int m = 0; m < v.KD; ++m) hp.P32[(size_t)r * v.KD_pad + m] = (float)P[(size_t)r * v.KD + m];
+        if (tc) {
+            hp.Pbf.assign((size_t)v.KD_tc * v.d_pad, __float2bfloat16_rn(0.0f));
+            for (int r = 0; r < v.d; ++r)
+                for (int m = 0; m < v.KD; ++m) {
+                    const double x = P[(size_t)r * v.KD + m];
+                    if (!bf16_exact(x))
+                        return fail(QST_ERR_INVALID_ARG,
+                                    "problem %d: packed projector entry %.17g is not exact in bf16; use QST_PREC_FP32",
+                                    i, x);
+                    hp.Pbf[(size_t)m * v.d_pad + r] = __float2bfloat16_rn((float)x);
+                }
+        }
+        // deviance weights: log L = C0 + sum_{c>0} c log(p * invf), invf = P_k / c (as float)
+        hp.cnt.assign(hp.KDmax, 0.0f);
+        hp.invf.assign(hp.KDmax, 1.0f);
+        double C0 = 0.0, Ntot = 0.0;
+        for (int k = 0; k < d.num_povms; ++k) {
+            int64_t Pk = 0;
+            for (int l = 0; l < v.D; ++l) Pk += d.counts[k * v.D + l];
+            for (int l = 0; l < v.D; ++l) {
+                const int m = k * v.D + l;
+                const int c = d.counts[m];
+                if (c == 0) continue;
+                const float invf = (float)((double)Pk / (double)c);
+                hp.cnt[m] = (float)c;
+                hp.invf[m] = invf;
+                C0 -= (double)c * std::log((double)invf);
+                Ntot += (double)c;
+            }
+        }
+        v.C0 = C0;
+        v.Ntot = Ntot;
+        v.ngroups = 1;
+        if (tc) {
+            v.ngroups = tc_ngroups(v, v.R);
+        } else {
+            v.ngroups = fp32_ngroups(v, v.R);
+        }
+        v.qr_passes = cfg->qr_passes;
+        v.n_slots = accept_slots(v.R);
+        v.n_diag = (int)std::min<int64_t>(cfg->diag_chains, v.R);
+        v.traj_cap = cfg->traj_capacity;
+        if (v.traj_cap == 0) v.n_diag = 0;
+        v.trace_steps = cfg->trace_steps;
+        Layout &L = hp.off;
+        const int64_t R = v.R;
+        L.P32 = take(sizeof(float) * hp.P32.size());
+        L.Pbf = take(tc ? sizeof(__nv_bfloat16) * hp.Pbf.size() : 0);
+        L.cnt = take(sizeof(float) * hp.KDmax);
+        L.invf = take(sizeof(float) * hp.KDmax);
+        L.y = take(sizeof(float) * 2 * R * v.nx);
+        L.cur = take(R);
+        L.rho_cur = take(sizeof(float) * R * v.d_pad);
+        L.rho_prop = take(sizeof(float) * R * v.d_pad);
+        L.rho_split = take(tc ? sizeof(__nv_bfloat16) * 3 * R * v.d_pad : 0);
+        L.trace_prop = take(sizeof(double) * R);
+        L.logl_cur = take(sizeof(double) * R);
+        L.logl_part = take(sizeof(double) * v.ngroups * R);
+        L.beta = take(sizeof(double) * R);
+        L.acc_win = take(sizeof(int32_t) * R);
+        L.acc_total = take(sizeof(int64_t) * R);
+        L.pool = take(sizeof(double) * v.n_slots * v.d);
+        L.traj = take(sizeof(float) * (size_t)v.n_diag * v.traj_cap * v.d);
+        L.trace_acc = take((size_t)v.trace_steps * R);
+        L.trace_logl = take(sizeof(double) * v.trace_steps * R);
+        L.red = take(sizeof(double) * v.d);
+        L.acf = take(sizeof(double) * (size_t)std::max(v.n_diag, 1) * (cfg->acf_lmax + 1));
+        L.logl_eval = take(sizeof(double) * R);
+        L.end = off;
+    }
+    plan.status_off = take(256);
+    plan.bytes = off;
+    return QST_OK;
+}
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+}  // namespace
+
+struct qst_handle {
+    Plan plan;
+    qst_sampler_cfg cfg{};
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    uint32_t *d_status = nullptr;
+    int64_t steps_done = 0;
+    int64_t kept = 0;
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<EventPair> pending;
+    std::vector<EventPair> spare;
+    double kind_ms[QST_KERNEL_KINDS] = {0, 0, 0, 0};
+    int64_t kind_launches[QST_KERNEL_KINDS] = {0, 0, 0, 0};
+    SamplerParams sp{};
+};
+
+namespace {
+
+template <class F>
+qst_status launch(qst_handle *h, int kind, const char *what, F &&f) {
+    EventPair ev{};
+    if (h->prof) {
+        if (!h->spare.empty()) {
+            ev = h->spare.back();
+            h->spare.pop_back();
+        } else {
+            QST_CUDA(cudaEventCreate(&ev.a), "cudaEventCreate");
+            QST_CUDA(cudaEventCreate(&ev.b), "cudaEventCreate");
+        }
+        ev.kind = kind;
+        QST_CUDA(cudaEventRecord(ev.a, h->stream), "cudaEventRecord");
+    }
+    cudaError_t e = f();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (h->prof) {
+        QST_CUDA(cudaEventRecord(ev.b, h->stream), "cudaEventRecord");
+        h->pending.push_back(ev);
+    }
+    h->launches += 1;
+    h->kind_launches[kind] += 1;
+    return QST_OK;
+}
+
+qst_status harvest(qst_handle *h) {
+    for (auto &ev : h->pending) {
+        QST_CUDA(cudaEventSynchronize(ev.b), "cudaEventSynchronize");
+        float ms = 0.0f;
+        QST_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b), "cudaEventElapsedTime");
+        h->kind_ms[ev.kind] += ms;
+        h->spare.push_back(ev);
+    }
+    h->pending.clear();
+    return QST_OK;
+}
+
+qst_status check_status(qst_handle *h) {
+    QST_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    uint32_t st = 0;
+    QST_CUDA(cudaMemcpy(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost), "read status");
+    if (st & STATUS_TIMEOUT) return fail(QST_ERR_TIMEOUT, "a device wait gave up (status 0x%x)", st);
+    if (st & (STATUS_BOUNDS | STATUS_BAD_LAUNCH)) return fail(QST_ERR_NUMERIC, "device check failed (status 0x%x)", st);
+    return QST_OK;
+}
+
+qst_status bind_problem(qst_handle *h, HostProblem &hp) {
+    char *b = h->ws;
+    ProblemView &v = hp.v;
+    const Layout &L = hp.off;
+    v.P32 = reinterpret_cast<const float *>(b + L.P32);
+    v.Pbf = reinterpret_cast<const __nv_bfloat16 *>(b + L.Pbf);
+    v.cnt = reinterpret_cast<const float *>(b + L.cnt);
+    v.invf = reinterpret_cast<const float *>(b + L.invf);
+    v.y = reinterpret_cast<float *>(b + L.y);
+    v.cur = reinterpret_cast<uint8_t *>(b + L.cur);
+    v.rho_cur = reinterpret_cast<float *>(b + L.rho_cur);
+    v.rho_prop = reinterpret_cast<float *>(b + L.rho_prop);
+    v.rho_split = reinterpret_cast<__nv_bfloat16 *>(b + L.rho_split);
+    v.trace_prop = reinterpret_cast<double *>(b + L.trace_prop);
+    v.logl_cur = reinterpret_cast<double *>(b + L.logl_cur);
+    v.logl_part = reinterpret_cast<double *>(b + L.logl_part);
+    v.beta = reinterpret_cast<double *>(b + L.beta);
+    v.acc_win = reinterpret_cast<int32_t *>(b + L.acc_win);
+    v.acc_total = reinterpret_cast<int64_t *>(b + L.acc_total);
+    v.pool = reinterpret_cast<double *>(b + L.pool);
+    v.traj = reinterpret_cast<float *>(b + L.traj);
+    v.trace_acc = reinterpret_cast<uint8_t *>(b + L.trace_acc);
+    v.trace_logl = reinterpret_cast<double *>(b + L.trace_logl);
+    return QST_OK;
+}
+
+bool is_tc(const qst_handle *h) { return h->cfg.precision == QST_PREC_BF16X3; }
+
+// proposal -> projection -> (accept) for one problem
+qst_status enqueue_projection(qst_handle *h, HostProblem &hp, int64_t rows, float *p_out) {
+    ProblemView &v = hp.v;
+    if (is_tc(h)) {
+        return launch(h, QST_KERNEL_PROJECT, "projection (tcgen05)", [&] {
+            return launch_project_tc(hp.tc, v, rows, v.logl_part, p_out, h->d_status, h->stream);
+        });
+    }
+    return launch(h, QST_KERNEL_PROJECT, "projection (fp32)", [&] {
+        return launch_project_fp32(v, v.rho_prop, rows, v.logl_part, p_out, h->stream);
+    });
+}
+
+qst_status enqueue_init(qst_handle *h, HostProblem &hp) {
+    ProblemView &v = hp.v;
+    qst_status st = launch(h, QST_KERNEL_PROPOSE, "propose (init)", [&] {
+        return launch_propose(v, MODE_INIT, 0u, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
+    });
+    if (st != QST_OK) return st;
+    st = enqueue_projection(h, hp, v.R, nullptr);
+    if (st != QST_OK) return st;
+    return launch(h, QST_KERNEL_ACCEPT, "accept (init)", [&] {
+        return launch_accept(v, h->sp, MODE_INIT, 0u, false, 0, h->d_status, h->stream);
+    });
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+const char *qst_status_string(qst_status s) {
+    switch (s) {
+        case QST_OK: return "ok";
+        case QST_ERR_INVALID_ARG: return "invalid argument";
+        case QST_ERR_CUDA: return "CUDA error";
+        case QST_ERR_OOM: return "out of memory";
+        case QST_ERR_TIMEOUT: return "device wait timed out";
+        case QST_ERR_NUMERIC: return "numeric or device check failure";
+        case QST_ERR_STATE: return "invalid state";
+        case QST_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *qst_last_error(void) { return g_last_error.c_str(); }
+
+void qst_default_config(qst_sampler_cfg *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->beta0 = 0.1;
+    cfg->adapt_interval = 500;
+    cfg->acc_lo = 0.2;
+    cfg->acc_hi = 0.6;
+    cfg->adapt_factor = 1.1;
+    cfg->beta_max = 1.0;
+    cfg->thin = 1;
+    cfg->burn_in = 0;
+    cfg->diag_chains = 256;
+    cfg->traj_capacity = 1024;
+    cfg->acf_lmax = 200;
+    cfg->trace_steps = 0;
+    cfg->precision = QST_PREC_FP32;
+    cfg->qr_passes = 2;
+}
+
+qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_problems, const qst_sampler_cfg *cfg,
+                              size_t *bytes) {
+    if (!bytes) return fail(QST_ERR_INVALID_ARG, "bytes is NULL");
+    Plan plan;
+    qst_status st = make_plan(problems, num_problems, cfg, plan);
+    if (st != QST_OK) return st;
+    *bytes = plan.bytes;
+    return QST_OK;
+}
+
+qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, const qst_sampler_cfg *cfg,
+                      void *d_workspace, size_t workspace_bytes, void *cuda_stream, qst_handle **out) {
+    if (!out) return fail(QST_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::unique_ptr<qst_handle> h(new qst_handle());
+    qst_status st = make_plan(problems, num_problems, cfg, h->plan);
+    if (st != QST_OK) return st;
+    h->cfg = *cfg;
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    h->sp.adapt_interval = cfg->adapt_interval;
+    h->sp.acc_lo = cfg->acc_lo;
+    h->sp.acc_hi = cfg->acc_hi;
+    h->sp.adapt_factor = cfg->adapt_factor;
+    h->sp.beta_max = cfg->beta_max;
+    if (d_workspace) {
+        if (workspace_bytes < h->plan.bytes)
+            return fail(QST_ERR_OOM, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
+                        h->plan.bytes);
+        if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+            return fail(QST_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        h->ws = static_cast<char *>(d_workspace);
+        h->ws_bytes = workspace_bytes;
+    } else {
+        void *p = nullptr;
+        QST_CUDA(cudaMalloc(&p, h->plan.bytes), "cudaMalloc(workspace)");
+        h->ws = static_cast<char *>(p);
+        h->ws_bytes = h->plan.bytes;
+        h->own_ws = true;
+    }
+    QST_CUDA(cudaMemsetAsync(h->ws, 0, h->plan.bytes, h->stream), "clear workspace");
+    h->d_status = reinterpret_cast<uint32_t *>(h->ws + h->plan.status_off);
+    for (auto &hp : h->plan.probs) {
+        bind_problem(h.get(), hp);
+        ProblemView &v = hp.v;
+        const Layout &L = hp.off;
+        QST_CUDA(cudaMemcpyAsync(h->ws + L.P32, hp.P32.data(), sizeof(float) * hp.P32.size(), cudaMemcpyHostToDevice,
+                                 h->stream), "upload P");
+        if (is_tc(h.get()))
+            QST_CUDA(cudaMemcpyAsync(h->ws + L.Pbf, hp.Pbf.data(), sizeof(__nv_bfloat16) * hp.Pbf.size(),
+                                     cudaMemcpyHostToDevice, h->stream), "upload P (bf16)");
+        QST_CUDA(cudaMemcpyAsync(h->ws + L.cnt, hp.cnt.data(), sizeof(float) * hp.KDmax, cudaMemcpyHostToDevice,
+                                 h->stream), "upload counts");
+        QST_CUDA(cudaMemcpyAsync(h->ws + L.invf, hp.invf.data(), sizeof(float) * hp.KDmax, cudaMemcpyHostToDevice,
+                                 h->stream), "upload weights");
+        std::vector<double> beta(v.R, hp.beta0);
+        QST_CUDA(cudaMemcpyAsync(v.beta, beta.data(), sizeof(double) * v.R, cudaMemcpyHostToDevice, h->stream),
+                 "upload beta");
+        // pageable copies above are staged synchronously; keep the host vectors alive until then
+        QST_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
+        if (is_tc(h.get())) {
+            cudaError_t e = tc_plan_create(v, v.rho_split, v.R, &hp.tc);
+            if (e != cudaSuccess) return cuda_fail(e, "tensor-core plan");
+        }
+        st = enqueue_init(h.get(), hp);
+        if (st != QST_OK) return st;
+        std::vector<float>().swap(hp.P32);
+        std::vector<__nv_bfloat16>().swap(hp.Pbf);
+    }
+    *out = h.release();
+    return QST_OK;
+}
+
+qst_status qst_run_chains(qst_handle *h, int64_t num_steps) {
+    if (!h) return fail(QST_ERR_INVALID_ARG, "handle is NULL");
+    if (num_steps < 0) return fail(QST_ERR_INVALID_ARG, "num_steps must be >= 0");
+    if (h->steps_done + num_steps > 0xffffffffLL) return fail(QST_ERR_INVALID_ARG, "step counter exceeds 32 bits");
+    for (int64_t s = 0; s < num_steps; ++s) {
+        const int64_t j = h->steps_done + 1;
+        const bool kept = (j % h->cfg.thin == 0) && (j > h->cfg.burn_in);
+        for (auto &hp : h->plan.probs) {
+            ProblemView &v = hp.v;
+            qst_status st = launch(h, QST_KERNEL_PROPOSE, "propose", [&] {
+                return launch_propose(v, MODE_STEP, (uint32_t)j, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
+            });
+            if (st != QST_OK) return st;
+            st = enqueue_projection(h, hp, v.R, nullptr);
+            if (st != QST_OK) return st;
+            st = launch(h, QST_KERNEL_ACCEPT, "accept", [&] {
+                return launch_accept(v, h->sp, MODE_STEP, (uint32_t)j, kept, h->kept, h->d_status, h->stream);
+            });
+            if (st != QST_OK) return st;
+        }
+        h->steps_done = j;
+        if (kept) h->kept += 1;
+    }
+    return QST_OK;
+}
+
+static qst_status get_problem(qst_handle *h, int32_t problem, HostProblem **hp) {
+    if (!h) return fail(QST_ERR_INVALID_ARG, "handle is NULL");
+    if (problem < 0 || problem >= (int32_t)h->plan.probs.size())
+        return fail(QST_ERR_INVALID_ARG, "problem index %d out of range", problem);
+    *hp = &h->plan.probs[problem];
+    return QST_OK;
+}
+
+qst_status qst_posterior_mean(qst_handle *h, int32_t problem, double *rho_re, double *rho_im, int64_t *num_pooled) {
+    HostProblem *hp;
+    qst_status st = get_problem(h, problem, &hp);
+    if (st != QST_OK) return st;
+    const ProblemView &v = hp->v;
+    const int64_t n = h->kept * v.R;
+    if (num_pooled) *num_pooled = n;
+    if (n == 0) return fail(QST_ERR_STATE, "no state has been pooled yet");
+    double *red = reinterpret_cast<double *>(h->ws + hp->off.red);
+    st = launch(h, QST_KERNEL_DIAG, "pool reduce", [&] { return launch_pool_reduce(v, red, h->stream); });
+    if (st != QST_OK) return st;
+    std::vector<double> sum(v.d);
+    QST_CUDA(cudaMemcpyAsync(sum.data(), red, sizeof(double) * v.d, cudaMemcpyDeviceToHost, h->stream), "read pool");
+    st = check_status(h);
+    if (st != QST_OK) return st;
+    const int D = v.D;
+    for (int i = 0; i < D; ++i)
+        for (int j = i; j < D; ++j) {
+            const double re = sum[i * D + j] / (double)n;
+            const double im = (i < j) ? -sum[j * D + i] / (double)n : 0.0;
+            if (rho_re) {
+                rho_re[i * D + j] = re;
+                rho_re[j * D + i] = re;
+            }
+            if (rho_im) {
+                rho_im[i * D + j] = im;
+                rho_im[j * D + i] = -im;
+            }
+        }
+    return QST_OK;
+}
+
+qst_status qst_diagnostics(qst_handle *h, int32_t problem, qst_diag *out, double *acf, double *tau) {
+    HostProblem *hp;
+    qst_status st = get_problem(h, problem, &hp);
+    if (st != QST_OK) return st;
+    if (!out) return fail(QST_ERR_INVALID_ARG, "out is NULL");
+    const ProblemView &v = hp->v;
+    std::memset(out, 0, sizeof(*out));
+    out->steps_done = h->steps_done;
+    out->num_kept = h->kept;
+    out->num_pooled = h->kept * v.R;
+    out->acf_lmax = h->cfg.acf_lmax;
+    std::vector<double> beta(v.R), logl(v.R);
+    std::vector<int64_t> acc(v.R);
+    QST_CUDA(cudaMemcpyAsync(beta.data(), v.beta, sizeof(double) * v.R, cudaMemcpyDeviceToHost, h->stream), "read beta");
+    QST_CUDA(cudaMemcpyAsync(logl.data(), v.logl_cur, sizeof(double) * v.R, cudaMemcpyDeviceToHost, h->stream), "read logl");
+    QST_CUDA(cudaMemcpyAsync(acc.data(), v.acc_total, sizeof(int64_t) * v.R, cudaMemcpyDeviceToHost, h->stream), "read acc");
+    const int lmax = h->cfg.acf_lmax;
+    const int n_kept = (int)std::min<int64_t>(h->kept, v.traj_cap);
+    const bool do_acf = v.n_diag > 0 && n_kept > lmax;
+    std::vector<double> raw;
+    if (do_acf) {
+        double *acf_dev = reinterpret_cast<double *>(h->ws + hp->off.acf);
+        st = launch(h, QST_KERNEL_DIAG, "acf", [&] { return launch_acf(v, n_kept, lmax, acf_dev, h->stream); });
+        if (st != QST_OK) return st;
+        raw.resize((size_t)v.n_diag * (lmax + 1));
+        QST_CUDA(cudaMemcpyAsync(raw.data(), acf_dev, sizeof(double) * raw.size(), cudaMemcpyDeviceToHost, h->stream),
+                 "read acf");
+    }
+    st = check_status(h);
+    uint32_t status = 0;
+    cudaMemcpy(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost);
+    out->device_status = status;
+    if (st != QST_OK) return st;
+    double bmin = 1e300, bmax = -1e300, bsum = 0.0;
+    int64_t acc_sum = 0, nonfinite = 0;
+    for (int64_t r = 0; r < v.R; ++r) {
+        bmin = std::min(bmin, beta[r]);
+        bmax = std::max(bmax, beta[r]);
+        bsum += beta[r];
+        acc_sum += acc[r];
+        if (!std::isfinite(logl[r])) nonfinite += 1;
+    }
+    out->beta_min = bmin;
+    out->beta_max = bmax;
+    out->beta_mean = bsum / (double)v.R;
+    out->accept_rate = h->steps_done > 0 ? (double)acc_sum / ((double)h->steps_done * (double)v.R) : 0.0;
+    out->num_nonfinite = nonfinite;
+    if (do_acf) {
+        out->diag_chains = v.n_diag;
+        std::vector<double> mean_c(lmax + 1, 0.0);
+        double tsum = 0.0, tmax = -1e300;
+        int used = 0;
+        for (int c = 0; c < v.n_diag; ++c) {
+            const double *rc = &raw[(size_t)c * (lmax + 1)];
+            if (!(rc[0] > 0.0)) {
+                if (tau) tau[c] = NAN;
+                continue;
+            }
+            double t = 1.0;
+            for (int l = 1; l <= lmax; ++l) t += 2.0 * rc[l] / rc[0];
+            for (int l = 0; l <= lmax; ++l) mean_c[l] += rc[l] / rc[0];
+            if (tau) tau[c] = t;
+            tsum += t;
+            tmax = std::max(tmax, t);
+            used += 1;
+        }
+        if (used > 0) {
+            out->tau_mean = tsum / used;
+            out->tau_max = tmax;
+            out->n_eff = (double)out->num_pooled / out->tau_mean;
+            if (acf)
+                for (int l = 0; l <= lmax; ++l) acf[l] = mean_c[l] / used;
+        }
+        out->diag_chains = used;
+    }
+    return QST_OK;
+}
+
+qst_status qst_synchronize(qst_handle *h) {
+    if (!h) return fail(QST_ERR_INVALID_ARG, "handle is NULL");
+    return check_status(h);
+}
+
+void qst_destroy(qst_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto &hp : h->plan.probs)
+        if (hp.tc) tc_plan_destroy(hp.tc);
+    for (auto &ev : h->pending) {
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    for (auto &ev : h->spare) {
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+}
+
+qst_status qst_get_state(qst_handle *h, int32_t problem, float *y, double *logl, double *beta, int64_t *accepts) {
+    HostProblem *hp;
+    qst_status st = get_problem(h, problem, &hp);
+    if (st != QST_OK) return st;
+    const ProblemView &v = hp->v;
+    if (y) {
+        std::vector<uint8_t> cur(v.R);
+        QST_CUDA(cudaMemcpyAsync(cur.data(), v.cur, v.R, cudaMemcpyDeviceToHost, h->stream), "read cur");
+        QST_CUDA(cudaStreamSynchronize(h->stream), "sync");
+        for (int64_t r = 0; r < v.R; ++r)
+            QST_CUDA(cudaMemcpyAsync(y + r * v.nx, v.y + ((int64_t)cur[r] * v.R + r) * v.nx, sizeof(float) * v.nx,
+                                     cudaMemcpyDeviceToHost, h->stream), "read y");
+    }
+    if (logl) QST_CUDA(cudaMemcpyAsync(logl, v.logl_cur, sizeof(double) * v.R, cudaMemcpyDeviceToHost, h->stream), "read logl");
+    if (beta) QST_CUDA(cudaMemcpyAsync(beta, v.beta, sizeof(double) * v.R, cudaMemcpyDeviceToHost, h->stream), "read beta");
+    if (accepts)
+        QST_CUDA(cudaMemcpyAsync(accepts, v.acc_total, sizeof(int64_t) * v.R, cudaMemcpyDeviceToHost, h->stream),
+                 "read accepts");
+    return check_status(h);
+}
+
+qst_status qst_get_trace(qst_handle *h, int32_t problem, uint8_t *accept, double *logl_prop) {
+    HostProblem *hp;
+    qst_status st = get_problem(h, problem, &hp);
+    if (st != QST_OK) return st;
+    const ProblemView &v = hp->v;
+    const size_t n = (size_t)v.trace_steps * v.R;
+    if (accept && n) QST_CUDA(cudaMemcpyAsync(accept, v.trace_acc, n, cudaMemcpyDeviceToHost, h->stream), "read trace");
+    if (logl_prop && n)
+        QST_CUDA(cudaMemcpyAsync(logl_prop, v.trace_logl, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream),
+                 "read trace");
+    return check_status(h);
+}
+
+// Checkpoint: header (steps, kept) then every problem's state region [y .. end).
+static size_t state_bytes(const HostProblem &hp) { return hp.off.end - hp.off.y; }
+
+qst_status qst_checkpoint_size(qst_handle *h, size_t *bytes) {
+    if (!h || !bytes) return fail(QST_ERR_INVALID_ARG, "NULL argument");
+    size_t n = 2 * sizeof(int64_t);
+    for (auto &hp : h->plan.probs) n += state_bytes(hp);
+    *bytes = n;
+    return QST_OK;
+}
+
+qst_status qst_checkpoint(qst_handle *h, void *buffer, size_t bytes) {
+    size_t need = 0;
+    qst_status st = qst_checkpoint_size(h, &need);
+    if (st != QST_OK) return st;
+    if (!buffer || bytes < need) return fail(QST_ERR_INVALID_ARG, "checkpoint buffer needs %zu bytes", need);
+    char *p = static_cast<char *>(buffer);
+    std::memcpy(p, &h->steps_done, sizeof(int64_t));
+    std::memcpy(p + sizeof(int64_t), &h->kept, sizeof(int64_t));
+    p += 2 * sizeof(int64_t);
+    for (auto &hp : h->plan.probs) {
+        QST_CUDA(cudaMemcpyAsync(p, h->ws + hp.off.y, state_bytes(hp), cudaMemcpyDeviceToHost, h->stream),
+                 "checkpoint copy");
+        p += state_bytes(hp);
+    }
+    return check_status(h);
+}
+
+qst_status qst_restore(qst_handle *h, const void *buffer, size_t bytes) {
+    size_t need = 0;
+    qst_status st = qst_checkpoint_size(h, &need);
+    if (st != QST_OK) return st;
+    if (!buffer || bytes != need) return fail(QST_ERR_INVALID_ARG, "checkpoint must be exactly %zu bytes", need);
+    const char *p = static_cast<const char *>(buffer);
+    int64_t steps, kept;
+    std::memcpy(&steps, p, sizeof(int64_t));
+    std::memcpy(&kept, p + sizeof(int64_t), sizeof(int64_t));
+    p += 2 * sizeof(int64_t);
+    QST_CUDA(cudaStreamSynchronize(h->stream), "sync");
+    for (auto &hp : h->plan.probs) {
+        QST_CUDA(cudaMemcpy(h->ws + hp.off.y, p, state_bytes(hp), cudaMemcpyHostToDevice), "restore copy");
+        p += state_bytes(hp);
+    }
+    h->steps_done = steps;
+    h->kept = kept;
+    return check_status(h);
+}
+
+qst_status qst_evaluate(qst_handle *h, int32_t problem, const float *x, int64_t n, float *rho, float *p, double *logl) {
+    HostProblem *hp;
+    qst_status st = get_problem(h, problem, &hp);
+    if (st != QST_OK) return st;
+    ProblemView &v = hp->v;
+    if (n < 0 || n > v.R) return fail(QST_ERR_INVALID_ARG, "n must be in [0, num_chains]");
+    if (n == 0) return QST_OK;
+    if (!x) return fail(QST_ERR_INVALID_ARG, "x is NULL");
+    st = launch(h, QST_KERNEL_PROPOSE, "propose (eval)", [&] {
+        return launch_propose(v, MODE_EVAL, 0u, x, n, is_tc(h), rho, h->d_status, h->stream);
+    });
+    if (st != QST_OK) return st;
+    st = enqueue_projection(h, *hp, n, p);
+    if (st != QST_OK) return st;
+    if (logl) {
+        st = launch(h, QST_KERNEL_DIAG, "logl combine", [&] { return launch_logl_combine(v, n, logl, h->stream); });
+        if (st != QST_OK) return st;
+    }
+    return QST_OK;
+}
+
+qst_status qst_set_profiling(qst_handle *h, int32_t enabled) {
+    if (!h) return fail(QST_ERR_INVALID_ARG, "handle is NULL");
+    h->prof = enabled != 0;
+    return QST_OK;
+}
+
+qst_status qst_kernel_time(qst_handle *h, int32_t kind, int32_t reset, double *total_ms, int64_t *launches) {
+    if (!h) return fail(QST_ERR_INVALID_ARG, "handle is NULL");
+    if (kind < 0 || kind >= QST_KERNEL_KINDS) return fail(QST_ERR_INVALID_ARG, "unknown kernel kind");
+    qst_status st = harvest(h);
+    if (st != QST_OK) return st;
+    if (total_ms) *total_ms = h->kind_ms[kind];
+    if (launches) *launches = h->kind_launches[kind];
+    if (reset) {
+        for (int k = 0; k < QST_KERNEL_KINDS; ++k) {
+            h->kind_ms[k] = 0.0;
+            h->kind_launches[k] = 0;
+        }
+    }
+    return QST_OK;
+}
+
+int64_t qst_launch_count(const qst_handle *h) { return h ? h->launches : 0; }
+
+qst_status qst_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uint32_t chain0, int64_t nchains,
+                             uint32_t block0, int32_t nblocks, uint32_t *out, void *cuda_stream) {
+    if (nchains < 0 || nblocks < 0 || (!out && nchains * nblocks > 0)) return fail(QST_ERR_INVALID_ARG, "bad sizes");
+    cudaError_t e = launch_philox_blocks(seed, step, tag, chain0, nchains, block0, nblocks, out,
+                                         reinterpret_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "philox");
+    return QST_OK;
+}
+
+qst_status qst_pack_projectors(int32_t num_qubits, int32_t num_povms, const double *povm_re, const double *povm_im,
+                               float *P_out) {
+    if (num_qubits < 1 || num_qubits > 5 || num_povms < 1 || !povm_re || !povm_im || !P_out)
+        return fail(QST_ERR_INVALID_ARG, "bad arguments");
+    const int D = 1 << num_qubits, KD = num_povms * D;
+    std::vector<double> P((size_t)D * D * KD);
+    pack_projectors(D, KD, povm_re, povm_im, P.data(), KD);
+    for (size_t i = 0; i < P.size(); ++i) P_out[i] = (float)P[i];
+    return QST_OK;
+}
+
+qst_status qst_inject_nan(qst_handle *h, int32_t problem, int64_t chain) {
+    HostProblem *hp;
+    qst_status st = get_problem(h, problem, &hp);
+    if (st != QST_OK) return st;
+    if (chain < 0 || chain >= hp->v.R) return fail(QST_ERR_INVALID_ARG, "chain out of range");
+    return launch(h, QST_KERNEL_DIAG, "inject nan", [&] { return launch_inject_nan(hp->v, chain, h->stream); });
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// Plain FP32 form of the projector contraction and log-likelihood (Sec. II,
+// p_kl = Tr Lambda_kl rho; Eq. likelihood).
+//
+// p = A . P with A = packed vec_h(rho) rows [rows][d_pad] and P the packed projector
+// matrix [d_pad][KD_pad].  A CTA owns 128 chains and sweeps a group of 128-column
+// tiles; each thread keeps an 8 x 8 register tile.  The epilogue evaluates the
+// likelihood in deviance form,
+//     log L = C0 - N log t + sum_{c_kl > 0} c_kl log(q_kl * invf_kl),   invf_kl = P_k / c_kl,
+// (q = vec_h(rho) . P, t the exact trace of the stored rho, p = q / t), which equals
+// sum c log p exactly in real arithmetic (C0 = -sum c log invf) but keeps every FP32
+// term O(1); each thread sums its terms in FP32, the 16 threads sharing a chain
+// combine in FP64, and one FP64 partial per (column group, chain) is written.  The
+// constant and trace terms are added by the accept kernel.
+#include "qst_internal.cuh"
+
+namespace qst {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 16, kThreads = 256;
+
+struct ProjectArgs {
+    const float *A;      // [rows][d_pad]
+    const float *P;      // [d_pad][KD_pad]
+    const float *cnt;    // [KD_pad]
+    const float *invf;   // [KD_pad]
+    double *out;         // [ngroups][rows]
+    float *p_out;        // [rows][KD] or null: p = q / t
+    const double *trace; // [rows] t, the exact trace of the stored rho (used only for p_out)
+    int64_t rows;
+    int d_pad, KD, KD_pad;
+    int tiles_per_group;
+};
+
+__global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+    __shared__ float cnt_s[BN], invf_s[BN];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int n_tiles_total = a.KD_pad / BN;
+    const int t_begin = blockIdx.y * a.tiles_per_group;
+    const int t_end = min(t_begin + a.tiles_per_group, n_tiles_total);
+
+    float rowsum[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rowsum[i] = 0.0f;
+
+    const int k_steps = a.d_pad / BK;
+    for (int nt = t_begin; nt < t_end; ++nt) {
+        const int n0 = nt * BN;
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.0f;
+
+        // register staging for the next K slice
+        float4 ra[2], rb[2];
+        auto load_global = [&](int k0) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = tid + u * kThreads;   // 0..511
+                const int r = idx / 4, q = idx % 4;
+                const int64_t row = m0 + r;
+                ra[u] = (row < a.rows) ? *reinterpret_cast<const float4 *>(a.A + row * a.d_pad + k0 + 4 * q)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int kk = idx / 32, cq = idx % 32;
+                rb[u] = *reinterpret_cast<const float4 *>(a.P + (int64_t)(k0 + kk) * a.KD_pad + n0 + 4 * cq);
+            }
+        };
+        auto store_shared = [&](int buf) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = tid + u * kThreads;
+                const int r = idx / 4, q = idx % 4;
+                As[buf][4 * q + 0][r] = ra[u].x;
+                As[buf][4 * q + 1][r] = ra[u].y;
+                As[buf][4 * q + 2][r] = ra[u].z;
+                As[buf][4 * q + 3][r] = ra[u].w;
+                const int kk = idx / 32, cq = idx % 32;
+                *reinterpret_cast<float4 *>(&Bs[buf][kk][4 * cq]) = rb[u];
+            }
+        };
+
+        if (tid < BN) {
+            cnt_s[tid] = a.cnt[n0 + tid];
+            invf_s[tid] = a.invf[n0 + tid];
+        }
+        load_global(0);
+        store_shared(0);
+        __syncthreads();
+        for (int ks = 0; ks < k_steps; ++ks) {
+            const int buf = ks & 1;
+            if (ks + 1 < k_steps) load_global((ks + 1) * BK);
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) acc[i][jj] = __fmaf_rn(av[i], bv[jj], acc[i][jj]);
+            }
+            if (ks + 1 < k_steps) {
+                store_shared(buf ^ 1);
+            }
+            __syncthreads();
+        }
+
+        // epilogue: deviance terms of this tile
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+            const int64_t row = m0 + r;
+            const float inv_tr = (a.p_out && row < a.rows) ? (float)(1.0 / a.trace[row]) : 0.0f;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int col = (jj < 4) ? tx * 4 + jj : 64 + tx * 4 + (jj - 4);
+                const float pv = acc[i][jj];
+                const float cv = cnt_s[col];
+                if (cv > 0.0f) rowsum[i] += cv * logf(pv * invf_s[col]);
+                if (a.p_out && row < a.rows && n0 + col < a.KD) a.p_out[row * a.KD + n0 + col] = pv * inv_tr;
+            }
+        }
+        __syncthreads();   // cnt_s / invf_s reuse
+    }
+
+    // combine the 16 threads (tx) that share each row, in FP64
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        double v = (double)rowsum[i];
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+        const int64_t row = m0 + r;
+        if (tx == 0 && row < a.rows) a.out[(int64_t)blockIdx.y * a.rows + row] = v;
+    }
+}
+
+}  // namespace
+
+int fp32_ngroups(const ProblemView &p, int64_t rows) {
+    // enough CTAs to fill the machine: split the columns when there are few row tiles
+    const int64_t mt = (rows + BM - 1) / BM;
+    const int nt = p.KD_pad / BN;
+    int g = 1;
+    while (g < nt && mt * g < 2 * 152) g *= 2;
+    return g > nt ? nt : g;
+}
+
+cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t rows, double *out_part, float *p_out,
+                                cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    if (p.KD_pad % BN != 0 || p.d_pad % BK != 0) return cudaErrorInvalidValue;
+    ProjectArgs a;
+    a.A = A;
+    a.P = p.P32;
+    a.cnt = p.cnt;
+    a.invf = p.invf;
+    a.out = out_part;
+    a.p_out = p_out;
+    a.trace = p.trace_prop;
+    a.rows = rows;
+    a.d_pad = p.d_pad;
+    a.KD = p.KD;
+    a.KD_pad = p.KD_pad;
+    const int nt = p.KD_pad / BN;
+    const int groups = p.ngroups;
+    a.tiles_per_group = (nt + groups - 1) / groups;
+    dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)groups);
+    project_fp32_kernel<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace qst

@@ -1,0 +1,142 @@
+// Internal definitions of the GB300 sampler: device-side problem view, kernel
+// argument blocks, the counter-based generator and launch declarations.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qst {
+
+// Device status bits (read back by synchronising calls).
+enum : uint32_t {
+    STATUS_TIMEOUT = 1u << 0,     // a bounded mbarrier wait gave up
+    STATUS_BOUNDS = 1u << 1,      // a kernel's own bounds check failed
+    STATUS_BAD_LAUNCH = 1u << 2,  // a kernel was launched with an unsupported shape
+};
+
+// Stream tags of the counter layout (block, step j, global chain id, tag).
+enum : uint32_t { TAG_INIT = 0, TAG_PROPOSAL = 1, TAG_ALPHA = 2 };
+
+enum ProposeMode : int { MODE_INIT = 0, MODE_STEP = 1, MODE_EVAL = 2 };
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplications whose high halves are xored into the other two words with the
+// round key, the key bumped by the Weyl constants after every round.
+// ---------------------------------------------------------------------------------------
+struct Philox {
+    static constexpr uint32_t kMulA = 0xD2511F53u;
+    static constexpr uint32_t kMulB = 0xCD9E8D57u;
+    static constexpr uint32_t kWeylA = 0x9E3779B9u;
+    static constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+    __device__ __forceinline__ static uint4 block(uint4 ctr, uint32_t key_lo, uint32_t key_hi) {
+#pragma unroll
+        for (int round = 0; round < 10; ++round) {
+            const uint32_t pa_hi = __umulhi(kMulA, ctr.x);
+            const uint32_t pa_lo = kMulA * ctr.x;
+            const uint32_t pb_hi = __umulhi(kMulB, ctr.z);
+            const uint32_t pb_lo = kMulB * ctr.z;
+            ctr = make_uint4(pb_hi ^ ctr.y ^ key_lo, pb_lo, pa_hi ^ ctr.w ^ key_hi, pa_lo);
+            key_lo += kWeylA;
+            key_hi += kWeylB;
+        }
+        return ctr;
+    }
+
+    // Open-interval uniform from the top 23 bits: (2 m + 1) 2^-24, exact in float.
+    __device__ __forceinline__ static float uniform(uint32_t word) {
+        return __fmaf_rn((float)(word >> 9), 0x1p-23f, 0x1p-24f);
+    }
+
+    // Box-Muller on one uniform pair: (sqrt(-2 ln u) cos 2 pi v, sqrt(-2 ln u) sin 2 pi v).
+    __device__ __forceinline__ static void gaussian_pair(uint32_t wu, uint32_t wv, float &z0, float &z1) {
+        const float u = uniform(wu);
+        const float v = uniform(wv);
+        const float radius = sqrtf(-2.0f * logf(u));
+        float s, c;
+        sincospif(2.0f * v, &s, &c);
+        z0 = radius * c;
+        z1 = radius * s;
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// Device view of one problem.  Dimensions: D = 2^Q, d = D^2 (packed rho), nx = 4 D^2
+// (latent), KD = K*D projectors, d_pad = d rounded up to 64 (operand rows), KD_pad =
+// KD rounded up to the contraction's column tile.
+// ---------------------------------------------------------------------------------------
+struct ProblemView {
+    int D, d, nx, KD, KD_pad, d_pad;
+    int KD_tc;                   // columns of the tensor-core operand (multiple of its N tile)
+    int64_t R;
+    int64_t chain_offset;
+    uint64_t seed;
+    double C0;     // -sum_{c>0} c log(invf): constant of the deviance form (see the projection kernels)
+    double Ntot;   // sum of all counts: weight of log t (trace of the stored rho) in log L
+
+    // packed projector operands and per-column likelihood weights
+    const float *P32;            // [d_pad][KD_pad]  (row = packed rho index, contiguous columns)
+    const __nv_bfloat16 *Pbf;    // [KD_tc][d_pad]   (row = projector, contiguous packed index)
+    const float *cnt;            // [max(KD_pad, KD_tc)] counts as float, 0 on padding
+    const float *invf;           // [max(KD_pad, KD_tc)] P_k / c_kl (1 where c_kl = 0)
+
+    // chain state
+    float *y;                    // [2][R][nx] double-buffered latent states
+    uint8_t *cur;                // [R] which y buffer holds the current state
+    float *rho_cur;              // [R][d_pad] packed rho of the current state
+    float *rho_prop;             // [R][d_pad] packed rho of the proposal (FP32 operand)
+    __nv_bfloat16 *rho_split;    // [R][3][d_pad] bf16 hi/mid/lo of the same (tensor operand)
+    double *trace_prop;          // [R] exact FP64 sum of rho_prop's stored diagonal (1 up to rounding)
+    double *logl_cur;            // [R]
+    double *logl_part;           // [ngroups][R] partial deviance sums of the proposal
+    double *beta;                // [R]
+    int32_t *acc_win;            // [R] accepts in the current adaptation window
+    int64_t *acc_total;          // [R]
+    double *pool;                // [n_slots][d] FP64 pooled sums, one slot per accept CTA
+    int n_slots;
+    float *traj;                 // [n_diag][traj_cap][d] kept states of the diagnostic chains
+    int n_diag;
+    int traj_cap;
+    uint8_t *trace_acc;          // [trace_steps][R]
+    double *trace_logl;          // [trace_steps][R]
+    int trace_steps;
+    int ngroups;                 // column groups of the projection (partial sums per group)
+    int qr_passes;               // 1 or 2 modified Gram-Schmidt passes
+};
+
+struct SamplerParams {
+    int32_t adapt_interval;
+    double acc_lo, acc_hi, adapt_factor, beta_max;
+};
+
+// ---------------------------------------------------------------------------------------
+// Launchers (each returns the CUDA launch error).
+// ---------------------------------------------------------------------------------------
+cudaError_t launch_propose(const ProblemView &p, int mode, uint32_t step, const float *x_eval, int64_t n_eval,
+                           bool want_split, float *rho_norm_out, uint32_t *status, cudaStream_t s);
+cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t rows, double *out_part,
+                                float *p_out, cudaStream_t s);
+cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mode, uint32_t step, bool kept,
+                          int64_t kept_idx, uint32_t *status, cudaStream_t s);
+cudaError_t launch_pool_reduce(const ProblemView &p, double *out, cudaStream_t s);
+cudaError_t launch_acf(const ProblemView &p, int n_kept, int lmax, double *acf_raw, cudaStream_t s);
+cudaError_t launch_logl_combine(const ProblemView &p, int64_t rows, double *out, cudaStream_t s);
+cudaError_t launch_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uint32_t chain0, int64_t nchains,
+                                 uint32_t block0, int32_t nblocks, uint32_t *out, cudaStream_t s);
+cudaError_t launch_inject_nan(const ProblemView &p, int64_t chain, cudaStream_t s);
+
+// tcgen05 BF16x3 projection (sm_103a).  Returns cudaErrorNotSupported if the shape is
+// outside what the kernel handles.
+struct TcPlan;
+cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, int64_t rows, TcPlan **plan);
+void tc_plan_destroy(TcPlan *plan);
+cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t rows, double *out_part,
+                              float *p_out, uint32_t *status, cudaStream_t s);
+int tc_ngroups(const ProblemView &p, int64_t rows);
+int tc_column_tile(int KD);       // N tile of the tensor-core contraction for KD columns (0 = unsupported)
+int fp32_ngroups(const ProblemView &p, int64_t rows);
+int accept_slots(int64_t R);
+
+}  // namespace qst

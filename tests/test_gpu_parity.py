@@ -1,0 +1,310 @@
+"""GPU parity tests: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (derived from the arithmetic; DESIGN.md Sec. "Tolerances"):
+* Philox words: bit-exact.
+* p_kl on identical latent x: 1e-6 absolute whenever cond(H) <= 1e3.  The FP32
+  assembly's forward error in U is O(cond(H) * 2^-24), and p inherits it.
+* log L reduction: |logL_gpu - sum c log p_gpu (FP64)| <= sum_{c>0} c * 6 * 2^-24 (per term, one
+  rounding each for p*invf, logf and the product, doubled for the FP32 partial sums).
+* accept decisions: identical, except where |log alpha - Delta log L| is below the
+  measured log L error (a near tie); a chain's later steps are not compared after one.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_17334_gb300 import workload as W
+from tests._helpers import unpack_rho
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+PRECISIONS = ["fp32", "bf16x3"]
+
+
+def _prec(qst, name):
+    return qst.PREC_FP32 if name == "fp32" else qst.PREC_BF16X3
+
+
+def _sampler(qst, prob, prec="fp32", **kw):
+    try:
+        return qst.Sampler(prob, precision=_prec(qst, prec), **kw)
+    except qst.QstError as e:
+        if e.status == 7:
+            pytest.skip(f"{prec} not supported by this build: {e}")
+        raise
+
+
+# ------------------------------------------------------------------------------- Philox
+
+@pytest.mark.parametrize("seed", [0, 3004, 0xFEDCBA9876543210])
+@pytest.mark.parametrize("tag", [0, 1, 2])
+def test_philox_bit_exact(qst, oracle_mod, cuda_ok, seed, tag):
+    torch = _torch()
+    for step, chain0, nchains, block0, nblocks in [(0, 0, 3, 0, 16), (17, 5, 4, 3, 5),
+                                                   (4294967295, 4294967290, 5, 250, 6), (1000, 65530, 7, 0, 256)]:
+        got = qst.philox_blocks(seed, step, tag, chain0, nchains, block0, nblocks)
+        torch.cuda.synchronize()
+        got = got.cpu().numpy().view(np.uint32)
+        for i in range(nchains):
+            want = oracle_mod.philox_blocks(seed, step, chain0 + i, tag, block0, nblocks)
+            assert np.array_equal(got[i], want), (step, chain0 + i)
+
+
+# ------------------------------------------------------------------------------- evaluation
+
+def _cond(x, D):
+    d = D * D
+    H = (x[:, 2 * d:3 * d] + 1j * x[:, 3 * d:]).reshape(-1, D, D).transpose(0, 2, 1)
+    return np.linalg.cond(H)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("q,n", [(1, 300), (2, 517), (3, 1000), (4, 777)])
+def test_evaluate_matches_oracle(qst, oracle_mod, cuda_ok, prec, q, n):
+    torch = _torch()
+    prob = W.config_problem(q, num_chains=max(n, 1024), num_steps=1)
+    s = _sampler(qst, prob, prec, diag_chains=0)
+    D = 1 << q
+    x32 = W.latent_batch(n, q, seed=100 + q).astype(np.float32)
+    rho_p, p_gpu, ll_gpu = s.evaluate(torch.from_numpy(x32).cuda())
+    torch.cuda.synchronize()
+    rho_gpu = unpack_rho(rho_p.cpu().numpy(), D)
+    p_gpu = p_gpu.cpu().numpy().astype(np.float64)
+    ll_gpu = ll_gpu.cpu().numpy()
+    rho_ref, p_ref, ll_ref = oracle_mod.evaluate(prob, x32.astype(np.float64))
+    kappa = _cond(x32.astype(np.float64), D)
+    ok = kappa <= 1e3
+    assert ok.mean() > 0.95
+    # rho and p on identical x
+    assert np.abs(rho_gpu - rho_ref).max(axis=(1, 2))[ok].max() < 2e-6
+    assert np.abs(p_gpu - p_ref).max(axis=1)[ok].max() < 1e-6
+    # log-likelihood reduction on the GPU's own p
+    c = prob.counts.astype(np.float64)
+    ll_own = np.array([oracle_mod.loglik(prob.counts, p_gpu[i]) for i in range(n)])
+    bound = np.sum(c) * 6 * 2.0 ** -24
+    finite = np.isfinite(ll_own)
+    assert np.abs(ll_gpu[finite] - ll_own[finite]).max() < bound
+    # end to end against the oracle's own p (relative; prior draws have large |log L|)
+    rel = np.abs(ll_gpu - ll_ref) / np.abs(ll_ref)
+    assert np.nanmax(rel[ok]) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 127, 128, 129])
+def test_evaluate_ragged_sizes(qst, oracle_mod, cuda_ok, n):
+    torch = _torch()
+    prob = W.config_problem(3, num_chains=256, num_steps=1)
+    s = _sampler(qst, prob, "fp32", diag_chains=0)
+    x32 = W.latent_batch(max(n, 1), 3, seed=7).astype(np.float32)[:n]
+    rho_p, p_gpu, ll_gpu = s.evaluate(torch.from_numpy(x32).cuda().reshape(n, 4 * 64))
+    torch.cuda.synchronize()
+    if n:
+        _, p_ref, _ = oracle_mod.evaluate(prob, x32.astype(np.float64))
+        assert np.abs(p_gpu.cpu().numpy() - p_ref).max() < 1e-6
+    s.close()
+
+
+# ------------------------------------------------------------------------------- chains
+
+def _compare_decisions(acc_gpu, acc_ref, margin, tol):
+    """Per chain, the first mismatch must be a near tie; returns (compared, mismatched)."""
+    R, S = acc_ref.shape
+    compared = 0
+    mism = 0
+    for r in range(R):
+        bad = np.nonzero(acc_gpu[r] != acc_ref[r])[0]
+        if bad.size == 0:
+            compared += S
+            continue
+        t = bad[0]
+        assert abs(margin[r, t]) < tol, f"chain {r} step {t + 1}: decisions differ away from a tie ({margin[r, t]})"
+        compared += t
+        mism += 1
+    return compared, mism
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("q,R,beta0", [(1, 256, 0.1), (2, 256, 0.05), (3, 256, 0.1), (4, 256, 0.02)])
+def test_first_200_decisions(qst, oracle_mod, cuda_ok, prec, q, R, beta0):
+    prob = W.config_problem(q, num_chains=R, num_steps=200)
+    prob.beta0 = beta0
+    s = _sampler(qst, prob, prec, trace_steps=200, diag_chains=0)
+    s.run_chains(200)
+    acc_gpu, ll_prop_gpu = s.get_trace()
+    st = s.get_state()
+    s.close()
+    ref = oracle_mod.run(prob, num_steps=200, trace_steps=200, want_final=True)
+    margin = ref["trace_log_alpha"] - (ref["trace_logl_prop"] - ref["trace_logl_cur"])
+    compared, mism = _compare_decisions(acc_gpu.T, ref["trace_accept"], margin, tol=5e-2)
+    assert mism <= max(2, R // 50), f"{mism} chains hit near-tie mismatches"
+    assert compared >= 0.9 * R * 200
+    # log L of the proposals agree where trajectories still coincide: relative error of
+    # the FP32 assembly, largest for proposals deep in the tails (p_kl -> 0 for counted
+    # outcomes, which are rejected anyway)
+    same = np.all(acc_gpu.T == ref["trace_accept"], axis=1)
+    d = np.abs(ll_prop_gpu.T[same] - ref["trace_logl_prop"][same])
+    fin = np.isfinite(ref["trace_logl_prop"][same])
+    rel = d[fin] / np.abs(ref["trace_logl_prop"][same][fin])
+    assert np.median(rel) < 1e-7
+    assert rel.max() < 1e-4
+    # the final states of identical chains agree to FP32 drift
+    assert np.abs(st["y"][same] - ref["final_y"][same]).max() < 1e-3
+    assert np.array_equal(st["beta"][same], ref["final_beta"][same])
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_pooled_mean_and_acf_match_oracle(qst, oracle_mod, cuda_ok, prec):
+    prob = W.config_problem(2, num_chains=512, num_steps=600)
+    s = _sampler(qst, prob, prec, diag_chains=8, traj_capacity=600, acf_lmax=50, adapt_interval=100)
+    s.run_chains(600)
+    rho, n = s.posterior_mean()
+    dg = s.diagnostics()
+    s.close()
+    ref = oracle_mod.run(prob, num_steps=600, traj_chains=8, traj_capacity=600, want_chain_pool=True,
+                         adapt_interval=100)
+    assert n == ref["num_pooled"] == 512 * 600
+    # Monte Carlo error from the spread of per-chain means (chains are independent)
+    per_chain = ref["chain_pool"] / 600
+    se = per_chain.std(axis=0) / np.sqrt(512)
+    assert np.all(np.abs(rho - ref["mean"]) <= 3 * se + 1e-7)
+    assert abs(oracle_mod.fidelity(ref["mean"], rho) - 1) < 1e-6
+    # IACT of the diagnostic chains
+    taus = np.array([oracle_mod.iact(oracle_mod.acf(ref["traj"][c], 50)) for c in range(8)])
+    assert dg["diag_chains"] == 8
+    assert np.allclose(np.sort(dg["tau"]), np.sort(taus), rtol=0.05, atol=0.05)
+    assert abs(dg["tau_mean"] - taus.mean()) < 0.05 * taus.mean() + 0.05
+
+
+def test_zero_counts_sample_the_prior(qst, oracle_mod, cuda_ok):
+    prob = W.config_problem(2, num_chains=4096, num_steps=300)
+    prob.counts = np.zeros_like(prob.counts)
+    s = _sampler(qst, prob, "fp32", adapt_interval=100, diag_chains=0)
+    s.run_chains(300)
+    st = s.get_state()
+    rho, n = s.posterior_mean()
+    dg = s.diagnostics()
+    s.close()
+    assert np.all(st["accepts"] == 300)
+    assert dg["accept_rate"] == 1.0
+    assert np.all(st["beta"] == min(prob.beta0 * 1.1 * 1.1 * 1.1, 1.0))
+    assert np.abs(rho - np.eye(4) / 4).max() < 5 * 0.5 / np.sqrt(4096)
+    y = st["y"].astype(np.float64)
+    assert abs(y.var() - 1) < 5 * np.sqrt(2 / y.size)
+
+
+@pytest.mark.parametrize("thin,burn", [(1, 0), (3, 0), (4, 10)])
+def test_thinning_counts_and_trajectories(qst, oracle_mod, cuda_ok, thin, burn):
+    prob = W.config_problem(2, num_chains=64, num_steps=100)
+    s = _sampler(qst, prob, "fp32", thin=thin, burn_in=burn, diag_chains=2, traj_capacity=100, acf_lmax=5)
+    s.run_chains(100)
+    rho, n = s.posterior_mean()
+    s.close()
+    ref = oracle_mod.run(prob, num_steps=100, thin=thin, burn_in=burn)
+    assert n == ref["num_pooled"]
+    assert np.abs(rho - ref["mean"]).max() < 1e-3
+
+
+def test_multi_problem_handle_matches_single(qst, cuda_ok):
+    probs = [W.config_problem(q, num_chains=R, num_steps=50) for q, R in [(1, 100), (3, 300), (2, 257)]]
+    multi = _sampler(qst, probs, "fp32", diag_chains=0)
+    multi.run_chains(50)
+    for i, p in enumerate(probs):
+        single = _sampler(qst, p, "fp32", diag_chains=0)
+        single.run_chains(50)
+        a = multi.get_state(i)
+        b = single.get_state(0)
+        assert np.array_equal(a["y"], b["y"])
+        assert np.array_equal(multi.posterior_mean(i)[0], single.posterior_mean(0)[0])
+        single.close()
+    multi.close()
+
+
+def test_chain_offset_partition_is_exact(qst, cuda_ok):
+    """Chains keyed by global id: [0,96) at once equals [0,40) + [40,96) as two handles."""
+    prob = W.config_problem(3, num_chains=96, num_steps=40)
+    full = _sampler(qst, prob, "fp32", diag_chains=0)
+    full.run_chains(40)
+    a_p = W.config_problem(3, num_chains=40, num_steps=40)
+    b_p = W.config_problem(3, num_chains=56, num_steps=40)
+    a = qst.Sampler(a_p, chain_offsets=[0], diag_chains=0)
+    b = qst.Sampler(b_p, chain_offsets=[40], diag_chains=0)
+    a.run_chains(40)
+    b.run_chains(40)
+    y = full.get_state()["y"]
+    assert np.array_equal(np.concatenate([a.get_state()["y"], b.get_state()["y"]]), y)
+    ra, na = a.posterior_mean()
+    rb, nb = b.posterior_mean()
+    rf, nf = full.posterior_mean()
+    assert na + nb == nf
+    # pooled sums differ only by the order of the FP32 per-CTA tile sums
+    assert np.abs((ra * na + rb * nb) / nf - rf).max() < 1e-7
+    for h in (full, a, b):
+        h.close()
+
+
+def test_checkpoint_restore_is_bit_exact(qst, cuda_ok):
+    prob = W.config_problem(3, num_chains=200, num_steps=60)
+    straight = _sampler(qst, prob, "fp32", diag_chains=4, traj_capacity=64, acf_lmax=5, adapt_interval=20)
+    straight.run_chains(60)
+    first = _sampler(qst, prob, "fp32", diag_chains=4, traj_capacity=64, acf_lmax=5, adapt_interval=20)
+    first.run_chains(30)
+    ck = first.checkpoint()
+    first.close()
+    second = _sampler(qst, prob, "fp32", diag_chains=4, traj_capacity=64, acf_lmax=5, adapt_interval=20)
+    second.restore(ck)
+    second.run_chains(30)
+    a, b = straight.get_state(), second.get_state()
+    for k in ("y", "logl", "beta", "accepts"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(straight.posterior_mean()[0], second.posterior_mean()[0])
+    straight.close()
+    second.close()
+
+
+def test_nan_injection_is_contained(qst, cuda_ok):
+    prob = W.config_problem(2, num_chains=256, num_steps=50)
+    s = _sampler(qst, prob, "fp32", diag_chains=0)
+    s.run_chains(10)
+    before = s.get_state()
+    s.inject_nan(17)
+    s.run_chains(40)
+    after = s.get_state()
+    rho, n = s.posterior_mean()
+    assert np.all(np.isfinite(rho))
+    assert after["accepts"][17] == before["accepts"][17]   # every later proposal rejected
+    assert np.isfinite(after["logl"][17])                   # keeps its last valid state
+    assert after["accepts"].sum() > before["accepts"].sum()
+    s.close()
+
+
+# ------------------------------------------------------------------------------- full size
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_config4_full_size_sampled_chains(qst, oracle_mod, cuda_ok, prec):
+    """65536 chains in the benchmark's launch configuration; 24 sampled chains are
+    re-run alone by the oracle (chains are independent and keyed by global id)."""
+    prob = W.config_problem(4, num_chains=65536, num_steps=40)
+    s = _sampler(qst, prob, prec, trace_steps=40)
+    s.run_chains(40)
+    st = s.get_state()
+    acc, _ = s.get_trace()
+    rho, n = s.posterior_mean()
+    s.close()
+    assert n == 65536 * 40
+    assert abs(np.trace(rho).real - 1) < 1e-6
+    assert np.linalg.eigvalsh(rho).min() > -1e-7
+    rng = np.random.default_rng(0)
+    sample = np.concatenate([[0, 1, 65535], rng.choice(65536, 21, replace=False)])
+    agree = 0
+    for c in sample:
+        ref = oracle_mod.run(prob, num_chains=1, chain_begin=int(c), num_steps=40, trace_steps=40, want_final=True)
+        if np.array_equal(acc[:, c], ref["trace_accept"][0]):
+            agree += 1
+            assert np.abs(st["y"][c] - ref["final_y"][0]).max() < 1e-3
+            assert abs(st["logl"][c] - ref["final_logl"][0]) < 1e-3 * max(1.0, abs(ref["final_logl"][0]) * 1e-6) + 5e-3
+    assert agree >= len(sample) - 1
