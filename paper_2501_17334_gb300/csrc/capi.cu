@@ -61,17 +61,18 @@ void pack_projectors(int D, int KD, const double *re, const double *im, double *
     }
 }
 
+// Is v a bf16 value up to FP64 round-off of its construction (relative 1e-12, the same
+// tolerance as the completeness check)?  Then the bf16 value is used.
 bool bf16_exact(double v) {
-    const float f = (float)v;
-    if ((double)f != v) return false;
-    return __bfloat162float(__float2bfloat16_rn(f)) == f;
+    const double r = (double)__bfloat162float(__float2bfloat16_rn((float)v));
+    return std::fabs(r - v) <= 1e-12 * std::fabs(v);
 }
 
 // ------------------------------------------------------------------------------------------
 // Per-problem host record and workspace layout
 // ------------------------------------------------------------------------------------------
 struct Layout {
-    size_t P32, Pbf, cnt, invf, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, acc_win,
+    size_t P32, Pbf, cnt, invf, ptot, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, acc_win,
         acc_total, pool, traj, trace_acc, trace_logl, red, acf, logl_eval, end;
 };
 
@@ -82,7 +83,7 @@ struct HostProblem {
     Layout off{};
     std::vector<float> P32;
     std::vector<__nv_bfloat16> Pbf;
-    std::vector<float> cnt, invf;
+    std::vector<float> cnt, invf, ptot;
     TcPlan *tc = nullptr;
 };
 
@@ -207,15 +208,18 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
                                     "problem %d: packed projector entry %.17g is not exact in bf16; use QST_PREC_FP32",
                                     i, x);
                     hp.Pbf[(size_t)m * v.d_pad + r] = __float2bfloat16_rn((float)x);
+                    hp.P32[(size_t)r * v.KD_pad + m] = __bfloat162float(hp.Pbf[(size_t)m * v.d_pad + r]);
                 }
         }
         // deviance weights: log L = C0 + sum_{c>0} c log(p * invf), invf = P_k / c (as float)
         hp.cnt.assign(hp.KDmax, 0.0f);
         hp.invf.assign(hp.KDmax, 1.0f);
+        hp.ptot.assign(hp.KDmax / v.D, 0.0f);
         double C0 = 0.0, Ntot = 0.0;
         for (int k = 0; k < d.num_povms; ++k) {
             int64_t Pk = 0;
             for (int l = 0; l < v.D; ++l) Pk += d.counts[k * v.D + l];
+            hp.ptot[k] = (float)Pk;
             for (int l = 0; l < v.D; ++l) {
                 const int m = k * v.D + l;
                 const int c = d.counts[m];
@@ -247,6 +251,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         L.Pbf = take(tc ? sizeof(__nv_bfloat16) * hp.Pbf.size() : 0);
         L.cnt = take(sizeof(float) * hp.KDmax);
         L.invf = take(sizeof(float) * hp.KDmax);
+        L.ptot = take(sizeof(float) * (hp.KDmax / v.D));
         L.y = take(sizeof(float) * 2 * R * v.nx);
         L.cur = take(R);
         L.rho_cur = take(sizeof(float) * R * v.d_pad);
@@ -354,6 +359,7 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     v.Pbf = reinterpret_cast<const __nv_bfloat16 *>(b + L.Pbf);
     v.cnt = reinterpret_cast<const float *>(b + L.cnt);
     v.invf = reinterpret_cast<const float *>(b + L.invf);
+    v.ptot = reinterpret_cast<const float *>(b + L.ptot);
     v.y = reinterpret_cast<float *>(b + L.y);
     v.cur = reinterpret_cast<uint8_t *>(b + L.cur);
     v.rho_cur = reinterpret_cast<float *>(b + L.rho_cur);
@@ -496,6 +502,8 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
                                  h->stream), "upload counts");
         QST_CUDA(cudaMemcpyAsync(h->ws + L.invf, hp.invf.data(), sizeof(float) * hp.KDmax, cudaMemcpyHostToDevice,
                                  h->stream), "upload weights");
+        QST_CUDA(cudaMemcpyAsync(h->ws + L.ptot, hp.ptot.data(), sizeof(float) * hp.ptot.size(), cudaMemcpyHostToDevice,
+                                 h->stream), "upload setting totals");
         std::vector<double> beta(v.R, hp.beta0);
         QST_CUDA(cudaMemcpyAsync(v.beta, beta.data(), sizeof(double) * v.R, cudaMemcpyHostToDevice, h->stream),
                  "upload beta");

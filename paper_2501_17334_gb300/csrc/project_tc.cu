@@ -1,22 +1,493 @@
-// tcgen05 BF16x3 projector contraction (placeholder until the tensor-core kernel lands).
+// Mixed-precision projector contraction on the 5th-generation tensor cores (sm_103a)
+// with the fused log-likelihood epilogue (Sec. II, p_kl = Tr Lambda_kl rho; Eq. likelihood).
+//
+// q = vec_h(rho) . P as a BF16 GEMM with FP32 accumulation: the Pauli projector matrix P
+// is exact in bf16 (entries 0 or +-2^-m), and the FP32 packed rho is split exactly into
+// rho = hi + mid + lo (three bf16 terms, 24 significant bits), so
+//     q = hi . P + mid . P + lo . P
+// is one tcgen05 GEMM with K = 3 d_pad and FP32 accumulation in tensor memory.
+//
+// One CTA owns a tile of 128 chains (M = 128) and a group of 128-column N tiles:
+//   warp 0 (one lane)  TMA producer: the whole A tile (128 x 3 d_pad bf16, SWIZZLE_128B,
+//                      resident for the CTA's lifetime) then a 2-stage ring of
+//                      P tiles (128 projectors x 64 K);
+//   warp 1             allocates 256 TMEM columns (two 128-column FP32 accumulators);
+//                      one lane issues tcgen05.mma (M128 N128 K16) and commits;
+//   warps 2-17         epilogue, four warps per TMEM lane quadrant (warp w may only read
+//                      lanes 32 (w mod 4) ..), each owning 32 of a tile's 128 columns:
+//                      tcgen05.ld its accumulator slice (TMEM lane = chain) and form the
+//                      log-likelihood of each measurement setting k (D consecutive
+//                      columns, all in one thread):
+//                        sum_l c_kl log(q_kl invf_kl) - P_k log(S_k / t),  S_k = sum_l q_kl,
+//                      FP32 per tile, FP64 across tiles.
+// Renormalising every setting by its own computed sum S_k (instead of the trace t) is exact
+// for a complete POVM (sum_l Lambda_kl = I gives S_k = t in real arithmetic) and cancels any
+// error common to a setting's outcomes -- in particular the one-sided rounding of the
+// tensor cores' FP32 accumulation, which otherwise shifts every q_kl of a chain the same
+// way and adds N * bias to log L.  S_k is a pairwise sum with TwoSum error terms.
+// Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the kernel sets the
+// status word's TIMEOUT bit, stops every role, drains its MMAs and TMA loads (bounded
+// again), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "qst_internal.cuh"
 
 namespace qst {
+namespace {
 
-struct TcPlan {
-    int dummy;
+constexpr int TC_M = 128;
+constexpr int TC_N = 128;
+constexpr int TC_KATOM = 64;                       // bf16 elements per 128-byte swizzle row
+constexpr int TC_ATOM_BYTES = TC_M * TC_KATOM * 2; // 16 KB: 128 rows x 128 B
+constexpr int TC_BSTAGES = 2;
+constexpr int TC_EPI_PER_QUAD = 4;                           // epilogue warps per lane quadrant
+constexpr int TC_EPI_COLS = TC_N / TC_EPI_PER_QUAD;           // columns per epilogue warp (32)
+constexpr int TC_THREADS = 64 + 4 * TC_EPI_PER_QUAD * 32;     // 576
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr uint64_t TC_WAIT_NS = 1000000000ull;     // 1 s
+
+struct TcArgs {
+    const float *cnt;      // [KD_tc]
+    const float *invf;     // [KD_tc]
+    const float *ptot;     // [KD_tc / D] shots per setting
+    const double *trace;   // [rows] exact trace of the stored rho (for p_out)
+    double *out;           // [ngroups][rows]
+    float *p_out;          // [rows][KD] or null
+    uint32_t *status;
+    int64_t rows;
+    int KD;
+    int n_katoms;          // d_pad / 64
+    int ntiles;            // KD_tc / 128
+    int tiles_per_group;
 };
 
-int tc_column_tile(int KD) { (void)KD; return 0; }
-int tc_ngroups(const ProblemView &p, int64_t rows) { (void)p; (void)rows; return 1; }
-cudaError_t tc_plan_create(const ProblemView &, const __nv_bfloat16 *, int64_t, TcPlan **plan) {
-    *plan = nullptr;
-    return cudaErrorNotSupported;
+// ---- PTX wrappers ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+__device__ __forceinline__ uint64_t global_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait: true when the phase of `parity` completed; false on abort or timeout.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t *status) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0; it < (1u << 28); ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 31) == 31) {
+            if (*abort_flag) return false;
+            const uint64_t now = global_timer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > TC_WAIT_NS) {
+                break;
+            }
+        }
+    }
+    *abort_flag = 1;
+    atomicOr(status, STATUS_TIMEOUT);
+    return false;
+}
+// Wait used while draining after an abort: ignores the abort flag, still bounded.
+__device__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = global_timer();
+    for (uint32_t it = 0; it < (1u << 28); ++it) {
+        if (mbar_try(bar, parity)) return;
+        if ((it & 31) == 31 && global_timer() - t0 > TC_WAIT_NS) return;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// UMMA shared-memory descriptor: K-major, SWIZZLE_128B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+    return d;
+}
+// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                            ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// sum of D values as an unevaluated pair hi + lo: pairwise, each addition's rounding error
+// recovered exactly by TwoSum and accumulated into lo.
+template <int D>
+__device__ __forceinline__ void compensated_sum(const float *v, float &hi, float &lo) {
+    float s[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) s[i] = v[i];
+    float err = 0.0f;
+#pragma unroll
+    for (int w = D; w > 1; w /= 2) {
+#pragma unroll
+        for (int i = 0; i < w / 2; ++i) {
+            const float x = s[2 * i], y = s[2 * i + 1];
+            const float sum = x + y;
+            const float bb = sum - x;
+            err += (x - (sum - bb)) + (y - bb);
+            s[i] = sum;
+        }
+    }
+    hi = s[0];
+    lo = err;
+}
+
+template <int D>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    project_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ __align__(8) uint64_t bar_a_full;
+    __shared__ __align__(8) uint64_t bar_b_full[TC_BSTAGES];
+    __shared__ __align__(8) uint64_t bar_b_empty[TC_BSTAGES];
+    __shared__ __align__(8) uint64_t bar_acc_full[2];
+    __shared__ __align__(8) uint64_t bar_acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_mma_done;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+    const int n_aatoms = 3 * a.n_katoms;
+    uint8_t *smA = base;
+    uint8_t *smB = base + (size_t)n_aatoms * TC_ATOM_BYTES;
+
+    const int64_t m0 = (int64_t)blockIdx.x * TC_M;
+    const int t_begin = blockIdx.y * a.tiles_per_group;
+    const int t_end = min(t_begin + a.tiles_per_group, a.ntiles);
+    const int nt = max(0, t_end - t_begin);
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar_a_full), 1);
+        for (int s = 0; s < TC_BSTAGES; ++s) {
+            mbar_init(smem_u32(&bar_b_full[s]), 1);
+            mbar_init(smem_u32(&bar_b_empty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&bar_acc_full[s]), 1);
+            mbar_init(smem_u32(&bar_acc_empty[s]), 4 * TC_EPI_PER_QUAD * 32);
+        }
+        mbar_init(smem_u32(&bar_mma_done), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    if (warp == 0 && lane == 0 && nt > 0) {
+        // ---------------- TMA producer ----------------
+        mbar_expect_tx(smem_u32(&bar_a_full), (uint32_t)(n_aatoms * TC_ATOM_BYTES));
+        for (int at = 0; at < n_aatoms; ++at)
+            tma_load_2d(smem_u32(smA + (size_t)at * TC_ATOM_BYTES), &tmA, at * TC_KATOM, (int)m0,
+                        smem_u32(&bar_a_full));
+        int it = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            for (int kc = 0; kc < a.n_katoms; ++kc, ++it) {
+                const int s = it % TC_BSTAGES;
+                const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
+                if (!mbar_wait(smem_u32(&bar_b_empty[s]), ph ^ 1u, &abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(smem_u32(&bar_b_full[s]), (uint32_t)TC_ATOM_BYTES);
+                tma_load_2d(smem_u32(smB + (size_t)s * TC_ATOM_BYTES), &tmB, kc * TC_KATOM, t * TC_N,
+                            smem_u32(&bar_b_full[s]));
+            }
+        }
+        if (!ok) {
+            // make sure no copy is still writing shared memory when the CTA exits
+            mbar_drain(smem_u32(&bar_a_full), 0u);
+            for (int back = 1; back <= TC_BSTAGES && it - back >= 0; ++back) {
+                const int i2 = it - back;
+                mbar_drain(smem_u32(&bar_b_full[i2 % TC_BSTAGES]), (uint32_t)(i2 / TC_BSTAGES) & 1u);
+            }
+        }
+    } else if (warp == 1 && lane == 0 && nt > 0) {
+        // ---------------- MMA issuer ----------------
+        bool ok = mbar_wait(smem_u32(&bar_a_full), 0u, &abort_flag, a.status);
+        tc_fence_after();
+        int it = 0;
+        const uint32_t a_base = smem_u32(smA), b_base = smem_u32(smB);
+        for (int tl = 0; tl < nt && ok; ++tl) {
+            const int acc = tl & 1;
+            const uint32_t use = (uint32_t)(tl >> 1) & 1u;
+            if (!mbar_wait(smem_u32(&bar_acc_empty[acc]), use ^ 1u, &abort_flag, a.status)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem + (uint32_t)(acc * TC_N);
+            for (int kc = 0; kc < a.n_katoms; ++kc, ++it) {
+                const int s = it % TC_BSTAGES;
+                const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
+                if (!mbar_wait(smem_u32(&bar_b_full[s]), ph, &abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int sp = 0; sp < 3; ++sp) {
+#pragma unroll
+                    for (int kk = 0; kk < TC_KATOM / 16; ++kk) {
+                        const uint64_t ad = sw128_desc(a_base + (uint32_t)((sp * a.n_katoms + kc) * TC_ATOM_BYTES + kk * 32));
+                        const uint64_t bd = sw128_desc(b_base + (uint32_t)(s * TC_ATOM_BYTES + kk * 32));
+                        mma_bf16(d_tmem, ad, bd, (kc | sp | kk) != 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(smem_u32(&bar_b_empty[s]));
+            }
+            if (!ok) break;
+            mma_commit(smem_u32(&bar_acc_full[acc]));
+        }
+        if (!ok) {
+            // every MMA issued so far must finish before TMEM and shared memory go away
+            mma_commit(smem_u32(&bar_mma_done));
+            mbar_drain(smem_u32(&bar_mma_done), 0u);
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
+        const int col0 = ((warp - 2) / 4) * TC_EPI_COLS;
+        const int row = quad * 32 + lane;
+        const int64_t grow = m0 + row;
+        const bool valid = grow < a.rows;
+        const double t = valid ? a.trace[grow] : 1.0;
+        const float inv_t = (float)(1.0 / t);
+        const float t_hi = (float)t;
+        const float t_lo = (float)(t - (double)t_hi);
+        double total = 0.0;
+        for (int tl = 0; tl < nt; ++tl) {
+            const int acc = tl & 1;
+            const uint32_t use = (uint32_t)(tl >> 1) & 1u;
+            if (!mbar_wait(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) break;
+            tc_fence_after();
+            const int n0 = (t_begin + tl) * TC_N + col0;
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N + col0), v);
+            tc_fence_before();
+            mbar_arrive(smem_u32(&bar_acc_empty[acc]));   // the slice is in registers
+            float tile_sum = 0.0f;
+#pragma unroll
+            for (int sk = 0; sk < TC_EPI_COLS / D; ++sk) {
+                const int nb = n0 + sk * D;               // first column of setting nb / D
+                const float pk = __ldg(a.ptot + nb / D);
+                if (pk > 0.0f) {
+                    float dev = 0.0f;
+#pragma unroll
+                    for (int l = 0; l < D; ++l) {
+                        const float cv = __ldg(a.cnt + nb + l);
+                        if (cv > 0.0f) dev += cv * logf(v[sk * D + l] * __ldg(a.invf + nb + l));
+                    }
+                    float s_hi, s_lo;
+                    compensated_sum<D>(v + sk * D, s_hi, s_lo);
+                    // log(S_k / t) with S_k - t formed from the compensated pair
+                    const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
+                    tile_sum += dev - pk * log1pf(rel);
+                }
+            }
+            if (a.p_out && valid) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
+            }
+            total += (double)tile_sum;
+        }
+        // The four warps of a lane quadrant add their column partials through shared memory.
+        // The P-tile ring is free now: this warp saw the last accumulator, so every MMA has
+        // completed and every TMA load has been consumed.
+        reinterpret_cast<double *>(smB)[(warp - 2) * 32 + lane] = total;
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+    } else if (warp >= 2 && warp < 6) {
+        const int quad = warp & 3;
+        const int64_t grow = m0 + quad * 32 + lane;
+        double total = 0.0;
+#pragma unroll
+        for (int e = 0; e < TC_EPI_PER_QUAD; ++e) total += reinterpret_cast<const double *>(smB)[(warp - 2 + 4 * e) * 32 + lane];
+        if (grow < a.rows) a.out[(int64_t)blockIdx.y * a.rows + grow] = total;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool encode_bf16_2d(CUtensorMap *map, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                    uint32_t box_outer) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t tc_smem_bytes(int n_katoms) { return 1024 + (size_t)(3 * n_katoms + TC_BSTAGES) * TC_ATOM_BYTES; }
+
+}  // namespace
+
+struct TcPlan {
+    CUtensorMap a;
+    CUtensorMap b;
+    int n_katoms;
+    int ntiles;
+};
+
+namespace {
+template <int D>
+cudaError_t launch_tc_d(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(project_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = smem;
+    }
+    project_tc_kernel<D><<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
+    return cudaGetLastError();
+}
+}  // namespace
+
+int tc_column_tile(int KD) { return KD > 0 ? TC_N : 0; }
+// (a setting's D outcome columns never straddle a 128-column tile: D divides 128)
+
+int tc_ngroups(const ProblemView &p, int64_t rows) {
+    const int64_t mt = (rows + TC_M - 1) / TC_M;
+    const int ntiles = p.KD_tc / TC_N;
+    int g = 1;
+    while (g < ntiles && mt * g < 152) g *= 2;
+    return g > ntiles ? ntiles : g;
+}
+
+cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, int64_t rows, TcPlan **plan) {
+    *plan = nullptr;
+    if (p.d_pad % TC_KATOM != 0 || p.KD_tc % TC_N != 0 || p.KD_tc <= 0) return cudaErrorNotSupported;
+    const int n_katoms = p.d_pad / TC_KATOM;
+    if (tc_smem_bytes(n_katoms) > 227 * 1024 - 256) return cudaErrorNotSupported;
+    if (reinterpret_cast<uintptr_t>(A_split) % 16 != 0 || reinterpret_cast<uintptr_t>(p.Pbf) % 16 != 0)
+        return cudaErrorMisalignedAddress;
+    TcPlan *pl = new TcPlan();
+    pl->n_katoms = n_katoms;
+    pl->ntiles = p.KD_tc / TC_N;
+    const bool ok_a = encode_bf16_2d(&pl->a, A_split, (uint64_t)3 * p.d_pad, (uint64_t)rows, TC_KATOM, TC_M);
+    const bool ok_b = encode_bf16_2d(&pl->b, p.Pbf, (uint64_t)p.d_pad, (uint64_t)p.KD_tc, TC_KATOM, TC_N);
+    if (!ok_a || !ok_b) {
+        delete pl;
+        return cudaErrorInvalidValue;
+    }
+    *plan = pl;
+    return cudaSuccess;
+}
+
 void tc_plan_destroy(TcPlan *plan) { delete plan; }
-cudaError_t launch_project_tc(const TcPlan *, const ProblemView &, int64_t, double *, float *, uint32_t *,
-                              cudaStream_t) {
-    return cudaErrorNotSupported;
+
+cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t rows, double *out_part, float *p_out,
+                              uint32_t *status, cudaStream_t s) {
+    if (!plan) return cudaErrorInvalidValue;
+    if (rows <= 0) return cudaSuccess;
+    TcArgs a;
+    a.cnt = p.cnt;
+    a.invf = p.invf;
+    a.ptot = p.ptot;
+    a.trace = p.trace_prop;
+    a.out = out_part;
+    a.p_out = p_out;
+    a.status = status;
+    a.rows = rows;
+    a.KD = p.KD;
+    a.n_katoms = plan->n_katoms;
+    a.ntiles = plan->ntiles;
+    const int groups = p.ngroups;
+    a.tiles_per_group = (plan->ntiles + groups - 1) / groups;
+    const size_t smem = tc_smem_bytes(plan->n_katoms);
+    dim3 grid((unsigned)((rows + TC_M - 1) / TC_M), (unsigned)groups);
+    switch (p.D) {
+        case 2: return launch_tc_d<2>(plan, a, grid, smem, s);
+        case 4: return launch_tc_d<4>(plan, a, grid, smem, s);
+        case 8: return launch_tc_d<8>(plan, a, grid, smem, s);
+        case 16: return launch_tc_d<16>(plan, a, grid, smem, s);
+        default: return cudaErrorNotSupported;
+    }
 }
 
 }  // namespace qst

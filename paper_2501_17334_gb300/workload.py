@@ -57,10 +57,35 @@ def pauli_vectors(num_qubits: int) -> np.ndarray:
     return out
 
 
+# single-qubit eigenprojectors, index [setting][outcome], entries exactly 0, +-1/2, +-i/2, 1
+_PROJ = np.array(
+    [
+        [[[0.5, 0.5], [0.5, 0.5]], [[0.5, -0.5], [-0.5, 0.5]]],            # X+ , X-
+        [[[0.5, -0.5j], [0.5j, 0.5]], [[0.5, 0.5j], [-0.5j, 0.5]]],        # Y+ , Y-
+        [[[1.0, 0.0], [0.0, 0.0]], [[0.0, 0.0], [0.0, 1.0]]],              # Z+ , Z-
+    ],
+    dtype=np.complex128,
+)
+
+
 def pauli_povms(num_qubits: int):
-    """All ``3**Q`` Pauli-basis POVMs as real and imaginary ``[K*D, D, D]`` float64 arrays."""
-    phi = pauli_vectors(num_qubits)
-    lam = phi[:, :, None] * phi[:, None, :].conj()
+    """All ``3**Q`` Pauli-basis POVMs as real and imaginary ``[K*D, D, D]`` float64 arrays.
+
+    Built as Kronecker products of the exact single-qubit projectors, so every entry is
+    0 or +-2^-m (times 1 or i) with no rounding.
+    """
+    q = int(num_qubits)
+    d = 1 << q
+    k_count = 3 ** q
+    lam = np.empty((k_count * d, d, d), dtype=np.complex128)
+    for k in range(k_count):
+        settings = [(k // 3 ** (q - 1 - i)) % 3 for i in range(q)]
+        for l in range(d):
+            bits = [(l >> (q - 1 - i)) & 1 for i in range(q)]
+            m = np.array([[1.0 + 0j]])
+            for s_, b in zip(settings, bits):
+                m = np.kron(m, _PROJ[s_, b])
+            lam[k * d + l] = m
     return np.ascontiguousarray(lam.real), np.ascontiguousarray(lam.imag)
 
 
