@@ -230,6 +230,41 @@ qst_status qst_pack_projectors(int32_t num_qubits, int32_t num_povms, const doub
  * pooling) its last valid rho.  Device-side only, asynchronous. */
 qst_status qst_inject_nan(qst_handle *h, int32_t problem, int64_t chain);
 
+/* ---- evaluation without device allocation ---------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point: it serves callers that must not
+ * allocate device memory on their call path -- a library or plugin whose host application
+ * owns the device memory through its own allocator, or an asynchronous pipeline that
+ * cannot afford cudaMalloc/cudaFree, which may synchronise the whole device.
+ *
+ * qst_loglik_noalloc computes log L(x) of Eq. likelihood for n latent vectors x exactly as
+ * qst_evaluate does with QST_PREC_FP32 (Algorithm 1 with two Gram-Schmidt passes, the FP32
+ * projector contraction, the deviance-form FP64 reduction), but needs no handle and no
+ * workspace: its intermediates live in one device array of QST_NOALLOC_SCRATCH_BYTES
+ * (about 5.8 MiB) defined in the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   num_qubits  Q, 1..4
+ *   num_povms   K, with K * 2^Q <= 1408 (all 81 Pauli settings of 4 qubits fit)
+ *   P           device [D^2][K D] float: the packed projector matrix, as qst_pack_projectors
+ *               produces it; caller-owned, read during the call
+ *   counts      host [K D] int32 outcome counts c_kl >= 0; read before the call returns
+ *   x           device [n][4 D^2] float latent vectors (layout as in the header comment)
+ *   n           0 <= n <= QST_NOALLOC_MAX_ROWS rows per call (larger batches: call again)
+ *   logl        device [n] double, written
+ *   cuda_stream cudaStream_t the work is enqueued on (NULL = default stream)
+ * Returns QST_ERR_INVALID_ARG for a size beyond these limits, a NULL pointer or a negative
+ * count, QST_ERR_CUDA for a CUDA failure (message in qst_last_error()).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The first call on a device (with
+ * that device current) looks up the scratch array's device address once; make that first
+ * call before any stream capture.  All calls share the one scratch array, which keeps the
+ * previous call's contents (each call rewrites what it reads): calls that can overlap on
+ * the GPU -- on different streams without ordering between them -- race and must be
+ * serialised by the caller. */
+#define QST_NOALLOC_MAX_ROWS 4096
+#define QST_NOALLOC_SCRATCH_BYTES 6040576
+qst_status qst_loglik_noalloc(int32_t num_qubits, int32_t num_povms, const float *P, const int32_t *counts,
+                              const float *x, int64_t n, double *logl, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -277,6 +277,12 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
     return QST_OK;
 }
 
+}  // namespace
+
+void qst::set_last_error(const char *msg) { g_last_error = msg; }
+
+namespace {
+
 struct EventPair {
     cudaEvent_t a, b;
     int kind;

@@ -86,7 +86,10 @@ _SIGS = {
                                          ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, _P, _P]),
     "qst_pack_projectors": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "qst_inject_nan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
+    "qst_loglik_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
 }
+
+NOALLOC_MAX_ROWS = 4096
 
 
 def library_path() -> str:
@@ -313,6 +316,14 @@ def philox_blocks(seed, step, tag, chain0, nchains, block0, nblocks, stream=None
     _check(load().qst_philox_blocks(seed, step, tag, chain0, nchains, block0, nblocks, out.data_ptr(),
                                     _stream_ptr(stream)))
     return out
+
+
+def loglik_noalloc(num_qubits: int, num_povms: int, P, counts, x, logl, stream=None):
+    """qst_loglik_noalloc: log L of the rows of ``x`` into ``logl`` without any device allocation
+    by the library (P, x, logl: torch CUDA tensors owned by the caller; counts: host int32)."""
+    c = np.ascontiguousarray(counts, dtype=np.int32)
+    _check(load().qst_loglik_noalloc(num_qubits, num_povms, _ptr(P), c.ctypes.data, _ptr(x), int(x.shape[0]),
+                                     _ptr(logl), _stream_ptr(stream)))
 
 
 def pack_projectors(num_qubits: int, povm_re: np.ndarray, povm_im: np.ndarray) -> np.ndarray:
