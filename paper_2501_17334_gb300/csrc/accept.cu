@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
                     if (rate < a.sp.acc_lo) beta = beta / a.sp.adapt_factor;
                     if (beta > a.sp.beta_max) beta = a.sp.beta_max;
                     p.beta[c] = beta;
+                    p.coef[c] = make_float2((float)sqrt(1.0 - beta * beta), (float)beta);
                     win = 0;
                 }
                 p.acc_win[c] = win;

@@ -72,7 +72,8 @@ bool bf16_exact(double v) {
 // Per-problem host record and workspace layout
 // ------------------------------------------------------------------------------------------
 struct Layout {
-    size_t P32, Pbf, cnt, invf, ptot, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, acc_win,
+    size_t P32, Pbf, cnt, invf, ptot, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, coef,
+        acc_win,
         acc_total, pool, traj, trace_acc, trace_logl, red, acf, logl_eval, end;
 };
 
@@ -261,6 +262,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         L.logl_cur = take(sizeof(double) * R);
         L.logl_part = take(sizeof(double) * v.ngroups * R);
         L.beta = take(sizeof(double) * R);
+        L.coef = take(sizeof(float2) * R);
         L.acc_win = take(sizeof(int32_t) * R);
         L.acc_total = take(sizeof(int64_t) * R);
         L.pool = take(sizeof(double) * v.n_slots * v.d);
@@ -375,6 +377,7 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     v.logl_cur = reinterpret_cast<double *>(b + L.logl_cur);
     v.logl_part = reinterpret_cast<double *>(b + L.logl_part);
     v.beta = reinterpret_cast<double *>(b + L.beta);
+    v.coef = reinterpret_cast<float2 *>(b + L.coef);
     v.acc_win = reinterpret_cast<int32_t *>(b + L.acc_win);
     v.acc_total = reinterpret_cast<int64_t *>(b + L.acc_total);
     v.pool = reinterpret_cast<double *>(b + L.pool);
@@ -513,6 +516,9 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
         std::vector<double> beta(v.R, hp.beta0);
         QST_CUDA(cudaMemcpyAsync(v.beta, beta.data(), sizeof(double) * v.R, cudaMemcpyHostToDevice, h->stream),
                  "upload beta");
+        std::vector<float2> coef(v.R, make_float2((float)std::sqrt(1.0 - hp.beta0 * hp.beta0), (float)hp.beta0));
+        QST_CUDA(cudaMemcpyAsync(v.coef, coef.data(), sizeof(float2) * v.R, cudaMemcpyHostToDevice, h->stream),
+                 "upload proposal coefficients");
         // pageable copies above are staged synchronously; keep the host vectors alive until then
         QST_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
         if (is_tc(h.get())) {

@@ -3,8 +3,9 @@
 // One chain is handled by D consecutive lanes; lane j owns column j of the D x D
 // blocks G and H (the latent layout is column-major, so a column is D contiguous
 // floats of each of the four parts).  Per chain:
-//   1. eta from Philox (tag 1, step j) and y' = sqrt(1 - beta^2) y + beta eta; y'
-//      is written to the chain's other y buffer (the accept kernel flips to it);
+//   1. eta from Philox (tag 1, step j) and y' = sqrt(1 - beta^2) y + beta eta, one
+//      Philox block (four entries) at a time; y' goes to the chain's other y buffer (the
+//      accept kernel flips to it) and to shared memory (G's column, H's column);
 //   2. modified Gram-Schmidt on the columns of H: lane k normalises column k and
 //      publishes it, lanes j > k project it out.  MGS yields the unitary factor whose
 //      R has a positive real diagonal, i.e. U = Q Lambda of Algorithm 1 l.5.  A second
@@ -15,10 +16,11 @@
 //   4. rho = W W^dag / Tr: lane a computes entries (a, a+t mod D) for t = 0..D/2
 //      (the Hermitian half, balanced over lanes), packed as vec_h and scaled by the FP32
 //      reciprocal of the trace.  The rounding of that scaling is not left in the
-//      probabilities: the exact FP64 sum t of the *stored* FP32 diagonal (1 up to a few
-//      ulps) is written too, and the likelihood uses p = (vec_h . P) / t, i.e. subtracts
-//      N log t in FP64.  Then sum_l p_kl = 1 holds to the contraction's rounding, with no
-//      coherent shift of every probability (which would cost N * 2^-24 in log L);
+//      probabilities: the exact sum t of the *stored* FP32 diagonal (1 up to a few ulps,
+//      formed by a TwoSum reduction) is written too, and the likelihood uses
+//      p = (vec_h . P) / t, i.e. subtracts N log t in FP64.  Then sum_l p_kl = 1 holds to
+//      the contraction's rounding, with no coherent shift of every probability (which
+//      would cost N * 2^-24 in log L);
 //   5. the packed row is stored as FP32 and, for the tensor-core contraction, as the
 //      exact three-term bf16 split hi + mid + lo.
 #include "qst_internal.cuh"
@@ -26,31 +28,105 @@
 namespace qst {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 
+// Shared memory per chain (floats), laid out so every access is free of bank conflicts:
+//   area A: H's real and imaginary planes (column-major, column stride D) -> U's planes ->
+//           W row-major (complex, rows padded to D + 2) once U is no longer needed;
+//   area B: G's real and imaginary planes (column-major, column stride D + 4 so that the
+//           128-bit stores and loads of eight consecutive lanes' columns hit different
+//           banks) -> packed rho (row stride D + 1) once G is in registers.
 template <int D>
 struct Shape {
     static constexpr int d = D * D;
     static constexpr int chains_per_block = kThreads / D;
-    // per-chain shared memory: U then W (D x D complex) + packed rho (d floats) + pad
-    static constexpr int smem_floats = 3 * D * D + 4;
+    static constexpr int row_stride = D + 2;                   // float2 per row of W (padded)
+    static constexpr int gcol = D + 4;                          // floats per column of a G plane
+    static constexpr int pk_stride = D + 1;                     // floats per row of the staged rho
+    static constexpr int area_a = (2 * D * D > 2 * D * row_stride) ? 2 * D * D : 2 * D * row_stride;
+    static constexpr int area_b = 2 * D * gcol;
+    static constexpr int smem_floats = area_a + area_b;
 };
 
+// Box-Muller with the fast hardware log and sine/cosine: the angle is reduced to
+// 2 pi (v - 1/2) in (-pi, pi), where the intrinsics are accurate to ~2^-21 absolute, and
+// cos/sin(2 pi v) = -cos/-sin(2 pi (v - 1/2)).  v - 1/2 is exact.  The normals agree with
+// the FP64 Box-Muller of the same uniforms to about 1e-6 relative.
+__device__ __forceinline__ void gaussian_pair_fast(uint32_t wu, uint32_t wv, float &z0, float &z1) {
+    const float u = Philox::uniform(wu);
+    const float v = Philox::uniform(wv);
+    const float radius = sqrtf(-2.0f * __logf(u));
+    float s, c;
+    __sincosf(6.283185307179586f * (v - 0.5f), &s, &c);
+    z0 = -radius * c;
+    z1 = -radius * s;
+}
+
+// a D-float column of a plane into / from registers, 128-bit at a time where D allows
 template <int D>
-__device__ __forceinline__ double group_sum(double v) {
+__device__ __forceinline__ void load_column(const float *src, float (&v)[D]) {
+    if constexpr (D >= 4) {
+#pragma unroll
+        for (int i = 0; i < D; i += 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(src + i);
+            v[i] = t.x;
+            v[i + 1] = t.y;
+            v[i + 2] = t.z;
+            v[i + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] = src[i];
+    }
+}
+template <int D>
+__device__ __forceinline__ void store_column(float *dst, const float (&v)[D]) {
+    if constexpr (D >= 4) {
+#pragma unroll
+        for (int i = 0; i < D; i += 4)
+            *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) dst[i] = v[i];
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
     for (int off = D / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
+}
+
+// Exact sum over the D lanes of a chain as an unevaluated pair hi + lo (TwoSum at every level).
+template <int D>
+__device__ __forceinline__ void group_sum_exact(float v, float &hi, float &lo) {
+    float err = 0.0f;
+#pragma unroll
+    for (int off = D / 2; off > 0; off >>= 1) {
+        const float pv = __shfl_xor_sync(0xffffffffu, v, off);
+        const float pe = __shfl_xor_sync(0xffffffffu, err, off);
+        // both partners form the same sum: order the operands by lane so they round alike
+        const bool low = (threadIdx.x & off) == 0;
+        const float x = low ? v : pv, y = low ? pv : v;
+        const float sum = x + y;
+        const float bb = sum - x;
+        const float e = (x - (sum - bb)) + (y - bb);
+        err = (low ? err + pe : pe + err) + e;
+        v = sum;
+    }
+    hi = v;
+    lo = err;
 }
 
 struct ProposeArgs {
     const float *x_eval;        // MODE_EVAL: [rows][nx] latent vectors
     float *y;                   // [2][R][nx]
     const uint8_t *cur;         // [R]
-    const double *beta;         // [R]
+    const float2 *coef;         // [R] (sqrt(1 - beta^2), beta) as floats
     float *rho_out;             // [rows][d_pad] packed rho (FP32-normalised)
     __nv_bfloat16 *split_out;   // [rows][3][d_pad] or null
-    double *trace_out;          // [rows] exact FP64 trace of the stored rho (1 up to rounding)
+    double *trace_out;          // [rows] exact trace of the stored rho (1 up to rounding)
     float *rho_norm_out;        // MODE_EVAL, optional: [rows][d] copy of the packed rho
     int64_t rows;
     int64_t R;
@@ -62,140 +138,163 @@ struct ProposeArgs {
 };
 
 template <int D, int PASSES>
-__global__ void __launch_bounds__(kThreads) propose_kernel(ProposeArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     using S = Shape<D>;
     constexpr int d = S::d;
     constexpr int nx = 4 * d;
-    extern __shared__ float smem[];
+    constexpr int RS = S::row_stride;
+    constexpr int GC = S::gcol;
+    constexpr int PK = S::pk_stride;
+    extern __shared__ __align__(16) float smem[];
 
     const int j = threadIdx.x % D;       // owned column (and, in step 4, owned row)
     const int g = threadIdx.x / D;       // chain slot in the block
     const int64_t c = (int64_t)blockIdx.x * S::chains_per_block + g;
     const bool active = c < a.rows;
     float *sm = smem + g * S::smem_floats;
-    float2 *mat = reinterpret_cast<float2 *>(sm);   // column-major complex D x D
-    float *packed = sm + 2 * d;
+    float *hre = sm, *him = sm + d;                     // H planes, then U planes (column stride D)
+    float2 *wsm = reinterpret_cast<float2 *>(sm);        // W row-major (row stride RS), replaces U
+    float *gre = sm + S::area_a, *gim = gre + D * GC;    // G planes (column stride GC)
+    float *packed = sm + S::area_a;                      // staged rho (row stride PK), replaces G
 
-    // ---- 1. latent proposal: the four D-long column slices this lane owns -----------------
-    float yv[4][D];
+    // ---- 1. latent proposal --------------------------------------------------------------
     float coef_y = 1.0f, coef_eta = 0.0f;
     int cur = 0;
     if (active && a.mode == MODE_STEP) {
         cur = a.cur[c];
-        const double b = a.beta[c];
-        coef_y = (float)sqrt(1.0 - b * b);
-        coef_eta = (float)b;
+        const float2 cf = a.coef[c];
+        coef_y = cf.x;
+        coef_eta = cf.y;
     } else if (a.mode == MODE_INIT) {
         coef_y = 0.0f;
         coef_eta = 1.0f;
     }
-    const uint32_t chain_id = (uint32_t)(a.chain_offset + (active ? c : 0));
+    const int64_t cc = active ? c : 0;
+    const uint32_t chain_id = (uint32_t)(a.chain_offset + cc);
     const uint32_t tag = (a.mode == MODE_INIT) ? TAG_INIT : TAG_PROPOSAL;
     const uint32_t key_lo = (uint32_t)(a.seed & 0xffffffffu), key_hi = (uint32_t)(a.seed >> 32);
-#pragma unroll
-    for (int part = 0; part < 4; ++part) {
-        const int base = part * d + j * D;   // element index of (row 0, column j)
-        if (a.mode == MODE_EVAL) {
-            const float *src = a.x_eval + (active ? c : 0) * nx + base;
-#pragma unroll
-            for (int i = 0; i < D; ++i) yv[part][i] = active ? src[i] : 0.0f;
-            continue;
-        }
-        float y0[D];
-        if (a.mode == MODE_STEP) {
-            const float *src = a.y + ((int64_t)cur * a.R + (active ? c : 0)) * nx + base;
-            if (D >= 4) {
-#pragma unroll
-                for (int i = 0; i < D; i += 4) {
-                    const float4 v = active ? *reinterpret_cast<const float4 *>(src + i) : make_float4(0, 0, 0, 0);
-                    y0[i] = v.x; y0[i + 1] = v.y; y0[i + 2] = v.z; y0[i + 3] = v.w;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < D; ++i) y0[i] = active ? src[i] : 0.0f;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < D; ++i) y0[i] = 0.0f;
-        }
-        float eta[D];
-        if (D >= 4) {
+    const float *ysrc = a.y + ((int64_t)cur * a.R + cc) * nx;
+    float *ydst = a.y + ((int64_t)(1 - cur) * a.R + cc) * nx;
+    if constexpr (D >= 4) {
+        // lane j owns entries j D .. j D + D - 1 of each part: D/4 Philox blocks per part
+#pragma unroll 1
+        for (int part = 0; part < 4; ++part) {
+            const int e0 = part * d + j * D;    // element index of (row 0, column j)
+            float4 y0[D / 4];
 #pragma unroll
             for (int q = 0; q < D / 4; ++q) {
-                const uint4 w = Philox::block(make_uint4((uint32_t)(base / 4 + q), a.step, chain_id, tag), key_lo, key_hi);
-                Philox::gaussian_pair(w.x, w.y, eta[4 * q], eta[4 * q + 1]);
-                Philox::gaussian_pair(w.z, w.w, eta[4 * q + 2], eta[4 * q + 3]);
+                y0[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (active && a.mode == MODE_STEP) y0[q] = *reinterpret_cast<const float4 *>(ysrc + e0 + 4 * q);
+                if (active && a.mode == MODE_EVAL) y0[q] = *reinterpret_cast<const float4 *>(a.x_eval + cc * nx + e0 + 4 * q);
             }
-        } else {
-            // D == 2: the column is half of block `part`; lane j takes uniform pair j
-            const uint4 w = Philox::block(make_uint4((uint32_t)part, a.step, chain_id, tag), key_lo, key_hi);
-            const uint32_t wu = (j == 0) ? w.x : w.z;
-            const uint32_t wv = (j == 0) ? w.y : w.w;
-            Philox::gaussian_pair(wu, wv, eta[0], eta[D - 1]);
+            float *plane = (part == 0) ? gre : (part == 1) ? gim : (part == 2) ? hre : him;
+            const int col = (part < 2) ? j * GC : j * D;
+#pragma unroll
+            for (int q = 0; q < D / 4; ++q) {
+                float4 yn = y0[q];
+                if (a.mode != MODE_EVAL) {
+                    const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), a.step, chain_id, tag), key_lo, key_hi);
+                    float z0, z1, z2, z3;
+                    gaussian_pair_fast(w.x, w.y, z0, z1);
+                    gaussian_pair_fast(w.z, w.w, z2, z3);
+                    yn.x = __fmaf_rn(coef_y, y0[q].x, coef_eta * z0);
+                    yn.y = __fmaf_rn(coef_y, y0[q].y, coef_eta * z1);
+                    yn.z = __fmaf_rn(coef_y, y0[q].z, coef_eta * z2);
+                    yn.w = __fmaf_rn(coef_y, y0[q].w, coef_eta * z3);
+                    if (active) *reinterpret_cast<float4 *>(ydst + e0 + 4 * q) = yn;
+                }
+                *reinterpret_cast<float4 *>(plane + col + 4 * q) = yn;
+            }
         }
+    } else {
+        // D == 2: each part is one Philox block shared by the two lanes; lane j takes pair j
 #pragma unroll
-        for (int i = 0; i < D; ++i) yv[part][i] = __fmaf_rn(coef_y, y0[i], coef_eta * eta[i]);
-        if (active) {
-            float *dst = a.y + ((int64_t)(1 - cur) * a.R + c) * nx + base;
-            if (D >= 4) {
-#pragma unroll
-                for (int i = 0; i < D; i += 4)
-                    *reinterpret_cast<float4 *>(dst + i) = make_float4(yv[part][i], yv[part][i + 1], yv[part][i + 2], yv[part][i + 3]);
+        for (int part = 0; part < 4; ++part) {
+            const int e = part * d + j * D;
+            float y0v = 0.0f, y1v = 0.0f;
+            if (a.mode == MODE_EVAL) {
+                if (active) {
+                    y0v = a.x_eval[cc * nx + e];
+                    y1v = a.x_eval[cc * nx + e + 1];
+                }
             } else {
-#pragma unroll
-                for (int i = 0; i < D; ++i) dst[i] = yv[part][i];
+                const uint4 w = Philox::block(make_uint4((uint32_t)part, a.step, chain_id, tag), key_lo, key_hi);
+                float z0, z1;
+                gaussian_pair_fast(j == 0 ? w.x : w.z, j == 0 ? w.y : w.w, z0, z1);
+                float o0 = 0.0f, o1 = 0.0f;
+                if (a.mode == MODE_STEP && active) {
+                    o0 = ysrc[e];
+                    o1 = ysrc[e + 1];
+                }
+                y0v = __fmaf_rn(coef_y, o0, coef_eta * z0);
+                y1v = __fmaf_rn(coef_y, o1, coef_eta * z1);
+                if (active) {
+                    ydst[e] = y0v;
+                    ydst[e + 1] = y1v;
+                }
             }
+            float *plane = (part == 0) ? gre : (part == 1) ? gim : (part == 2) ? hre : him;
+            const int col = (part < 2) ? j * GC : j * D;
+            plane[col] = y0v;
+            plane[col + 1] = y1v;
         }
     }
-    float(&gr)[D] = yv[0];
-    float(&gi)[D] = yv[1];
-    float(&hr)[D] = yv[2];
-    float(&hi)[D] = yv[3];
+    // this lane's column of H (staged by this lane only)
+    float hr[D], hi[D];
+    load_column<D>(hre + j * D, hr);
+    load_column<D>(him + j * D, hi);
+    __syncwarp();
 
     // ---- 2. modified Gram-Schmidt on the columns of H -> U (Algorithm 1 l.4-5) -----------
 #pragma unroll 1
     for (int pass = 0; pass < PASSES; ++pass) {
+#pragma unroll 1
+        for (int k = 0; k < D; ++k) {
+            if (j == k) {
+                float n0 = 0.0f, n1 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (j == k) {
-            float nrm = 0.0f;
+                for (int i = 0; i < D; i += 2) {
+                    n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
+                    n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
+                }
+                const float inv = 1.0f / sqrtf(n0 + n1);
 #pragma unroll
-            for (int i = 0; i < D; ++i) nrm = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], nrm));
-            const float inv = 1.0f / sqrtf(nrm);
+                for (int i = 0; i < D; ++i) {
+                    hr[i] *= inv;
+                    hi[i] *= inv;
+                }
+                store_column<D>(hre + k * D, hr);
+                store_column<D>(him + k * D, hi);
+            }
+            __syncwarp();
+            if (j > k) {
+                float qr[D], qi[D];
+                load_column<D>(hre + k * D, qr);
+                load_column<D>(him + k * D, qi);
+                // r = q^dag h with two independent accumulator pairs
+                float rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                hr[i] *= inv;
-                hi[i] *= inv;
-                mat[k * D + i] = make_float2(hr[i], hi[i]);
+                for (int i = 0; i < D; i += 2) {
+                    rr0 = __fmaf_rn(qr[i], hr[i], __fmaf_rn(qi[i], hi[i], rr0));
+                    ri0 = __fmaf_rn(qr[i], hi[i], __fmaf_rn(-qi[i], hr[i], ri0));
+                    rr1 = __fmaf_rn(qr[i + 1], hr[i + 1], __fmaf_rn(qi[i + 1], hi[i + 1], rr1));
+                    ri1 = __fmaf_rn(qr[i + 1], hi[i + 1], __fmaf_rn(-qi[i + 1], hr[i + 1], ri1));
+                }
+                const float rr = rr0 + rr1, ri = ri0 + ri1;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    hr[i] = __fmaf_rn(-rr, qr[i], __fmaf_rn(ri, qi[i], hr[i]));
+                    hi[i] = __fmaf_rn(-rr, qi[i], __fmaf_rn(-ri, qr[i], hi[i]));
+                }
             }
         }
         __syncwarp();
-        if (j > k) {
-            float qr[D], qi[D];
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                const float2 q = mat[k * D + i];
-                qr[i] = q.x;
-                qi[i] = q.y;
-            }
-            float rr = 0.0f, ri = 0.0f;   // r = q^dag h
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                rr = __fmaf_rn(qr[i], hr[i], __fmaf_rn(qi[i], hi[i], rr));
-                ri = __fmaf_rn(qr[i], hi[i], __fmaf_rn(-qi[i], hr[i], ri));
-            }
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                hr[i] = __fmaf_rn(-rr, qr[i], __fmaf_rn(ri, qi[i], hr[i]));
-                hi[i] = __fmaf_rn(-rr, qi[i], __fmaf_rn(-ri, qr[i], hi[i]));
-            }
-        }
-    }
-    __syncwarp();
     }
 
     // ---- 3. W = (U + I) G, column j: W[:,j] = G[:,j] + sum_k U[:,k] G[k,j] ------------------
-    float wr[D], wi[D];
+    float gr[D], gi[D], wr[D], wi[D];
+    load_column<D>(gre + j * GC, gr);
+    load_column<D>(gim + j * GC, gi);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         wr[i] = gr[i];
@@ -203,64 +302,73 @@ __global__ void __launch_bounds__(kThreads) propose_kernel(ProposeArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        const float gkr = gr[k], gki = gi[k];
+        float ur[D], ui[D];
+        load_column<D>(hre + k * D, ur);
+        load_column<D>(him + k * D, ui);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const float2 u = mat[k * D + i];
-            wr[i] = __fmaf_rn(u.x, gkr, __fmaf_rn(-u.y, gki, wr[i]));
-            wi[i] = __fmaf_rn(u.x, gki, __fmaf_rn(u.y, gkr, wi[i]));
+            wr[i] = __fmaf_rn(ur[i], gr[k], __fmaf_rn(-ui[i], gi[k], wr[i]));
+            wi[i] = __fmaf_rn(ur[i], gi[k], __fmaf_rn(ui[i], gr[k], wi[i]));
         }
     }
     __syncwarp();
+    // W row-major with padded rows: W[i][j] at wsm[i * RS + j] (replaces U)
 #pragma unroll
-    for (int i = 0; i < D; ++i) mat[j * D + i] = make_float2(wr[i], wi[i]);
+    for (int i = 0; i < D; ++i) wsm[i * RS + j] = make_float2(wr[i], wi[i]);
     __syncwarp();
 
     // ---- 4. rho = W W^dag / Tr: lane a owns entries (a, a + t mod D), t = 0..D/2 ------------
     const int arow = j;
     float war[D], wai[D];
 #pragma unroll
-    for (int jj = 0; jj < D; ++jj) {
-        const float2 w = mat[jj * D + arow];
-        war[jj] = w.x;
-        wai[jj] = w.y;
+    for (int jj = 0; jj < D; jj += 2) {
+        const float4 v = *reinterpret_cast<const float4 *>(wsm + arow * RS + jj);
+        war[jj] = v.x;
+        wai[jj] = v.y;
+        war[jj + 1] = v.z;
+        wai[jj + 1] = v.w;
     }
     float diag = 0.0f;
 #pragma unroll
     for (int jj = 0; jj < D; ++jj) diag = __fmaf_rn(war[jj], war[jj], __fmaf_rn(wai[jj], wai[jj], diag));
-    const float inv_tr = (float)(1.0 / group_sum<D>((double)diag));
+    const float inv_tr = 1.0f / group_sum<D>(diag);
     const float diag_n = diag * inv_tr;
-    const double trace = group_sum<D>((double)diag_n);   // exact sum of the stored diagonal
-    packed[arow * D + arow] = diag_n;
-#pragma unroll
+    float tr_hi, tr_lo;
+    group_sum_exact<D>(diag_n, tr_hi, tr_lo);   // exact trace of the stored diagonal
+    packed[arow * PK + arow] = diag_n;
+#pragma unroll 1
     for (int t = 1; t <= D / 2; ++t) {
         const int b = (arow + t) & (D - 1);
         if (t == D / 2 && arow >= D / 2) continue;  // (a, a + D/2) is done by the lower lane
-        float re = 0.0f, im = 0.0f;   // (W W^dag)_ab = sum_jj W[a,jj] conj(W[b,jj])
+        float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;   // (W W^dag)_ab = sum W[a,jj] conj(W[b,jj])
 #pragma unroll
-        for (int jj = 0; jj < D; ++jj) {
-            const float2 wb = mat[jj * D + b];
-            re = __fmaf_rn(war[jj], wb.x, __fmaf_rn(wai[jj], wb.y, re));
-            im = __fmaf_rn(wai[jj], wb.x, __fmaf_rn(-war[jj], wb.y, im));
+        for (int jj = 0; jj < D; jj += 2) {
+            const float4 wb = *reinterpret_cast<const float4 *>(wsm + b * RS + jj);
+            re0 = __fmaf_rn(war[jj], wb.x, __fmaf_rn(wai[jj], wb.y, re0));
+            im0 = __fmaf_rn(wai[jj], wb.x, __fmaf_rn(-war[jj], wb.y, im0));
+            re1 = __fmaf_rn(war[jj + 1], wb.z, __fmaf_rn(wai[jj + 1], wb.w, re1));
+            im1 = __fmaf_rn(wai[jj + 1], wb.z, __fmaf_rn(-war[jj + 1], wb.w, im1));
         }
-        re *= inv_tr;
-        im *= inv_tr;
+        const float re = (re0 + re1) * inv_tr;
+        const float im = (im0 + im1) * inv_tr;
         if (arow < b) {
-            packed[arow * D + b] = re;
-            packed[b * D + arow] = -im;
+            packed[arow * PK + b] = re;
+            packed[b * PK + arow] = -im;
         } else {
-            packed[arow * D + b] = im;
-            packed[b * D + arow] = re;
+            packed[arow * PK + b] = im;
+            packed[b * PK + arow] = re;
         }
     }
-    if (active && j == 0) a.trace_out[c] = trace;
+    if (active && j == 0) a.trace_out[c] = (double)tr_hi + (double)tr_lo;
     __syncwarp();
 
     // ---- 5. store packed rho (FP32) and its exact bf16 split ----------------------------------
     if (active) {
         float *dst = a.rho_out + c * a.d_pad;
         for (int e = 4 * j; e < d; e += 4 * D) {
-            const float4 v = *reinterpret_cast<const float4 *>(packed + e);
+            // entries e .. e+3 of the row-major packed rho, staged with row stride PK
+            auto staged = [&](int ee) { return packed[(ee / D) * PK + (ee % D)]; };
+            const float4 v = make_float4(staged(e), staged(e + 1), staged(e + 2), staged(e + 3));
             *reinterpret_cast<float4 *>(dst + e) = v;
             if (a.rho_norm_out) *reinterpret_cast<float4 *>(a.rho_norm_out + c * d + e) = v;
             if (a.split_out) {
@@ -285,13 +393,13 @@ __global__ void __launch_bounds__(kThreads) propose_kernel(ProposeArgs a) {
 
 template <int D, int PASSES>
 cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, const float *x_eval, int64_t rows,
-                             bool want_split, float *rho_norm_out, cudaStream_t s) {
+                              bool want_split, float *rho_norm_out, cudaStream_t s) {
     using S = Shape<D>;
     ProposeArgs a;
     a.x_eval = x_eval;
     a.y = p.y;
     a.cur = p.cur;
-    a.beta = p.beta;
+    a.coef = p.coef;
     a.rho_out = p.rho_prop;
     a.split_out = want_split ? p.rho_split : nullptr;
     a.trace_out = p.trace_prop;
@@ -307,6 +415,9 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }

@@ -93,6 +93,7 @@ struct ProblemView {
     double *logl_cur;            // [R]
     double *logl_part;           // [ngroups][R] partial deviance sums of the proposal
     double *beta;                // [R]
+    float2 *coef;                // [R] (sqrt(1 - beta^2), beta) rounded to FP32, for the proposal
     int32_t *acc_win;            // [R] accepts in the current adaptation window
     int64_t *acc_total;          // [R]
     double *pool;                // [n_slots][d] FP64 pooled sums, one slot per accept CTA
