@@ -72,7 +72,7 @@ bool bf16_exact(double v) {
 // Per-problem host record and workspace layout
 // ------------------------------------------------------------------------------------------
 struct Layout {
-    size_t P32, Pbf, cnt, invf, ptot, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, coef,
+    size_t P32, Pbf, cnt, invf, ptot, colw, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, coef,
         acc_win,
         acc_total, pool, traj, trace_acc, trace_logl, red, acf, logl_eval, end;
 };
@@ -253,6 +253,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         L.cnt = take(sizeof(float) * hp.KDmax);
         L.invf = take(sizeof(float) * hp.KDmax);
         L.ptot = take(sizeof(float) * (hp.KDmax / v.D));
+        L.colw = take(sizeof(float2) * hp.KDmax);
         L.y = take(sizeof(float) * 2 * R * v.nx);
         L.cur = take(R);
         L.rho_cur = take(sizeof(float) * R * v.d_pad);
@@ -368,6 +369,7 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     v.cnt = reinterpret_cast<const float *>(b + L.cnt);
     v.invf = reinterpret_cast<const float *>(b + L.invf);
     v.ptot = reinterpret_cast<const float *>(b + L.ptot);
+    v.colw = reinterpret_cast<const float2 *>(b + L.colw);
     v.y = reinterpret_cast<float *>(b + L.y);
     v.cur = reinterpret_cast<uint8_t *>(b + L.cur);
     v.rho_cur = reinterpret_cast<float *>(b + L.rho_cur);
@@ -513,6 +515,10 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
                                  h->stream), "upload weights");
         QST_CUDA(cudaMemcpyAsync(h->ws + L.ptot, hp.ptot.data(), sizeof(float) * hp.ptot.size(), cudaMemcpyHostToDevice,
                                  h->stream), "upload setting totals");
+        std::vector<float2> colw(hp.KDmax);
+        for (int m = 0; m < hp.KDmax; ++m) colw[m] = make_float2(hp.cnt[m], hp.invf[m]);
+        QST_CUDA(cudaMemcpyAsync(h->ws + L.colw, colw.data(), sizeof(float2) * colw.size(), cudaMemcpyHostToDevice,
+                                 h->stream), "upload column weights");
         std::vector<double> beta(v.R, hp.beta0);
         QST_CUDA(cudaMemcpyAsync(v.beta, beta.data(), sizeof(double) * v.R, cudaMemcpyHostToDevice, h->stream),
                  "upload beta");

@@ -7,14 +7,17 @@
 //     q = hi . P + mid . P + lo . P
 // is one tcgen05 GEMM with K = 3 d_pad and FP32 accumulation in tensor memory.
 //
-// One CTA owns a tile of 128 chains (M = 128) and a group of 128-column N tiles:
-//   warp 0 (one lane)  TMA producer: the whole A tile (128 x 3 d_pad bf16, SWIZZLE_128B,
-//                      resident for the CTA's lifetime) then a 2-stage ring of
-//                      P tiles (128 projectors x 64 K);
+// Persistent CTAs (one per SM) loop over work units: a tile of 128 chains (M = 128) times a
+// group of 128-column N tiles.
+//   warp 0 (one lane)  TMA producer of P tiles (128 projectors x 64 K) through a 2-stage ring;
 //   warp 1             allocates 256 TMEM columns (two 128-column FP32 accumulators);
 //                      one lane issues tcgen05.mma (M128 N128 K16) and commits;
-//   warps 2-17         epilogue, four warps per TMEM lane quadrant (warp w may only read
-//                      lanes 32 (w mod 4) ..), each owning 32 of a tile's 128 columns:
+//   warp 2 (one lane)  TMA producer of the A tile (128 x 3 d_pad bf16, SWIZZLE_128B, resident
+//                      while a unit's N tiles run), one barrier pair per 64-wide K chunk: the
+//                      next unit's chunk is loaded as soon as the last MMAs reading it finish;
+//   warps 3-18         epilogue, four warps per TMEM lane quadrant (warp w may only read
+//                      lanes 32 (w mod 4) ..), each owning 32 of a tile's 128 columns and
+//                      writing its own partial sum per chain:
 //                      tcgen05.ld its accumulator slice (TMEM lane = chain) and form the
 //                      log-likelihood of each measurement setting k (D consecutive
 //                      columns, all in one thread):
@@ -28,6 +31,8 @@
 // Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the kernel sets the
 // status word's TIMEOUT bit, stops every role, drains its MMAs and TMA loads (bounded
 // again), frees TMEM and returns.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -43,23 +48,26 @@ constexpr int TC_ATOM_BYTES = TC_M * TC_KATOM * 2; // 16 KB: 128 rows x 128 B
 constexpr int TC_BSTAGES = 2;
 constexpr int TC_EPI_PER_QUAD = 4;                           // epilogue warps per lane quadrant
 constexpr int TC_EPI_COLS = TC_N / TC_EPI_PER_QUAD;           // columns per epilogue warp (32)
-constexpr int TC_THREADS = 64 + 4 * TC_EPI_PER_QUAD * 32;     // 576
+constexpr int TC_FIRST_EPI = 3;                               // first epilogue warp
+constexpr int TC_THREADS = (TC_FIRST_EPI + 4 * TC_EPI_PER_QUAD) * 32;   // 608
+constexpr int TC_MAX_KCHUNK = 4;                              // d_pad <= 256
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;     // 1 s
 
 struct TcArgs {
-    const float *cnt;      // [KD_tc]
-    const float *invf;     // [KD_tc]
+    const float2 *colw;    // [KD_tc] (count, invf) per column
     const float *ptot;     // [KD_tc / D] shots per setting
-    const double *trace;   // [rows] exact trace of the stored rho (for p_out)
-    double *out;           // [ngroups][rows]
+    const double *trace;   // [rows] exact trace of the stored rho
+    double *out;           // [ngroups * 4][rows] partial sums (one per epilogue column slice)
     float *p_out;          // [rows][KD] or null
     uint32_t *status;
     int64_t rows;
+    int64_t units;         // M tiles * ngroups
     int KD;
     int n_katoms;          // d_pad / 64
     int ntiles;            // KD_tc / 128
     int tiles_per_group;
+    int ngroups;
 };
 
 // ---- PTX wrappers ---------------------------------------------------------------------------
@@ -191,7 +199,8 @@ template <int D>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     project_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
     extern __shared__ uint8_t dyn_smem[];
-    __shared__ __align__(8) uint64_t bar_a_full;
+    __shared__ __align__(8) uint64_t bar_a_full[TC_MAX_KCHUNK];
+    __shared__ __align__(8) uint64_t bar_a_empty[TC_MAX_KCHUNK];
     __shared__ __align__(8) uint64_t bar_b_full[TC_BSTAGES];
     __shared__ __align__(8) uint64_t bar_b_empty[TC_BSTAGES];
     __shared__ __align__(8) uint64_t bar_acc_full[2];
@@ -202,17 +211,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
-    const int n_aatoms = 3 * a.n_katoms;
-    uint8_t *smA = base;
-    uint8_t *smB = base + (size_t)n_aatoms * TC_ATOM_BYTES;
-
-    const int64_t m0 = (int64_t)blockIdx.x * TC_M;
-    const int t_begin = blockIdx.y * a.tiles_per_group;
-    const int t_end = min(t_begin + a.tiles_per_group, a.ntiles);
-    const int nt = max(0, t_end - t_begin);
+    const int nk = a.n_katoms;
+    uint8_t *smA = base;                                          // atom (split sp, chunk kc) at sp * nk + kc
+    uint8_t *smB = base + (size_t)3 * nk * TC_ATOM_BYTES;
+    // N tiles of work unit u: [tb, te)
+    auto unit_tiles = [&](int64_t u, int &tb, int &te) {
+        const int g = (int)(u % a.ngroups);
+        tb = g * a.tiles_per_group;
+        te = min(tb + a.tiles_per_group, a.ntiles);
+    };
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&bar_a_full), 1);
+        for (int kc = 0; kc < TC_MAX_KCHUNK; ++kc) {
+            mbar_init(smem_u32(&bar_a_full[kc]), 1);
+            mbar_init(smem_u32(&bar_a_empty[kc]), 1);
+        }
         for (int s = 0; s < TC_BSTAGES; ++s) {
             mbar_init(smem_u32(&bar_b_full[s]), 1);
             mbar_init(smem_u32(&bar_b_empty[s]), 1);
@@ -235,129 +248,168 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
 
-    if (warp == 0 && lane == 0 && nt > 0) {
-        // ---------------- TMA producer ----------------
-        mbar_expect_tx(smem_u32(&bar_a_full), (uint32_t)(n_aatoms * TC_ATOM_BYTES));
-        for (int at = 0; at < n_aatoms; ++at)
-            tma_load_2d(smem_u32(smA + (size_t)at * TC_ATOM_BYTES), &tmA, at * TC_KATOM, (int)m0,
-                        smem_u32(&bar_a_full));
+    if (warp == 0 && lane == 0) {
+        // ---------------- P-tile producer ----------------
         int it = 0;
         bool ok = true;
-        for (int t = t_begin; t < t_end && ok; ++t) {
-            for (int kc = 0; kc < a.n_katoms; ++kc, ++it) {
-                const int s = it % TC_BSTAGES;
-                const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bar_b_empty[s]), ph ^ 1u, &abort_flag, a.status)) {
-                    ok = false;
-                    break;
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+            int tb, te;
+            unit_tiles(u, tb, te);
+            for (int t = tb; t < te && ok; ++t) {
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % TC_BSTAGES;
+                    const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&bar_b_empty[s]), ph ^ 1u, &abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(smem_u32(&bar_b_full[s]), (uint32_t)TC_ATOM_BYTES);
+                    tma_load_2d(smem_u32(smB + (size_t)s * TC_ATOM_BYTES), &tmB, kc * TC_KATOM, t * TC_N,
+                                smem_u32(&bar_b_full[s]));
                 }
-                mbar_expect_tx(smem_u32(&bar_b_full[s]), (uint32_t)TC_ATOM_BYTES);
-                tma_load_2d(smem_u32(smB + (size_t)s * TC_ATOM_BYTES), &tmB, kc * TC_KATOM, t * TC_N,
-                            smem_u32(&bar_b_full[s]));
             }
         }
         if (!ok) {
-            // make sure no copy is still writing shared memory when the CTA exits
-            mbar_drain(smem_u32(&bar_a_full), 0u);
+            // no copy may still be writing shared memory when the CTA exits
             for (int back = 1; back <= TC_BSTAGES && it - back >= 0; ++back) {
                 const int i2 = it - back;
                 mbar_drain(smem_u32(&bar_b_full[i2 % TC_BSTAGES]), (uint32_t)(i2 / TC_BSTAGES) & 1u);
             }
         }
-    } else if (warp == 1 && lane == 0 && nt > 0) {
-        // ---------------- MMA issuer ----------------
-        bool ok = mbar_wait(smem_u32(&bar_a_full), 0u, &abort_flag, a.status);
-        tc_fence_after();
-        int it = 0;
-        const uint32_t a_base = smem_u32(smA), b_base = smem_u32(smB);
-        for (int tl = 0; tl < nt && ok; ++tl) {
-            const int acc = tl & 1;
-            const uint32_t use = (uint32_t)(tl >> 1) & 1u;
-            if (!mbar_wait(smem_u32(&bar_acc_empty[acc]), use ^ 1u, &abort_flag, a.status)) {
-                ok = false;
-                break;
+    } else if (warp == 2 && lane == 0) {
+        // ---------------- A-tile producer ----------------
+        uint32_t uc = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+            int tb, te;
+            unit_tiles(u, tb, te);
+            if (te <= tb) continue;
+            const int m0 = (int)((u / a.ngroups) * TC_M);
+            for (int kc = 0; kc < nk; ++kc) {
+                if (!mbar_wait(smem_u32(&bar_a_empty[kc]), (uc & 1u) ^ 1u, &abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(smem_u32(&bar_a_full[kc]), (uint32_t)(3 * TC_ATOM_BYTES));
+                for (int sp = 0; sp < 3; ++sp)
+                    tma_load_2d(smem_u32(smA + (size_t)(sp * nk + kc) * TC_ATOM_BYTES), &tmA, (sp * nk + kc) * TC_KATOM,
+                                m0, smem_u32(&bar_a_full[kc]));
             }
-            tc_fence_after();
-            const uint32_t d_tmem = tmem + (uint32_t)(acc * TC_N);
-            for (int kc = 0; kc < a.n_katoms; ++kc, ++it) {
-                const int s = it % TC_BSTAGES;
-                const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
-                if (!mbar_wait(smem_u32(&bar_b_full[s]), ph, &abort_flag, a.status)) {
+            ++uc;
+        }
+        if (!ok) {
+            // the last unit's chunks that were issued
+            for (int kc = 0; kc < nk; ++kc) mbar_drain(smem_u32(&bar_a_full[kc]), uc & 1u);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        int it = 0, tcount = 0;
+        uint32_t uc = 0;
+        bool ok = true;
+        const uint32_t a_base = smem_u32(smA), b_base = smem_u32(smB);
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+            int tb, te;
+            unit_tiles(u, tb, te);
+            if (te <= tb) continue;
+            for (int t = tb; t < te && ok; ++t, ++tcount) {
+                const int acc = tcount & 1;
+                const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
+                if (!mbar_wait(smem_u32(&bar_acc_empty[acc]), use ^ 1u, &abort_flag, a.status)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-#pragma unroll
-                for (int sp = 0; sp < 3; ++sp) {
-#pragma unroll
-                    for (int kk = 0; kk < TC_KATOM / 16; ++kk) {
-                        const uint64_t ad = sw128_desc(a_base + (uint32_t)((sp * a.n_katoms + kc) * TC_ATOM_BYTES + kk * 32));
-                        const uint64_t bd = sw128_desc(b_base + (uint32_t)(s * TC_ATOM_BYTES + kk * 32));
-                        mma_bf16(d_tmem, ad, bd, (kc | sp | kk) != 0 ? 1u : 0u);
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * TC_N);
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % TC_BSTAGES;
+                    const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&bar_b_full[s]), ph, &abort_flag, a.status) ||
+                        (t == tb && !mbar_wait(smem_u32(&bar_a_full[kc]), uc & 1u, &abort_flag, a.status))) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+#pragma unroll
+                    for (int sp = 0; sp < 3; ++sp) {
+#pragma unroll
+                        for (int kk = 0; kk < TC_KATOM / 16; ++kk) {
+                            const uint64_t ad = sw128_desc(a_base + (uint32_t)((sp * nk + kc) * TC_ATOM_BYTES + kk * 32));
+                            const uint64_t bd = sw128_desc(b_base + (uint32_t)(s * TC_ATOM_BYTES + kk * 32));
+                            mma_bf16(d_tmem, ad, bd, (kc | sp | kk) != 0 ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(smem_u32(&bar_b_empty[s]));
+                    if (t == te - 1) mma_commit(smem_u32(&bar_a_empty[kc]));   // last reader of this A chunk
                 }
-                mma_commit(smem_u32(&bar_b_empty[s]));
+                if (!ok) break;
+                mma_commit(smem_u32(&bar_acc_full[acc]));
             }
-            if (!ok) break;
-            mma_commit(smem_u32(&bar_acc_full[acc]));
+            ++uc;
         }
         if (!ok) {
             // every MMA issued so far must finish before TMEM and shared memory go away
             mma_commit(smem_u32(&bar_mma_done));
             mbar_drain(smem_u32(&bar_mma_done), 0u);
         }
-    } else if (warp >= 2) {
+    } else if (warp >= TC_FIRST_EPI) {
         // ---------------- epilogue ----------------
-        const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
-        const int col0 = ((warp - 2) / 4) * TC_EPI_COLS;
-        const int row = quad * 32 + lane;
-        const int64_t grow = m0 + row;
-        const bool valid = grow < a.rows;
-        const double t = valid ? a.trace[grow] : 1.0;
-        const float inv_t = (float)(1.0 / t);
-        const float t_hi = (float)t;
-        const float t_lo = (float)(t - (double)t_hi);
-        double total = 0.0;
-        for (int tl = 0; tl < nt; ++tl) {
-            const int acc = tl & 1;
-            const uint32_t use = (uint32_t)(tl >> 1) & 1u;
-            if (!mbar_wait(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) break;
-            tc_fence_after();
-            const int n0 = (t_begin + tl) * TC_N + col0;
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N + col0), v);
-            tc_fence_before();
-            mbar_arrive(smem_u32(&bar_acc_empty[acc]));   // the slice is in registers
-            float tile_sum = 0.0f;
-#pragma unroll
-            for (int sk = 0; sk < TC_EPI_COLS / D; ++sk) {
-                const int nb = n0 + sk * D;               // first column of setting nb / D
-                const float pk = __ldg(a.ptot + nb / D);
-                if (pk > 0.0f) {
-                    float dev = 0.0f;
-#pragma unroll
-                    for (int l = 0; l < D; ++l) {
-                        const float cv = __ldg(a.cnt + nb + l);
-                        if (cv > 0.0f) dev += cv * logf(v[sk * D + l] * __ldg(a.invf + nb + l));
-                    }
-                    float s_hi, s_lo;
-                    compensated_sum<D>(v + sk * D, s_hi, s_lo);
-                    // log(S_k / t) with S_k - t formed from the compensated pair
-                    const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
-                    tile_sum += dev - pk * log1pf(rel);
+        const int quad = warp & 3;                        // TMEM lane quadrant this warp may access
+        const int sub = (warp - TC_FIRST_EPI) / 4;        // column slice of every tile
+        const int col0 = sub * TC_EPI_COLS;
+        int tcount = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+            int tb, te;
+            unit_tiles(u, tb, te);
+            const int g = (int)(u % a.ngroups);
+            const int64_t grow = (u / a.ngroups) * TC_M + quad * 32 + lane;
+            const bool valid = grow < a.rows;
+            const double t = valid ? a.trace[grow] : 1.0;
+            const float inv_t = (float)(1.0 / t);
+            const float t_hi = (float)t;
+            const float t_lo = (float)(t - (double)t_hi);
+            double total = 0.0;
+            for (int tt = tb; tt < te; ++tt, ++tcount) {
+                const int acc = tcount & 1;
+                const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
+                if (!mbar_wait(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
+                    ok = false;
+                    break;
                 }
-            }
-            if (a.p_out && valid) {
+                tc_fence_after();
+                const int n0 = tt * TC_N + col0;
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N + col0), v);
+                tc_fence_before();
+                mbar_arrive(smem_u32(&bar_acc_empty[acc]));   // the slice is in registers
+                float tile_sum = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
+                for (int sk = 0; sk < TC_EPI_COLS / D; ++sk) {
+                    const int nb = n0 + sk * D;               // first column of setting nb / D
+                    const float pk = __ldg(a.ptot + nb / D);
+                    if (pk > 0.0f) {
+                        float dev = 0.0f;
+#pragma unroll
+                        for (int l = 0; l < D; ++l) {
+                            const float2 w = __ldg(a.colw + nb + l);   // (count, invf)
+                            if (w.x > 0.0f) dev += w.x * logf(v[sk * D + l] * w.y);
+                        }
+                        float s_hi, s_lo;
+                        compensated_sum<D>(v + sk * D, s_hi, s_lo);
+                        // log(S_k / t) with S_k - t formed from the compensated pair
+                        const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
+                        tile_sum += dev - pk * log1pf(rel);
+                    }
+                }
+                if (a.p_out && valid) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
+                }
+                total += (double)tile_sum;
             }
-            total += (double)tile_sum;
+            if (ok && valid) a.out[(int64_t)(g * 4 + sub) * a.rows + grow] = total;
         }
-        // The four warps of a lane quadrant add their column partials through shared memory.
-        // The P-tile ring is free now: this warp saw the last accumulator, so every MMA has
-        // completed and every TMA load has been consumed.
-        reinterpret_cast<double *>(smB)[(warp - 2) * 32 + lane] = total;
     }
 
     tc_fence_before();
@@ -366,13 +418,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-    } else if (warp >= 2 && warp < 6) {
-        const int quad = warp & 3;
-        const int64_t grow = m0 + quad * 32 + lane;
-        double total = 0.0;
-#pragma unroll
-        for (int e = 0; e < TC_EPI_PER_QUAD; ++e) total += reinterpret_cast<const double *>(smB)[(warp - 2 + 4 * e) * 32 + lane];
-        if (grow < a.rows) a.out[(int64_t)blockIdx.y * a.rows + grow] = total;
     }
 }
 
@@ -431,18 +476,21 @@ cudaError_t launch_tc_d(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t s
 int tc_column_tile(int KD) { return KD > 0 ? TC_N : 0; }
 // (a setting's D outcome columns never straddle a 128-column tile: D divides 128)
 
+// Partial sums per chain: four column slices times the column groups that split the N tiles
+// when there are too few chain tiles to occupy every SM.
 int tc_ngroups(const ProblemView &p, int64_t rows) {
     const int64_t mt = (rows + TC_M - 1) / TC_M;
     const int ntiles = p.KD_tc / TC_N;
     int g = 1;
     while (g < ntiles && mt * g < 152) g *= 2;
-    return g > ntiles ? ntiles : g;
+    return 4 * (g > ntiles ? ntiles : g);
 }
 
 cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, int64_t rows, TcPlan **plan) {
     *plan = nullptr;
     if (p.d_pad % TC_KATOM != 0 || p.KD_tc % TC_N != 0 || p.KD_tc <= 0) return cudaErrorNotSupported;
     const int n_katoms = p.d_pad / TC_KATOM;
+    if (n_katoms > TC_MAX_KCHUNK) return cudaErrorNotSupported;
     if (tc_smem_bytes(n_katoms) > 227 * 1024 - 256) return cudaErrorNotSupported;
     if (reinterpret_cast<uintptr_t>(A_split) % 16 != 0 || reinterpret_cast<uintptr_t>(p.Pbf) % 16 != 0)
         return cudaErrorMisalignedAddress;
@@ -466,8 +514,7 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     if (!plan) return cudaErrorInvalidValue;
     if (rows <= 0) return cudaSuccess;
     TcArgs a;
-    a.cnt = p.cnt;
-    a.invf = p.invf;
+    a.colw = p.colw;
     a.ptot = p.ptot;
     a.trace = p.trace_prop;
     a.out = out_part;
@@ -477,10 +524,19 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     a.KD = p.KD;
     a.n_katoms = plan->n_katoms;
     a.ntiles = plan->ntiles;
-    const int groups = p.ngroups;
+    const int groups = p.ngroups / 4;   // the epilogue writes four column-slice partials per group
+    a.ngroups = groups;
     a.tiles_per_group = (plan->ntiles + groups - 1) / groups;
+    a.units = ((rows + TC_M - 1) / TC_M) * groups;
     const size_t smem = tc_smem_bytes(plan->n_katoms);
-    dim3 grid((unsigned)((rows + TC_M - 1) / TC_M), (unsigned)groups);
+    static int num_sms = 0;
+    if (num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms <= 0)
+            num_sms = 148;
+    }
+    dim3 grid((unsigned)std::min<int64_t>(a.units, num_sms));
     switch (p.D) {
         case 2: return launch_tc_d<2>(plan, a, grid, smem, s);
         case 4: return launch_tc_d<4>(plan, a, grid, smem, s);

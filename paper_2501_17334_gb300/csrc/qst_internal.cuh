@@ -82,6 +82,7 @@ struct ProblemView {
     const float *cnt;            // [max(KD_pad, KD_tc)] counts as float, 0 on padding
     const float *invf;           // [max(KD_pad, KD_tc)] P_k / c_kl (1 where c_kl = 0)
     const float *ptot;           // [max(KD_pad, KD_tc) / D] shots P_k of each setting (0 on padding)
+    const float2 *colw;          // [max(KD_pad, KD_tc)] (count, invf) interleaved, for the tensor epilogue
 
     // chain state
     float *y;                    // [2][R][nx] double-buffered latent states
