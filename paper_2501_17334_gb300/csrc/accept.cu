@@ -22,7 +22,6 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
     const ProblemView &p = a.p;
     __shared__ uint8_t flag[kChainsPerCta];
     __shared__ float inv_tr[kChainsPerCta];
-    __shared__ float part[kThreads];
     const int tid = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * kChainsPerCta;
     const int nc = (int)min((int64_t)kChainsPerCta, p.R - c0);
@@ -84,41 +83,74 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
     __syncthreads();
 
     // ---- phase 2: rho write-back, pooling of the current state, trajectories ------------
-    // Threads cover the packed entries; with fewer entries than threads, several thread
-    // groups split the chains and combine through shared memory.
+    // Thread t moves float4 number (t mod V) of a chain's packed rho (V = d/4 per chain) for
+    // the chains t/V, t/V + P, ... (P = 256/V chains in flight per pass, four passes
+    // unrolled so that several independent loads are outstanding).  Pool sums: per-thread
+    // float4 partials, then a shared-memory reduction over the P chain lanes.
     const int d = p.d;
-    const int width = d < kThreads ? d : kThreads;
-    const int ngrp = kThreads / width;
-    const int e_local = tid % width, grp = tid / width;
+    const int V = d / 4;
+    const int P = kThreads / V < 1 ? 1 : kThreads / V;
     const bool pool_now = (a.mode == MODE_STEP) && a.kept;
-    for (int e0 = 0; e0 < d; e0 += width) {
-        const int e = e0 + e_local;
-        float sum = 0.0f;
-        if (grp < ngrp) {
-            for (int k = grp; k < nc; k += ngrp) {
+    const int vi = tid % V, lane_c = tid / V;
+    __shared__ float4 red4[kThreads];
+    for (int v0 = 0; v0 < V; v0 += kThreads) {          // d > 1024 only: several vector columns per thread
+        const int vv = v0 + (V < kThreads ? vi : tid);
+        const bool vthread = (V < kThreads) ? (lane_c < P) : (vv < V);
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (vthread) {
+#pragma unroll 4
+            for (int k = (V < kThreads ? lane_c : 0); k < nc; k += (V < kThreads ? P : 1)) {
                 const int64_t c = c0 + k;
-                float v;
+                float4 val;
                 if (flag[k]) {
-                    v = p.rho_prop[c * p.d_pad + e] * inv_tr[k];
-                    p.rho_cur[c * p.d_pad + e] = v;
+                    const float4 q = reinterpret_cast<const float4 *>(p.rho_prop + c * p.d_pad)[vv];
+                    const float s_ = inv_tr[k];
+                    val = make_float4(q.x * s_, q.y * s_, q.z * s_, q.w * s_);
+                    reinterpret_cast<float4 *>(p.rho_cur + c * p.d_pad)[vv] = val;
+                } else if (pool_now) {
+                    val = reinterpret_cast<const float4 *>(p.rho_cur + c * p.d_pad)[vv];
                 } else {
-                    v = pool_now ? p.rho_cur[c * p.d_pad + e] : 0.0f;
+                    continue;
                 }
-                sum += v;
-                if (pool_now && c < p.n_diag && a.kept_idx < p.traj_cap)
-                    p.traj[((int64_t)c * p.traj_cap + a.kept_idx) * d + e] = v;
+                if (pool_now) {
+                    sum.x += val.x;
+                    sum.y += val.y;
+                    sum.z += val.z;
+                    sum.w += val.w;
+                    if (c < p.n_diag && a.kept_idx < p.traj_cap)
+                        reinterpret_cast<float4 *>(p.traj + ((int64_t)c * p.traj_cap + a.kept_idx) * d)[vv] = val;
+                }
             }
         }
         if (pool_now) {
-            part[tid] = sum;
+            red4[tid] = sum;
             __syncthreads();
-            if (grp == 0) {
-                float tot = 0.0f;
-                for (int q = 0; q < ngrp; ++q) tot += part[q * width + e_local];
-                p.pool[(int64_t)blockIdx.x * d + e] += (double)tot;
+            if (V < kThreads) {
+                if (tid < V) {
+                    float4 tot = red4[tid];
+                    for (int q = 1; q < P; ++q) {
+                        const float4 o = red4[q * V + tid];
+                        tot.x += o.x;
+                        tot.y += o.y;
+                        tot.z += o.z;
+                        tot.w += o.w;
+                    }
+                    double *slot = p.pool + (int64_t)blockIdx.x * d + 4 * tid;
+                    slot[0] += (double)tot.x;
+                    slot[1] += (double)tot.y;
+                    slot[2] += (double)tot.z;
+                    slot[3] += (double)tot.w;
+                }
+            } else if (vthread) {
+                double *slot = p.pool + (int64_t)blockIdx.x * d + 4 * vv;
+                slot[0] += (double)sum.x;
+                slot[1] += (double)sum.y;
+                slot[2] += (double)sum.z;
+                slot[3] += (double)sum.w;
             }
             __syncthreads();
         }
+        if (V < kThreads) break;
     }
 }
 
