@@ -6,6 +6,7 @@ Algorithm 1 assembly, projector contraction, log-likelihood, accept/adapt, pooli
 and trajectory store (65536 chain-steps).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --profile-case [--chains C] [--steps K]     # short run for ncu captures
 
 Under torchrun (N > 1) every rank runs its own 65536 chains with a disjoint global
 chain-id range (weak scaling; chains never communicate), timed between barriers and
@@ -14,6 +15,7 @@ reported as the max over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -31,6 +33,53 @@ METRIC = "4-qubit pCN chain-steps/s, mixed vs plain FP32 form, at logL err ≤1e
 UNIT = "chain-steps/s"
 CONFIG_INDEX = 4
 CHAINS = 65536
+WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 projectors, 1000 shots/basis), "
+            "Haar pure truth depolarised 0.02, beta0 0.02")
+
+# DRAM bytes per launch of each kernel from one ncu capture (bench.py --profile-case,
+# config 4 problem at `chains` chains, the second launch of the kernel), scaled to a launch
+# over the benchmark's chains in proportion to the chains processed.  The capture is only
+# used while the kernel's source file still has the recorded SHA-256.
+NCU_TRAFFIC = {
+    "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu", "sha256": None, "chains": 32768, "bytes": None},
+    "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu", "sha256": None, "chains": 32768,
+                "bytes": None},
+}
+
+
+def _sha256(path):
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def ncu_traffic(kernel, chains):
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec or rec["bytes"] is None or rec["sha256"] != _sha256(rec["source"]):
+        return None
+    return rec["bytes"] * chains / rec["chains"]
+
+
+# ---- algorithmic work per chain-step ("Kernels and rooflines") ------------------
+
+def propose_flops(D):
+    """FP32 FLOPs of Algorithm 1 + pCN as implemented (FMA = 2): two MGS passes, W = (U+I)G,
+    the Hermitian half of W W^dag and its scaling, the pCN update."""
+    mgs_pass = 6 * D * D + 8 * D * D * (D - 1)
+    w = 8 * D ** 3 + 2 * D * D
+    rho = 4 * D * D + 4 * D * D * (D - 1) + D * D
+    pcn = 2 * 4 * D * D
+    return 2 * mgs_pass + w + rho + pcn
+
+
+def project_flops(D, KD, split=3):
+    """bf16 tensor FLOPs of the contraction q = vec_h(rho) . P with rho split into `split` terms."""
+    return split * 2 * D * D * KD
+
+
+def propose_bytes(D, tc):
+    """HBM bytes per chain-step: read y, write y', write the packed rho (+ its bf16 split), trace."""
+    n = 4 * D * D
+    return 4 * n + 4 * n + 4 * D * D + (6 * D * D if tc else 0) + 8
 
 
 def _peaks():
@@ -57,7 +106,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -83,9 +132,16 @@ class Clocks:
 
     def summary(self):
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(s[1]) for s in self.samples) if v is not None]
+        mx = [v for v in (num(s[2]) for s in self.samples) if v is not None]
+        pw = [v for v in (num(s[3]) for s in self.samples) if v is not None]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for s in self.samples:
@@ -93,7 +149,7 @@ class Clocks:
                 if v.strip().lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.samples)}
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
 def _dist():
@@ -119,18 +175,13 @@ def _max_over_ranks(v, world):
     return float(t.item())
 
 
-def _l2_flush_buffer():
-    import torch
-    return torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-
-def time_form(qst, prob, precision, steps, warmup, world, chain_offset, profile=True):
-    """Device-timed steps of one form (inputs resident in HBM)."""
+def time_form(qst, prob, precision, steps, warmup, world, chain_offset):
+    """Device-timed steps of one form; inputs (chain state, projectors, counts) resident in HBM."""
     import torch
     s = qst.Sampler(prob, precision=precision, chain_offsets=[chain_offset])
     s.run_chains(warmup)
     torch.cuda.synchronize()
-    s.set_profiling(profile)
+    s.set_profiling(True)
     for k in range(4):
         s.kernel_time(k, reset=True)
     launches0 = s.launch_count()
@@ -150,7 +201,7 @@ def time_form(qst, prob, precision, steps, warmup, world, chain_offset, profile=
 
 
 def logl_error(qst, oracle, s, prob, nsample=1024):
-    """max |log L_gpu - log L_oracle| on the current states of nsample chains."""
+    """|log L_gpu - log L_oracle| on the current states of nsample chains (identical y)."""
     import torch
     st = s.get_state()
     idx = np.linspace(0, prob.num_chains - 1, nsample).astype(np.int64)
@@ -159,7 +210,8 @@ def logl_error(qst, oracle, s, prob, nsample=1024):
     torch.cuda.synchronize()
     _, _, ll_ref = oracle.evaluate(prob, y.astype(np.float64), want_rho=False, want_p=False)
     d = np.abs(ll.cpu().numpy() - ll_ref)
-    return float(np.max(d)), float(np.median(d))
+    return {"max_abs": float(np.max(d)), "median_abs": float(np.median(d)),
+            "frac_le_1e-3": float(np.mean(d <= 1e-3)), "sample": f"{nsample} chains' current states"}
 
 
 def cpu_baseline(oracle, prob, seconds_target=15.0):
@@ -169,18 +221,16 @@ def cpu_baseline(oracle, prob, seconds_target=15.0):
     t0 = time.perf_counter()
     oracle.run(prob, num_chains=chains, num_steps=0)
     init = time.perf_counter() - t0
-    steps = 1
     t1 = time.perf_counter()
-    oracle.run(prob, num_chains=chains, num_steps=steps)
-    one = time.perf_counter() - t1 - init
-    per_step = max(one, 1e-6)
+    oracle.run(prob, num_chains=chains, num_steps=1)
+    per_step = max(time.perf_counter() - t1 - init, 1e-6)
     steps = int(max(1, min(50, (seconds_target - init) / per_step)))
     t2 = time.perf_counter()
     oracle.run(prob, num_chains=chains, num_steps=steps)
     total = time.perf_counter() - t2 - init
     return {"value": chains * steps / total, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"config 4 problem, {chains} chains x {steps} steps (FP64 C oracle, OpenMP over chains); "
-                      f"init of y0 subtracted"}
+                      f"the y0 initialisation time is subtracted"}
 
 
 def run_reference(args):
@@ -206,21 +256,36 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "config 4: 4-qubit Pauli QST, 1296 projectors, 81000 shots, Haar pure truth "
-                                   "depolarised 0.02, beta0 0.02; each step a bounded sample of "
-                                   f"{chains} chains (65536 in the GPU arm)", "chains": chains},
+            "config": {"workload": WORKLOAD + f"; each step a bounded sample of {chains} chains "
+                                              f"(65536 in the GPU arm)", "chains": chains},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                              "sample": f"{chains} chains x {args.steps} steps of config 4 per timed run"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """A short run of the headline form for ncu captures (no timing)."""
+    import torch
+    from paper_2501_17334_gb300 import qst, workload as W
+    qst.load()
+    prec = qst.PREC_FP32 if args.form == "fp32" else qst.PREC_BF16X3
+    s = qst.Sampler(W.config_problem(CONFIG_INDEX, num_chains=args.chains), precision=prec, diag_chains=0)
+    s.run_chains(args.steps)
+    s.synchronize()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": True, "chains": args.chains, "steps": args.steps, "form": args.form}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chains", type=int, default=CHAINS)
+    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
@@ -228,6 +293,9 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_case:
+        run_profile_case(args)
         return
 
     import torch
@@ -238,23 +306,20 @@ def main():
         dist.init_process_group("nccl")
     from paper_2501_17334_gb300 import qst, workload as W
     qst.load()
-    prob = W.config_problem(CONFIG_INDEX)
-    offset = rank * CHAINS
+    chains = args.chains
+    prob = W.config_problem(CONFIG_INDEX, num_chains=chains)
+    offset = rank * chains
     peaks, peak_src = _peaks()
+    D, KD = prob.dim, prob.num_povms * prob.dim
 
-    # the mixed form if this build has it, else the plain form is the headline
-    forms = []
-    try:
-        qst.Sampler(W.config_problem(CONFIG_INDEX, num_chains=128, num_steps=1), precision=qst.PREC_BF16X3).close()
-        forms.append(("bf16x3", qst.PREC_BF16X3))
-    except qst.QstError:
-        pass
-    if not args.no_plain or not forms:
+    forms = [("bf16x3", qst.PREC_BF16X3)]
+    if not args.no_plain:
         forms.append(("fp32", qst.PREC_FP32))
 
     clocks = Clocks(local)
     results = {}
     clocks.start()
+    time.sleep(0.3)
     for name, prec in forms:
         s, ms, launches, kms = time_form(qst, prob, prec, args.steps, args.warmup, world, offset)
         ms = _max_over_ranks(ms, world)
@@ -262,83 +327,82 @@ def main():
     clocks.stop()
     head_name = forms[0][0]
     head = results[head_name]
-    total_chain_steps = CHAINS * args.steps * world
+    total_chain_steps = chains * args.steps * world
     value = total_chain_steps / (head["ms"] / 1000.0)
 
-    # dominant kernel of the headline form and its roofline
+    # rooflines: the dominant kernel of the headline form, and the tensor-core projection
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     kms = head["kernels"]
-    dom = max(kms, key=lambda k: kms[k][0])
-    dom_ms, dom_n = kms[dom]
-    avg_s = dom_ms / 1000.0 / max(dom_n, 1)
-    D = 16
-    if dom == "project" and head_name == "bf16x3":
-        flops = 3 * 2.0 * D * D * 1296 * CHAINS
-        achieved = flops / avg_s / 1e12
+
+    def kernel_avg_s(name):
+        ms_, n_ = kms[name]
+        return ms_ / 1000.0 / max(n_, 1)
+
+    def roof_propose():
+        t = kernel_avg_s("propose")
+        ach = propose_flops(D) * chains / t / 1e12
+        traffic = ncu_traffic("propose", chains)
+        return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": traffic, "kernel": "propose",
+                "algorithmic_bytes": propose_bytes(D, True) * chains,
+                "hbm_achieved_gbs": propose_bytes(D, True) * chains / t / 1e9,
+                "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock (recipe's unit counts)"}
+
+    def roof_project():
+        t = kernel_avg_s("project")
+        ach = project_flops(D, KD) * chains / t / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": f"{peak_src} bf16 sustained"}
-    elif dom == "project":
-        flops = 2.0 * D * D * 1296 * CHAINS
-        achieved = flops / avg_s / 1e12
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"}
-    else:
-        # propose: FP32 FFMA work of Algorithm 1 per chain-step
-        flops_chain = 8 * D * D * (D - 1) / 2 * 2 + 8 * D ** 3 + 8 * D * D * (D + 2) / 2
-        achieved = flops_chain * CHAINS / avg_s / 1e12
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"}
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": ncu_traffic("project", chains), "kernel": "project (tcgen05 BF16x3)",
+                "peak_source": f"{peak_src} bf16 sustained (cuBLAS); FLOPs = 3 splits x 2 x D^2 x KD per chain"}
 
-    # logL error of the headline form on identical states (sampled chains)
+    dom = max(kms, key=lambda k: kms[k][0])
+    roof = roof_propose() if dom == "propose" else roof_project()
+
     import oracle
-    err_max, err_med = logl_error(qst, oracle, head["sampler"], prob)
+    err = logl_error(qst, oracle, head["sampler"], prob)
+    err["form"] = head_name
+    err_plain = None
+    if "fp32" in results:
+        err_plain = logl_error(qst, oracle, results["fp32"]["sampler"], prob)
 
-    # end to end through the C ABI with host buffers: create (H2D of counts and projectors),
-    # run, read the posterior mean back (D2H)
-    e2e = None
-    if rank == 0 or world > 1:
-        e2e_steps = args.steps
-        for r in results.values():
-            r["sampler"].close()
-        torch.cuda.synchronize()
-        _barrier(world)
-        t0 = time.perf_counter()
-        s = qst.Sampler(prob, precision=forms[0][1], chain_offsets=[offset])
-        s.run_chains(e2e_steps)
-        mean, npool = s.posterior_mean()
-        t1 = time.perf_counter()
-        s.close()
-        e2e_s = _max_over_ranks(t1 - t0, world)
-        h2d = prob.counts.nbytes + prob.povm_re.nbytes + prob.povm_im.nbytes
-        e2e = {"value": CHAINS * e2e_steps * world / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": 2 * 8 * D * D / e2e_steps,
-               "includes": "qst_create (validation, packing, upload, y0 init) + run + posterior mean read-back"}
+    # end to end through the C ABI with host buffers: qst_create from host counts and
+    # projectors (H2D), run, read the posterior mean back (D2H)
+    for r in results.values():
+        r["sampler"].close()
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    s = qst.Sampler(prob, precision=forms[0][1], chain_offsets=[offset])
+    s.run_chains(args.steps)
+    mean, npool = s.posterior_mean()
+    t1 = time.perf_counter()
+    s.close()
+    e2e_s = _max_over_ranks(t1 - t0, world)
+    h2d = prob.counts.nbytes + prob.povm_re.nbytes + prob.povm_im.nbytes
+    e2e = {"value": chains * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 2 * 8 * D * D / args.steps,
+           "includes": "qst_create (validation, packing, upload, y0 init) + run + posterior-mean read-back"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+bf16x3" if head_name == "bf16x3" else "f32",
-        "data": "synthetic",
-        "config": {"workload": "config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 projectors, "
-                               "1000 shots/basis), Haar pure truth depolarised 0.02, 65536 chains/GPU, beta0 0.02",
-                   "chains_per_gpu": CHAINS, "form": head_name,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "chains_per_gpu": chains, "form": head_name,
                    "l2": "chain state 0.6 GB/GPU > 129 MB L2: every step streams it from HBM"},
-        "logl_err": {"max_abs": err_max, "median_abs": err_med, "sample": "1024 chains' current states",
-                     "form": head_name},
+        "logl_err": err,
         "forms": {n: {"value": total_chain_steps / (r["ms"] / 1000.0), "ms_per_step": r["ms"] / args.steps,
                       "kernel_ms_per_step": {k: v[0] / args.steps for k, v in r["kernels"].items()}}
                   for n, r in results.items()},
         "roofline": roof,
+        "roofline_tensor": roof_project(),
         "clocks": clocks.summary(),
         "gpu_launches": head["launches"],
         "e2e": e2e,
     }
-    if "fp32" in results and head_name != "fp32":
+    if err_plain is not None:
+        line["forms"]["fp32"]["logl_err"] = err_plain
         line["speedup_vs_plain_fp32"] = results["fp32"]["ms"] / head["ms"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(oracle, prob)
