@@ -41,9 +41,14 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 # over the benchmark's chains in proportion to the chains processed.  The capture is only
 # used while the kernel's source file still has the recorded SHA-256.
 NCU_TRAFFIC = {
-    "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu", "sha256": None, "chains": 32768, "bytes": None},
-    "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu", "sha256": None, "chains": 32768,
-                "bytes": None},
+    # profiles/propose_kernel_config4.md
+    "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
+                "sha256": "7140d3f20c5f91504e802eca9f1611e6a5b5193245c52b0e78b113f022960706",
+                "chains": 32768, "bytes": 134.738176e6 + 157.768960e6},
+    # profiles/project_tc_kernel_config4.md
+    "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
+                "sha256": "45d2971f0db79e074720de7d00d18706049219d253c294c34a4552d5b425ebf6",
+                "chains": 32768, "bytes": 51.382272e6 + 0.022272e6},
 }
 
 
