@@ -76,9 +76,14 @@ def propose_flops(D):
     return 2 * mgs_pass + w + rho + pcn
 
 
-def project_flops(D, KD, split=3):
-    """bf16 tensor FLOPs of the contraction q = vec_h(rho) . P with rho split into `split` terms."""
-    return split * 2 * D * D * KD
+def project_flops(D, KD):
+    """Algorithmic FLOPs of the contraction q = vec_h(rho) . P per chain (2 d KD)."""
+    return 2 * D * D * KD
+
+
+def project_issued_flops(D, KD_tc, split=3):
+    """bf16 tensor FLOPs issued per chain: rho split into `split` terms, KD padded to KD_tc."""
+    return split * 2 * D * D * KD_tc
 
 
 def propose_bytes(D, tc):
@@ -312,8 +317,9 @@ def main():
     from paper_2501_17334_gb300 import qst, workload as W
     qst.load()
     chains = args.chains
+    from paper_2501_17334_gb300 import shard
     prob = W.config_problem(CONFIG_INDEX, num_chains=chains)
-    offset = rank * chains
+    offset, _ = shard.chain_range(rank, world, world * chains)   # weak scaling: `chains` per rank
     peaks, peak_src = _peaks()
     D, KD = prob.dim, prob.num_povms * prob.dim
 
@@ -357,10 +363,13 @@ def main():
     def roof_project():
         t = kernel_avg_s("project")
         ach = project_flops(D, KD) * chains / t / 1e12
+        issued = project_issued_flops(D, -(-KD // 128) * 128) * chains / t / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": ncu_traffic("project", chains), "kernel": "project (tcgen05 BF16x3)",
-                "peak_source": f"{peak_src} bf16 sustained (cuBLAS); FLOPs = 3 splits x 2 x D^2 x KD per chain"}
+                "issued_tflops": issued, "issued_frac": issued / peak,
+                "peak_source": f"{peak_src} bf16 sustained (cuBLAS); achieved = 2 d KD per chain-step "
+                               f"(algorithmic); issued = 3 bf16 splits x 2 d KD_tc"}
 
     dom = max(kms, key=lambda k: kms[k][0])
     roof = roof_propose() if dom == "propose" else roof_project()
@@ -382,13 +391,16 @@ def main():
     s = qst.Sampler(prob, precision=forms[0][1], chain_offsets=[offset])
     s.run_chains(args.steps)
     mean, npool = s.posterior_mean()
+    if world > 1:   # the one exchange of the path: merge the pooled FP64 sums of all ranks
+        mean, npool = shard.merge_posterior_mean(mean, npool)
     t1 = time.perf_counter()
     s.close()
     e2e_s = _max_over_ranks(t1 - t0, world)
     h2d = prob.counts.nbytes + prob.povm_re.nbytes + prob.povm_im.nbytes
     e2e = {"value": chains * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 2 * 8 * D * D / args.steps,
-           "includes": "qst_create (validation, packing, upload, y0 init) + run + posterior-mean read-back"}
+           "includes": "qst_create (validation, packing, upload, y0 init) + run + posterior-mean read-back"
+                       + (" + merge over ranks" if world > 1 else "")}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
