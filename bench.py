@@ -67,13 +67,15 @@ def ncu_traffic(kernel, chains):
 # ---- algorithmic work per chain-step ("Kernels and rooflines") ------------------
 
 def propose_flops(D):
-    """FP32 FLOPs of Algorithm 1 + pCN as implemented (FMA = 2): two MGS passes, W = (U+I)G,
-    the Hermitian half of W W^dag and its scaling, the pCN update."""
-    mgs_pass = 6 * D * D + 8 * D * D * (D - 1)
+    """FP32 FLOPs of Algorithm 1 + pCN as implemented (FMA = 2, no redundant work counted):
+    one MGS pass, the first-order re-orthogonalisation (Gram upper half, Q1 (I - F)),
+    W = (U+I)G, the Hermitian half of W W^dag and its scaling, the pCN update."""
+    mgs_pass = 8 * D * D * (D - 1) + 6 * D * D
+    reorth = 2 * 4 * D * D * (D + 1)
     w = 8 * D ** 3 + 2 * D * D
     rho = 4 * D * D + 4 * D * D * (D - 1) + D * D
     pcn = 2 * 4 * D * D
-    return 2 * mgs_pass + w + rho + pcn
+    return mgs_pass + reorth + w + rho + pcn
 
 
 def project_flops(D, KD):

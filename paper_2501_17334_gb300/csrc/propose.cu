@@ -5,13 +5,19 @@
 // floats of each of the four parts).  Per chain:
 //   1. eta from Philox (tag 1, step j) and y' = sqrt(1 - beta^2) y + beta eta, one
 //      Philox block (four entries) at a time; y' goes to the chain's other y buffer (the
-//      accept kernel flips to it) and to shared memory (G's column, H's column);
-//   2. modified Gram-Schmidt on the columns of H: lane k normalises column k and
-//      publishes it, lanes j > k project it out.  MGS yields the unitary factor whose
-//      R has a positive real diagonal, i.e. U = Q Lambda of Algorithm 1 l.5.  A second
-//      pass over the result (PASSES = 2) re-orthogonalises it: Q1 = Q2 R2 with R2 upper
-//      triangular with positive diagonal, so Q2 is still the same factor of H, and its
-//      FP32 error drops from O(cond(H) 2^-24) loss of orthogonality to O(2^-24);
+//      accept kernel flips to it); lane j keeps H's column j in registers.  G's column is
+//      read back from those same (own) global writes in step 3.
+//   2. QR of H (Algorithm 1 l.4-5).  Modified Gram-Schmidt: at step k lane k publishes its
+//      (unnormalised) column v_k, and every lane j > k loads it, forms |v_k|^2 and v_k^dag h_j
+//      itself and removes the projection -- no lane works alone on a normalisation.  The
+//      columns are normalised at the end.  MGS yields the unitary factor whose R has a
+//      positive real diagonal, i.e. U = Q Lambda of Algorithm 1 l.5.  Its FP32 columns are
+//      orthogonal only to O(cond(H) 2^-24); with PASSES = 2 they are re-orthogonalised once:
+//      Q1 = Q2 R2 with R2 = chol(Q1^dag Q1) = I + F + O(E^2), E = Q1^dag Q1 - I,
+//      F = strict upper part of E plus half its (real) diagonal, so Q2 = Q1 (I - F) is the
+//      same QR factor of H to O(E^2) (E < 1e-4 after one pass for cond(H) < 1e4, so E^2
+//      is below FP32 rounding).  Unlike a second Gram-Schmidt sweep this is two balanced
+//      products: lane a forms entries (a, a + t) of E, then row a of Q1 (I - F).
 //   3. W = (U + I) G, lane j computing column j;
 //   4. rho = W W^dag / Tr: lane a computes entries (a, a+t mod D) for t = 0..D/2
 //      (the Hermitian half, balanced over lanes), packed as vec_h and scaled by the FP32
@@ -31,21 +37,25 @@ namespace {
 constexpr int kThreads = 128;
 
 // Shared memory per chain (floats), laid out so every access is free of bank conflicts:
-//   area A: H's real and imaginary planes (column-major, column stride D) -> U's planes ->
-//           W row-major (complex, rows padded to D + 2) once U is no longer needed;
-//   area B: G's real and imaginary planes (column-major, column stride D + 4 so that the
-//           128-bit stores and loads of eight consecutive lanes' columns hit different
-//           banks) -> packed rho (row stride D + 1) once G is in registers.
+//   area A: the real and imaginary planes of H's columns as they are orthogonalised (column
+//           stride D + 4, so that 128-bit accesses of eight consecutive lanes' columns hit
+//           different banks) -> W row-major (complex, rows padded to D + 2) once U is no
+//           longer needed;
+//   area B: F, dense complex column-major (only i <= j + 1 is written and read) -> packed
+//           rho (row stride D + 1).
+// The per-chain stride is an odd multiple of 16 floats, so the two chains of a warp that
+// read the same offset in their own areas use opposite halves of the banks.
 template <int D>
 struct Shape {
     static constexpr int d = D * D;
     static constexpr int chains_per_block = kThreads / D;
-    static constexpr int row_stride = D + 2;                   // float2 per row of W (padded)
-    static constexpr int gcol = D + 4;                          // floats per column of a G plane
+    static constexpr int row_stride = D + 2;                    // float2 per row of W (padded)
+    static constexpr int qcol = D + 4;                          // floats per column of a Q plane
     static constexpr int pk_stride = D + 1;                     // floats per row of the staged rho
-    static constexpr int area_a = (2 * D * D > 2 * D * row_stride) ? 2 * D * D : 2 * D * row_stride;
-    static constexpr int area_b = 2 * D * gcol;
-    static constexpr int smem_floats = area_a + area_b;
+    static constexpr int area_a = (2 * D * qcol > 2 * D * row_stride) ? 2 * D * qcol : 2 * D * row_stride;
+    static constexpr int area_b = (2 * D * D > D * pk_stride) ? 2 * D * D : D * pk_stride;
+    static constexpr int raw = area_a + area_b;
+    static constexpr int smem_floats = (raw + 31) / 32 * 32 + 16;
 };
 
 // Box-Muller with the fast hardware log and sine/cosine: the angle is reduced to
@@ -62,7 +72,7 @@ __device__ __forceinline__ void gaussian_pair_fast(uint32_t wu, uint32_t wv, flo
     z1 = -radius * s;
 }
 
-// a D-float column of a plane into / from registers, 128-bit at a time where D allows
+// a D-float column into / from registers, 128-bit at a time where D allows
 template <int D>
 __device__ __forceinline__ void load_column(const float *src, float (&v)[D]) {
     if constexpr (D >= 4) {
@@ -143,19 +153,19 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     constexpr int d = S::d;
     constexpr int nx = 4 * d;
     constexpr int RS = S::row_stride;
-    constexpr int GC = S::gcol;
+    constexpr int QC = S::qcol;
     constexpr int PK = S::pk_stride;
     extern __shared__ __align__(16) float smem[];
 
-    const int j = threadIdx.x % D;       // owned column (and, in step 4, owned row)
+    const int j = threadIdx.x % D;       // owned column (and, in steps 2b and 4, owned row)
     const int g = threadIdx.x / D;       // chain slot in the block
     const int64_t c = (int64_t)blockIdx.x * S::chains_per_block + g;
     const bool active = c < a.rows;
     float *sm = smem + g * S::smem_floats;
-    float *hre = sm, *him = sm + d;                     // H planes, then U planes (column stride D)
-    float2 *wsm = reinterpret_cast<float2 *>(sm);        // W row-major (row stride RS), replaces U
-    float *gre = sm + S::area_a, *gim = gre + D * GC;    // G planes (column stride GC)
-    float *packed = sm + S::area_a;                      // staged rho (row stride PK), replaces G
+    float *qre = sm, *qim = sm + D * QC;                 // Q planes (column stride QC)
+    float2 *wsm = reinterpret_cast<float2 *>(sm);        // W row-major (row stride RS), replaces Q
+    float2 *fsm = reinterpret_cast<float2 *>(sm + S::area_a);   // F column-major (stride D)
+    float *packed = sm + S::area_a;                      // staged rho (row stride PK), replaces F
 
     // ---- 1. latent proposal --------------------------------------------------------------
     float coef_y = 1.0f, coef_eta = 0.0f;
@@ -175,6 +185,9 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     const uint32_t key_lo = (uint32_t)(a.seed & 0xffffffffu), key_hi = (uint32_t)(a.seed >> 32);
     const float *ysrc = a.y + ((int64_t)cur * a.R + cc) * nx;
     float *ydst = a.y + ((int64_t)(1 - cur) * a.R + cc) * nx;
+    // where G's column j is read back in step 3: this lane's own y' writes, or the input row
+    const float *gsrc = (a.mode == MODE_EVAL) ? a.x_eval + cc * nx : ydst;
+    float hr[D], hi[D];   // H's column j
     if constexpr (D >= 4) {
         // lane j owns entries j D .. j D + D - 1 of each part: D/4 Philox blocks per part
 #pragma unroll 1
@@ -187,8 +200,6 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                 if (active && a.mode == MODE_STEP) y0[q] = *reinterpret_cast<const float4 *>(ysrc + e0 + 4 * q);
                 if (active && a.mode == MODE_EVAL) y0[q] = *reinterpret_cast<const float4 *>(a.x_eval + cc * nx + e0 + 4 * q);
             }
-            float *plane = (part == 0) ? gre : (part == 1) ? gim : (part == 2) ? hre : him;
-            const int col = (part < 2) ? j * GC : j * D;
 #pragma unroll
             for (int q = 0; q < D / 4; ++q) {
                 float4 yn = y0[q];
@@ -203,7 +214,11 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                     yn.w = __fmaf_rn(coef_y, y0[q].w, coef_eta * z3);
                     if (active) *reinterpret_cast<float4 *>(ydst + e0 + 4 * q) = yn;
                 }
-                *reinterpret_cast<float4 *>(plane + col + 4 * q) = yn;
+                if (part == 2) {
+                    hr[4 * q] = yn.x; hr[4 * q + 1] = yn.y; hr[4 * q + 2] = yn.z; hr[4 * q + 3] = yn.w;
+                } else if (part == 3) {
+                    hi[4 * q] = yn.x; hi[4 * q + 1] = yn.y; hi[4 * q + 2] = yn.z; hi[4 * q + 3] = yn.w;
+                }
             }
         }
     } else {
@@ -233,59 +248,125 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                     ydst[e + 1] = y1v;
                 }
             }
-            float *plane = (part == 0) ? gre : (part == 1) ? gim : (part == 2) ? hre : him;
-            const int col = (part < 2) ? j * GC : j * D;
-            plane[col] = y0v;
-            plane[col + 1] = y1v;
+            if (part == 2) {
+                hr[0] = y0v;
+                hr[1] = y1v;
+            } else if (part == 3) {
+                hi[0] = y0v;
+                hi[1] = y1v;
+            }
         }
     }
-    // this lane's column of H (staged by this lane only)
-    float hr[D], hi[D];
-    load_column<D>(hre + j * D, hr);
-    load_column<D>(him + j * D, hi);
-    __syncwarp();
 
-    // ---- 2. modified Gram-Schmidt on the columns of H -> U (Algorithm 1 l.4-5) -----------
+    // ---- 2a. modified Gram-Schmidt on the columns of H (Algorithm 1 l.4-5) ------------------
 #pragma unroll 1
-    for (int pass = 0; pass < PASSES; ++pass) {
-#pragma unroll 1
-        for (int k = 0; k < D; ++k) {
-            if (j == k) {
-                float n0 = 0.0f, n1 = 0.0f;
+    for (int k = 0; k < D; ++k) {
+        if (j == k) {   // column k is final: publish it
+            store_column<D>(qre + k * QC, hr);
+            store_column<D>(qim + k * QC, hi);
+        }
+        __syncwarp();
+        if (j > k) {
+            float vr[D], vi[D];
+            load_column<D>(qre + k * QC, vr);
+            load_column<D>(qim + k * QC, vi);
+            // |v|^2 and r = v^dag h, each with two independent accumulators
+            float n0 = 0.0f, n1 = 0.0f, rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
 #pragma unroll
-                for (int i = 0; i < D; i += 2) {
-                    n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
-                    n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
-                }
-                const float inv = 1.0f / sqrtf(n0 + n1);
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    hr[i] *= inv;
-                    hi[i] *= inv;
-                }
-                store_column<D>(hre + k * D, hr);
-                store_column<D>(him + k * D, hi);
+            for (int i = 0; i < D; i += 2) {
+                n0 = __fmaf_rn(vr[i], vr[i], __fmaf_rn(vi[i], vi[i], n0));
+                n1 = __fmaf_rn(vr[i + 1], vr[i + 1], __fmaf_rn(vi[i + 1], vi[i + 1], n1));
+                rr0 = __fmaf_rn(vr[i], hr[i], __fmaf_rn(vi[i], hi[i], rr0));
+                ri0 = __fmaf_rn(vr[i], hi[i], __fmaf_rn(-vi[i], hr[i], ri0));
+                rr1 = __fmaf_rn(vr[i + 1], hr[i + 1], __fmaf_rn(vi[i + 1], hi[i + 1], rr1));
+                ri1 = __fmaf_rn(vr[i + 1], hi[i + 1], __fmaf_rn(-vi[i + 1], hr[i + 1], ri1));
             }
-            __syncwarp();
-            if (j > k) {
-                float qr[D], qi[D];
-                load_column<D>(hre + k * D, qr);
-                load_column<D>(him + k * D, qi);
-                // r = q^dag h with two independent accumulator pairs
-                float rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
+            const float inv_n = 1.0f / (n0 + n1);
+            const float sr = (rr0 + rr1) * inv_n, si = (ri0 + ri1) * inv_n;
 #pragma unroll
-                for (int i = 0; i < D; i += 2) {
-                    rr0 = __fmaf_rn(qr[i], hr[i], __fmaf_rn(qi[i], hi[i], rr0));
-                    ri0 = __fmaf_rn(qr[i], hi[i], __fmaf_rn(-qi[i], hr[i], ri0));
-                    rr1 = __fmaf_rn(qr[i + 1], hr[i + 1], __fmaf_rn(qi[i + 1], hi[i + 1], rr1));
-                    ri1 = __fmaf_rn(qr[i + 1], hi[i + 1], __fmaf_rn(-qi[i + 1], hr[i + 1], ri1));
-                }
-                const float rr = rr0 + rr1, ri = ri0 + ri1;
+            for (int i = 0; i < D; ++i) {
+                hr[i] = __fmaf_rn(-sr, vr[i], __fmaf_rn(si, vi[i], hr[i]));
+                hi[i] = __fmaf_rn(-sr, vi[i], __fmaf_rn(-si, vr[i], hi[i]));
+            }
+        }
+    }
+    {   // normalise the own column and publish it
+        float n0 = 0.0f, n1 = 0.0f;
 #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    hr[i] = __fmaf_rn(-rr, qr[i], __fmaf_rn(ri, qi[i], hr[i]));
-                    hi[i] = __fmaf_rn(-rr, qi[i], __fmaf_rn(-ri, qr[i], hi[i]));
+        for (int i = 0; i < D; i += 2) {
+            n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
+            n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
+        }
+        const float inv = 1.0f / sqrtf(n0 + n1);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            hr[i] *= inv;
+            hi[i] *= inv;
+        }
+        __syncwarp();
+        store_column<D>(qre + j * QC, hr);
+        store_column<D>(qim + j * QC, hi);
+        __syncwarp();
+    }
+
+    if constexpr (PASSES == 2) {
+        // ---- 2b. re-orthogonalisation Q2 = Q1 (I - F) --------------------------------------
+        // E_ab = q_a^dag q_b - delta_ab: lane a forms (a, a + t mod D), t = 0..D/2, from its own
+        // column (registers) and column b (shared); F_ab = E_ab (a < b), F_aa = E_aa / 2.
+#pragma unroll 1
+        for (int t = 0; t <= D / 2; ++t) {
+            const int b = (j + t) & (D - 1);
+            if (t == D / 2 && j >= D / 2) continue;   // (a, a + D/2) is done by the lower lane
+            float br[D], bim[D];
+            load_column<D>(qre + b * QC, br);
+            load_column<D>(qim + b * QC, bim);
+            float er0 = 0.0f, ei0 = 0.0f, er1 = 0.0f, ei1 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; i += 2) {
+                er0 = __fmaf_rn(hr[i], br[i], __fmaf_rn(hi[i], bim[i], er0));
+                ei0 = __fmaf_rn(hr[i], bim[i], __fmaf_rn(-hi[i], br[i], ei0));
+                er1 = __fmaf_rn(hr[i + 1], br[i + 1], __fmaf_rn(hi[i + 1], bim[i + 1], er1));
+                ei1 = __fmaf_rn(hr[i + 1], bim[i + 1], __fmaf_rn(-hi[i + 1], br[i + 1], ei1));
+            }
+            const float er = er0 + er1, ei = ei0 + ei1;    // q_j^dag q_b
+            if (t == 0) {
+                fsm[j * D + j] = make_float2(0.5f * (er - 1.0f), 0.0f);
+                if (j + 1 < D) fsm[j * D + j + 1] = make_float2(0.0f, 0.0f);   // read as a pair, never used
+            } else if (j < b) {
+                fsm[b * D + j] = make_float2(er, ei);        // F[j][b]
+            } else {
+                fsm[j * D + b] = make_float2(er, -ei);       // F[b][j] = conj(q_j^dag q_b)
+            }
+        }
+        __syncwarp();
+        // row a of Q2: x_m - sum_{i <= m} x_i F[i][m], x = row a of Q1 (lane a = j)
+        {
+            float xr[D], xi[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                xr[i] = qre[i * QC + j];
+                xi[i] = qim[i * QC + j];
+            }
+#pragma unroll
+            for (int m = D - 1; m >= 0; --m) {   // descending: x_m is still Q1's when row m is formed
+                float accr = xr[m], acci = xi[m];
+#pragma unroll
+                for (int i = 0; i <= m; i += 2) {
+                    const float4 f = *reinterpret_cast<const float4 *>(fsm + m * D + i);   // F[i][m], F[i+1][m]
+                    accr = __fmaf_rn(-xr[i], f.x, __fmaf_rn(xi[i], f.y, accr));
+                    acci = __fmaf_rn(-xr[i], f.y, __fmaf_rn(-xi[i], f.x, acci));
+                    if (i + 1 <= m) {
+                        accr = __fmaf_rn(-xr[i + 1], f.z, __fmaf_rn(xi[i + 1], f.w, accr));
+                        acci = __fmaf_rn(-xr[i + 1], f.w, __fmaf_rn(-xi[i + 1], f.z, acci));
+                    }
                 }
+                xr[m] = accr;
+                xi[m] = acci;
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                qre[i * QC + j] = xr[i];
+                qim[i * QC + j] = xi[i];
             }
         }
         __syncwarp();
@@ -293,8 +374,16 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
 
     // ---- 3. W = (U + I) G, column j: W[:,j] = G[:,j] + sum_k U[:,k] G[k,j] ------------------
     float gr[D], gi[D], wr[D], wi[D];
-    load_column<D>(gre + j * GC, gr);
-    load_column<D>(gim + j * GC, gi);
+    if (active) {
+        load_column<D>(gsrc + j * D, gr);
+        load_column<D>(gsrc + d + j * D, gi);
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            gr[i] = 0.0f;
+            gi[i] = 0.0f;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         wr[i] = gr[i];
@@ -303,8 +392,8 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         float ur[D], ui[D];
-        load_column<D>(hre + k * D, ur);
-        load_column<D>(him + k * D, ui);
+        load_column<D>(qre + k * QC, ur);
+        load_column<D>(qim + k * QC, ui);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             wr[i] = __fmaf_rn(ur[i], gr[k], __fmaf_rn(-ui[i], gi[k], wr[i]));
@@ -312,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         }
     }
     __syncwarp();
-    // W row-major with padded rows: W[i][j] at wsm[i * RS + j] (replaces U)
+    // W row-major with padded rows: W[i][j] at wsm[i * RS + j] (replaces Q)
 #pragma unroll
     for (int i = 0; i < D; ++i) wsm[i * RS + j] = make_float2(wr[i], wi[i]);
     __syncwarp();
