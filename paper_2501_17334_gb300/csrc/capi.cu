@@ -253,7 +253,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         L.cnt = take(sizeof(float) * hp.KDmax);
         L.invf = take(sizeof(float) * hp.KDmax);
         L.ptot = take(sizeof(float) * (hp.KDmax / v.D));
-        L.colw = take(sizeof(float2) * hp.KDmax);
+        L.colw = take(sizeof(float4) * (hp.KDmax / 2));
         L.y = take(sizeof(float) * 2 * R * v.nx);
         L.cur = take(R);
         L.rho_cur = take(sizeof(float) * R * v.d_pad);
@@ -369,7 +369,7 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     v.cnt = reinterpret_cast<const float *>(b + L.cnt);
     v.invf = reinterpret_cast<const float *>(b + L.invf);
     v.ptot = reinterpret_cast<const float *>(b + L.ptot);
-    v.colw = reinterpret_cast<const float2 *>(b + L.colw);
+    v.colw = reinterpret_cast<const float4 *>(b + L.colw);
     v.y = reinterpret_cast<float *>(b + L.y);
     v.cur = reinterpret_cast<uint8_t *>(b + L.cur);
     v.rho_cur = reinterpret_cast<float *>(b + L.rho_cur);
@@ -515,9 +515,15 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
                                  h->stream), "upload weights");
         QST_CUDA(cudaMemcpyAsync(h->ws + L.ptot, hp.ptot.data(), sizeof(float) * hp.ptot.size(), cudaMemcpyHostToDevice,
                                  h->stream), "upload setting totals");
-        std::vector<float2> colw(hp.KDmax);
-        for (int m = 0; m < hp.KDmax; ++m) colw[m] = make_float2(hp.cnt[m], hp.invf[m]);
-        QST_CUDA(cudaMemcpyAsync(h->ws + L.colw, colw.data(), sizeof(float2) * colw.size(), cudaMemcpyHostToDevice,
+        // per column pair (2p, 2p+1): (invf, invf, add, add) with x = q invf + add; a column
+        // without counts gets invf = 0, add = 1, so its log is exactly 0
+        std::vector<float4> colw(hp.KDmax / 2);
+        for (int m = 0; m < hp.KDmax; m += 2) {
+            const bool c0 = hp.cnt[m] > 0.0f, c1 = hp.cnt[m + 1] > 0.0f;
+            colw[m / 2] = make_float4(c0 ? hp.invf[m] : 0.0f, c1 ? hp.invf[m + 1] : 0.0f, c0 ? 0.0f : 1.0f,
+                                      c1 ? 0.0f : 1.0f);
+        }
+        QST_CUDA(cudaMemcpyAsync(h->ws + L.colw, colw.data(), sizeof(float4) * colw.size(), cudaMemcpyHostToDevice,
                                  h->stream), "upload column weights");
         std::vector<double> beta(v.R, hp.beta0);
         QST_CUDA(cudaMemcpyAsync(v.beta, beta.data(), sizeof(double) * v.R, cudaMemcpyHostToDevice, h->stream),

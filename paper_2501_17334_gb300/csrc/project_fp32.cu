@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
                 const int col = (jj < 4) ? tx * 4 + jj : 64 + tx * 4 + (jj - 4);
                 const float pv = acc[i][jj];
                 const float cv = cnt_s[col];
-                if (cv > 0.0f) rowsum[i] += cv * logf(pv * invf_s[col]);
+                if (cv > 0.0f) rowsum[i] += cv * deviance_log(pv * invf_s[col]);
                 if (a.p_out && row < a.rows && n0 + col < a.KD) a.p_out[row * a.KD + n0 + col] = pv * inv_tr;
             }
         }

@@ -9,12 +9,14 @@
 //
 // Persistent CTAs (one per SM) loop over work units: a tile of 128 chains (M = 128) times a
 // group of 128-column N tiles.
-//   warp 0 (one lane)  TMA producer of P tiles (128 projectors x 64 K) through a 2-stage ring;
-//   warp 1             allocates 256 TMEM columns (two 128-column FP32 accumulators);
-//                      one lane issues tcgen05.mma (M128 N128 K16) and commits;
-//   warp 2 (one lane)  TMA producer of the A tile (128 x 3 d_pad bf16, SWIZZLE_128B, resident
-//                      while a unit's N tiles run), one barrier pair per 64-wide K chunk: the
-//                      next unit's chunk is loaded as soon as the last MMAs reading it finish;
+//   warp 0 (one lane)  TMA producer of P tiles (128 projectors x 64 K) through a 6-stage ring;
+//   warp 1             allocates all 512 TMEM columns (two 128-column FP32 accumulators and
+//                      two buffers for the lo split of A); one lane issues tcgen05.mma
+//                      (M128 N128 K16) and commits;
+//   warp 2 (one lane)  TMA producer of the hi and mid splits of the A tile (128 x 2 d_pad
+//                      bf16, SWIZZLE_128B, resident while a unit's N tiles run), one barrier
+//                      pair per 64-wide K chunk: the next unit's chunk is loaded as soon as
+//                      the last MMAs reading it finish;
 //   warps 3-18         epilogue, four warps per TMEM lane quadrant (warp w may only read
 //                      lanes 32 (w mod 4) ..), each owning 32 of a tile's 128 columns and
 //                      writing its own partial sum per chain:
@@ -22,12 +24,17 @@
 //                      log-likelihood of each measurement setting k (D consecutive
 //                      columns, all in one thread):
 //                        sum_l c_kl log(q_kl invf_kl) - P_k log(S_k / t),  S_k = sum_l q_kl,
-//                      FP32 per tile, FP64 across tiles.
+//                      FP32 per tile, FP64 across tiles.  At the start of a unit the same
+//                      warps copy the next unit's lo split from global memory into the idle
+//                      TMEM buffer (tcgen05.st), where the lo-split MMAs read A.  Keeping a
+//                      third of A out of shared memory leaves room for six P stages, enough to
+//                      cover the L2 latency of the P tiles.
 // Renormalising every setting by its own computed sum S_k (instead of the trace t) is exact
 // for a complete POVM (sum_l Lambda_kl = I gives S_k = t in real arithmetic) and cancels any
 // error common to a setting's outcomes -- in particular the one-sided rounding of the
 // tensor cores' FP32 accumulation, which otherwise shifts every q_kl of a chain the same
-// way and adds N * bias to log L.  S_k is a pairwise sum with TwoSum error terms.
+// way and adds N * bias to log L.  S_k is summed exactly as a hi + lo pair (each q split at
+// 2^-20).  The last N tile of a problem issues its MMAs with N = the columns it has left.
 // Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the kernel sets the
 // status word's TIMEOUT bit, stops every role, drains its MMAs and TMA loads (bounded
 // again), frees TMEM and returns.
@@ -45,17 +52,20 @@ constexpr int TC_M = 128;
 constexpr int TC_N = 128;
 constexpr int TC_KATOM = 64;                       // bf16 elements per 128-byte swizzle row
 constexpr int TC_ATOM_BYTES = TC_M * TC_KATOM * 2; // 16 KB: 128 rows x 128 B
-constexpr int TC_BSTAGES = 2;
+constexpr int TC_BSTAGES = 6;
 constexpr int TC_EPI_PER_QUAD = 4;                           // epilogue warps per lane quadrant
 constexpr int TC_EPI_COLS = TC_N / TC_EPI_PER_QUAD;           // columns per epilogue warp (32)
 constexpr int TC_FIRST_EPI = 3;                               // first epilogue warp
 constexpr int TC_THREADS = (TC_FIRST_EPI + 4 * TC_EPI_PER_QUAD) * 32;   // 608
 constexpr int TC_MAX_KCHUNK = 4;                              // d_pad <= 256
-constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr uint32_t TC_TMEM_COLS = 512;   // 2 accumulators + 2 buffers of the lo split
+constexpr uint32_t TC_ALO_COL = 2 * TC_N;      // first column of the lo-split buffers
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;     // 1 s
 
 struct TcArgs {
-    const float2 *colw;    // [KD_tc] (count, invf) per column
+    const __nv_bfloat16 *a_split;   // [rows][3 d_pad] hi, mid, lo (the lo part goes through TMEM)
+    const float4 *colw;    // [KD_tc / 2] per column pair (invf, invf, add, add): x = q invf + add
+    const float *cnt;      // [KD_tc] counts as float
     const float *ptot;     // [KD_tc / D] shots per setting
     const double *trace;   // [rows] exact trace of the stored rho
     double *out;           // [ngroups * 4][rows] partial sums (one per epilogue column slice)
@@ -88,12 +98,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// One bounded try: the thread is suspended until the phase completes or about 1 ms has passed
+// (the time hint), so waiting warps do not take issue slots from the working ones.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(1000000u)
         : "memory");
     return done != 0;
 }
@@ -114,6 +126,29 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_fla
     }
     *abort_flag = 1;
     atomicOr(status, STATUS_TIMEOUT);
+    return false;
+}
+// The same bounded wait taken by a whole warp in lockstep: every lane polls, the warp votes,
+// so the loop and everything after it stay warp-uniform (values the MMA issuer derives there
+// can live in uniform registers).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t *status) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0; it < (1u << 28); ++it) {
+        if (__all_sync(0xffffffffu, mbar_try(bar, parity))) return true;
+        if ((it & 31) == 31) {
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) return false;
+            const uint64_t now = __shfl_sync(0xffffffffu, global_timer(), 0);
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > TC_WAIT_NS) {
+                break;
+            }
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        *abort_flag = 1;
+        atomicOr(status, STATUS_TIMEOUT);
+    }
     return false;
 }
 // Wait used while draining after an abort: ignores the abort flag, still bounded.
@@ -141,18 +176,34 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
     return d;
 }
-// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                            ((uint32_t)(TC_M >> 4) << 24);
+// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128, N = n (a multiple
+// of 16, at most 128: the last N tile of a problem only covers its remaining columns).
+__host__ __device__ constexpr uint32_t mma_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// the same MMA with A read from tensor memory (row m = TMEM lane m, K packed two per column)
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// one lane of the (converged) warp: true in exactly one lane
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred;
+    asm volatile("{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n" : "=r"(pred));
+    return pred != 0;
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -172,28 +223,89 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// sum of D values as an unevaluated pair hi + lo: pairwise, each addition's rounding error
-// recovered exactly by TwoSum and accumulated into lo.
-template <int D>
-__device__ __forceinline__ void compensated_sum(const float *v, float &hi, float &lo) {
-    float s[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) s[i] = v[i];
-    float err = 0.0f;
-#pragma unroll
-    for (int w = D; w > 1; w /= 2) {
-#pragma unroll
-        for (int i = 0; i < w / 2; ++i) {
-            const float x = s[2 * i], y = s[2 * i + 1];
-            const float sum = x + y;
-            const float bb = sum - x;
-            err += (x - (sum - bb)) + (y - bb);
-            s[i] = sum;
-        }
-    }
-    hi = s[0];
-    lo = err;
+// ---- packed FP32 pairs (f32x2: one instruction, two IEEE operations) -------------------------
+// The pair is packed into a 64-bit register inside the asm (mov.b64 {lo, hi}), so no float2
+// is ever reinterpreted through memory.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
 }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n add.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mul.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+
+// qst_log_poly (log_poly.h) on two arguments at once, operation for operation, so each
+// result has the same bits as the scalar function; arguments must be positive normal finite
+// (the caller checks that separately).
+__device__ __forceinline__ float2 log_poly2(float2 x) {
+    const int ix0 = __float_as_int(x.x), ix1 = __float_as_int(x.y);
+    const int k0 = (ix0 - 0x3f3504f3) >> 23, k1 = (ix1 - 0x3f3504f3) >> 23;
+    const float2 m = make_float2(__int_as_float(ix0 - (k0 << 23)), __int_as_float(ix1 - (k1 << 23)));
+    const float2 f = add2(m, splat2(-1.0f));
+    const float2 kf = make_float2((float)k0, (float)k1);
+    float2 q = splat2(-0.08064694682313636f);
+    q = fma2(q, f, splat2(0.1291790293475221f));
+    q = fma2(q, f, splat2(-0.13072555472249744f));
+    q = fma2(q, f, splat2(0.14173450906326862f));
+    q = fma2(q, f, splat2(-0.16628919666247013f));
+    q = fma2(q, f, splat2(0.20002695649848323f));
+    q = fma2(q, f, splat2(-0.25000751231191953f));
+    q = fma2(q, f, splat2(0.33333312940994586f));
+    q = fma2(q, f, splat2(-0.49999997733204976f));
+    const float2 f2 = mul2(f, f);
+    const float2 r = fma2(f2, q, fma2(kf, splat2(1.42860677e-06f), f));
+    return fma2(kf, splat2(0.693145751953125f), r);
+}
+
+// 32 lanes x NC columns of 32-bit words from registers into tensor memory
+template <int NC>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&r)[NC]) {
+    static_assert(NC == 8 || NC == 32, "tmem_st: 8 or 32 columns");
+    if constexpr (NC == 8) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                     "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                     : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+            "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+            "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+            "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+            "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+            "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+            : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Padded K (d_pad) of the packed rho for D: D^2 rounded up to 64.
+__host__ __device__ constexpr int tc_dpad(int D) { return (D * D + 63) / 64 * 64; }
 
 template <int D>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -205,20 +317,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ __align__(8) uint64_t bar_b_empty[TC_BSTAGES];
     __shared__ __align__(8) uint64_t bar_acc_full[2];
     __shared__ __align__(8) uint64_t bar_acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_alo_full[2];
     __shared__ __align__(8) uint64_t bar_mma_done;
     __shared__ uint32_t tmem_base_s;
     __shared__ volatile int abort_flag;
 
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x / 32), 0);   // provably warp-uniform
+    const int lane = threadIdx.x % 32;
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
     const int nk = a.n_katoms;
-    uint8_t *smA = base;                                          // atom (split sp, chunk kc) at sp * nk + kc
-    uint8_t *smB = base + (size_t)3 * nk * TC_ATOM_BYTES;
-    // N tiles of work unit u: [tb, te)
+    uint8_t *smA = base;                                          // atom (split sp < 2, chunk kc) at sp * nk + kc
+    uint8_t *smB = base + (size_t)2 * nk * TC_ATOM_BYTES;
+    // N tiles of work unit u: [tb, te), a balanced split of the tiles over the column groups
+    // (never empty: ngroups <= ntiles)
     auto unit_tiles = [&](int64_t u, int &tb, int &te) {
         const int g = (int)(u % a.ngroups);
-        tb = g * a.tiles_per_group;
-        te = min(tb + a.tiles_per_group, a.ntiles);
+        tb = g * a.ntiles / a.ngroups;
+        te = (g + 1) * a.ntiles / a.ngroups;
+    };
+    // i-th tile a unit visits: its range rotated by the unit's chain tile, so the CTAs running
+    // side by side read different P tiles from L2 instead of all the same lines at once
+    auto tile_at = [&](int64_t u, int tb, int te, int i) {
+        const int len = te - tb;
+        int j = i + (int)((u / a.ngroups) % len);
+        if (j >= len) j -= len;
+        return tb + j;
     };
 
     if (threadIdx.x == 0) {
@@ -233,6 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&bar_acc_full[s]), 1);
             mbar_init(smem_u32(&bar_acc_empty[s]), 4 * TC_EPI_PER_QUAD * 32);
+            mbar_init(smem_u32(&bar_alo_full[s]), 4 * TC_EPI_PER_QUAD * 32);
         }
         mbar_init(smem_u32(&bar_mma_done), 1);
         abort_flag = 0;
@@ -255,7 +379,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
             int tb, te;
             unit_tiles(u, tb, te);
-            for (int t = tb; t < te && ok; ++t) {
+            for (int i = 0; i < te - tb && ok; ++i) {
+                const int t = tile_at(u, tb, te, i);
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int s = it % TC_BSTAGES;
                     const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
@@ -290,8 +415,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(smem_u32(&bar_a_full[kc]), (uint32_t)(3 * TC_ATOM_BYTES));
-                for (int sp = 0; sp < 3; ++sp)
+                mbar_expect_tx(smem_u32(&bar_a_full[kc]), (uint32_t)(2 * TC_ATOM_BYTES));
+                for (int sp = 0; sp < 2; ++sp)
                     tma_load_2d(smem_u32(smA + (size_t)(sp * nk + kc) * TC_ATOM_BYTES), &tmA, (sp * nk + kc) * TC_KATOM,
                                 m0, smem_u32(&bar_a_full[kc]));
             }
@@ -301,64 +426,113 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // the last unit's chunks that were issued
             for (int kc = 0; kc < nk; ++kc) mbar_drain(smem_u32(&bar_a_full[kc]), uc & 1u);
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
+        // The whole warp runs the loop (so the descriptors are warp-uniform values); lane 0 issues
+        // the MMAs and commits.  Descriptors advance by (byte offset >> 4) in their start field.
         int it = 0, tcount = 0;
         uint32_t uc = 0;
         bool ok = true;
-        const uint32_t a_base = smem_u32(smA), b_base = smem_u32(smB);
+        const uint64_t adesc0 = sw128_desc(smem_u32(smA)), bdesc0 = sw128_desc(smem_u32(smB));
+        auto wait_all = [&](uint32_t bar, uint32_t parity) {
+            return mbar_wait_warp(bar, parity, &abort_flag, a.status);
+        };
         for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
             int tb, te;
             unit_tiles(u, tb, te);
-            if (te <= tb) continue;
-            for (int t = tb; t < te && ok; ++t, ++tcount) {
+            for (int i = 0; i < te - tb && ok; ++i, ++tcount) {
+                const int t = tile_at(u, tb, te, i);
                 const int acc = tcount & 1;
                 const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
-                if (!mbar_wait(smem_u32(&bar_acc_empty[acc]), use ^ 1u, &abort_flag, a.status)) {
+                if (!wait_all(smem_u32(&bar_acc_empty[acc]), use ^ 1u) ||
+                    (i == 0 && !wait_all(smem_u32(&bar_alo_full[uc & 1u]), (uc >> 1) & 1u))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc * TC_N);
+                const int n_valid = min(TC_N, (a.KD - t * TC_N + 15) / 16 * 16);
+                const uint32_t idesc = mma_idesc(n_valid);
+                const uint32_t alo_tmem = tmem + TC_ALO_COL + (uc & 1u) * (uint32_t)TC_N;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int s = it % TC_BSTAGES;
                     const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
-                    if (!mbar_wait(smem_u32(&bar_b_full[s]), ph, &abort_flag, a.status) ||
-                        (t == tb && !mbar_wait(smem_u32(&bar_a_full[kc]), uc & 1u, &abort_flag, a.status))) {
+                    if (!wait_all(smem_u32(&bar_b_full[s]), ph) ||
+                        (i == 0 && !wait_all(smem_u32(&bar_a_full[kc]), uc & 1u))) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    const uint64_t bd = bdesc0 + (uint64_t)((s * TC_ATOM_BYTES) >> 4);
+                    const uint64_t ad_hi = adesc0 + (uint64_t)((kc * TC_ATOM_BYTES) >> 4);
+                    const uint64_t ad_mid = adesc0 + (uint64_t)(((nk + kc) * TC_ATOM_BYTES) >> 4);
+                    const uint32_t ad_lo = alo_tmem + (uint32_t)(kc * TC_KATOM / 2);
+                    if (elect_one()) {
 #pragma unroll
-                    for (int sp = 0; sp < 3; ++sp) {
+                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)   // 16 K = 32 bytes = 2 descriptor units
+                            mma_bf16(d_tmem, ad_hi + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
 #pragma unroll
-                        for (int kk = 0; kk < TC_KATOM / 16; ++kk) {
-                            const uint64_t ad = sw128_desc(a_base + (uint32_t)((sp * nk + kc) * TC_ATOM_BYTES + kk * 32));
-                            const uint64_t bd = sw128_desc(b_base + (uint32_t)(s * TC_ATOM_BYTES + kk * 32));
-                            mma_bf16(d_tmem, ad, bd, (kc | sp | kk) != 0 ? 1u : 0u);
-                        }
+                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)
+                            mma_bf16(d_tmem, ad_mid + 2 * kk, bd + 2 * kk, idesc, 1u);
+#pragma unroll
+                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)   // lo split, A from tensor memory
+                            mma_bf16_ta(d_tmem, ad_lo + (uint32_t)(kk * 8), bd + 2 * kk, idesc, 1u);
+                        mma_commit(smem_u32(&bar_b_empty[s]));
+                        if (i == te - tb - 1) mma_commit(smem_u32(&bar_a_empty[kc]));   // last reader of this A chunk
                     }
-                    mma_commit(smem_u32(&bar_b_empty[s]));
-                    if (t == te - 1) mma_commit(smem_u32(&bar_a_empty[kc]));   // last reader of this A chunk
+                    __syncwarp();
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(&bar_acc_full[acc]));
+                if (elect_one()) mma_commit(smem_u32(&bar_acc_full[acc]));
+                __syncwarp();
             }
             ++uc;
         }
-        if (!ok) {
+        if (!ok && lane == 0) {
             // every MMA issued so far must finish before TMEM and shared memory go away
             mma_commit(smem_u32(&bar_mma_done));
             mbar_drain(smem_u32(&bar_mma_done), 0u);
         }
+        __syncwarp();
     } else if (warp >= TC_FIRST_EPI) {
         // ---------------- epilogue ----------------
         const int quad = warp & 3;                        // TMEM lane quadrant this warp may access
         const int sub = (warp - TC_FIRST_EPI) / 4;        // column slice of every tile
         const int col0 = sub * TC_EPI_COLS;
+        // The lo split of a unit's A rows goes from global memory into TMEM buffer b (the MMAs
+        // read it there): this warp writes lanes 32 quad.., K elements [sub DP/4, (sub+1) DP/4).
+        constexpr int DP = tc_dpad(D);
+        constexpr int NCW = DP / 2 / TC_EPI_PER_QUAD;   // 32-bit TMEM columns per warp
+        auto write_alo = [&](int64_t u, uint32_t b) {
+            const int64_t row = (u / a.ngroups) * TC_M + quad * 32 + lane;
+            uint32_t r[NCW];
+            if (row < a.rows) {
+                const uint4 *src =
+                    reinterpret_cast<const uint4 *>(a.a_split + row * 3 * DP + 2 * DP + sub * (DP / TC_EPI_PER_QUAD));
+#pragma unroll
+                for (int i = 0; i < NCW / 4; ++i) {
+                    const uint4 w = __ldg(src + i);
+                    r[4 * i] = w.x;
+                    r[4 * i + 1] = w.y;
+                    r[4 * i + 2] = w.z;
+                    r[4 * i + 3] = w.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NCW; ++i) r[i] = 0u;
+            }
+            tmem_st<NCW>(tmem + ((uint32_t)(quad * 32) << 16) + TC_ALO_COL + b * (uint32_t)TC_N + (uint32_t)(sub * NCW), r);
+            tc_fence_before();
+            mbar_arrive(smem_u32(&bar_alo_full[b]));
+        };
+        if (blockIdx.x < a.units) write_alo(blockIdx.x, 0u);
         int tcount = 0;
+        uint32_t ucount = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x, ++ucount) {
+            // next unit's lo split into the other buffer: its last readers (the MMAs of the unit
+            // before this one) completed before this warp received that unit's last accumulator
+            if (u + gridDim.x < a.units) write_alo(u + gridDim.x, (ucount + 1) & 1u);
             int tb, te;
             unit_tiles(u, tb, te);
             const int g = (int)(u % a.ngroups);
@@ -369,7 +543,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float t_hi = (float)t;
             const float t_lo = (float)(t - (double)t_hi);
             double total = 0.0;
-            for (int tt = tb; tt < te; ++tt, ++tcount) {
+            for (int i = 0; i < te - tb; ++i, ++tcount) {
+                const int tt = tile_at(u, tb, te, i);
                 const int acc = tcount & 1;
                 const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
                 if (!mbar_wait(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
@@ -383,28 +558,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_before();
                 mbar_arrive(smem_u32(&bar_acc_empty[acc]));   // the slice is in registers
                 float tile_sum = 0.0f;
+                if (n0 < a.KD) {   // (columns past KD: the last tile's MMA did not write them)
+                    int xmin = 0x7fffffff;   // smallest bit pattern of a log argument (sign included)
 #pragma unroll
-                for (int sk = 0; sk < TC_EPI_COLS / D; ++sk) {
-                    const int nb = n0 + sk * D;               // first column of setting nb / D
-                    const float pk = __ldg(a.ptot + nb / D);
-                    if (pk > 0.0f) {
-                        float dev = 0.0f;
+                    for (int sk = 0; sk < TC_EPI_COLS / D; ++sk) {
+                        const int nb = n0 + sk * D;               // first column of setting nb / D
+                        const float pk = __ldg(a.ptot + nb / D);
+                        if (pk > 0.0f) {
+                            // S_k = sum_l q_kl exactly as hi + lo: every q in (-4, 4) is split at
+                            // 2^-20 by adding and removing 12 (so the hi parts add exactly), the
+                            // lo parts are below 2^-21
+                            float2 sh = splat2(0.0f), sl = splat2(0.0f), dev = splat2(0.0f);
 #pragma unroll
-                        for (int l = 0; l < D; ++l) {
-                            const float2 w = __ldg(a.colw + nb + l);   // (count, invf)
-                            if (w.x > 0.0f) dev += w.x * logf(v[sk * D + l] * w.y);
+                            for (int l = 0; l < D; l += 2) {
+                                const float2 q = make_float2(v[sk * D + l], v[sk * D + l + 1]);
+                                const float2 h = sub2(add2(q, splat2(12.0f)), splat2(12.0f));
+                                sh = add2(sh, h);
+                                sl = add2(sl, sub2(q, h));
+                                // deviance terms c log(q invf); columns without counts get x = 1
+                                const float4 w = __ldg(a.colw + (nb + l) / 2);
+                                const float2 c = __ldg(reinterpret_cast<const float2 *>(a.cnt + nb + l));
+                                const float2 x = fma2(q, make_float2(w.x, w.y), make_float2(w.z, w.w));
+                                xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
+                                dev = fma2(c, log_poly2(x), dev);
+                            }
+                            const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;   // (s_hi exact)
+                            // log(S_k / t), S_k - t formed from the exact pairs (Sterbenz: s_hi - t_hi exact)
+                            const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
+                            // log1p(rel): |rel| is a few ulps, where three terms are exact to 2^-40
+                            const float l1p = fabsf(rel) < 0x1p-10f
+                                                  ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
+                                                  : log1pf(rel);
+                            tile_sum += (dev.x + dev.y) - pk * l1p;
                         }
-                        float s_hi, s_lo;
-                        compensated_sum<D>(v + sk * D, s_hi, s_lo);
-                        // log(S_k / t) with S_k - t formed from the compensated pair
-                        const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
-                        tile_sum += dev - pk * log1pf(rel);
                     }
-                }
-                if (a.p_out && valid) {
+                    // a counted outcome with q <= 0 (or below the normal range): log L = -inf
+                    if (xmin < 0x00800000) tile_sum = -INFINITY;
+                    if (a.p_out && valid) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
+                        for (int i = 0; i < 32; ++i)
+                            if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
+                    }
                 }
                 total += (double)tile_sum;
             }
@@ -448,13 +642,14 @@ bool encode_bf16_2d(CUtensorMap *map, const void *ptr, uint64_t inner, uint64_t 
     return r == CUDA_SUCCESS;
 }
 
-size_t tc_smem_bytes(int n_katoms) { return 1024 + (size_t)(3 * n_katoms + TC_BSTAGES) * TC_ATOM_BYTES; }
+size_t tc_smem_bytes(int n_katoms) { return 1024 + (size_t)(2 * n_katoms + TC_BSTAGES) * TC_ATOM_BYTES; }
 
 }  // namespace
 
 struct TcPlan {
     CUtensorMap a;
     CUtensorMap b;
+    const __nv_bfloat16 *a_split;
     int n_katoms;
     int ntiles;
 };
@@ -491,11 +686,13 @@ cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, i
     if (p.d_pad % TC_KATOM != 0 || p.KD_tc % TC_N != 0 || p.KD_tc <= 0) return cudaErrorNotSupported;
     const int n_katoms = p.d_pad / TC_KATOM;
     if (n_katoms > TC_MAX_KCHUNK) return cudaErrorNotSupported;
+    if (p.d_pad != tc_dpad(p.D)) return cudaErrorNotSupported;
     if (tc_smem_bytes(n_katoms) > 227 * 1024 - 256) return cudaErrorNotSupported;
     if (reinterpret_cast<uintptr_t>(A_split) % 16 != 0 || reinterpret_cast<uintptr_t>(p.Pbf) % 16 != 0)
         return cudaErrorMisalignedAddress;
     TcPlan *pl = new TcPlan();
     pl->n_katoms = n_katoms;
+    pl->a_split = A_split;
     pl->ntiles = p.KD_tc / TC_N;
     const bool ok_a = encode_bf16_2d(&pl->a, A_split, (uint64_t)3 * p.d_pad, (uint64_t)rows, TC_KATOM, TC_M);
     const bool ok_b = encode_bf16_2d(&pl->b, p.Pbf, (uint64_t)p.d_pad, (uint64_t)p.KD_tc, TC_KATOM, TC_N);
@@ -514,7 +711,9 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     if (!plan) return cudaErrorInvalidValue;
     if (rows <= 0) return cudaSuccess;
     TcArgs a;
+    a.a_split = plan->a_split;
     a.colw = p.colw;
+    a.cnt = p.cnt;
     a.ptot = p.ptot;
     a.trace = p.trace_prop;
     a.out = out_part;

@@ -2,6 +2,7 @@
 // argument blocks, the counter-based generator and launch declarations.
 #pragma once
 
+#include "log_poly.h"
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -67,6 +68,15 @@ struct Philox {
 // (latent), KD = K*D projectors, d_pad = d rounded up to 64 (operand rows), KD_pad =
 // KD rounded up to the contraction's column tile.
 // ---------------------------------------------------------------------------------------
+// log x for the likelihood terms: the polynomial logarithm (log_poly.h, <= 1 ulp) for
+// positive normal x; -inf when x <= 0 (or below the normal range), so a counted outcome
+// with p <= 0 makes log L = -inf and the proposal is rejected.  (A NaN or infinite rho
+// reaches log L through its trace instead.)
+__device__ __forceinline__ float deviance_log(float x) {
+    const float r = qst_log_poly(x);
+    return (__float_as_int(x) >= 0x00800000) ? r : -INFINITY;
+}
+
 struct ProblemView {
     int D, d, nx, KD, KD_pad, d_pad;
     int KD_tc;                   // columns of the tensor-core operand (multiple of its N tile)
@@ -82,7 +92,7 @@ struct ProblemView {
     const float *cnt;            // [max(KD_pad, KD_tc)] counts as float, 0 on padding
     const float *invf;           // [max(KD_pad, KD_tc)] P_k / c_kl (1 where c_kl = 0)
     const float *ptot;           // [max(KD_pad, KD_tc) / D] shots P_k of each setting (0 on padding)
-    const float2 *colw;          // [max(KD_pad, KD_tc)] (count, invf) interleaved, for the tensor epilogue
+    const float4 *colw;          // [max(KD_pad, KD_tc) / 2] per column pair (invf, invf, add, add), tensor epilogue
 
     // chain state
     float *y;                    // [2][R][nx] double-buffered latent states
