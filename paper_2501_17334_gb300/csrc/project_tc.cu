@@ -52,7 +52,7 @@ constexpr int TC_M = 128;
 constexpr int TC_N = 128;
 constexpr int TC_KATOM = 64;                       // bf16 elements per 128-byte swizzle row
 constexpr int TC_ATOM_BYTES = TC_M * TC_KATOM * 2; // 16 KB: 128 rows x 128 B
-constexpr int TC_BSTAGES = 6;
+constexpr int TC_BSTAGES = 5;
 constexpr int TC_EPI_PER_QUAD = 4;                           // epilogue warps per lane quadrant
 constexpr int TC_EPI_COLS = TC_N / TC_EPI_PER_QUAD;           // columns per epilogue warp (32)
 constexpr int TC_FIRST_EPI = 3;                               // first epilogue warp
@@ -109,28 +109,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Bounded wait: true when the phase of `parity` completed; false on abort or timeout.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t *status) {
-    uint64_t t0 = 0;
-    for (uint32_t it = 0; it < (1u << 28); ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 31) == 31) {
-            if (*abort_flag) return false;
-            const uint64_t now = global_timer();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > TC_WAIT_NS) {
-                break;
-            }
-        }
-    }
-    *abort_flag = 1;
-    atomicOr(status, STATUS_TIMEOUT);
-    return false;
-}
-// The same bounded wait taken by a whole warp in lockstep: every lane polls, the warp votes,
-// so the loop and everything after it stay warp-uniform (values the MMA issuer derives there
-// can live in uniform registers).
+// Bounded wait, taken by a whole warp in lockstep: true when the phase of `parity` completed,
+// false on abort or after about 1 s (then the status word's TIMEOUT bit is set and every role
+// stops).  Every lane polls and the warp votes, so the loop and everything after it stay
+// warp-uniform (values the issuing warps derive there can live in uniform registers).
 __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t *status) {
     uint64_t t0 = 0;
     for (uint32_t it = 0; it < (1u << 28); ++it) {
@@ -328,6 +310,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nk = a.n_katoms;
     uint8_t *smA = base;                                          // atom (split sp < 2, chunk kc) at sp * nk + kc
     uint8_t *smB = base + (size_t)2 * nk * TC_ATOM_BYTES;
+    // the epilogue's per-column weights, staged once: (invf, invf, add, add) and (c, c) per column
+    // pair, shots per setting
+    const int kd_tc = a.ntiles * TC_N;
+    float4 *w_q = reinterpret_cast<float4 *>(smB + (size_t)TC_BSTAGES * TC_ATOM_BYTES);
+    float2 *w_c = reinterpret_cast<float2 *>(w_q + kd_tc / 2);
+    float *w_p = reinterpret_cast<float *>(w_c + kd_tc / 2);
+    for (int i = threadIdx.x; i < kd_tc / 2; i += blockDim.x) {
+        w_q[i] = __ldg(a.colw + i);
+        w_c[i] = __ldg(reinterpret_cast<const float2 *>(a.cnt) + i);
+    }
+    for (int i = threadIdx.x; i < kd_tc / D; i += blockDim.x) w_p[i] = __ldg(a.ptot + i);
     // N tiles of work unit u: [tb, te), a balanced split of the tiles over the column groups
     // (never empty: ngroups <= ntiles)
     auto unit_tiles = [&](int64_t u, int &tb, int &te) {
@@ -372,8 +365,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- P-tile producer ----------------
+    if (warp == 0) {
+        // ---------------- P-tile producer (whole warp in lockstep, one lane issues) ----------------
         int it = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
@@ -384,25 +377,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int s = it % TC_BSTAGES;
                     const uint32_t ph = (uint32_t)(it / TC_BSTAGES) & 1u;
-                    if (!mbar_wait(smem_u32(&bar_b_empty[s]), ph ^ 1u, &abort_flag, a.status)) {
+                    if (!mbar_wait_warp(smem_u32(&bar_b_empty[s]), ph ^ 1u, &abort_flag, a.status)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(smem_u32(&bar_b_full[s]), (uint32_t)TC_ATOM_BYTES);
-                    tma_load_2d(smem_u32(smB + (size_t)s * TC_ATOM_BYTES), &tmB, kc * TC_KATOM, t * TC_N,
-                                smem_u32(&bar_b_full[s]));
+                    if (elect_one()) {
+                        mbar_expect_tx(smem_u32(&bar_b_full[s]), (uint32_t)TC_ATOM_BYTES);
+                        tma_load_2d(smem_u32(smB + (size_t)s * TC_ATOM_BYTES), &tmB, kc * TC_KATOM, t * TC_N,
+                                    smem_u32(&bar_b_full[s]));
+                    }
+                    __syncwarp();
                 }
             }
         }
-        if (!ok) {
+        if (!ok && lane == 0) {
             // no copy may still be writing shared memory when the CTA exits
             for (int back = 1; back <= TC_BSTAGES && it - back >= 0; ++back) {
                 const int i2 = it - back;
                 mbar_drain(smem_u32(&bar_b_full[i2 % TC_BSTAGES]), (uint32_t)(i2 / TC_BSTAGES) & 1u);
             }
         }
-    } else if (warp == 2 && lane == 0) {
-        // ---------------- A-tile producer ----------------
+    } else if (warp == 2) {
+        // ---------------- A-tile producer (whole warp in lockstep, one lane issues) ----------------
         uint32_t uc = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
@@ -411,18 +407,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (te <= tb) continue;
             const int m0 = (int)((u / a.ngroups) * TC_M);
             for (int kc = 0; kc < nk; ++kc) {
-                if (!mbar_wait(smem_u32(&bar_a_empty[kc]), (uc & 1u) ^ 1u, &abort_flag, a.status)) {
+                if (!mbar_wait_warp(smem_u32(&bar_a_empty[kc]), (uc & 1u) ^ 1u, &abort_flag, a.status)) {
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(smem_u32(&bar_a_full[kc]), (uint32_t)(2 * TC_ATOM_BYTES));
-                for (int sp = 0; sp < 2; ++sp)
-                    tma_load_2d(smem_u32(smA + (size_t)(sp * nk + kc) * TC_ATOM_BYTES), &tmA, (sp * nk + kc) * TC_KATOM,
-                                m0, smem_u32(&bar_a_full[kc]));
+                if (elect_one()) {
+                    mbar_expect_tx(smem_u32(&bar_a_full[kc]), (uint32_t)(2 * TC_ATOM_BYTES));
+                    for (int sp = 0; sp < 2; ++sp)
+                        tma_load_2d(smem_u32(smA + (size_t)(sp * nk + kc) * TC_ATOM_BYTES), &tmA,
+                                    (sp * nk + kc) * TC_KATOM, m0, smem_u32(&bar_a_full[kc]));
+                }
+                __syncwarp();
             }
             ++uc;
         }
-        if (!ok) {
+        if (!ok && lane == 0) {
             // the last unit's chunks that were issued
             for (int kc = 0; kc < nk; ++kc) mbar_drain(smem_u32(&bar_a_full[kc]), uc & 1u);
         }
@@ -547,7 +546,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int tt = tile_at(u, tb, te, i);
                 const int acc = tcount & 1;
                 const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
-                if (!mbar_wait(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
+                if (!mbar_wait_warp(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
                     ok = false;
                     break;
                 }
@@ -563,21 +562,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int sk = 0; sk < TC_EPI_COLS / D; ++sk) {
                         const int nb = n0 + sk * D;               // first column of setting nb / D
-                        const float pk = __ldg(a.ptot + nb / D);
+                        const float pk = w_p[nb / D];
                         if (pk > 0.0f) {
                             // S_k = sum_l q_kl exactly as hi + lo: every q in (-4, 4) is split at
                             // 2^-20 by adding and removing 12 (so the hi parts add exactly), the
                             // lo parts are below 2^-21
                             float2 sh = splat2(0.0f), sl = splat2(0.0f), dev = splat2(0.0f);
+                            float4 w_next = w_q[nb / 2];
+                            float2 c_next = w_c[nb / 2];
 #pragma unroll
                             for (int l = 0; l < D; l += 2) {
+                                const float4 w = w_next;   // this pair's weights, the next pair's requested now
+                                const float2 c = c_next;
+                                if (l + 2 < D) {
+                                    w_next = w_q[(nb + l + 2) / 2];
+                                    c_next = w_c[(nb + l + 2) / 2];
+                                }
                                 const float2 q = make_float2(v[sk * D + l], v[sk * D + l + 1]);
                                 const float2 h = sub2(add2(q, splat2(12.0f)), splat2(12.0f));
                                 sh = add2(sh, h);
                                 sl = add2(sl, sub2(q, h));
                                 // deviance terms c log(q invf); columns without counts get x = 1
-                                const float4 w = __ldg(a.colw + (nb + l) / 2);
-                                const float2 c = __ldg(reinterpret_cast<const float2 *>(a.cnt + nb + l));
                                 const float2 x = fma2(q, make_float2(w.x, w.y), make_float2(w.z, w.w));
                                 xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
                                 dev = fma2(c, log_poly2(x), dev);
@@ -642,7 +647,11 @@ bool encode_bf16_2d(CUtensorMap *map, const void *ptr, uint64_t inner, uint64_t 
     return r == CUDA_SUCCESS;
 }
 
-size_t tc_smem_bytes(int n_katoms) { return 1024 + (size_t)(2 * n_katoms + TC_BSTAGES) * TC_ATOM_BYTES; }
+// A (hi, mid), the P ring, then the epilogue's weights
+size_t tc_smem_bytes(int n_katoms, int kd_tc, int D) {
+    return 1024 + (size_t)(2 * n_katoms + TC_BSTAGES) * TC_ATOM_BYTES + (size_t)(kd_tc / 2) * (sizeof(float4) + sizeof(float2)) +
+           (size_t)(kd_tc / D) * sizeof(float);
+}
 
 }  // namespace
 
@@ -687,7 +696,7 @@ cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, i
     const int n_katoms = p.d_pad / TC_KATOM;
     if (n_katoms > TC_MAX_KCHUNK) return cudaErrorNotSupported;
     if (p.d_pad != tc_dpad(p.D)) return cudaErrorNotSupported;
-    if (tc_smem_bytes(n_katoms) > 227 * 1024 - 256) return cudaErrorNotSupported;
+    if (tc_smem_bytes(n_katoms, p.KD_tc, p.D) > 227 * 1024 - 256) return cudaErrorNotSupported;
     if (reinterpret_cast<uintptr_t>(A_split) % 16 != 0 || reinterpret_cast<uintptr_t>(p.Pbf) % 16 != 0)
         return cudaErrorMisalignedAddress;
     TcPlan *pl = new TcPlan();
@@ -727,7 +736,7 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     a.ngroups = groups;
     a.tiles_per_group = (plan->ntiles + groups - 1) / groups;
     a.units = ((rows + TC_M - 1) / TC_M) * groups;
-    const size_t smem = tc_smem_bytes(plan->n_katoms);
+    const size_t smem = tc_smem_bytes(plan->n_katoms, plan->ntiles * TC_N, p.D);
     static int num_sms = 0;
     if (num_sms == 0) {
         int dev = 0;
