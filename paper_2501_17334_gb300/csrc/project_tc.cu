@@ -268,8 +268,12 @@ __device__ __forceinline__ float2 log_poly2(float2 x) {
 // 32 lanes x NC columns of 32-bit words from registers into tensor memory
 template <int NC>
 __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&r)[NC]) {
-    static_assert(NC == 8 || NC == 32, "tmem_st: 8 or 32 columns");
-    if constexpr (NC == 8) {
+    static_assert(NC == 4 || NC == 8 || NC == 32, "tmem_st: 4, 8 or 32 columns");
+    if constexpr (NC == 4) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+                     "r"(r[2]), "r"(r[3])
+                     : "memory");
+    } else if constexpr (NC == 8) {
         asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
                      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
                      : "memory");
@@ -502,36 +506,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // read it there): this warp writes lanes 32 quad.., K elements [sub DP/4, (sub+1) DP/4).
         constexpr int DP = tc_dpad(D);
         constexpr int NCW = DP / 2 / TC_EPI_PER_QUAD;   // 32-bit TMEM columns per warp
-        auto write_alo = [&](int64_t u, uint32_t b) {
+        // It moves in pieces of 4 columns (16 bytes of each row): the next unit's pieces are
+        // fetched one per tile at the start of the tile and stored at its end, so the global
+        // loads never stall the epilogue.
+        constexpr int NP = NCW / 4;
+        auto alo_fetch = [&](int64_t u, int piece) {
             const int64_t row = (u / a.ngroups) * TC_M + quad * 32 + lane;
-            uint32_t r[NCW];
-            if (row < a.rows) {
-                const uint4 *src =
-                    reinterpret_cast<const uint4 *>(a.a_split + row * 3 * DP + 2 * DP + sub * (DP / TC_EPI_PER_QUAD));
-#pragma unroll
-                for (int i = 0; i < NCW / 4; ++i) {
-                    const uint4 w = __ldg(src + i);
-                    r[4 * i] = w.x;
-                    r[4 * i + 1] = w.y;
-                    r[4 * i + 2] = w.z;
-                    r[4 * i + 3] = w.w;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < NCW; ++i) r[i] = 0u;
-            }
-            tmem_st<NCW>(tmem + ((uint32_t)(quad * 32) << 16) + TC_ALO_COL + b * (uint32_t)TC_N + (uint32_t)(sub * NCW), r);
+            if (row >= a.rows) return make_uint4(0u, 0u, 0u, 0u);
+            const uint4 *src =
+                reinterpret_cast<const uint4 *>(a.a_split + row * 3 * DP + 2 * DP + sub * (DP / TC_EPI_PER_QUAD));
+            return __ldg(src + piece);
+        };
+        auto alo_store = [&](uint32_t b, int piece, uint4 w) {
+            const uint32_t r[4] = {w.x, w.y, w.z, w.w};
+            tmem_st<4>(tmem + ((uint32_t)(quad * 32) << 16) + TC_ALO_COL + b * (uint32_t)TC_N +
+                           (uint32_t)(sub * NCW + 4 * piece),
+                       r);
+        };
+        auto alo_done = [&](uint32_t b) {
             tc_fence_before();
             mbar_arrive(smem_u32(&bar_alo_full[b]));
         };
-        if (blockIdx.x < a.units) write_alo(blockIdx.x, 0u);
+        if (blockIdx.x < a.units) {
+            for (int piece = 0; piece < NP; ++piece) alo_store(0u, piece, alo_fetch(blockIdx.x, piece));
+            alo_done(0u);
+        }
         int tcount = 0;
         uint32_t ucount = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x, ++ucount) {
-            // next unit's lo split into the other buffer: its last readers (the MMAs of the unit
-            // before this one) completed before this warp received that unit's last accumulator
-            if (u + gridDim.x < a.units) write_alo(u + gridDim.x, (ucount + 1) & 1u);
+            // the next unit's lo split goes into the other buffer: its last readers (the MMAs of
+            // the unit before this one) completed before this warp received that unit's last
+            // accumulator
+            const bool has_next = u + gridDim.x < a.units;
+            const uint32_t nb_buf = (ucount + 1) & 1u;
             int tb, te;
             unit_tiles(u, tb, te);
             const int g = (int)(u % a.ngroups);
@@ -544,6 +552,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             double total = 0.0;
             for (int i = 0; i < te - tb; ++i, ++tcount) {
                 const int tt = tile_at(u, tb, te, i);
+                const uint4 piece_w = (has_next && i < NP) ? alo_fetch(u + gridDim.x, i) : make_uint4(0u, 0u, 0u, 0u);
                 const int acc = tcount & 1;
                 const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
                 if (!mbar_wait_warp(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
@@ -606,6 +615,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
                 total += (double)tile_sum;
+                if (has_next) {
+                    if (i < NP) alo_store(nb_buf, i, piece_w);
+                    if (i == te - tb - 1) {   // last tile of the unit: whatever is left, then publish
+                        for (int piece = i + 1; piece < NP; ++piece)
+                            alo_store(nb_buf, piece, alo_fetch(u + gridDim.x, piece));
+                        alo_done(nb_buf);
+                    }
+                }
             }
             if (ok && valid) a.out[(int64_t)(g * 4 + sub) * a.rows + grow] = total;
         }
