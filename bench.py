@@ -43,12 +43,12 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "7140d3f20c5f91504e802eca9f1611e6a5b5193245c52b0e78b113f022960706",
-                "chains": 32768, "bytes": 134.738176e6 + 157.768960e6},
+                "sha256": "d21a2f5d26a17c645dd1937b703b2bc87d330e4de2bfca5202fe0df052b35a3b",
+                "chains": 32768, "bytes": 134.682880e6 + 160.286208e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "45d2971f0db79e074720de7d00d18706049219d253c294c34a4552d5b425ebf6",
-                "chains": 32768, "bytes": 51.382272e6 + 0.022272e6},
+                "sha256": "bc7718df75d75efe9cfe831466550380fc8063c876f6fc6e619876f7729e57c8",
+                "chains": 32768, "bytes": 51.390464e6 + 0.004608e6},
 }
 
 
