@@ -480,10 +480,353 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     }
 }
 
+// ---- five qubits (D = 32): one warp per chain ----------------------------------------------
+// The same algorithm with the same lane ownership (lane j: column j, then row j), but at D = 32 a
+// lane cannot also hold the operand it is multiplied with, so that operand is streamed from
+// shared memory four complex entries (two 128-bit loads) at a time.
+struct Wide {
+    static constexpr int D = 32;
+    static constexpr int d = D * D;
+    static constexpr int chains_per_block = kThreads / D;   // 4
+    static constexpr int row_stride = D + 2;                // float2 per row of W
+    static constexpr int qcol = D + 4;                      // floats per column of a Q plane
+    static constexpr int pk_stride = D + 1;
+    static constexpr int area_a = 2 * D * qcol;             // >= 2 D row_stride
+    static constexpr int area_b = 2 * D * D;                // >= D pk_stride
+    static constexpr int smem_floats = (area_a + area_b + 31) / 32 * 32 + 16;
+};
+static_assert(Wide::area_a >= 2 * Wide::D * Wide::row_stride && Wide::area_b >= Wide::D * Wide::pk_stride, "areas");
+
+template <int PASSES>
+__global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a) {
+    using S = Wide;
+    constexpr int D = S::D, d = S::d, nx = 4 * d, RS = S::row_stride, QC = S::qcol, PK = S::pk_stride;
+    extern __shared__ __align__(16) float smem[];
+    const int j = threadIdx.x % D;
+    const int g = threadIdx.x / D;
+    const int64_t c = (int64_t)blockIdx.x * S::chains_per_block + g;
+    const bool active = c < a.rows;
+    float *sm = smem + g * S::smem_floats;
+    float *qre = sm, *qim = sm + D * QC;
+    float2 *wsm = reinterpret_cast<float2 *>(sm);
+    float2 *fsm = reinterpret_cast<float2 *>(sm + S::area_a);
+    float *packed = sm + S::area_a;
+
+    // ---- 1. latent proposal (as in the D <= 16 kernel: lane j owns column j of each part) ------
+    float coef_y = 1.0f, coef_eta = 0.0f;
+    int cur = 0;
+    if (active && a.mode == MODE_STEP) {
+        cur = a.cur[c];
+        const float2 cf = a.coef[c];
+        coef_y = cf.x;
+        coef_eta = cf.y;
+    } else if (a.mode == MODE_INIT) {
+        coef_y = 0.0f;
+        coef_eta = 1.0f;
+    }
+    const int64_t cc = active ? c : 0;
+    const uint32_t chain_id = (uint32_t)(a.chain_offset + cc);
+    const uint32_t tag = (a.mode == MODE_INIT) ? TAG_INIT : TAG_PROPOSAL;
+    const uint32_t key_lo = (uint32_t)(a.seed & 0xffffffffu), key_hi = (uint32_t)(a.seed >> 32);
+    const float *ysrc = a.y + ((int64_t)cur * a.R + cc) * nx;
+    float *ydst = a.y + ((int64_t)(1 - cur) * a.R + cc) * nx;
+    const float *gsrc = (a.mode == MODE_EVAL) ? a.x_eval + cc * nx : ydst;
+    float hr[D], hi[D];
+#pragma unroll 1
+    for (int part = 0; part < 4; ++part) {
+        const int e0 = part * d + j * D;
+#pragma unroll
+        for (int q = 0; q < D / 4; ++q) {
+            float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (active && a.mode == MODE_STEP) y0 = *reinterpret_cast<const float4 *>(ysrc + e0 + 4 * q);
+            if (active && a.mode == MODE_EVAL) y0 = *reinterpret_cast<const float4 *>(a.x_eval + cc * nx + e0 + 4 * q);
+            float4 yn = y0;
+            if (a.mode != MODE_EVAL) {
+                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), a.step, chain_id, tag), key_lo, key_hi);
+                float z0, z1, z2, z3;
+                gaussian_pair_fast(w.x, w.y, z0, z1);
+                gaussian_pair_fast(w.z, w.w, z2, z3);
+                yn.x = __fmaf_rn(coef_y, y0.x, coef_eta * z0);
+                yn.y = __fmaf_rn(coef_y, y0.y, coef_eta * z1);
+                yn.z = __fmaf_rn(coef_y, y0.z, coef_eta * z2);
+                yn.w = __fmaf_rn(coef_y, y0.w, coef_eta * z3);
+                if (active) *reinterpret_cast<float4 *>(ydst + e0 + 4 * q) = yn;
+            }
+            if (part == 2) {
+                hr[4 * q] = yn.x; hr[4 * q + 1] = yn.y; hr[4 * q + 2] = yn.z; hr[4 * q + 3] = yn.w;
+            } else if (part == 3) {
+                hi[4 * q] = yn.x; hi[4 * q + 1] = yn.y; hi[4 * q + 2] = yn.z; hi[4 * q + 3] = yn.w;
+            }
+        }
+    }
+
+    // ---- 2a. modified Gram-Schmidt, the published column streamed in chunks --------------------
+#pragma unroll 1
+    for (int k = 0; k < D; ++k) {
+        if (j == k) {
+            store_column<D>(qre + k * QC, hr);
+            store_column<D>(qim + k * QC, hi);
+        }
+        __syncwarp();
+        if (j > k) {
+            const float *vre = qre + k * QC, *vim = qim + k * QC;
+            float n0 = 0.0f, n1 = 0.0f, rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; i += 4) {
+                const float4 vr = *reinterpret_cast<const float4 *>(vre + i);
+                const float4 vi = *reinterpret_cast<const float4 *>(vim + i);
+                n0 = __fmaf_rn(vr.x, vr.x, __fmaf_rn(vi.x, vi.x, n0));
+                n1 = __fmaf_rn(vr.y, vr.y, __fmaf_rn(vi.y, vi.y, n1));
+                n0 = __fmaf_rn(vr.z, vr.z, __fmaf_rn(vi.z, vi.z, n0));
+                n1 = __fmaf_rn(vr.w, vr.w, __fmaf_rn(vi.w, vi.w, n1));
+                rr0 = __fmaf_rn(vr.x, hr[i], __fmaf_rn(vi.x, hi[i], rr0));
+                ri0 = __fmaf_rn(vr.x, hi[i], __fmaf_rn(-vi.x, hr[i], ri0));
+                rr1 = __fmaf_rn(vr.y, hr[i + 1], __fmaf_rn(vi.y, hi[i + 1], rr1));
+                ri1 = __fmaf_rn(vr.y, hi[i + 1], __fmaf_rn(-vi.y, hr[i + 1], ri1));
+                rr0 = __fmaf_rn(vr.z, hr[i + 2], __fmaf_rn(vi.z, hi[i + 2], rr0));
+                ri0 = __fmaf_rn(vr.z, hi[i + 2], __fmaf_rn(-vi.z, hr[i + 2], ri0));
+                rr1 = __fmaf_rn(vr.w, hr[i + 3], __fmaf_rn(vi.w, hi[i + 3], rr1));
+                ri1 = __fmaf_rn(vr.w, hi[i + 3], __fmaf_rn(-vi.w, hr[i + 3], ri1));
+            }
+            const float inv_n = 1.0f / (n0 + n1);
+            const float sr = (rr0 + rr1) * inv_n, si = (ri0 + ri1) * inv_n;
+#pragma unroll
+            for (int i = 0; i < D; i += 4) {
+                const float4 vr = *reinterpret_cast<const float4 *>(vre + i);
+                const float4 vi = *reinterpret_cast<const float4 *>(vim + i);
+                const float vrr[4] = {vr.x, vr.y, vr.z, vr.w}, vii[4] = {vi.x, vi.y, vi.z, vi.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    hr[i + u] = __fmaf_rn(-sr, vrr[u], __fmaf_rn(si, vii[u], hr[i + u]));
+                    hi[i + u] = __fmaf_rn(-sr, vii[u], __fmaf_rn(-si, vrr[u], hi[i + u]));
+                }
+            }
+        }
+    }
+    {
+        float n0 = 0.0f, n1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < D; i += 2) {
+            n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
+            n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
+        }
+        const float inv = 1.0f / sqrtf(n0 + n1);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            hr[i] *= inv;
+            hi[i] *= inv;
+        }
+        __syncwarp();
+        store_column<D>(qre + j * QC, hr);
+        store_column<D>(qim + j * QC, hi);
+        __syncwarp();
+    }
+
+    if constexpr (PASSES == 2) {
+        // ---- 2b. Q2 = Q1 (I - F): Gram entries (a, a + t), then row a of Q1 (I - F) ------------
+#pragma unroll 1
+        for (int t = 0; t <= D / 2; ++t) {
+            const int b = (j + t) & (D - 1);
+            if (t == D / 2 && j >= D / 2) continue;
+            const float *bre = qre + b * QC, *bim = qim + b * QC;
+            float er0 = 0.0f, ei0 = 0.0f, er1 = 0.0f, ei1 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; i += 4) {
+                const float4 br = *reinterpret_cast<const float4 *>(bre + i);
+                const float4 bi = *reinterpret_cast<const float4 *>(bim + i);
+                er0 = __fmaf_rn(hr[i], br.x, __fmaf_rn(hi[i], bi.x, er0));
+                ei0 = __fmaf_rn(hr[i], bi.x, __fmaf_rn(-hi[i], br.x, ei0));
+                er1 = __fmaf_rn(hr[i + 1], br.y, __fmaf_rn(hi[i + 1], bi.y, er1));
+                ei1 = __fmaf_rn(hr[i + 1], bi.y, __fmaf_rn(-hi[i + 1], br.y, ei1));
+                er0 = __fmaf_rn(hr[i + 2], br.z, __fmaf_rn(hi[i + 2], bi.z, er0));
+                ei0 = __fmaf_rn(hr[i + 2], bi.z, __fmaf_rn(-hi[i + 2], br.z, ei0));
+                er1 = __fmaf_rn(hr[i + 3], br.w, __fmaf_rn(hi[i + 3], bi.w, er1));
+                ei1 = __fmaf_rn(hr[i + 3], bi.w, __fmaf_rn(-hi[i + 3], br.w, ei1));
+            }
+            const float er = er0 + er1, ei = ei0 + ei1;
+            if (t == 0) {
+                fsm[j * D + j] = make_float2(0.5f * (er - 1.0f), 0.0f);
+                if (j + 1 < D) fsm[j * D + j + 1] = make_float2(0.0f, 0.0f);
+            } else if (j < b) {
+                fsm[b * D + j] = make_float2(er, ei);
+            } else {
+                fsm[j * D + b] = make_float2(er, -ei);
+            }
+        }
+        __syncwarp();
+        {
+            float xr[D], xi[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                xr[i] = qre[i * QC + j];
+                xi[i] = qim[i * QC + j];
+            }
+#pragma unroll
+            for (int m = D - 1; m >= 0; --m) {
+                float accr = xr[m], acci = xi[m];
+#pragma unroll
+                for (int i = 0; i <= m; i += 2) {
+                    const float4 f = *reinterpret_cast<const float4 *>(fsm + m * D + i);
+                    accr = __fmaf_rn(-xr[i], f.x, __fmaf_rn(xi[i], f.y, accr));
+                    acci = __fmaf_rn(-xr[i], f.y, __fmaf_rn(-xi[i], f.x, acci));
+                    if (i + 1 <= m) {
+                        accr = __fmaf_rn(-xr[i + 1], f.z, __fmaf_rn(xi[i + 1], f.w, accr));
+                        acci = __fmaf_rn(-xr[i + 1], f.w, __fmaf_rn(-xi[i + 1], f.z, acci));
+                    }
+                }
+                xr[m] = accr;
+                xi[m] = acci;
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                qre[i * QC + j] = xr[i];
+                qim[i * QC + j] = xi[i];
+            }
+        }
+        __syncwarp();
+    }
+
+    // ---- 3. W[:, j] = G[:, j] + sum_k U[:, k] G[k, j], U streamed, G read back four rows at a time
+    float wr[D], wi[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        wr[i] = 0.0f;
+        wi[i] = 0.0f;
+    }
+#pragma unroll 1
+    for (int k0 = 0; k0 < D; k0 += 4) {
+        float4 g4r = make_float4(0.f, 0.f, 0.f, 0.f), g4i = g4r;
+        if (active) {
+            g4r = *reinterpret_cast<const float4 *>(gsrc + j * D + k0);
+            g4i = *reinterpret_cast<const float4 *>(gsrc + d + j * D + k0);
+        }
+        const float gkr[4] = {g4r.x, g4r.y, g4r.z, g4r.w}, gki[4] = {g4i.x, g4i.y, g4i.z, g4i.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float *ure = qre + (k0 + u) * QC, *uim = qim + (k0 + u) * QC;
+#pragma unroll
+            for (int i = 0; i < D; i += 4) {
+                const float4 ur = *reinterpret_cast<const float4 *>(ure + i);
+                const float4 ui = *reinterpret_cast<const float4 *>(uim + i);
+                const float urr[4] = {ur.x, ur.y, ur.z, ur.w}, uii[4] = {ui.x, ui.y, ui.z, ui.w};
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    wr[i + v] = __fmaf_rn(urr[v], gkr[u], __fmaf_rn(-uii[v], gki[u], wr[i + v]));
+                    wi[i + v] = __fmaf_rn(urr[v], gki[u], __fmaf_rn(uii[v], gkr[u], wi[i + v]));
+                }
+            }
+        }
+    }
+    if (active) {   // + G[:, j]
+#pragma unroll
+        for (int i = 0; i < D; i += 4) {
+            const float4 gr4 = *reinterpret_cast<const float4 *>(gsrc + j * D + i);
+            const float4 gi4 = *reinterpret_cast<const float4 *>(gsrc + d + j * D + i);
+            wr[i] += gr4.x; wr[i + 1] += gr4.y; wr[i + 2] += gr4.z; wr[i + 3] += gr4.w;
+            wi[i] += gi4.x; wi[i + 1] += gi4.y; wi[i + 2] += gi4.z; wi[i + 3] += gi4.w;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < D; ++i) wsm[i * RS + j] = make_float2(wr[i], wi[i]);
+    __syncwarp();
+
+    // ---- 4. rho = W W^dag / Tr, lane a: entries (a, a + t mod D), row b streamed --------------
+    const int arow = j;
+    float war[D], wai[D];
+#pragma unroll
+    for (int jj = 0; jj < D; jj += 2) {
+        const float4 v = *reinterpret_cast<const float4 *>(wsm + arow * RS + jj);
+        war[jj] = v.x;
+        wai[jj] = v.y;
+        war[jj + 1] = v.z;
+        wai[jj + 1] = v.w;
+    }
+    float diag = 0.0f;
+#pragma unroll
+    for (int jj = 0; jj < D; ++jj) diag = __fmaf_rn(war[jj], war[jj], __fmaf_rn(wai[jj], wai[jj], diag));
+    const float inv_tr = 1.0f / group_sum<D>(diag);
+    const float diag_n = diag * inv_tr;
+    float tr_hi, tr_lo;
+    group_sum_exact<D>(diag_n, tr_hi, tr_lo);
+    __syncwarp();
+    packed[arow * PK + arow] = diag_n;
+#pragma unroll 1
+    for (int t = 1; t <= D / 2; ++t) {
+        const int b = (arow + t) & (D - 1);
+        if (t == D / 2 && arow >= D / 2) continue;
+        float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;
+#pragma unroll
+        for (int jj = 0; jj < D; jj += 2) {
+            const float4 wb = *reinterpret_cast<const float4 *>(wsm + b * RS + jj);
+            re0 = __fmaf_rn(war[jj], wb.x, __fmaf_rn(wai[jj], wb.y, re0));
+            im0 = __fmaf_rn(wai[jj], wb.x, __fmaf_rn(-war[jj], wb.y, im0));
+            re1 = __fmaf_rn(war[jj + 1], wb.z, __fmaf_rn(wai[jj + 1], wb.w, re1));
+            im1 = __fmaf_rn(wai[jj + 1], wb.z, __fmaf_rn(-war[jj + 1], wb.w, im1));
+        }
+        const float re = (re0 + re1) * inv_tr;
+        const float im = (im0 + im1) * inv_tr;
+        if (arow < b) {
+            packed[arow * PK + b] = re;
+            packed[b * PK + arow] = -im;
+        } else {
+            packed[arow * PK + b] = im;
+            packed[b * PK + arow] = re;
+        }
+    }
+    if (active && j == 0) a.trace_out[c] = (double)tr_hi + (double)tr_lo;
+    __syncwarp();
+
+    // ---- 5. store packed rho (FP32) and its exact bf16 split ----------------------------------
+    if (active) {
+        float *dst = a.rho_out + c * a.d_pad;
+        for (int e = 4 * j; e < d; e += 4 * D) {
+            auto staged = [&](int ee) { return packed[(ee / D) * PK + (ee % D)]; };
+            const float4 v = make_float4(staged(e), staged(e + 1), staged(e + 2), staged(e + 3));
+            *reinterpret_cast<float4 *>(dst + e) = v;
+            if (a.rho_norm_out) *reinterpret_cast<float4 *>(a.rho_norm_out + c * d + e) = v;
+            if (a.split_out) {
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+                __nv_bfloat16 hs[4], ms[4], ls[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    hs[u] = __float2bfloat16_rn(vv[u]);
+                    const float r1 = vv[u] - __bfloat162float(hs[u]);
+                    ms[u] = __float2bfloat16_rn(r1);
+                    const float r2 = r1 - __bfloat162float(ms[u]);
+                    ls[u] = __float2bfloat16_rn(r2);
+                }
+                __nv_bfloat16 *sp = a.split_out + c * 3 * (int64_t)a.d_pad + e;
+                *reinterpret_cast<uint2 *>(sp) = *reinterpret_cast<const uint2 *>(hs);
+                *reinterpret_cast<uint2 *>(sp + a.d_pad) = *reinterpret_cast<const uint2 *>(ms);
+                *reinterpret_cast<uint2 *>(sp + 2 * a.d_pad) = *reinterpret_cast<const uint2 *>(ls);
+            }
+        }
+    }
+}
+
+template <int PASSES>
+cudaError_t launch_propose_d32(const ProposeArgs &a, cudaStream_t s) {
+    using S = Wide;
+    const size_t smem = sizeof(float) * S::smem_floats * S::chains_per_block;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(propose_kernel_d32<PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(propose_kernel_d32<PASSES>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t blocks = (a.rows + S::chains_per_block - 1) / S::chains_per_block;
+    if (blocks == 0) return cudaSuccess;
+    propose_kernel_d32<PASSES><<<(unsigned)blocks, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int D, int PASSES>
 cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, const float *x_eval, int64_t rows,
                               bool want_split, float *rho_norm_out, cudaStream_t s) {
-    using S = Shape<D>;
     ProposeArgs a;
     a.x_eval = x_eval;
     a.y = p.y;
@@ -500,20 +843,26 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.step = step;
     a.mode = mode;
     a.d_pad = p.d_pad;
-    const size_t smem = sizeof(float) * S::smem_floats * S::chains_per_block;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    if constexpr (D == 32) {
+        return launch_propose_d32<PASSES>(a, s);
+    } else {
+        using S = Shape<D>;
+        const size_t smem = sizeof(float) * S::smem_floats * S::chains_per_block;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e =
+                cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        const int64_t blocks = (rows + S::chains_per_block - 1) / S::chains_per_block;
+        if (blocks == 0) return cudaSuccess;
+        propose_kernel<D, PASSES><<<(unsigned)blocks, kThreads, smem, s>>>(a);
+        return cudaGetLastError();
     }
-    const int64_t blocks = (rows + S::chains_per_block - 1) / S::chains_per_block;
-    if (blocks == 0) return cudaSuccess;
-    propose_kernel<D, PASSES><<<(unsigned)blocks, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
 }
 
 template <int D>
@@ -534,6 +883,7 @@ cudaError_t launch_propose(const ProblemView &p, int mode, uint32_t step, const 
         case 4: return launch_propose_d<4>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
         case 8: return launch_propose_d<8>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
         case 16: return launch_propose_d<16>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
+        case 32: return launch_propose_d<32>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
         default: return cudaErrorInvalidValue;
     }
 }

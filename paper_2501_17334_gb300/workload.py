@@ -195,6 +195,14 @@ def config_problem(index: int, num_chains: Optional[int] = None, num_steps: Opti
     return make_problem(q, truth, shots, r, s, b, 2000 + index, 3000 + index, name=f"config{index}")
 
 
+def five_qubit_problem(num_chains: int = 256, num_steps: int = 100, seed: int = 1006) -> Problem:
+    """A 5-qubit problem (D = 32, 243 bases x 32 outcomes = 7776 projectors): Ginibre truth of
+    rank 3 mixed with I/D at weight 0.05, 1000 shots per basis, beta0 0.05."""
+    rng = np.random.default_rng(seed)
+    truth = depolarise(ginibre_state(32, 3, rng), 0.05)
+    return make_problem(5, truth, 1000, num_chains, num_steps, 0.05, seed + 1000, seed + 2000, name="five_qubits")
+
+
 def heterogeneous_batch(num_problems: int = 64, seed: int = 1005, max_qubits: int = 5,
                         chain_scale: float = 1.0) -> List[Problem]:
     """Batch of independent problems of uneven size (configuration 5).

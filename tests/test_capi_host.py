@@ -78,6 +78,15 @@ def test_validation_rejects_bad_inputs(qst):
     assert "identity" in qst.load().qst_last_error().decode() or True
 
 
+def test_five_qubits_need_the_fp32_form(qst):
+    prob = W.five_qubit_problem(num_chains=8, num_steps=1)
+    assert qst.workspace_size([prob], qst.default_config()) > 0
+    assert _status(lambda: qst.workspace_size([prob], qst.default_config(precision=qst.PREC_BF16X3))) == 7
+    six = W.five_qubit_problem(num_chains=8, num_steps=1)
+    six.num_qubits = 6
+    assert _status(lambda: qst.workspace_size([six], qst.default_config())) == 1
+
+
 @pytest.mark.parametrize("q", [1, 2, 3, 4])
 def test_packed_projectors_reproduce_direct_trace(qst, oracle_mod, q):
     """p = vec_h(rho) . P (the contraction the kernels run) equals Tr(Lambda rho) of the oracle."""

@@ -1,0 +1,77 @@
+"""Five qubits (D = 32, 7776 Pauli projectors) on the GPU against the FP64 oracle.
+
+At D = 32 the proposal kernel runs one warp per chain and streams the second operand of
+every product from shared memory; the projection runs in the plain FP32 form (the tensor-core
+form is limited to Q <= 4 and must say so).  The parity bars are those of the D <= 16 tests:
+rho within 2e-6 and p within 1e-6 on rows with cond(H) <= 1e3, the reduction within
+sum c * 6 * 2^-24 of the oracle's sum on the GPU's own p, and accept decisions that agree
+except at near-ties.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_17334_gb300 import workload as W
+from tests._helpers import unpack_rho
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def prob5():
+    return W.five_qubit_problem(num_chains=64, num_steps=40)
+
+
+def test_five_qubit_evaluate_matches_oracle(qst, oracle_mod, cuda_ok, prob5):
+    import torch
+    n = 64   # evaluate takes at most num_chains rows
+    s = qst.Sampler(prob5, precision=qst.PREC_FP32, diag_chains=0)
+    x32 = W.latent_batch(n, 5, seed=505).astype(np.float32)
+    rho_p, p_gpu, ll_gpu = s.evaluate(torch.from_numpy(x32).cuda())
+    torch.cuda.synchronize()
+    s.close()
+    rho_gpu = unpack_rho(rho_p.cpu().numpy(), 32)
+    p_gpu = p_gpu.cpu().numpy().astype(np.float64)
+    ll_gpu = ll_gpu.cpu().numpy()
+    rho_ref, p_ref, ll_ref = oracle_mod.evaluate(prob5, x32.astype(np.float64))
+    x = x32.astype(np.float64)
+    H = (x[:, 2048:3072] + 1j * x[:, 3072:]).reshape(n, 32, 32).transpose(0, 2, 1)
+    ok = np.linalg.cond(H) <= 1e3
+    assert ok.mean() > 0.9
+    assert np.abs(rho_gpu - rho_ref).max(axis=(1, 2))[ok].max() < 2e-6
+    assert np.abs(p_gpu - p_ref).max(axis=1)[ok].max() < 1e-6
+    c = prob5.counts.astype(np.float64)
+    ll_own = np.array([oracle_mod.loglik(prob5.counts, p_gpu[i]) for i in range(n)])
+    fin = np.isfinite(ll_own)
+    assert np.abs(ll_gpu[fin] - ll_own[fin]).max() < np.sum(c) * 6 * 2.0 ** -24
+    rel = np.abs(ll_gpu - ll_ref) / np.abs(ll_ref)
+    assert np.nanmax(rel[ok]) < 1e-5
+
+
+def test_five_qubit_tensor_form_is_refused(qst, cuda_ok, prob5):
+    with pytest.raises(qst.QstError) as e:
+        qst.Sampler(prob5, precision=qst.PREC_BF16X3, diag_chains=0)
+    assert e.value.status == 7
+
+
+def test_five_qubit_decisions_match_oracle(qst, oracle_mod, cuda_ok, prob5):
+    R, S = 32, 40
+    prob = W.five_qubit_problem(num_chains=R, num_steps=S)
+    s = qst.Sampler(prob, precision=qst.PREC_FP32, trace_steps=S, diag_chains=0)
+    s.run_chains(S)
+    acc_gpu, _ = s.get_trace()
+    mean, n = s.posterior_mean()
+    s.close()
+    ref = oracle_mod.run(prob, num_steps=S, trace_steps=S, want_final=True)
+    margin = ref["trace_log_alpha"] - (ref["trace_logl_prop"] - ref["trace_logl_cur"])
+    mism = 0
+    for r in range(R):
+        bad = np.nonzero(acc_gpu.T[r] != ref["trace_accept"][r])[0]
+        if bad.size:
+            assert abs(margin[r, bad[0]]) < 5e-2, (r, bad[0], margin[r, bad[0]])
+            mism += 1
+    assert mism <= 2
+    assert n == ref["num_pooled"] == R * S
+    assert abs(np.trace(mean).real - 1) < 1e-6
+    same = np.all(acc_gpu.T == ref["trace_accept"], axis=1)
+    if same.all():
+        assert np.abs(mean - ref["mean"]).max() < 1e-5
