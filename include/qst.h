@@ -84,7 +84,10 @@ typedef struct {
     int32_t precision;      /* qst_precision */
     int32_t qr_passes;      /* modified Gram-Schmidt passes computing U of Algorithm 1 l.4-5: 1, or 2
                                (default) re-orthogonalising once, which cuts U's FP32 error ~10x */
-    int32_t reserved[3];    /* zero */
+    int32_t use_graph;      /* 1 (default): qst_run_chains replays one step captured as a CUDA graph
+                               (the step counter lives on the device); 0: plain launches. Kernel
+                               timing (qst_set_profiling) always uses plain launches */
+    int32_t reserved[2];    /* zero */
 } qst_sampler_cfg;
 
 /* Diagnostics of one problem (Sec. IV). */
@@ -148,6 +151,10 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
 /* Enqueues num_steps steps j -> j+1 of Algorithm 2 for every chain of every problem
  * (proposal, Algorithm 1, likelihood, accept, adaptation, thinning and pooling).
  * Asynchronous on the handle's stream; resumable (step numbering continues).
+ * A step is one small kernel that advances the device-side step counter, then the
+ * proposal, projection and accept kernels of every problem.  With use_graph the first
+ * call captures that sequence once (on a private stream) and every step launches the
+ * graph; the results are bit-identical to plain launches.
  * Errors: QST_ERR_INVALID_ARG if num_steps < 0. */
 qst_status qst_run_chains(qst_handle *h, int64_t num_steps);
 

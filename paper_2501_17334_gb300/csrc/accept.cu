@@ -15,11 +15,17 @@ struct AcceptArgs {
     uint32_t step;     // j
     int kept;          // j is a kept step (j % T == 0 and j > burn_in)
     int64_t kept_idx;  // index of this kept state (0-based) in the trajectories
+    const StepState *step_dev;   // when not null: step, kept and kept_idx come from here
 };
 
 // One CTA owns chains [128 b, 128 b + 128) and pool slot b.
 __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
     const ProblemView &p = a.p;
+    if (a.step_dev) {   // (a is this thread's copy of the parameters)
+        a.step = a.step_dev->step;
+        a.kept = a.step_dev->kept;
+        a.kept_idx = a.step_dev->kept_idx;
+    }
     __shared__ uint8_t flag[kChainsPerCta];
     __shared__ float inv_tr[kChainsPerCta];
     const int tid = threadIdx.x;
@@ -229,10 +235,25 @@ __global__ void inject_nan_kernel(float *y, const uint8_t *cur, int64_t R, int n
     for (int e = threadIdx.x; e < nx; e += blockDim.x) y[((int64_t)b * R + chain) * nx + e] = __int_as_float(0x7fc00000);
 }
 
+// Opens step j = step + 1 (one thread): whether j is kept and at which index.
+__global__ void advance_step_kernel(StepState *st, int thin, int burn_in) {
+    const uint32_t j = st->step + 1u;
+    const int kept = (j % (uint32_t)thin == 0u) && ((int64_t)j > (int64_t)burn_in);
+    st->step = j;
+    st->kept = kept;
+    st->kept_idx = st->kept_count;
+    st->kept_count += kept;
+}
+
 }  // namespace
 
-cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mode, uint32_t step, bool kept,
-                          int64_t kept_idx, uint32_t *status, cudaStream_t s) {
+cudaError_t launch_advance_step(StepState *st, int thin, int burn_in, cudaStream_t s) {
+    advance_step_kernel<<<1, 1, 0, s>>>(st, thin, burn_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mode, const StepState *step_dev, uint32_t step,
+                          bool kept, int64_t kept_idx, uint32_t *status, cudaStream_t s) {
     (void)status;
     AcceptArgs a;
     a.p = p;
@@ -241,6 +262,7 @@ cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mod
     a.step = step;
     a.kept = kept ? 1 : 0;
     a.kept_idx = kept_idx;
+    a.step_dev = step_dev;
     const int64_t blocks = (p.R + kChainsPerCta - 1) / kChainsPerCta;
     accept_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(a);
     return cudaGetLastError();

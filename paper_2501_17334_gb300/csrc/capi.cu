@@ -91,6 +91,7 @@ struct HostProblem {
 struct Plan {
     std::vector<HostProblem> probs;
     size_t status_off = 0;  // device status word
+    size_t step_off = 0;    // device StepState
     size_t bytes = 0;       // total workspace bytes
 };
 
@@ -110,6 +111,7 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
         return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
     if (cfg->qr_passes != 1 && cfg->qr_passes != 2)
         return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1 or 2");
+    if (cfg->use_graph != 0 && cfg->use_graph != 1) return fail(QST_ERR_INVALID_ARG, "use_graph must be 0 or 1");
     return QST_OK;
 }
 
@@ -279,6 +281,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         L.end = off;
     }
     plan.status_off = take(256);
+    plan.step_off = take(256);
     plan.bytes = off;
     return QST_OK;
 }
@@ -304,6 +307,11 @@ struct qst_handle {
     size_t ws_bytes = 0;
     bool own_ws = false;
     uint32_t *d_status = nullptr;
+    StepState *d_step = nullptr;
+    cudaStream_t capture_stream = nullptr;   // private stream the step graph is captured on
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_kernels = 0;               // kernel launches one replay performs
     int64_t steps_done = 0;
     int64_t kept = 0;
     int64_t launches = 0;
@@ -410,13 +418,13 @@ qst_status enqueue_projection(qst_handle *h, HostProblem &hp, int64_t rows, floa
 qst_status enqueue_init(qst_handle *h, HostProblem &hp) {
     ProblemView &v = hp.v;
     qst_status st = launch(h, QST_KERNEL_PROPOSE, "propose (init)", [&] {
-        return launch_propose(v, MODE_INIT, 0u, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
+        return launch_propose(v, MODE_INIT, 0u, nullptr, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
     });
     if (st != QST_OK) return st;
     st = enqueue_projection(h, hp, v.R, nullptr);
     if (st != QST_OK) return st;
     return launch(h, QST_KERNEL_ACCEPT, "accept (init)", [&] {
-        return launch_accept(v, h->sp, MODE_INIT, 0u, false, 0, h->d_status, h->stream);
+        return launch_accept(v, h->sp, MODE_INIT, nullptr, 0u, false, 0, h->d_status, h->stream);
     });
 }
 
@@ -460,6 +468,7 @@ void qst_default_config(qst_sampler_cfg *cfg) {
     cfg->trace_steps = 0;
     cfg->precision = QST_PREC_FP32;
     cfg->qr_passes = 2;
+    cfg->use_graph = 1;
 }
 
 qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_problems, const qst_sampler_cfg *cfg,
@@ -503,6 +512,7 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
     }
     QST_CUDA(cudaMemsetAsync(h->ws, 0, h->plan.bytes, h->stream), "clear workspace");
     h->d_status = reinterpret_cast<uint32_t *>(h->ws + h->plan.status_off);
+    h->d_step = reinterpret_cast<StepState *>(h->ws + h->plan.step_off);
     for (auto &hp : h->plan.probs) {
         bind_problem(h.get(), hp);
         ProblemView &v = hp.v;
@@ -549,24 +559,75 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
     return QST_OK;
 }
 
+namespace {
+
+// One step's launches on h->stream: open step j on the device, then every problem's
+// proposal, projection and accept, all reading j from the device.
+qst_status enqueue_step(qst_handle *h) {
+    qst_status st = launch(h, QST_KERNEL_ACCEPT, "advance step",
+                           [&] { return launch_advance_step(h->d_step, h->cfg.thin, h->cfg.burn_in, h->stream); });
+    if (st != QST_OK) return st;
+    for (auto &hp : h->plan.probs) {
+        ProblemView &v = hp.v;
+        st = launch(h, QST_KERNEL_PROPOSE, "propose", [&] {
+            return launch_propose(v, MODE_STEP, 0u, h->d_step, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
+        });
+        if (st != QST_OK) return st;
+        st = enqueue_projection(h, hp, v.R, nullptr);
+        if (st != QST_OK) return st;
+        st = launch(h, QST_KERNEL_ACCEPT, "accept", [&] {
+            return launch_accept(v, h->sp, MODE_STEP, h->d_step, 0u, false, 0, h->d_status, h->stream);
+        });
+        if (st != QST_OK) return st;
+    }
+    return QST_OK;
+}
+
+// Captures enqueue_step once on the private capture stream and instantiates it.
+qst_status build_step_graph(qst_handle *h) {
+    if (!h->capture_stream)
+        QST_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "create capture stream");
+    cudaStream_t user = h->stream;
+    const int64_t launches0 = h->launches;
+    h->stream = h->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    qst_status st = QST_OK;
+    if (e == cudaSuccess) st = enqueue_step(h);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = (e == cudaSuccess) ? cudaStreamEndCapture(h->capture_stream, &g) : e;
+    h->stream = user;
+    h->graph_kernels = h->launches - launches0;
+    h->launches = launches0;
+    if (e != cudaSuccess) return cuda_fail(e, "begin graph capture");
+    if (st != QST_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e_end != cudaSuccess) return cuda_fail(e_end, "end graph capture");
+    h->graph = g;
+    QST_CUDA(cudaGraphInstantiate(&h->graph_exec, g, 0), "instantiate step graph");
+    return QST_OK;
+}
+
+}  // namespace
+
 qst_status qst_run_chains(qst_handle *h, int64_t num_steps) {
     if (!h) return fail(QST_ERR_INVALID_ARG, "handle is NULL");
     if (num_steps < 0) return fail(QST_ERR_INVALID_ARG, "num_steps must be >= 0");
     if (h->steps_done + num_steps > 0xffffffffLL) return fail(QST_ERR_INVALID_ARG, "step counter exceeds 32 bits");
+    const bool graph = h->cfg.use_graph && !h->prof && num_steps > 0;
+    if (graph && !h->graph_exec) {
+        qst_status st = build_step_graph(h);
+        if (st != QST_OK) return st;
+    }
     for (int64_t s = 0; s < num_steps; ++s) {
         const int64_t j = h->steps_done + 1;
-        const bool kept = (j % h->cfg.thin == 0) && (j > h->cfg.burn_in);
-        for (auto &hp : h->plan.probs) {
-            ProblemView &v = hp.v;
-            qst_status st = launch(h, QST_KERNEL_PROPOSE, "propose", [&] {
-                return launch_propose(v, MODE_STEP, (uint32_t)j, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
-            });
-            if (st != QST_OK) return st;
-            st = enqueue_projection(h, hp, v.R, nullptr);
-            if (st != QST_OK) return st;
-            st = launch(h, QST_KERNEL_ACCEPT, "accept", [&] {
-                return launch_accept(v, h->sp, MODE_STEP, (uint32_t)j, kept, h->kept, h->d_status, h->stream);
-            });
+        const bool kept = (j % h->cfg.thin == 0) && (j > h->cfg.burn_in);   // mirrors advance_step_kernel
+        if (graph) {
+            QST_CUDA(cudaGraphLaunch(h->graph_exec, h->stream), "launch step graph");
+            h->launches += h->graph_kernels;
+        } else {
+            qst_status st = enqueue_step(h);
             if (st != QST_OK) return st;
         }
         h->steps_done = j;
@@ -711,6 +772,9 @@ void qst_destroy(qst_handle *h) {
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
     }
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->own_ws) cudaFree(h->ws);
     delete h;
 }
@@ -794,6 +858,10 @@ qst_status qst_restore(qst_handle *h, const void *buffer, size_t bytes) {
     }
     h->steps_done = steps;
     h->kept = kept;
+    StepState ss{};
+    ss.step = (uint32_t)steps;
+    ss.kept_count = kept;
+    QST_CUDA(cudaMemcpy(h->d_step, &ss, sizeof(ss), cudaMemcpyHostToDevice), "restore step counter");
     return check_status(h);
 }
 
@@ -806,7 +874,7 @@ qst_status qst_evaluate(qst_handle *h, int32_t problem, const float *x, int64_t 
     if (n == 0) return QST_OK;
     if (!x) return fail(QST_ERR_INVALID_ARG, "x is NULL");
     st = launch(h, QST_KERNEL_PROPOSE, "propose (eval)", [&] {
-        return launch_propose(v, MODE_EVAL, 0u, x, n, is_tc(h), rho, h->d_status, h->stream);
+        return launch_propose(v, MODE_EVAL, 0u, nullptr, x, n, is_tc(h), rho, h->d_status, h->stream);
     });
     if (st != QST_OK) return st;
     st = enqueue_projection(h, *hp, n, p);

@@ -147,7 +147,7 @@ extern "C" qst_status qst_loglik_noalloc(int32_t num_qubits, int32_t num_povms, 
         e = cudaMemcpyAsync(scratch + kOffInvf, invf, sizeof(float) * KD_pad, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && d < d_pad)   // padding columns of the operand must be zero
         e = cudaMemsetAsync(scratch + kOffRho, 0, sizeof(float) * (size_t)n * d_pad, s);
-    if (e == cudaSuccess) e = launch_propose(v, MODE_EVAL, 0u, x, n, false, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = launch_propose(v, MODE_EVAL, 0u, nullptr, x, n, false, nullptr, nullptr, s);
     if (e == cudaSuccess) e = launch_project_fp32(v, v.rho_prop, n, v.logl_part, nullptr, s);
     if (e == cudaSuccess) e = launch_logl_combine(v, n, logl, s);
     if (e != cudaSuccess) return noalloc_fail(QST_ERR_CUDA, cudaGetErrorString(e));

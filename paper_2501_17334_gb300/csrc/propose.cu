@@ -143,6 +143,7 @@ struct ProposeArgs {
     int64_t chain_offset;
     uint64_t seed;
     uint32_t step;
+    const StepState *step_dev;   // MODE_STEP: when not null the step is read from here
     int mode;
     int d_pad;
 };
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     const int g = threadIdx.x / D;       // chain slot in the block
     const int64_t c = (int64_t)blockIdx.x * S::chains_per_block + g;
     const bool active = c < a.rows;
+    const uint32_t step = (a.step_dev && a.mode == MODE_STEP) ? a.step_dev->step : a.step;
     float *sm = smem + g * S::smem_floats;
     float *qre = sm, *qim = sm + D * QC;                 // Q planes (column stride QC)
     float2 *wsm = reinterpret_cast<float2 *>(sm);        // W row-major (row stride RS), replaces Q
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
             for (int q = 0; q < D / 4; ++q) {
                 float4 yn = y0[q];
                 if (a.mode != MODE_EVAL) {
-                    const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), a.step, chain_id, tag), key_lo, key_hi);
+                    const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), key_lo, key_hi);
                     float z0, z1, z2, z3;
                     gaussian_pair_fast(w.x, w.y, z0, z1);
                     gaussian_pair_fast(w.z, w.w, z2, z3);
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                     y1v = a.x_eval[cc * nx + e + 1];
                 }
             } else {
-                const uint4 w = Philox::block(make_uint4((uint32_t)part, a.step, chain_id, tag), key_lo, key_hi);
+                const uint4 w = Philox::block(make_uint4((uint32_t)part, step, chain_id, tag), key_lo, key_hi);
                 float z0, z1;
                 gaussian_pair_fast(j == 0 ? w.x : w.z, j == 0 ? w.y : w.w, z0, z1);
                 float o0 = 0.0f, o1 = 0.0f;
@@ -506,6 +508,7 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
     const int g = threadIdx.x / D;
     const int64_t c = (int64_t)blockIdx.x * S::chains_per_block + g;
     const bool active = c < a.rows;
+    const uint32_t step = (a.step_dev && a.mode == MODE_STEP) ? a.step_dev->step : a.step;
     float *sm = smem + g * S::smem_floats;
     float *qre = sm, *qim = sm + D * QC;
     float2 *wsm = reinterpret_cast<float2 *>(sm);
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
             if (active && a.mode == MODE_EVAL) y0 = *reinterpret_cast<const float4 *>(a.x_eval + cc * nx + e0 + 4 * q);
             float4 yn = y0;
             if (a.mode != MODE_EVAL) {
-                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), a.step, chain_id, tag), key_lo, key_hi);
+                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), key_lo, key_hi);
                 float z0, z1, z2, z3;
                 gaussian_pair_fast(w.x, w.y, z0, z1);
                 gaussian_pair_fast(w.z, w.w, z2, z3);
@@ -825,8 +828,8 @@ cudaError_t launch_propose_d32(const ProposeArgs &a, cudaStream_t s) {
 }
 
 template <int D, int PASSES>
-cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, const float *x_eval, int64_t rows,
-                              bool want_split, float *rho_norm_out, cudaStream_t s) {
+cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, const StepState *step_dev,
+                              const float *x_eval, int64_t rows, bool want_split, float *rho_norm_out, cudaStream_t s) {
     ProposeArgs a;
     a.x_eval = x_eval;
     a.y = p.y;
@@ -841,6 +844,7 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.chain_offset = p.chain_offset;
     a.seed = p.seed;
     a.step = step;
+    a.step_dev = step_dev;
     a.mode = mode;
     a.d_pad = p.d_pad;
     if constexpr (D == 32) {
@@ -866,24 +870,24 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
 }
 
 template <int D>
-cudaError_t launch_propose_d(const ProblemView &p, int mode, uint32_t step, const float *x_eval, int64_t rows,
-                             bool want_split, float *rho_norm_out, cudaStream_t s) {
-    if (p.qr_passes == 1) return launch_propose_pd<D, 1>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
-    return launch_propose_pd<D, 2>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
+cudaError_t launch_propose_d(const ProblemView &p, int mode, uint32_t step, const StepState *step_dev, const float *x_eval,
+                             int64_t rows, bool want_split, float *rho_norm_out, cudaStream_t s) {
+    if (p.qr_passes == 1) return launch_propose_pd<D, 1>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+    return launch_propose_pd<D, 2>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
 }
 
 }  // namespace
 
-cudaError_t launch_propose(const ProblemView &p, int mode, uint32_t step, const float *x_eval, int64_t n_eval,
-                           bool want_split, float *rho_norm_out, uint32_t *status, cudaStream_t s) {
+cudaError_t launch_propose(const ProblemView &p, int mode, uint32_t step, const StepState *step_dev, const float *x_eval,
+                           int64_t n_eval, bool want_split, float *rho_norm_out, uint32_t *status, cudaStream_t s) {
     (void)status;
     const int64_t rows = (mode == MODE_EVAL) ? n_eval : p.R;
     switch (p.D) {
-        case 2: return launch_propose_d<2>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
-        case 4: return launch_propose_d<4>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
-        case 8: return launch_propose_d<8>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
-        case 16: return launch_propose_d<16>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
-        case 32: return launch_propose_d<32>(p, mode, step, x_eval, rows, want_split, rho_norm_out, s);
+        case 2: return launch_propose_d<2>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+        case 4: return launch_propose_d<4>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+        case 8: return launch_propose_d<8>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+        case 16: return launch_propose_d<16>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+        case 32: return launch_propose_d<32>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -77,6 +77,16 @@ __device__ __forceinline__ float deviance_log(float x) {
     return (__float_as_int(x) >= 0x00800000) ? r : -INFINITY;
 }
 
+// Step counter kept on the device, so that a step's launches have fixed arguments and can
+// be captured once in a CUDA graph: advance_step_kernel opens step j = step + 1 and decides
+// whether it is kept (j % T == 0 and j > burn_in) and at which trajectory index.
+struct StepState {
+    uint32_t step;       // j of the step being run (0 before the first)
+    int32_t kept;        // step j is kept
+    int64_t kept_idx;    // index of step j's state among the kept states
+    int64_t kept_count;  // kept states so far, this step included
+};
+
 struct ProblemView {
     int D, d, nx, KD, KD_pad, d_pad;
     int KD_tc;                   // columns of the tensor-core operand (multiple of its N tile)
@@ -127,11 +137,13 @@ struct SamplerParams {
 // ---------------------------------------------------------------------------------------
 // Launchers (each returns the CUDA launch error).
 // ---------------------------------------------------------------------------------------
-cudaError_t launch_propose(const ProblemView &p, int mode, uint32_t step, const float *x_eval, int64_t n_eval,
+cudaError_t launch_advance_step(StepState *st, int thin, int burn_in, cudaStream_t s);
+// step_dev: when not null the step is read from it (MODE_STEP), else `step` is used
+cudaError_t launch_propose(const ProblemView &p, int mode, uint32_t step, const StepState *step_dev, const float *x_eval, int64_t n_eval,
                            bool want_split, float *rho_norm_out, uint32_t *status, cudaStream_t s);
 cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t rows, double *out_part,
                                 float *p_out, cudaStream_t s);
-cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mode, uint32_t step, bool kept,
+cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mode, const StepState *step_dev, uint32_t step, bool kept,
                           int64_t kept_idx, uint32_t *status, cudaStream_t s);
 cudaError_t launch_pool_reduce(const ProblemView &p, double *out, cudaStream_t s);
 cudaError_t launch_acf(const ProblemView &p, int n_kept, int lmax, double *acf_raw, cudaStream_t s);

@@ -41,7 +41,8 @@ class SamplerCfg(ctypes.Structure):
                 ("acc_hi", ctypes.c_double), ("adapt_factor", ctypes.c_double), ("beta_max", ctypes.c_double),
                 ("thin", ctypes.c_int32), ("burn_in", ctypes.c_int32), ("diag_chains", ctypes.c_int32),
                 ("traj_capacity", ctypes.c_int32), ("acf_lmax", ctypes.c_int32), ("trace_steps", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("qr_passes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("precision", ctypes.c_int32), ("qr_passes", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Diag(ctypes.Structure):

@@ -162,6 +162,31 @@ def test_first_200_decisions(qst, oracle_mod, cuda_ok, prec, q, R, beta0):
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
+def test_four_qubit_posterior_fidelity_within_monte_carlo_error(qst, oracle_mod, cuda_ok, prec):
+    """Configuration 4 (4 qubits): pooled posterior mean and its fidelity to the truth agree
+    with the oracle's within 3 Monte Carlo standard errors (jackknife over 32 chain groups of
+    the oracle's per-chain sums; chains are independent, so groups are i.i.d.)."""
+    R, S = 512, 120
+    prob = W.config_problem(4, num_chains=R, num_steps=S)
+    s = _sampler(qst, prob, prec, diag_chains=0)
+    s.run_chains(S)
+    rho, n = s.posterior_mean()
+    s.close()
+    ref = oracle_mod.run(prob, num_steps=S, want_chain_pool=True)
+    assert n == ref["num_pooled"] == R * S
+    groups = ref["chain_pool"].reshape(32, R // 32, 16, 16).sum(axis=1)      # [32][D][D] sums
+    total = groups.sum(axis=0)
+    loo = (total[None] - groups) / ((R - R // 32) * S)                      # leave-one-group-out means
+    se = np.sqrt((32 - 1) / 32 * ((loo - loo.mean(axis=0)) ** 2).sum(axis=0))
+    assert np.all(np.abs(rho - ref["mean"]) <= 3 * se + 1e-9)
+    f_loo = np.array([oracle_mod.fidelity(m, prob.truth) for m in loo])
+    se_f = np.sqrt((32 - 1) / 32 * ((f_loo - f_loo.mean()) ** 2).sum())
+    f_gpu = oracle_mod.fidelity(rho, prob.truth)
+    f_ref = oracle_mod.fidelity(ref["mean"], prob.truth)
+    assert abs(f_gpu - f_ref) <= 3 * se_f, (f_gpu, f_ref, se_f)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
 def test_pooled_mean_and_acf_match_oracle(qst, oracle_mod, cuda_ok, prec):
     prob = W.config_problem(2, num_chains=512, num_steps=600)
     s = _sampler(qst, prob, prec, diag_chains=8, traj_capacity=600, acf_lmax=50, adapt_interval=100)
@@ -226,6 +251,29 @@ def test_multi_problem_handle_matches_single(qst, cuda_ok):
         assert np.array_equal(multi.posterior_mean(i)[0], single.posterior_mean(0)[0])
         single.close()
     multi.close()
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_graph_replay_matches_plain_launches(qst, cuda_ok, prec):
+    """A step captured once as a CUDA graph (device-side step counter) and replayed gives the
+    same bits as plain launches, across several qst_run_chains calls, thinning and burn-in."""
+    probs = [W.config_problem(q, num_chains=R, num_steps=40) for q, R in [(1, 100), (4, 300), (2, 257)]]
+    kw = dict(diag_chains=4, traj_capacity=16, acf_lmax=4, thin=3, burn_in=5, adapt_interval=7)
+    g = _sampler(qst, probs, prec, use_graph=1, **kw)
+    p = _sampler(qst, probs, prec, use_graph=0, **kw)
+    for n in (20, 1, 17):
+        g.run_chains(n)
+        p.run_chains(n)
+    for i in range(len(probs)):
+        a, b = g.get_state(i), p.get_state(i)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (i, k)
+        assert np.array_equal(g.posterior_mean(i)[0], p.posterior_mean(i)[0])
+        da, db = g.diagnostics(i), p.diagnostics(i)
+        assert np.array_equal(da["tau"], db["tau"]) and da["num_pooled"] == db["num_pooled"]
+    assert g.launch_count() == p.launch_count()
+    g.close()
+    p.close()
 
 
 def test_chain_offset_partition_is_exact(qst, cuda_ok):
