@@ -24,6 +24,8 @@ import dataclasses
 import math
 from typing import List, Optional
 
+import functools
+
 import numpy as np
 
 # single-qubit eigenvectors, index [setting][outcome] ; setting 0=X, 1=Y, 2=Z
@@ -38,22 +40,20 @@ _EIGVEC = np.array(
 )
 
 
+@functools.lru_cache(maxsize=None)
 def pauli_vectors(num_qubits: int) -> np.ndarray:
-    """Measurement vectors ``phi_kl`` (``Lambda_kl = |phi_kl><phi_kl|``), shape ``[K*D, D]``."""
+    """Measurement vectors ``phi_kl`` (``Lambda_kl = |phi_kl><phi_kl|``), shape ``[K*D, D]``,
+    index k*D + l as for ``pauli_povms``.  Cached per Q and read-only."""
     q = int(num_qubits)
     if q < 1:
         raise ValueError("num_qubits must be >= 1")
-    d = 1 << q
-    k_count = 3 ** q
-    out = np.empty((k_count * d, d), dtype=np.complex128)
-    for k in range(k_count):
-        settings = [(k // 3 ** (q - 1 - i)) % 3 for i in range(q)]
-        for l in range(d):
-            bits = [(l >> (q - 1 - i)) & 1 for i in range(q)]
-            v = np.array([1.0 + 0j])
-            for s, b in zip(settings, bits):
-                v = np.kron(v, _EIGVEC[s, b])
-            out[k * d + l] = v
+    t = np.ones((1, 1, 1), dtype=np.complex128)            # [setting, outcome, component]
+    for _ in range(q):
+        k, l, c = t.shape
+        t = np.einsum("klc,sbm->ksblcm", t, _EIGVEC).reshape(k * 3, 2, l, c * 2)
+        t = t.transpose(0, 2, 1, 3).reshape(k * 3, l * 2, c * 2)
+    out = np.ascontiguousarray(t.reshape(-1, 1 << q))
+    out.setflags(write=False)
     return out
 
 
@@ -68,25 +68,29 @@ _PROJ = np.array(
 )
 
 
+@functools.lru_cache(maxsize=None)
 def pauli_povms(num_qubits: int):
     """All ``3**Q`` Pauli-basis POVMs as real and imaginary ``[K*D, D, D]`` float64 arrays.
 
     Built as Kronecker products of the exact single-qubit projectors, so every entry is
-    0 or +-2^-m (times 1 or i) with no rounding.
+    0 or +-2^-m (times 1 or i) with no rounding.  Index k*D + l with setting
+    k = sum_q s_q 3^(Q-1-q) and outcome l = sum_q b_q 2^(Q-1-q), qubit 0 most significant.
+    The arrays are cached per Q and read-only.
     """
     q = int(num_qubits)
-    d = 1 << q
-    k_count = 3 ** q
-    lam = np.empty((k_count * d, d, d), dtype=np.complex128)
-    for k in range(k_count):
-        settings = [(k // 3 ** (q - 1 - i)) % 3 for i in range(q)]
-        for l in range(d):
-            bits = [(l >> (q - 1 - i)) & 1 for i in range(q)]
-            m = np.array([[1.0 + 0j]])
-            for s_, b in zip(settings, bits):
-                m = np.kron(m, _PROJ[s_, b])
-            lam[k * d + l] = m
-    return np.ascontiguousarray(lam.real), np.ascontiguousarray(lam.imag)
+    if q < 1:
+        raise ValueError("num_qubits must be >= 1")
+    t = np.ones((1, 1, 1, 1), dtype=np.complex128)          # [setting, outcome, row, col]
+    for _ in range(q):
+        k, l, r, c = t.shape
+        t = np.einsum("klij,sbmn->ksblimjn", t, _PROJ)
+        t = t.reshape(k * 3, 2, l, r * 2, c * 2)            # (k s), b, l, (i m), (j n)
+        t = t.transpose(0, 2, 1, 3, 4).reshape(k * 3, l * 2, r * 2, c * 2)   # outcome l*2 + b
+    lam = t.reshape(-1, 1 << q, 1 << q)
+    re, im = np.ascontiguousarray(lam.real), np.ascontiguousarray(lam.imag)
+    re.setflags(write=False)
+    im.setflags(write=False)
+    return re, im
 
 
 def ginibre_state(dim: int, rank: int, rng: np.random.Generator) -> np.ndarray:
