@@ -57,7 +57,7 @@ typedef enum {
 /* One tomography problem (Sec. III Steps 1-4).  All pointers are host memory,
  * read during qst_create only. */
 typedef struct {
-    int32_t num_qubits;     /* Q, 1..5 (D = 2^Q); Q = 5 only with QST_PREC_FP32 */
+    int32_t num_qubits;     /* Q, 1..5 (D = 2^Q) */
     int32_t num_povms;      /* K, the number of measurement settings (3^Q for Pauli) */
     const int32_t *counts;  /* [K*D] outcome counts c_kl >= 0, setting-major */
     const double *povm_re;  /* [K*D][D][D] row-major real parts of Lambda_kl */
@@ -136,7 +136,7 @@ qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_prob
                               const qst_sampler_cfg *cfg, size_t *bytes);
 
 /* Validates the problems (Sec. III Step 1: counts >= 0; each Lambda_kl Hermitian and
- * sum_l Lambda_kl = I to 1e-12; Q in 1..5 (Q = 5: FP32 form only, else QST_ERR_UNSUPPORTED); R >= 1; T >= 1; 0 < beta0 <= beta_max <= 1 for the
+ * sum_l Lambda_kl = I to 1e-12; Q in 1..5; R >= 1; T >= 1; 0 < beta0 <= beta_max <= 1 for the
  * config's and every problem's own beta0 (0 meaning the config's);
  * for QST_PREC_BF16X3 every packed projector entry exactly representable in bf16),
  * packs the projectors, uploads everything into the workspace and enqueues the chains'

@@ -118,10 +118,6 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
 qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sampler_cfg *cfg) {
     if (d.num_qubits < 1 || d.num_qubits > 5)
         return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..5", idx, d.num_qubits);
-    if (d.num_qubits == 5 && cfg->precision == QST_PREC_BF16X3)
-        return fail(QST_ERR_UNSUPPORTED,
-                    "problem %d: the tensor-core form holds a 128-chain tile of A in shared memory and TMEM, "
-                    "which covers Q <= 4; use QST_PREC_FP32 for Q = 5", idx);
     if (d.num_povms < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_povms must be >= 1", idx);
     if (!d.counts || !d.povm_re || !d.povm_im) return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
     if (d.num_chains < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_chains must be >= 1", idx);
@@ -191,7 +187,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         hp.beta0 = d.beta0 > 0.0 ? d.beta0 : cfg->beta0;
         const bool tc = cfg->precision == QST_PREC_BF16X3;
         if (tc) {
-            const int nt = tc_column_tile(v.KD);
+            const int nt = tc_column_tile(v.D, v.KD);
             if (nt <= 0) return fail(QST_ERR_UNSUPPORTED, "problem %d: no tensor-core column tile for %d projectors", i, v.KD);
             v.KD_tc = round_up(v.KD, nt);
         } else {

@@ -637,6 +637,214 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// ---- five qubits (D = 32): A streamed with every N tile ------------------------------------
+// A 128-chain tile of A is 3 x 1024 bf16 per chain (768 KB), more than an SM holds, so here a
+// work unit is one (chain tile, N tile) pair and A's K chunks are streamed with P's through a
+// 2-stage ring: stage = one 64-wide K chunk of A's hi, mid and lo splits (3 x 16 KB) and of
+// the P tile (256 projectors x 64 = 32 KB).  N tiles are 256 wide (M128 N256 K16 MMAs, both
+// operands from shared memory); TMEM holds two 256-column accumulators.  The epilogue is the
+// one above, on 64-column slices, with the weights read through L1 (they do not fit beside
+// the ring).
+constexpr int TCW_N = 256;
+constexpr int TCW_STAGES = 2;
+constexpr int TCW_STAGE_BYTES = 3 * TC_ATOM_BYTES + TCW_N * TC_KATOM * 2;   // 80 KB
+constexpr int TCW_EPI_COLS = TCW_N / TC_EPI_PER_QUAD;                        // 64
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    project_tc_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    constexpr int D = 32;
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ __align__(8) uint64_t bar_full[TCW_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TCW_STAGES];
+    __shared__ __align__(8) uint64_t bar_acc_full[2];
+    __shared__ __align__(8) uint64_t bar_acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_mma_done;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_flag;
+
+    const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x / 32), 0);
+    const int lane = threadIdx.x % 32;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+    const int nk = a.n_katoms;   // 16 K chunks per split
+    // unit u: chain tile u / ntiles, N tile u % ntiles
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TCW_STAGES; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&bar_acc_full[s]), 1);
+            mbar_init(smem_u32(&bar_acc_empty[s]), 4 * TC_EPI_PER_QUAD * 32);
+        }
+        mbar_init(smem_u32(&bar_mma_done), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(2 * TCW_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    if (warp == 0) {
+        // ---------------- producer of A and P chunks ----------------
+        int it = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+            const int m0 = (int)((u / a.ntiles) * TC_M);
+            const int t = (int)(u % a.ntiles);
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int s = it % TCW_STAGES;
+                const uint32_t ph = (uint32_t)(it / TCW_STAGES) & 1u;
+                if (!mbar_wait_warp(smem_u32(&bar_empty[s]), ph ^ 1u, &abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                if (elect_one()) {
+                    uint8_t *st = base + (size_t)s * TCW_STAGE_BYTES;
+                    mbar_expect_tx(smem_u32(&bar_full[s]), (uint32_t)TCW_STAGE_BYTES);
+                    for (int sp = 0; sp < 3; ++sp)
+                        tma_load_2d(smem_u32(st + (size_t)sp * TC_ATOM_BYTES), &tmA, (sp * nk + kc) * TC_KATOM, m0,
+                                    smem_u32(&bar_full[s]));
+                    tma_load_2d(smem_u32(st + 3 * TC_ATOM_BYTES), &tmB, kc * TC_KATOM, t * TCW_N, smem_u32(&bar_full[s]));
+                }
+                __syncwarp();
+            }
+        }
+        if (!ok && lane == 0) {
+            for (int back = 1; back <= TCW_STAGES && it - back >= 0; ++back) {
+                const int i2 = it - back;
+                mbar_drain(smem_u32(&bar_full[i2 % TCW_STAGES]), (uint32_t)(i2 / TCW_STAGES) & 1u);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        int it = 0, tcount = 0;
+        bool ok = true;
+        const uint64_t desc0 = sw128_desc(smem_u32(base));
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x, ++tcount) {
+            const int t = (int)(u % a.ntiles);
+            const int acc = tcount & 1;
+            const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
+            if (!mbar_wait_warp(smem_u32(&bar_acc_empty[acc]), use ^ 1u, &abort_flag, a.status)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem + (uint32_t)(acc * TCW_N);
+            const int n_valid = min(TCW_N, (a.KD - t * TCW_N + 15) / 16 * 16);
+            const uint32_t idesc = mma_idesc(n_valid);
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int s = it % TCW_STAGES;
+                const uint32_t ph = (uint32_t)(it / TCW_STAGES) & 1u;
+                if (!mbar_wait_warp(smem_u32(&bar_full[s]), ph, &abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t sd = desc0 + (uint64_t)(((size_t)s * TCW_STAGE_BYTES) >> 4);
+                const uint64_t bd = sd + (uint64_t)((3 * TC_ATOM_BYTES) >> 4);
+                if (elect_one()) {
+#pragma unroll
+                    for (int sp = 0; sp < 3; ++sp) {
+#pragma unroll
+                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)
+                            mma_bf16(d_tmem, sd + (uint64_t)((sp * TC_ATOM_BYTES) >> 4) + 2 * kk, bd + 2 * kk, idesc,
+                                     (kc | sp | kk) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&bar_empty[s]));
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (elect_one()) mma_commit(smem_u32(&bar_acc_full[acc]));
+            __syncwarp();
+        }
+        if (!ok && lane == 0) {
+            mma_commit(smem_u32(&bar_mma_done));
+            mbar_drain(smem_u32(&bar_mma_done), 0u);
+        }
+        __syncwarp();
+    } else if (warp >= TC_FIRST_EPI) {
+        // ---------------- epilogue (64-column slices) ----------------
+        const int quad = warp & 3;
+        const int sub = (warp - TC_FIRST_EPI) / 4;
+        const int col0 = sub * TCW_EPI_COLS;
+        int tcount = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x, ++tcount) {
+            const int t = (int)(u % a.ntiles);
+            const int64_t grow = (u / a.ntiles) * TC_M + quad * 32 + lane;
+            const bool valid = grow < a.rows;
+            const double tr = valid ? a.trace[grow] : 1.0;
+            const float inv_t = (float)(1.0 / tr);
+            const float t_hi = (float)tr;
+            const float t_lo = (float)(tr - (double)t_hi);
+            const int acc = tcount & 1;
+            const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
+            if (!mbar_wait_warp(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            float tile_sum = 0.0f;
+            int xmin = 0x7fffffff;
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+                const int n0 = t * TCW_N + col0 + 32 * half;   // one setting of 32 outcomes
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TCW_N + col0 + 32 * half), v);
+                if (half == 1) {
+                    tc_fence_before();
+                    mbar_arrive(smem_u32(&bar_acc_empty[acc]));   // both halves are in registers
+                }
+                if (n0 >= a.KD) continue;
+                const float pk = __ldg(a.ptot + n0 / D);
+                if (pk > 0.0f) {
+                    float2 sh = splat2(0.0f), sl = splat2(0.0f), dev = splat2(0.0f);
+#pragma unroll
+                    for (int l = 0; l < D; l += 2) {
+                        const float2 q = make_float2(v[l], v[l + 1]);
+                        const float2 h = sub2(add2(q, splat2(12.0f)), splat2(12.0f));
+                        sh = add2(sh, h);
+                        sl = add2(sl, sub2(q, h));
+                        const float4 w = __ldg(a.colw + (n0 + l) / 2);
+                        const float2 c = __ldg(reinterpret_cast<const float2 *>(a.cnt + n0 + l));
+                        const float2 x = fma2(q, make_float2(w.x, w.y), make_float2(w.z, w.w));
+                        xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
+                        dev = fma2(c, log_poly2(x), dev);
+                    }
+                    const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;
+                    const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
+                    const float l1p = fabsf(rel) < 0x1p-10f
+                                          ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
+                                          : log1pf(rel);
+                    tile_sum += (dev.x + dev.y) - pk * l1p;
+                }
+                if (a.p_out && valid) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
+                }
+            }
+            if (xmin < 0x00800000) tile_sum = -INFINITY;
+            if (valid) a.out[(int64_t)(t * 4 + sub) * a.rows + grow] = (double)tile_sum;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TCW_N));
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -694,12 +902,13 @@ cudaError_t launch_tc_d(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t s
 }
 }  // namespace
 
-int tc_column_tile(int KD) { return KD > 0 ? TC_N : 0; }
-// (a setting's D outcome columns never straddle a 128-column tile: D divides 128)
+int tc_column_tile(int D, int KD) { return KD > 0 ? (D == 32 ? TCW_N : TC_N) : 0; }
+// (a setting's D outcome columns never straddle a tile: D divides the tile width)
 
 // Partial sums per chain: four column slices times the column groups that split the N tiles
 // when there are too few chain tiles to occupy every SM.
 int tc_ngroups(const ProblemView &p, int64_t rows) {
+    if (p.D == 32) return 4 * (p.KD_tc / TCW_N);   // one partial per N tile and column slice
     const int64_t mt = (rows + TC_M - 1) / TC_M;
     const int ntiles = p.KD_tc / TC_N;
     int g = 1;
@@ -709,19 +918,21 @@ int tc_ngroups(const ProblemView &p, int64_t rows) {
 
 cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, int64_t rows, TcPlan **plan) {
     *plan = nullptr;
-    if (p.d_pad % TC_KATOM != 0 || p.KD_tc % TC_N != 0 || p.KD_tc <= 0) return cudaErrorNotSupported;
+    const bool wide = p.D == 32;
+    const int n_tile = wide ? TCW_N : TC_N;
+    if (p.d_pad % TC_KATOM != 0 || p.KD_tc % n_tile != 0 || p.KD_tc <= 0) return cudaErrorNotSupported;
     const int n_katoms = p.d_pad / TC_KATOM;
-    if (n_katoms > TC_MAX_KCHUNK) return cudaErrorNotSupported;
+    if (!wide && n_katoms > TC_MAX_KCHUNK) return cudaErrorNotSupported;
     if (p.d_pad != tc_dpad(p.D)) return cudaErrorNotSupported;
-    if (tc_smem_bytes(n_katoms, p.KD_tc, p.D) > 227 * 1024 - 256) return cudaErrorNotSupported;
+    if (!wide && tc_smem_bytes(n_katoms, p.KD_tc, p.D) > 227 * 1024 - 256) return cudaErrorNotSupported;
     if (reinterpret_cast<uintptr_t>(A_split) % 16 != 0 || reinterpret_cast<uintptr_t>(p.Pbf) % 16 != 0)
         return cudaErrorMisalignedAddress;
     TcPlan *pl = new TcPlan();
     pl->n_katoms = n_katoms;
     pl->a_split = A_split;
-    pl->ntiles = p.KD_tc / TC_N;
+    pl->ntiles = p.KD_tc / n_tile;
     const bool ok_a = encode_bf16_2d(&pl->a, A_split, (uint64_t)3 * p.d_pad, (uint64_t)rows, TC_KATOM, TC_M);
-    const bool ok_b = encode_bf16_2d(&pl->b, p.Pbf, (uint64_t)p.d_pad, (uint64_t)p.KD_tc, TC_KATOM, TC_N);
+    const bool ok_b = encode_bf16_2d(&pl->b, p.Pbf, (uint64_t)p.d_pad, (uint64_t)p.KD_tc, TC_KATOM, n_tile);
     if (!ok_a || !ok_b) {
         delete pl;
         return cudaErrorInvalidValue;
@@ -753,7 +964,6 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     a.ngroups = groups;
     a.tiles_per_group = (plan->ntiles + groups - 1) / groups;
     a.units = ((rows + TC_M - 1) / TC_M) * groups;
-    const size_t smem = tc_smem_bytes(plan->n_katoms, plan->ntiles * TC_N, p.D);
     static int num_sms = 0;
     if (num_sms == 0) {
         int dev = 0;
@@ -762,6 +972,18 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
             num_sms = 148;
     }
     dim3 grid((unsigned)std::min<int64_t>(a.units, num_sms));
+    if (p.D == 32) {   // units: (chain tile, N tile) pairs
+        const size_t smem = 1024 + (size_t)TCW_STAGES * TCW_STAGE_BYTES;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(project_tc_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        project_tc_wide_kernel<<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
+        return cudaGetLastError();
+    }
+    const size_t smem = tc_smem_bytes(plan->n_katoms, plan->ntiles * TC_N, p.D);
     switch (p.D) {
         case 2: return launch_tc_d<2>(plan, a, grid, smem, s);
         case 4: return launch_tc_d<4>(plan, a, grid, smem, s);

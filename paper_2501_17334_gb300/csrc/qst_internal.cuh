@@ -160,7 +160,7 @@ void tc_plan_destroy(TcPlan *plan);
 cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t rows, double *out_part,
                               float *p_out, uint32_t *status, cudaStream_t s);
 int tc_ngroups(const ProblemView &p, int64_t rows);
-int tc_column_tile(int KD);       // N tile of the tensor-core contraction for KD columns (0 = unsupported)
+int tc_column_tile(int D, int KD);       // N tile of the tensor-core contraction for KD columns (0 = unsupported)
 int fp32_ngroups(const ProblemView &p, int64_t rows);
 void set_last_error(const char *msg);   // message returned by qst_last_error()
 int accept_slots(int64_t R);

@@ -78,10 +78,10 @@ def test_validation_rejects_bad_inputs(qst):
     assert "identity" in qst.load().qst_last_error().decode() or True
 
 
-def test_five_qubits_need_the_fp32_form(qst):
+def test_five_qubits_are_accepted_and_six_refused(qst):
     prob = W.five_qubit_problem(num_chains=8, num_steps=1)
     assert qst.workspace_size([prob], qst.default_config()) > 0
-    assert _status(lambda: qst.workspace_size([prob], qst.default_config(precision=qst.PREC_BF16X3))) == 7
+    assert qst.workspace_size([prob], qst.default_config(precision=qst.PREC_BF16X3)) > 0
     six = W.five_qubit_problem(num_chains=8, num_steps=1)
     six.num_qubits = 6
     assert _status(lambda: qst.workspace_size([six], qst.default_config())) == 1
