@@ -212,6 +212,47 @@ def time_form(qst, prob, precision, steps, warmup, world, chain_offset):
     return s, ms, launches, kernel_ms
 
 
+def time_handle(qst, probs, precision, steps, warmup):
+    """ms per step of one handle over `probs` (device-timed, steps after warmup)."""
+    import torch
+    s = qst.Sampler(probs, precision=precision, diag_chains=0)
+    s.run_chains(warmup)
+    stream = torch.cuda.current_stream()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    s.run_chains(steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop) / steps
+    s.close()
+    return ms
+
+
+def other_configs(qst, W):
+    """The other workloads, measured briefly (one handle each; chain state resident)."""
+    out = {}
+    for c, form, steps in [(1, "fp32", 2000), (2, "fp32", 1000), (3, "fp32", 300), (3, "bf16x3", 300)]:
+        prob = W.config_problem(c)
+        prec = qst.PREC_FP32 if form == "fp32" else qst.PREC_BF16X3
+        ms = time_handle(qst, prob, prec, steps, 5)
+        out[f"config{c}_{form}"] = {"chains": prob.num_chains, "qubits": prob.num_qubits, "ms_per_step": ms,
+                                    "chain_steps_per_s": prob.num_chains / (ms / 1000.0), "steps": steps}
+    # configuration 5: 64 problems of 1..5 qubits with uneven chain counts in one handle (one
+    # launch per kernel and problem per step, replayed as a CUDA graph), mixed form; the plain
+    # FP32 form on the same batch for comparison (few steps: its 5-qubit projections are slow)
+    batch = W.heterogeneous_batch(64)
+    chains = sum(p.num_chains for p in batch)
+    ms_mixed = time_handle(qst, batch, qst.PREC_BF16X3, 20, 3)
+    ms_plain = time_handle(qst, batch, qst.PREC_FP32, 3, 1)
+    out["config5_heterogeneous"] = {
+        "problems": len(batch), "chains": chains,
+        "qubits_hist": [sum(p.num_qubits == q for p in batch) for q in range(1, 6)],
+        "ms_per_step_bf16x3": ms_mixed, "chain_steps_per_s_bf16x3": chains / (ms_mixed / 1000.0),
+        "ms_per_step_fp32": ms_plain, "chain_steps_per_s_fp32": chains / (ms_plain / 1000.0)}
+    return out
+
+
 def logl_error(qst, oracle, s, prob, nsample=1024):
     """|log L_gpu - log L_oracle| on the current states of nsample chains (identical y)."""
     import torch
@@ -300,6 +341,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the brief runs of the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -425,6 +467,8 @@ def main():
         line["speedup_vs_plain_fp32"] = results["fp32"]["ms"] / head["ms"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(oracle, prob)
+    if world == 1 and not args.no_configs:
+        line["configs"] = other_configs(qst, W)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
