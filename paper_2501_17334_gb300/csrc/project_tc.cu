@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x / 32), 0);   // provably warp-uniform
     const int lane = threadIdx.x % 32;
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned, by pointer arithmetic on the shared array (so accesses stay ld.shared)
+    uint8_t *base = dyn_smem + ((1024u - (smem_u32(dyn_smem) & 1023u)) & 1023u);
     const int nk = a.n_katoms;
     uint8_t *smA = base;                                          // atom (split sp < 2, chunk kc) at sp * nk + kc
     uint8_t *smB = base + (size_t)2 * nk * TC_ATOM_BYTES;
@@ -664,7 +665,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x / 32), 0);
     const int lane = threadIdx.x % 32;
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned, by pointer arithmetic on the shared array (so accesses stay ld.shared)
+    uint8_t *base = dyn_smem + ((1024u - (smem_u32(dyn_smem) & 1023u)) & 1023u);
     const int nk = a.n_katoms;   // 16 K chunks per split
     // unit u: chain tile u / ntiles, N tile u % ntiles
     if (threadIdx.x == 0) {
