@@ -153,7 +153,8 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
  * Asynchronous on the handle's stream; resumable (step numbering continues).
  * A step is one small kernel that advances the device-side step counter, then the
  * proposal, projection and accept kernels of every problem.  With use_graph the first
- * call captures that sequence once (on a private stream) and every step launches the
+ * call captures that sequence once (on private streams, the problems of a handle on up
+ * to eight parallel branches, since they are independent) and every step launches the
  * graph; the results are bit-identical to plain launches.
  * Errors: QST_ERR_INVALID_ARG if num_steps < 0. */
 qst_status qst_run_chains(qst_handle *h, int64_t num_steps);

@@ -305,6 +305,9 @@ struct qst_handle {
     uint32_t *d_status = nullptr;
     StepState *d_step = nullptr;
     cudaStream_t capture_stream = nullptr;   // private stream the step graph is captured on
+    static constexpr int kBranches = 8;      // problems of a graph step run on up to 8 parallel branches
+    cudaStream_t branch[kBranches] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kBranches] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_kernels = 0;               // kernel launches one replay performs
@@ -558,37 +561,67 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
 namespace {
 
 // One step's launches on h->stream: open step j on the device, then every problem's
-// proposal, projection and accept, all reading j from the device.
-qst_status enqueue_step(qst_handle *h) {
+// proposal, projection and accept, all reading j from the device.  With `branches` (graph
+// capture) the problems are spread over parallel branches -- they are independent -- so
+// the graph runs the kernels of different problems concurrently.
+qst_status enqueue_problem(qst_handle *h, HostProblem &hp) {
+    ProblemView &v = hp.v;
+    qst_status st = launch(h, QST_KERNEL_PROPOSE, "propose", [&] {
+        return launch_propose(v, MODE_STEP, 0u, h->d_step, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
+    });
+    if (st != QST_OK) return st;
+    st = enqueue_projection(h, hp, v.R, nullptr);
+    if (st != QST_OK) return st;
+    return launch(h, QST_KERNEL_ACCEPT, "accept", [&] {
+        return launch_accept(v, h->sp, MODE_STEP, h->d_step, 0u, false, 0, h->d_status, h->stream);
+    });
+}
+
+qst_status enqueue_step(qst_handle *h, bool branches) {
     qst_status st = launch(h, QST_KERNEL_ACCEPT, "advance step",
                            [&] { return launch_advance_step(h->d_step, h->cfg.thin, h->cfg.burn_in, h->stream); });
     if (st != QST_OK) return st;
-    for (auto &hp : h->plan.probs) {
-        ProblemView &v = hp.v;
-        st = launch(h, QST_KERNEL_PROPOSE, "propose", [&] {
-            return launch_propose(v, MODE_STEP, 0u, h->d_step, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
-        });
-        if (st != QST_OK) return st;
-        st = enqueue_projection(h, hp, v.R, nullptr);
-        if (st != QST_OK) return st;
-        st = launch(h, QST_KERNEL_ACCEPT, "accept", [&] {
-            return launch_accept(v, h->sp, MODE_STEP, h->d_step, 0u, false, 0, h->d_status, h->stream);
-        });
-        if (st != QST_OK) return st;
+    const int np = (int)h->plan.probs.size();
+    if (!branches || np == 1) {
+        for (auto &hp : h->plan.probs) {
+            st = enqueue_problem(h, hp);
+            if (st != QST_OK) return st;
+        }
+        return QST_OK;
+    }
+    const int nb = np < qst_handle::kBranches ? np : qst_handle::kBranches;
+    cudaStream_t origin = h->stream;
+    QST_CUDA(cudaEventRecord(h->fork_ev, origin), "fork");
+    for (int b = 0; b < nb; ++b) QST_CUDA(cudaStreamWaitEvent(h->branch[b], h->fork_ev, 0), "branch wait");
+    for (int i = 0; i < np && st == QST_OK; ++i) {
+        h->stream = h->branch[i % nb];
+        st = enqueue_problem(h, h->plan.probs[i]);
+    }
+    h->stream = origin;
+    if (st != QST_OK) return st;
+    for (int b = 0; b < nb; ++b) {
+        QST_CUDA(cudaEventRecord(h->join_ev[b], h->branch[b]), "join");
+        QST_CUDA(cudaStreamWaitEvent(origin, h->join_ev[b], 0), "join wait");
     }
     return QST_OK;
 }
 
 // Captures enqueue_step once on the private capture stream and instantiates it.
 qst_status build_step_graph(qst_handle *h) {
-    if (!h->capture_stream)
+    if (!h->capture_stream) {
         QST_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "create capture stream");
+        for (int b = 0; b < qst_handle::kBranches; ++b) {
+            QST_CUDA(cudaStreamCreateWithFlags(&h->branch[b], cudaStreamNonBlocking), "create branch stream");
+            QST_CUDA(cudaEventCreateWithFlags(&h->join_ev[b], cudaEventDisableTiming), "create event");
+        }
+        QST_CUDA(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming), "create event");
+    }
     cudaStream_t user = h->stream;
     const int64_t launches0 = h->launches;
     h->stream = h->capture_stream;
     cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
     qst_status st = QST_OK;
-    if (e == cudaSuccess) st = enqueue_step(h);
+    if (e == cudaSuccess) st = enqueue_step(h, true);
     cudaGraph_t g = nullptr;
     const cudaError_t e_end = (e == cudaSuccess) ? cudaStreamEndCapture(h->capture_stream, &g) : e;
     h->stream = user;
@@ -623,7 +656,7 @@ qst_status qst_run_chains(qst_handle *h, int64_t num_steps) {
             QST_CUDA(cudaGraphLaunch(h->graph_exec, h->stream), "launch step graph");
             h->launches += h->graph_kernels;
         } else {
-            qst_status st = enqueue_step(h);
+            qst_status st = enqueue_step(h, false);
             if (st != QST_OK) return st;
         }
         h->steps_done = j;
@@ -771,6 +804,11 @@ void qst_destroy(qst_handle *h) {
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    for (int b = 0; b < qst_handle::kBranches; ++b) {
+        if (h->branch[b]) cudaStreamDestroy(h->branch[b]);
+        if (h->join_ev[b]) cudaEventDestroy(h->join_ev[b]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->own_ws) cudaFree(h->ws);
     delete h;
 }
