@@ -87,7 +87,10 @@ typedef struct {
     int32_t use_graph;      /* 1 (default): qst_run_chains replays one step captured as a CUDA graph
                                (the step counter lives on the device); 0: plain launches. Kernel
                                timing (qst_set_profiling) always uses plain launches */
-    int32_t reserved[2];    /* zero */
+    int32_t autotune;       /* 1 (default): qst_create times the projection of every problem with
+                               each candidate number of column groups (the split of its N tiles
+                               over CTAs) and keeps the fastest; 0: a fixed rule */
+    int32_t reserved[1];    /* zero */
 } qst_sampler_cfg;
 
 /* Diagnostics of one problem (Sec. IV). */
@@ -104,7 +107,7 @@ typedef struct {
     double tau_max;
     double n_eff;            /* N R / tau_mean (Sec. IV) */
     uint32_t device_status;  /* raw status bits */
-    uint32_t reserved;
+    uint32_t column_groups;  /* column groups of the projection schedule in use (autotuned or fixed) */
 } qst_diag;
 
 typedef struct qst_handle qst_handle;

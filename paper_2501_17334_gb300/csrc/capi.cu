@@ -80,6 +80,8 @@ struct Layout {
 struct HostProblem {
     ProblemView v{};
     int Q = 0, K = 0, KDmax = 0;
+    int part_slots = 0;               // partial sums per chain the workspace holds (largest schedule)
+    std::vector<int> group_choices;   // candidate ngroups values for the autotuner
     double beta0 = 0.0;
     Layout off{};
     std::vector<float> P32;
@@ -112,6 +114,7 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
     if (cfg->qr_passes != 1 && cfg->qr_passes != 2)
         return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1 or 2");
     if (cfg->use_graph != 0 && cfg->use_graph != 1) return fail(QST_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+    if (cfg->autotune != 0 && cfg->autotune != 1) return fail(QST_ERR_INVALID_ARG, "autotune must be 0 or 1");
     return QST_OK;
 }
 
@@ -235,12 +238,24 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         }
         v.C0 = C0;
         v.Ntot = Ntot;
-        v.ngroups = 1;
+        // column groups: a fixed rule, and the candidates the autotuner may time instead
         if (tc) {
             v.ngroups = tc_ngroups(v, v.R);
+            const int ntiles = v.KD_tc / tc_column_tile(v.D, v.KD);
+            if (v.D == 32) {
+                hp.group_choices = {v.ngroups};
+            } else {
+                for (int g = 1; g < ntiles; g *= 2) hp.group_choices.push_back(4 * g);
+                hp.group_choices.push_back(4 * ntiles);
+            }
         } else {
             v.ngroups = fp32_ngroups(v, v.R);
+            const int nt = v.KD_pad / 128;
+            for (int g = 1; g < nt; g *= 2) hp.group_choices.push_back(g);
+            hp.group_choices.push_back(nt);
         }
+        hp.part_slots = v.ngroups;
+        for (int g : hp.group_choices) hp.part_slots = std::max(hp.part_slots, g);
         v.qr_passes = cfg->qr_passes;
         v.n_slots = accept_slots(v.R);
         v.n_diag = (int)std::min<int64_t>(cfg->diag_chains, v.R);
@@ -262,7 +277,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         L.rho_split = take(tc ? sizeof(__nv_bfloat16) * 3 * R * v.d_pad : 0);
         L.trace_prop = take(sizeof(double) * R);
         L.logl_cur = take(sizeof(double) * R);
-        L.logl_part = take(sizeof(double) * v.ngroups * R);
+        L.logl_part = take(sizeof(double) * hp.part_slots * R);
         L.beta = take(sizeof(double) * R);
         L.coef = take(sizeof(float2) * R);
         L.acc_win = take(sizeof(int32_t) * R);
@@ -468,6 +483,7 @@ void qst_default_config(qst_sampler_cfg *cfg) {
     cfg->precision = QST_PREC_FP32;
     cfg->qr_passes = 2;
     cfg->use_graph = 1;
+    cfg->autotune = 1;
 }
 
 qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_problems, const qst_sampler_cfg *cfg,
@@ -479,6 +495,49 @@ qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_prob
     *bytes = plan.bytes;
     return QST_OK;
 }
+
+namespace {
+
+// Times the projection of every problem with each candidate column-group count (one warm-up
+// launch, then three timed ones on the handle's stream, on the proposal buffers that hold
+// rho(y0) after initialisation) and keeps the fastest.  Only the schedule changes: every
+// candidate computes the same partial sums, split differently over CTAs.
+qst_status autotune_groups(qst_handle *h) {
+    cudaEvent_t e0, e1;
+    QST_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    QST_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    qst_status st = QST_OK;
+    for (auto &hp : h->plan.probs) {
+        if (hp.group_choices.size() < 2) continue;
+        int best = hp.v.ngroups;
+        float best_ms = 0.0f;
+        for (int g : hp.group_choices) {
+            hp.v.ngroups = g;
+            st = enqueue_projection(h, hp, hp.v.R, nullptr);
+            if (st != QST_OK) break;
+            if (cudaEventRecord(e0, h->stream) != cudaSuccess) { st = fail(QST_ERR_CUDA, "autotune: event"); break; }
+            for (int r = 0; r < 3 && st == QST_OK; ++r) st = enqueue_projection(h, hp, hp.v.R, nullptr);
+            if (st != QST_OK) break;
+            float ms = 0.0f;
+            if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = fail(QST_ERR_CUDA, "autotune: timing");
+                break;
+            }
+            if (best_ms == 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best = g;
+            }
+        }
+        hp.v.ngroups = best;
+        if (st != QST_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace
 
 qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, const qst_sampler_cfg *cfg,
                       void *d_workspace, size_t workspace_bytes, void *cuda_stream, qst_handle **out) {
@@ -553,6 +612,10 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
         if (st != QST_OK) return st;
         std::vector<float>().swap(hp.P32);
         std::vector<__nv_bfloat16>().swap(hp.Pbf);
+    }
+    if (cfg->autotune) {
+        st = autotune_groups(h.get());
+        if (st != QST_OK) return st;
     }
     *out = h.release();
     return QST_OK;
@@ -737,6 +800,7 @@ qst_status qst_diagnostics(qst_handle *h, int32_t problem, qst_diag *out, double
     uint32_t status = 0;
     cudaMemcpy(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost);
     out->device_status = status;
+    out->column_groups = (uint32_t)(is_tc(h) ? hp->v.ngroups / 4 : hp->v.ngroups);
     if (st != QST_OK) return st;
     double bmin = 1e300, bmax = -1e300, bsum = 0.0;
     int64_t acc_sum = 0, nonfinite = 0;

@@ -276,6 +276,23 @@ def test_graph_replay_matches_plain_launches(qst, cuda_ok, prec):
     p.close()
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_autotuned_schedule_gives_the_same_chains(qst, cuda_ok, prec):
+    """The autotuner only changes how the projection's N tiles are split over CTAs: the
+    partial sums are the same numbers associated differently in FP64, so the chains agree."""
+    prob = W.config_problem(2, num_chains=700, num_steps=30)
+    tuned = _sampler(qst, prob, prec, diag_chains=0, autotune=1)
+    fixed = _sampler(qst, prob, prec, diag_chains=0, autotune=0)
+    tuned.run_chains(30)
+    fixed.run_chains(30)
+    a, b = tuned.get_state(), fixed.get_state()
+    assert np.array_equal(a["accepts"], b["accepts"])
+    assert np.allclose(a["logl"], b["logl"], rtol=1e-12, atol=0)
+    assert tuned.diagnostics()["column_groups"] >= 1 and fixed.diagnostics()["column_groups"] >= 1
+    tuned.close()
+    fixed.close()
+
+
 def test_chain_offset_partition_is_exact(qst, cuda_ok):
     """Chains keyed by global id: [0,96) at once equals [0,40) + [40,96) as two handles."""
     prob = W.config_problem(3, num_chains=96, num_steps=40)
