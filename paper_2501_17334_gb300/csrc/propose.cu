@@ -374,39 +374,94 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         __syncwarp();
     }
 
-    // ---- 3. W = (U + I) G, column j: W[:,j] = G[:,j] + sum_k U[:,k] G[k,j] ------------------
-    float gr[D], gi[D], wr[D], wi[D];
-    if (active) {
-        load_column<D>(gsrc + j * D, gr);
-        load_column<D>(gsrc + d + j * D, gi);
+    if constexpr (D == 16) {
+        // ---- 3. W = (U + I) G in 4x4 register blocks: lane (bi, bj) forms W[4bi.., 4bj..] -----
+        // (four FMAs per float loaded from shared memory instead of two; G staged row-major
+        // in area B, free between the re-orthogonalisation and the packed rho)
+        float2 *gs2 = reinterpret_cast<float2 *>(sm + S::area_a);
+        {
+            float gr[D], gi[D];
+            if (active) {
+                load_column<D>(gsrc + j * D, gr);
+                load_column<D>(gsrc + d + j * D, gi);
+            } else {
+#pragma unroll
+                for (int i = 0; i < D; ++i) gr[i] = gi[i] = 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) gs2[i * D + j] = make_float2(gr[i], gi[i]);
+        }
+        __syncwarp();
+        const int bi = j >> 2, bj = j & 3;
+        float wr[4][4], wi[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 g01 = *reinterpret_cast<const float4 *>(gs2 + (4 * bi + r) * D + 4 * bj);
+            const float4 g23 = *reinterpret_cast<const float4 *>(gs2 + (4 * bi + r) * D + 4 * bj + 2);
+            wr[r][0] = g01.x; wi[r][0] = g01.y; wr[r][1] = g01.z; wi[r][1] = g01.w;
+            wr[r][2] = g23.x; wi[r][2] = g23.y; wr[r][3] = g23.z; wi[r][3] = g23.w;
+        }
+#pragma unroll 4
+        for (int k = 0; k < D; ++k) {
+            const float4 ur4 = *reinterpret_cast<const float4 *>(qre + k * QC + 4 * bi);
+            const float4 ui4 = *reinterpret_cast<const float4 *>(qim + k * QC + 4 * bi);
+            const float4 g01 = *reinterpret_cast<const float4 *>(gs2 + k * D + 4 * bj);
+            const float4 g23 = *reinterpret_cast<const float4 *>(gs2 + k * D + 4 * bj + 2);
+            const float ur[4] = {ur4.x, ur4.y, ur4.z, ur4.w}, ui[4] = {ui4.x, ui4.y, ui4.z, ui4.w};
+            const float gr[4] = {g01.x, g01.z, g23.x, g23.z}, gi[4] = {g01.y, g01.w, g23.y, g23.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    wr[r][q] = __fmaf_rn(ur[r], gr[q], __fmaf_rn(-ui[r], gi[q], wr[r][q]));
+                    wi[r][q] = __fmaf_rn(ur[r], gi[q], __fmaf_rn(ui[r], gr[q], wi[r][q]));
+                }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {   // W row-major with padded rows (replaces Q)
+            *reinterpret_cast<float4 *>(wsm + (4 * bi + r) * RS + 4 * bj) =
+                make_float4(wr[r][0], wi[r][0], wr[r][1], wi[r][1]);
+            *reinterpret_cast<float4 *>(wsm + (4 * bi + r) * RS + 4 * bj + 2) =
+                make_float4(wr[r][2], wi[r][2], wr[r][3], wi[r][3]);
+        }
+        __syncwarp();
     } else {
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            gr[i] = 0.0f;
-            gi[i] = 0.0f;
+    // ---- 3. W = (U + I) G, column j: W[:,j] = G[:,j] + sum_k U[:,k] G[k,j] ------------------
+        float gr[D], gi[D], wr[D], wi[D];
+        if (active) {
+            load_column<D>(gsrc + j * D, gr);
+            load_column<D>(gsrc + d + j * D, gi);
+        } else {
+    #pragma unroll
+            for (int i = 0; i < D; ++i) {
+                gr[i] = 0.0f;
+                gi[i] = 0.0f;
+            }
         }
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        wr[i] = gr[i];
-        wi[i] = gi[i];
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        float ur[D], ui[D];
-        load_column<D>(qre + k * QC, ur);
-        load_column<D>(qim + k * QC, ui);
-#pragma unroll
+    #pragma unroll
         for (int i = 0; i < D; ++i) {
-            wr[i] = __fmaf_rn(ur[i], gr[k], __fmaf_rn(-ui[i], gi[k], wr[i]));
-            wi[i] = __fmaf_rn(ur[i], gi[k], __fmaf_rn(ui[i], gr[k], wi[i]));
+            wr[i] = gr[i];
+            wi[i] = gi[i];
         }
+    #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            float ur[D], ui[D];
+            load_column<D>(qre + k * QC, ur);
+            load_column<D>(qim + k * QC, ui);
+    #pragma unroll
+            for (int i = 0; i < D; ++i) {
+                wr[i] = __fmaf_rn(ur[i], gr[k], __fmaf_rn(-ui[i], gi[k], wr[i]));
+                wi[i] = __fmaf_rn(ur[i], gi[k], __fmaf_rn(ui[i], gr[k], wi[i]));
+            }
+        }
+        __syncwarp();
+        // W row-major with padded rows: W[i][j] at wsm[i * RS + j] (replaces Q)
+    #pragma unroll
+        for (int i = 0; i < D; ++i) wsm[i * RS + j] = make_float2(wr[i], wi[i]);
+        __syncwarp();
+    
     }
-    __syncwarp();
-    // W row-major with padded rows: W[i][j] at wsm[i * RS + j] (replaces Q)
-#pragma unroll
-    for (int i = 0; i < D; ++i) wsm[i * RS + j] = make_float2(wr[i], wi[i]);
-    __syncwarp();
 
     // ---- 4. rho = W W^dag / Tr: lane a owns entries (a, a + t mod D), t = 0..D/2 ------------
     const int arow = j;
