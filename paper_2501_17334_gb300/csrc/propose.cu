@@ -261,6 +261,12 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     }
 
     // ---- 2a. modified Gram-Schmidt on the columns of H (Algorithm 1 l.4-5) ------------------
+    // Every lane loads the published column v_k and forms |v_k|^2 and r = v_k^dag h with its own
+    // column h.  Lanes j > k project; lane k keeps 1/|v_k|; a lane j < k holds its final v_j, so
+    // its r is conj(v_j^dag v_k) and gives the Gram entry E_jk = q_j^dag q_k of the normalised
+    // columns for the re-orthogonalisation -- the entries become available exactly as lanes
+    // fall idle, so the Gram matrix costs no separate pass.
+    float inv_own = 0.0f;   // 1 / |v_j| of this lane's final column
 #pragma unroll 1
     for (int k = 0; k < D; ++k) {
         if (j == k) {   // column k is final: publish it
@@ -268,42 +274,44 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
             store_column<D>(qim + k * QC, hi);
         }
         __syncwarp();
-        if (j > k) {
-            float vr[D], vi[D];
-            load_column<D>(qre + k * QC, vr);
-            load_column<D>(qim + k * QC, vi);
-            // |v|^2 and r = v^dag h, each with two independent accumulators
-            float n0 = 0.0f, n1 = 0.0f, rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
+        float vr[D], vi[D];
+        load_column<D>(qre + k * QC, vr);
+        load_column<D>(qim + k * QC, vi);
+        // |v|^2 and r = v^dag h, each with two independent accumulators
+        float n0 = 0.0f, n1 = 0.0f, rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
 #pragma unroll
-            for (int i = 0; i < D; i += 2) {
-                n0 = __fmaf_rn(vr[i], vr[i], __fmaf_rn(vi[i], vi[i], n0));
-                n1 = __fmaf_rn(vr[i + 1], vr[i + 1], __fmaf_rn(vi[i + 1], vi[i + 1], n1));
-                rr0 = __fmaf_rn(vr[i], hr[i], __fmaf_rn(vi[i], hi[i], rr0));
-                ri0 = __fmaf_rn(vr[i], hi[i], __fmaf_rn(-vi[i], hr[i], ri0));
-                rr1 = __fmaf_rn(vr[i + 1], hr[i + 1], __fmaf_rn(vi[i + 1], hi[i + 1], rr1));
-                ri1 = __fmaf_rn(vr[i + 1], hi[i + 1], __fmaf_rn(-vi[i + 1], hr[i + 1], ri1));
-            }
-            const float inv_n = 1.0f / (n0 + n1);
+        for (int i = 0; i < D; i += 2) {
+            n0 = __fmaf_rn(vr[i], vr[i], __fmaf_rn(vi[i], vi[i], n0));
+            n1 = __fmaf_rn(vr[i + 1], vr[i + 1], __fmaf_rn(vi[i + 1], vi[i + 1], n1));
+            rr0 = __fmaf_rn(vr[i], hr[i], __fmaf_rn(vi[i], hi[i], rr0));
+            ri0 = __fmaf_rn(vr[i], hi[i], __fmaf_rn(-vi[i], hr[i], ri0));
+            rr1 = __fmaf_rn(vr[i + 1], hr[i + 1], __fmaf_rn(vi[i + 1], hi[i + 1], rr1));
+            ri1 = __fmaf_rn(vr[i + 1], hi[i + 1], __fmaf_rn(-vi[i + 1], hr[i + 1], ri1));
+        }
+        const float nk = n0 + n1;
+        if (j > k) {
+            const float inv_n = 1.0f / nk;
             const float sr = (rr0 + rr1) * inv_n, si = (ri0 + ri1) * inv_n;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 hr[i] = __fmaf_rn(-sr, vr[i], __fmaf_rn(si, vi[i], hr[i]));
                 hi[i] = __fmaf_rn(-sr, vi[i], __fmaf_rn(-si, vr[i], hi[i]));
             }
+        } else {
+            const float inv_k = 1.0f / sqrtf(nk);
+            if (j == k) {
+                inv_own = inv_k;
+            } else if constexpr (PASSES == 2) {
+                const float sc = inv_own * inv_k;          // E_jk = conj(r) / (|v_j| |v_k|), j < k
+                fsm[k * D + j] = make_float2((rr0 + rr1) * sc, -(ri0 + ri1) * sc);
+            }
         }
     }
     {   // normalise the own column and publish it
-        float n0 = 0.0f, n1 = 0.0f;
-#pragma unroll
-        for (int i = 0; i < D; i += 2) {
-            n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
-            n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
-        }
-        const float inv = 1.0f / sqrtf(n0 + n1);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            hr[i] *= inv;
-            hi[i] *= inv;
+            hr[i] *= inv_own;
+            hi[i] *= inv_own;
         }
         __syncwarp();
         store_column<D>(qre + j * QC, hr);
@@ -312,33 +320,17 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     }
 
     if constexpr (PASSES == 2) {
-        // ---- 2b. re-orthogonalisation Q2 = Q1 (I - F) --------------------------------------
-        // E_ab = q_a^dag q_b - delta_ab: lane a forms (a, a + t mod D), t = 0..D/2, from its own
-        // column (registers) and column b (shared); F_ab = E_ab (a < b), F_aa = E_aa / 2.
-#pragma unroll 1
-        for (int t = 0; t <= D / 2; ++t) {
-            const int b = (j + t) & (D - 1);
-            if (t == D / 2 && j >= D / 2) continue;   // (a, a + D/2) is done by the lower lane
-            float br[D], bim[D];
-            load_column<D>(qre + b * QC, br);
-            load_column<D>(qim + b * QC, bim);
-            float er0 = 0.0f, ei0 = 0.0f, er1 = 0.0f, ei1 = 0.0f;
+        // ---- 2b. re-orthogonalisation Q2 = Q1 (I - F), F = strict upper part of E (formed in
+        // the sweep above) plus half the diagonal E_jj = |q_j|^2 - 1 of the stored columns ------
+        {
+            float n0 = 0.0f, n1 = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; i += 2) {
-                er0 = __fmaf_rn(hr[i], br[i], __fmaf_rn(hi[i], bim[i], er0));
-                ei0 = __fmaf_rn(hr[i], bim[i], __fmaf_rn(-hi[i], br[i], ei0));
-                er1 = __fmaf_rn(hr[i + 1], br[i + 1], __fmaf_rn(hi[i + 1], bim[i + 1], er1));
-                ei1 = __fmaf_rn(hr[i + 1], bim[i + 1], __fmaf_rn(-hi[i + 1], br[i + 1], ei1));
+                n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
+                n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
             }
-            const float er = er0 + er1, ei = ei0 + ei1;    // q_j^dag q_b
-            if (t == 0) {
-                fsm[j * D + j] = make_float2(0.5f * (er - 1.0f), 0.0f);
-                if (j + 1 < D) fsm[j * D + j + 1] = make_float2(0.0f, 0.0f);   // read as a pair, never used
-            } else if (j < b) {
-                fsm[b * D + j] = make_float2(er, ei);        // F[j][b]
-            } else {
-                fsm[j * D + b] = make_float2(er, -ei);       // F[b][j] = conj(q_j^dag q_b)
-            }
+            fsm[j * D + j] = make_float2(0.5f * ((n0 + n1) - 1.0f), 0.0f);
+            if (j + 1 < D) fsm[j * D + j + 1] = make_float2(0.0f, 0.0f);   // read as a pair, never used
         }
         __syncwarp();
         // row a of Q2: x_m - sum_{i <= m} x_i F[i][m], x = row a of Q1 (lane a = j)
