@@ -101,6 +101,33 @@ __device__ __forceinline__ void store_column(float *dst, const float (&v)[D]) {
     }
 }
 
+// a D-float column as D/2 pairs of consecutive entries (for the packed f32x2 arithmetic)
+template <int D>
+__device__ __forceinline__ void load_column2(const float *src, float2 (&v)[D / 2]) {
+    if constexpr (D >= 4) {
+#pragma unroll
+        for (int p = 0; p < D / 2; p += 2) {
+            const float4 t = *reinterpret_cast<const float4 *>(src + 2 * p);
+            v[p] = make_float2(t.x, t.y);
+            v[p + 1] = make_float2(t.z, t.w);
+        }
+    } else {
+        v[0] = *reinterpret_cast<const float2 *>(src);
+    }
+}
+template <int D>
+__device__ __forceinline__ void store_column2(float *dst, const float2 (&v)[D / 2]) {
+    if constexpr (D >= 4) {
+#pragma unroll
+        for (int p = 0; p < D / 2; p += 2)
+            *reinterpret_cast<float4 *>(dst + 2 * p) = make_float4(v[p].x, v[p].y, v[p + 1].x, v[p + 1].y);
+    } else {
+        *reinterpret_cast<float2 *>(dst) = v[0];
+    }
+}
+
+__device__ __forceinline__ float hsum(float2 v) { return v.x + v.y; }
+
 template <int D>
 __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
@@ -166,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     float *sm = smem + g * S::smem_floats;
     float *qre = sm, *qim = sm + D * QC;                 // Q planes (column stride QC)
     float2 *wsm = reinterpret_cast<float2 *>(sm);        // W row-major (row stride RS), replaces Q
-    float2 *fsm = reinterpret_cast<float2 *>(sm + S::area_a);   // F column-major (stride D)
+    float *fre = sm + S::area_a, *fim = fre + D * D;     // F column-major (stride D), re / im planes
     float *packed = sm + S::area_a;                      // staged rho (row stride PK), replaces F
 
     // ---- 1. latent proposal --------------------------------------------------------------
@@ -189,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     float *ydst = a.y + ((int64_t)(1 - cur) * a.R + cc) * nx;
     // where G's column j is read back in step 3: this lane's own y' writes, or the input row
     const float *gsrc = (a.mode == MODE_EVAL) ? a.x_eval + cc * nx : ydst;
-    float hr[D], hi[D];   // H's column j
+    float2 hr[D / 2], hi[D / 2];   // H's column j, entries (2p, 2p + 1) in pair p
     if constexpr (D >= 4) {
         // lane j owns entries j D .. j D + D - 1 of each part: D/4 Philox blocks per part
 #pragma unroll 1
@@ -217,9 +244,11 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                     if (active) *reinterpret_cast<float4 *>(ydst + e0 + 4 * q) = yn;
                 }
                 if (part == 2) {
-                    hr[4 * q] = yn.x; hr[4 * q + 1] = yn.y; hr[4 * q + 2] = yn.z; hr[4 * q + 3] = yn.w;
+                    hr[2 * q] = make_float2(yn.x, yn.y);
+                    hr[2 * q + 1] = make_float2(yn.z, yn.w);
                 } else if (part == 3) {
-                    hi[4 * q] = yn.x; hi[4 * q + 1] = yn.y; hi[4 * q + 2] = yn.z; hi[4 * q + 3] = yn.w;
+                    hi[2 * q] = make_float2(yn.x, yn.y);
+                    hi[2 * q + 1] = make_float2(yn.z, yn.w);
                 }
             }
         }
@@ -251,51 +280,52 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                 }
             }
             if (part == 2) {
-                hr[0] = y0v;
-                hr[1] = y1v;
+                hr[0] = make_float2(y0v, y1v);
             } else if (part == 3) {
-                hi[0] = y0v;
-                hi[1] = y1v;
+                hi[0] = make_float2(y0v, y1v);
             }
         }
     }
 
     // ---- 2a. modified Gram-Schmidt on the columns of H (Algorithm 1 l.4-5) ------------------
-    // Every lane loads the published column v_k and forms |v_k|^2 and r = v_k^dag h with its own
-    // column h.  Lanes j > k project; lane k keeps 1/|v_k|; a lane j < k holds its final v_j, so
-    // its r is conj(v_j^dag v_k) and gives the Gram entry E_jk = q_j^dag q_k of the normalised
-    // columns for the re-orthogonalisation -- the entries become available exactly as lanes
-    // fall idle, so the Gram matrix costs no separate pass.
+    // Every lane loads the published column v_k and forms r = v_k^dag h with its own column h
+    // (packed f32x2 products over pairs of rows).  Lane k's column is v_k itself, so its r is
+    // |v_k|^2, which the other lanes take by shuffle.  Lanes j > k project; lane k keeps
+    // 1/|v_k|; a lane j < k holds its final v_j, so its r is conj(v_j^dag v_k) and gives the
+    // Gram entry E_jk = q_j^dag q_k of the normalised columns for the re-orthogonalisation --
+    // the entries become available exactly as lanes fall idle, so the Gram matrix costs no
+    // separate pass.
     float inv_own = 0.0f;   // 1 / |v_j| of this lane's final column
 #pragma unroll 1
     for (int k = 0; k < D; ++k) {
         if (j == k) {   // column k is final: publish it
-            store_column<D>(qre + k * QC, hr);
-            store_column<D>(qim + k * QC, hi);
+            store_column2<D>(qre + k * QC, hr);
+            store_column2<D>(qim + k * QC, hi);
         }
         __syncwarp();
-        float vr[D], vi[D];
-        load_column<D>(qre + k * QC, vr);
-        load_column<D>(qim + k * QC, vi);
-        // |v|^2 and r = v^dag h, each with two independent accumulators
-        float n0 = 0.0f, n1 = 0.0f, rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
+        float2 vr[D / 2], vi[D / 2];
+        load_column2<D>(qre + k * QC, vr);
+        load_column2<D>(qim + k * QC, vi);
+        // r = v^dag h = sum (vr hr + vi hi) + i sum (vr hi - vi hr)
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
 #pragma unroll
-        for (int i = 0; i < D; i += 2) {
-            n0 = __fmaf_rn(vr[i], vr[i], __fmaf_rn(vi[i], vi[i], n0));
-            n1 = __fmaf_rn(vr[i + 1], vr[i + 1], __fmaf_rn(vi[i + 1], vi[i + 1], n1));
-            rr0 = __fmaf_rn(vr[i], hr[i], __fmaf_rn(vi[i], hi[i], rr0));
-            ri0 = __fmaf_rn(vr[i], hi[i], __fmaf_rn(-vi[i], hr[i], ri0));
-            rr1 = __fmaf_rn(vr[i + 1], hr[i + 1], __fmaf_rn(vi[i + 1], hi[i + 1], rr1));
-            ri1 = __fmaf_rn(vr[i + 1], hi[i + 1], __fmaf_rn(-vi[i + 1], hr[i + 1], ri1));
+        for (int p = 0; p < D / 2; ++p) {
+            a0 = __ffma2_rn(vr[p], hr[p], a0);
+            a1 = __ffma2_rn(vi[p], hi[p], a1);
+            b0 = __ffma2_rn(vr[p], hi[p], b0);
+            b1 = __ffma2_rn(vi[p], hr[p], b1);
         }
-        const float nk = n0 + n1;
+        const float rr = hsum(a0) + hsum(a1);
+        const float ri = hsum(b0) - hsum(b1);
+        const float nk = __shfl_sync(0xffffffffu, rr, k, D);   // |v_k|^2 from lane k
         if (j > k) {
             const float inv_n = 1.0f / nk;
-            const float sr = (rr0 + rr1) * inv_n, si = (ri0 + ri1) * inv_n;
+            const float sr = rr * inv_n, si = ri * inv_n;      // h -= (r / |v|^2) v
+            const float2 msr = make_float2(-sr, -sr), psi = make_float2(si, si), msi = make_float2(-si, -si);
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                hr[i] = __fmaf_rn(-sr, vr[i], __fmaf_rn(si, vi[i], hr[i]));
-                hi[i] = __fmaf_rn(-sr, vi[i], __fmaf_rn(-si, vr[i], hi[i]));
+            for (int p = 0; p < D / 2; ++p) {
+                hr[p] = __ffma2_rn(msr, vr[p], __ffma2_rn(psi, vi[p], hr[p]));
+                hi[p] = __ffma2_rn(msr, vi[p], __ffma2_rn(msi, vr[p], hi[p]));
             }
         } else {
             const float inv_k = 1.0f / sqrtf(nk);
@@ -303,19 +333,21 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                 inv_own = inv_k;
             } else if constexpr (PASSES == 2) {
                 const float sc = inv_own * inv_k;          // E_jk = conj(r) / (|v_j| |v_k|), j < k
-                fsm[k * D + j] = make_float2((rr0 + rr1) * sc, -(ri0 + ri1) * sc);
+                fre[k * D + j] = rr * sc;
+                fim[k * D + j] = -ri * sc;
             }
         }
     }
     {   // normalise the own column and publish it
+        const float2 sc = make_float2(inv_own, inv_own);
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            hr[i] *= inv_own;
-            hi[i] *= inv_own;
+        for (int p = 0; p < D / 2; ++p) {
+            hr[p] = __fmul2_rn(hr[p], sc);
+            hi[p] = __fmul2_rn(hi[p], sc);
         }
         __syncwarp();
-        store_column<D>(qre + j * QC, hr);
-        store_column<D>(qim + j * QC, hi);
+        store_column2<D>(qre + j * QC, hr);
+        store_column2<D>(qim + j * QC, hi);
         __syncwarp();
     }
 
@@ -323,44 +355,66 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         // ---- 2b. re-orthogonalisation Q2 = Q1 (I - F), F = strict upper part of E (formed in
         // the sweep above) plus half the diagonal E_jj = |q_j|^2 - 1 of the stored columns ------
         {
-            float n0 = 0.0f, n1 = 0.0f;
+            float2 n = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < D; i += 2) {
-                n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
-                n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
+            for (int p = 0; p < D / 2; ++p) n = __ffma2_rn(hr[p], hr[p], __ffma2_rn(hi[p], hi[p], n));
+            fre[j * D + j] = 0.5f * (hsum(n) - 1.0f);
+            fim[j * D + j] = 0.0f;
+            if (j + 1 < D) {   // F[j+1][j] = 0: read in the pair (j, j+1) of column j
+                fre[j * D + j + 1] = 0.0f;
+                fim[j * D + j + 1] = 0.0f;
             }
-            fsm[j * D + j] = make_float2(0.5f * ((n0 + n1) - 1.0f), 0.0f);
-            if (j + 1 < D) fsm[j * D + j + 1] = make_float2(0.0f, 0.0f);   // read as a pair, never used
         }
         __syncwarp();
-        // row a of Q2: x_m - sum_{i <= m} x_i F[i][m], x = row a of Q1 (lane a = j)
+        // row a of Q2: x_m - sum_{i <= m} x_i F[i][m], x = row a of Q1 (lane a = j), as pairs
+        // (x_2p, x_2p+1); a pair that reaches past m meets F[m+1][m] = 0
         {
-            float xr[D], xi[D];
+            float2 xr[D / 2], xi[D / 2];
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                xr[i] = qre[i * QC + j];
-                xi[i] = qim[i * QC + j];
+            for (int p = 0; p < D / 2; ++p) {
+                xr[p] = make_float2(qre[(2 * p) * QC + j], qre[(2 * p + 1) * QC + j]);
+                xi[p] = make_float2(qim[(2 * p) * QC + j], qim[(2 * p + 1) * QC + j]);
             }
 #pragma unroll
             for (int m = D - 1; m >= 0; --m) {   // descending: x_m is still Q1's when row m is formed
-                float accr = xr[m], acci = xi[m];
+                float2 ca = make_float2(0.f, 0.f), cb = ca, cc2 = ca, cd = ca;
 #pragma unroll
-                for (int i = 0; i <= m; i += 2) {
-                    const float4 f = *reinterpret_cast<const float4 *>(fsm + m * D + i);   // F[i][m], F[i+1][m]
-                    accr = __fmaf_rn(-xr[i], f.x, __fmaf_rn(xi[i], f.y, accr));
-                    acci = __fmaf_rn(-xr[i], f.y, __fmaf_rn(-xi[i], f.x, acci));
-                    if (i + 1 <= m) {
-                        accr = __fmaf_rn(-xr[i + 1], f.z, __fmaf_rn(xi[i + 1], f.w, accr));
-                        acci = __fmaf_rn(-xr[i + 1], f.w, __fmaf_rn(-xi[i + 1], f.z, acci));
+                for (int p = 0; 2 * p <= m; ++p) {
+                    float2 fx, fy;   // F[2p][m], F[2p+1][m]
+                    if constexpr (D >= 4) {
+                        if ((p & 1) == 0) {
+                            const float4 f4x = *reinterpret_cast<const float4 *>(fre + m * D + 2 * p);
+                            const float4 f4y = *reinterpret_cast<const float4 *>(fim + m * D + 2 * p);
+                            fx = make_float2(f4x.x, f4x.y);
+                            fy = make_float2(f4y.x, f4y.y);
+                        } else {
+                            fx = *reinterpret_cast<const float2 *>(fre + m * D + 2 * p);
+                            fy = *reinterpret_cast<const float2 *>(fim + m * D + 2 * p);
+                        }
+                    } else {
+                        fx = *reinterpret_cast<const float2 *>(fre + m * D + 2 * p);
+                        fy = *reinterpret_cast<const float2 *>(fim + m * D + 2 * p);
                     }
+                    ca = __ffma2_rn(xr[p], fx, ca);    // sum xr fx
+                    cb = __ffma2_rn(xi[p], fy, cb);    // sum xi fy
+                    cc2 = __ffma2_rn(xr[p], fy, cc2);  // sum xr fy
+                    cd = __ffma2_rn(xi[p], fx, cd);    // sum xi fx
                 }
-                xr[m] = accr;
-                xi[m] = acci;
+                const float dr = hsum(ca) - hsum(cb), di = hsum(cc2) + hsum(cd);
+                if (m & 1) {
+                    xr[m / 2].y -= dr;
+                    xi[m / 2].y -= di;
+                } else {
+                    xr[m / 2].x -= dr;
+                    xi[m / 2].x -= di;
+                }
             }
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                qre[i * QC + j] = xr[i];
-                qim[i * QC + j] = xi[i];
+            for (int p = 0; p < D / 2; ++p) {
+                qre[(2 * p) * QC + j] = xr[p].x;
+                qre[(2 * p + 1) * QC + j] = xr[p].y;
+                qim[(2 * p) * QC + j] = xi[p].x;
+                qim[(2 * p + 1) * QC + j] = xi[p].y;
             }
         }
         __syncwarp();
@@ -368,9 +422,11 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
 
     if constexpr (D == 16) {
         // ---- 3. W = (U + I) G in 4x4 register blocks: lane (bi, bj) forms W[4bi.., 4bj..] -----
-        // (four FMAs per float loaded from shared memory instead of two; G staged row-major
-        // in area B, free between the re-orthogonalisation and the packed rho)
-        float2 *gs2 = reinterpret_cast<float2 *>(sm + S::area_a);
+        // G is staged row-major as separate real and imaginary planes in area B (free between
+        // the re-orthogonalisation and the packed rho), so that columns (4bj, 4bj+1) and
+        // (4bj+2, 4bj+3) of a row are f32x2 pairs and U's entries enter broadcast: eight
+        // packed FMAs per row of U instead of sixteen scalar ones.
+        float *gsr = sm + S::area_a, *gsi = gsr + D * D;
         {
             float gr[D], gi[D];
             if (active) {
@@ -381,41 +437,50 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                 for (int i = 0; i < D; ++i) gr[i] = gi[i] = 0.0f;
             }
 #pragma unroll
-            for (int i = 0; i < D; ++i) gs2[i * D + j] = make_float2(gr[i], gi[i]);
+            for (int i = 0; i < D; ++i) {
+                gsr[i * D + j] = gr[i];
+                gsi[i * D + j] = gi[i];
+            }
         }
         __syncwarp();
         const int bi = j >> 2, bj = j & 3;
-        float wr[4][4], wi[4][4];
+        float2 wr[4][2], wi[4][2];   // W[4bi + r][4bj + 2h .. 4bj + 2h + 1]
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const float4 g01 = *reinterpret_cast<const float4 *>(gs2 + (4 * bi + r) * D + 4 * bj);
-            const float4 g23 = *reinterpret_cast<const float4 *>(gs2 + (4 * bi + r) * D + 4 * bj + 2);
-            wr[r][0] = g01.x; wi[r][0] = g01.y; wr[r][1] = g01.z; wi[r][1] = g01.w;
-            wr[r][2] = g23.x; wi[r][2] = g23.y; wr[r][3] = g23.z; wi[r][3] = g23.w;
+            const float4 g4r = *reinterpret_cast<const float4 *>(gsr + (4 * bi + r) * D + 4 * bj);
+            const float4 g4i = *reinterpret_cast<const float4 *>(gsi + (4 * bi + r) * D + 4 * bj);
+            wr[r][0] = make_float2(g4r.x, g4r.y);
+            wr[r][1] = make_float2(g4r.z, g4r.w);
+            wi[r][0] = make_float2(g4i.x, g4i.y);
+            wi[r][1] = make_float2(g4i.z, g4i.w);
         }
 #pragma unroll 4
         for (int k = 0; k < D; ++k) {
             const float4 ur4 = *reinterpret_cast<const float4 *>(qre + k * QC + 4 * bi);
             const float4 ui4 = *reinterpret_cast<const float4 *>(qim + k * QC + 4 * bi);
-            const float4 g01 = *reinterpret_cast<const float4 *>(gs2 + k * D + 4 * bj);
-            const float4 g23 = *reinterpret_cast<const float4 *>(gs2 + k * D + 4 * bj + 2);
+            const float4 g4r = *reinterpret_cast<const float4 *>(gsr + k * D + 4 * bj);
+            const float4 g4i = *reinterpret_cast<const float4 *>(gsi + k * D + 4 * bj);
+            const float2 gr2[2] = {make_float2(g4r.x, g4r.y), make_float2(g4r.z, g4r.w)};
+            const float2 gi2[2] = {make_float2(g4i.x, g4i.y), make_float2(g4i.z, g4i.w)};
             const float ur[4] = {ur4.x, ur4.y, ur4.z, ur4.w}, ui[4] = {ui4.x, ui4.y, ui4.z, ui4.w};
-            const float gr[4] = {g01.x, g01.z, g23.x, g23.z}, gi[4] = {g01.y, g01.w, g23.y, g23.w};
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 4; ++r) {
+                const float2 pu = make_float2(ur[r], ur[r]), pi = make_float2(ui[r], ui[r]);
+                const float2 mi = make_float2(-ui[r], -ui[r]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    wr[r][q] = __fmaf_rn(ur[r], gr[q], __fmaf_rn(-ui[r], gi[q], wr[r][q]));
-                    wi[r][q] = __fmaf_rn(ur[r], gi[q], __fmaf_rn(ui[r], gr[q], wi[r][q]));
+                for (int h = 0; h < 2; ++h) {
+                    wr[r][h] = __ffma2_rn(pu, gr2[h], __ffma2_rn(mi, gi2[h], wr[r][h]));
+                    wi[r][h] = __ffma2_rn(pu, gi2[h], __ffma2_rn(pi, gr2[h], wi[r][h]));
                 }
+            }
         }
         __syncwarp();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {   // W row-major with padded rows (replaces Q)
             *reinterpret_cast<float4 *>(wsm + (4 * bi + r) * RS + 4 * bj) =
-                make_float4(wr[r][0], wi[r][0], wr[r][1], wi[r][1]);
+                make_float4(wr[r][0].x, wi[r][0].x, wr[r][0].y, wi[r][0].y);
             *reinterpret_cast<float4 *>(wsm + (4 * bi + r) * RS + 4 * bj + 2) =
-                make_float4(wr[r][2], wi[r][2], wr[r][3], wi[r][3]);
+                make_float4(wr[r][1].x, wi[r][1].x, wr[r][1].y, wi[r][1].y);
         }
         __syncwarp();
     } else {
@@ -456,19 +521,29 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     }
 
     // ---- 4. rho = W W^dag / Tr: lane a owns entries (a, a + t mod D), t = 0..D/2 ------------
+    // (W W^dag)_ab = sum_m W[a,m] conj(W[b,m]): with the row of b read as complex pairs
+    // (Re, Im) W[b,m], Re is the sum of both halves of (Re, Im) W[a,m] * (Re, Im) W[b,m] and Im
+    // that of (Im, -Re) W[a,m] * (Re, Im) W[b,m]
     const int arow = j;
-    float war[D], wai[D];
+    float2 wa[D], wc[D];   // (Re, Im) W[a,m] and (Im, -Re) W[a,m]
 #pragma unroll
-    for (int jj = 0; jj < D; jj += 2) {
-        const float4 v = *reinterpret_cast<const float4 *>(wsm + arow * RS + jj);
-        war[jj] = v.x;
-        wai[jj] = v.y;
-        war[jj + 1] = v.z;
-        wai[jj + 1] = v.w;
+    for (int m = 0; m < D; m += 2) {
+        const float4 v = *reinterpret_cast<const float4 *>(wsm + arow * RS + m);
+        wa[m] = make_float2(v.x, v.y);
+        wa[m + 1] = make_float2(v.z, v.w);
+        wc[m] = make_float2(v.y, -v.x);
+        wc[m + 1] = make_float2(v.w, -v.z);
     }
-    float diag = 0.0f;
+    float diag;
+    {
+        float2 d0 = make_float2(0.f, 0.f), d1 = d0;
 #pragma unroll
-    for (int jj = 0; jj < D; ++jj) diag = __fmaf_rn(war[jj], war[jj], __fmaf_rn(wai[jj], wai[jj], diag));
+        for (int m = 0; m < D; m += 2) {
+            d0 = __ffma2_rn(wa[m], wa[m], d0);
+            d1 = __ffma2_rn(wa[m + 1], wa[m + 1], d1);
+        }
+        diag = hsum(d0) + hsum(d1);
+    }
     const float inv_tr = 1.0f / group_sum<D>(diag);
     const float diag_n = diag * inv_tr;
     float tr_hi, tr_lo;
@@ -478,17 +553,18 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     for (int t = 1; t <= D / 2; ++t) {
         const int b = (arow + t) & (D - 1);
         if (t == D / 2 && arow >= D / 2) continue;  // (a, a + D/2) is done by the lower lane
-        float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;   // (W W^dag)_ab = sum W[a,jj] conj(W[b,jj])
+        float2 re0 = make_float2(0.f, 0.f), im0 = re0, re1 = re0, im1 = re0;
 #pragma unroll
-        for (int jj = 0; jj < D; jj += 2) {
-            const float4 wb = *reinterpret_cast<const float4 *>(wsm + b * RS + jj);
-            re0 = __fmaf_rn(war[jj], wb.x, __fmaf_rn(wai[jj], wb.y, re0));
-            im0 = __fmaf_rn(wai[jj], wb.x, __fmaf_rn(-war[jj], wb.y, im0));
-            re1 = __fmaf_rn(war[jj + 1], wb.z, __fmaf_rn(wai[jj + 1], wb.w, re1));
-            im1 = __fmaf_rn(wai[jj + 1], wb.z, __fmaf_rn(-war[jj + 1], wb.w, im1));
+        for (int m = 0; m < D; m += 2) {
+            const float4 wb = *reinterpret_cast<const float4 *>(wsm + b * RS + m);
+            const float2 b0 = make_float2(wb.x, wb.y), b1 = make_float2(wb.z, wb.w);
+            re0 = __ffma2_rn(wa[m], b0, re0);
+            im0 = __ffma2_rn(wc[m], b0, im0);
+            re1 = __ffma2_rn(wa[m + 1], b1, re1);
+            im1 = __ffma2_rn(wc[m + 1], b1, im1);
         }
-        const float re = (re0 + re1) * inv_tr;
-        const float im = (im0 + im1) * inv_tr;
+        const float re = (hsum(re0) + hsum(re1)) * inv_tr;
+        const float im = (hsum(im0) + hsum(im1)) * inv_tr;
         if (arow < b) {
             packed[arow * PK + b] = re;
             packed[b * PK + arow] = -im;
