@@ -318,21 +318,24 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         const float rr = hsum(a0) + hsum(a1);
         const float ri = hsum(b0) - hsum(b1);
         const float nk = __shfl_sync(0xffffffffu, rr, k, D);   // |v_k|^2 from lane k
-        if (j > k) {
-            const float inv_n = 1.0f / nk;
-            const float sr = rr * inv_n, si = ri * inv_n;      // h -= (r / |v|^2) v
-            const float2 msr = make_float2(-sr, -sr), psi = make_float2(si, si), msi = make_float2(-si, -si);
+        // one hardware reciprocal square root, uniform over the lanes: its few-ulp error in the
+        // projection coefficient or the norm is of the size of the FP32 rounding the sweep
+        // already leaves, and the re-orthogonalisation removes both to first order
+        const float rs = rsqrtf(nk);
+        // h -= (r / |v|^2) v on lanes j > k; the coefficient is zero elsewhere, which leaves h
+        // unchanged, so the warp runs one branch-free path
+        const float coef = (j > k) ? rs * rs : 0.0f;
+        const float sr = rr * coef, si = ri * coef;
+        const float2 msr = make_float2(-sr, -sr), psi = make_float2(si, si), msi = make_float2(-si, -si);
 #pragma unroll
-            for (int p = 0; p < D / 2; ++p) {
-                hr[p] = __ffma2_rn(msr, vr[p], __ffma2_rn(psi, vi[p], hr[p]));
-                hi[p] = __ffma2_rn(msr, vi[p], __ffma2_rn(msi, vr[p], hi[p]));
-            }
-        } else {
-            const float inv_k = 1.0f / sqrtf(nk);
-            if (j == k) {
-                inv_own = inv_k;
-            } else if constexpr (PASSES == 2) {
-                const float sc = inv_own * inv_k;          // E_jk = conj(r) / (|v_j| |v_k|), j < k
+        for (int p = 0; p < D / 2; ++p) {
+            hr[p] = __ffma2_rn(msr, vr[p], __ffma2_rn(psi, vi[p], hr[p]));
+            hi[p] = __ffma2_rn(msr, vi[p], __ffma2_rn(msi, vr[p], hi[p]));
+        }
+        inv_own = (j == k) ? rs : inv_own;
+        if constexpr (PASSES == 2) {
+            if (j < k) {
+                const float sc = inv_own * rs;             // E_jk = conj(r) / (|v_j| |v_k|), j < k
                 fre[k * D + j] = rr * sc;
                 fim[k * D + j] = -ri * sc;
             }
@@ -549,10 +552,12 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     float tr_hi, tr_lo;
     group_sum_exact<D>(diag_n, tr_hi, tr_lo);   // exact trace of the stored diagonal
     packed[arow * PK + arow] = diag_n;
+    // For t = D/2 lanes a and a + D/2 both form the entry pair {a, a + D/2}; the two results are
+    // bitwise equal (the same products, accumulated in the same order, negated where the
+    // conjugate is taken), so both stores may stand.
 #pragma unroll 1
     for (int t = 1; t <= D / 2; ++t) {
         const int b = (arow + t) & (D - 1);
-        if (t == D / 2 && arow >= D / 2) continue;  // (a, a + D/2) is done by the lower lane
         float2 re0 = make_float2(0.f, 0.f), im0 = re0, re1 = re0, im1 = re0;
 #pragma unroll
         for (int m = 0; m < D; m += 2) {
@@ -565,13 +570,9 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         }
         const float re = (hsum(re0) + hsum(re1)) * inv_tr;
         const float im = (hsum(im0) + hsum(im1)) * inv_tr;
-        if (arow < b) {
-            packed[arow * PK + b] = re;
-            packed[b * PK + arow] = -im;
-        } else {
-            packed[arow * PK + b] = im;
-            packed[b * PK + arow] = re;
-        }
+        const bool upper = arow < b;
+        packed[arow * PK + b] = upper ? re : im;
+        packed[b * PK + arow] = upper ? -im : re;
     }
     if (active && j == 0) a.trace_out[c] = (double)tr_hi + (double)tr_lo;
     __syncwarp();
