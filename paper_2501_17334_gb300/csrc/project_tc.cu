@@ -4,15 +4,21 @@
 // q = vec_h(rho) . P as a BF16 GEMM with FP32 accumulation: the Pauli projector matrix P
 // is exact in bf16 (entries 0 or +-2^-m), and the FP32 packed rho is split exactly into
 // rho = hi + mid + lo (three bf16 terms, 24 significant bits), so
-//     q = hi . P + mid . P + lo . P
-// is one tcgen05 GEMM with K = 3 d_pad and FP32 accumulation in tensor memory.
+//     q = hi . P + (mid . P + lo . P)
+// is a tcgen05 GEMM with K = 3 d_pad and FP32 accumulation in tensor memory, into two
+// accumulators.  Every product hi_i P_ki has at most 8 significant bits, so the hi
+// accumulator sums them without rounding unless a term lies 2^16 below the running sum;
+// the mid and lo products go to a second accumulator, 2^8 smaller, whose roundings are
+// that much smaller too.  The epilogue adds the two: q carries one FP32 rounding instead
+// of one per MMA (a single accumulator rounds, one-sidedly, at the scale of q after each
+// of the 3 d_pad / 16 MMAs), which halves the log L error of the contraction.
 //
 // Persistent CTAs (one per SM) loop over work units: a tile of 128 chains (M = 128) times a
 // group of 128-column N tiles.
 //   warp 0 (one lane)  TMA producer of P tiles (128 projectors x 64 K) through a 6-stage ring;
-//   warp 1             allocates all 512 TMEM columns (two 128-column FP32 accumulators and
-//                      two buffers for the lo split of A); one lane issues tcgen05.mma
-//                      (M128 N128 K16) and commits;
+//   warp 1             allocates all 512 TMEM columns (the hi and the mid + lo FP32
+//                      accumulators, 128 columns each, and two buffers for the lo split of
+//                      A); one lane issues tcgen05.mma (M128 N128 K16) and commits;
 //   warp 2 (one lane)  TMA producer of the hi and mid splits of the A tile (128 x 2 d_pad
 //                      bf16, SWIZZLE_128B, resident while a unit's N tiles run), one barrier
 //                      pair per 64-wide K chunk: the next unit's chunk is loaded as soon as
@@ -20,7 +26,9 @@
 //   warps 3-18         epilogue, four warps per TMEM lane quadrant (warp w may only read
 //                      lanes 32 (w mod 4) ..), each owning 32 of a tile's 128 columns and
 //                      writing its own partial sum per chain:
-//                      tcgen05.ld its accumulator slice (TMEM lane = chain) and form the
+//                      tcgen05.ld its slice of both accumulators (TMEM lane = chain),
+//                      release them (the MMAs of the next tile start as soon as every
+//                      epilogue warp holds its slice in registers), add them and form the
 //                      log-likelihood of each measurement setting k (D consecutive
 //                      columns, all in one thread):
 //                        sum_l c_kl log(q_kl invf_kl) - P_k log(S_k / t),  S_k = sum_l q_kl,
@@ -58,7 +66,8 @@ constexpr int TC_EPI_COLS = TC_N / TC_EPI_PER_QUAD;           // columns per epi
 constexpr int TC_FIRST_EPI = 3;                               // first epilogue warp
 constexpr int TC_THREADS = (TC_FIRST_EPI + 4 * TC_EPI_PER_QUAD) * 32;   // 608
 constexpr int TC_MAX_KCHUNK = 4;                              // d_pad <= 256
-constexpr uint32_t TC_TMEM_COLS = 512;   // 2 accumulators + 2 buffers of the lo split
+constexpr uint32_t TC_TMEM_COLS = 512;   // hi and mid + lo accumulators, 2 buffers of the lo split
+constexpr uint32_t TC_REST_COL = TC_N;         // first column of the mid + lo accumulator
 constexpr uint32_t TC_ALO_COL = 2 * TC_N;      // first column of the lo-split buffers
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;     // 1 s
 
@@ -190,8 +199,9 @@ __device__ __forceinline__ bool elect_one() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// two 32-column slices (the same lanes), one wait for both
+__device__ __forceinline__ void tmem_ld32_pair(uint32_t ta, uint32_t tb, float (&va)[32], float (&vb)[32]) {
+    uint32_t r[32], q[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -199,10 +209,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]), "=r"(q[8]),
+          "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15]), "=r"(q[16]),
+          "=r"(q[17]), "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]), "=r"(q[23]), "=r"(q[24]),
+          "=r"(q[25]), "=r"(q[26]), "=r"(q[27]), "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
+        : "r"(tb));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) {
+        va[i] = __uint_as_float(r[i]);
+        vb[i] = __uint_as_float(q[i]);
+    }
 }
 
 // ---- packed FP32 pairs (f32x2: one instruction, two IEEE operations) -------------------------
@@ -301,8 +322,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ __align__(8) uint64_t bar_a_empty[TC_MAX_KCHUNK];
     __shared__ __align__(8) uint64_t bar_b_full[TC_BSTAGES];
     __shared__ __align__(8) uint64_t bar_b_empty[TC_BSTAGES];
-    __shared__ __align__(8) uint64_t bar_acc_full[2];
-    __shared__ __align__(8) uint64_t bar_acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_acc_full;
+    __shared__ __align__(8) uint64_t bar_acc_empty;
     __shared__ __align__(8) uint64_t bar_alo_full[2];
     __shared__ __align__(8) uint64_t bar_mma_done;
     __shared__ uint32_t tmem_base_s;
@@ -351,11 +372,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(smem_u32(&bar_b_full[s]), 1);
             mbar_init(smem_u32(&bar_b_empty[s]), 1);
         }
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(smem_u32(&bar_acc_full[s]), 1);
-            mbar_init(smem_u32(&bar_acc_empty[s]), 4 * TC_EPI_PER_QUAD * 32);
-            mbar_init(smem_u32(&bar_alo_full[s]), 4 * TC_EPI_PER_QUAD * 32);
-        }
+        mbar_init(smem_u32(&bar_acc_full), 1);
+        mbar_init(smem_u32(&bar_acc_empty), 4 * TC_EPI_PER_QUAD * 32);
+        for (int s = 0; s < 2; ++s) mbar_init(smem_u32(&bar_alo_full[s]), 4 * TC_EPI_PER_QUAD * 32);
         mbar_init(smem_u32(&bar_mma_done), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -446,15 +465,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             unit_tiles(u, tb, te);
             for (int i = 0; i < te - tb && ok; ++i, ++tcount) {
                 const int t = tile_at(u, tb, te, i);
-                const int acc = tcount & 1;
-                const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
-                if (!wait_all(smem_u32(&bar_acc_empty[acc]), use ^ 1u) ||
+                const uint32_t use = (uint32_t)tcount & 1u;   // the accumulators' use parity
+                if (!wait_all(smem_u32(&bar_acc_empty), use ^ 1u) ||
                     (i == 0 && !wait_all(smem_u32(&bar_alo_full[uc & 1u]), (uc >> 1) & 1u))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(acc * TC_N);
+                const uint32_t d_hi = tmem, d_rest = tmem + TC_REST_COL;
                 const int n_valid = min(TC_N, (a.KD - t * TC_N + 15) / 16 * 16);
                 const uint32_t idesc = mma_idesc(n_valid);
                 const uint32_t alo_tmem = tmem + TC_ALO_COL + (uc & 1u) * (uint32_t)TC_N;
@@ -474,20 +492,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (elect_one()) {
 #pragma unroll
                         for (int kk = 0; kk < TC_KATOM / 16; ++kk)   // 16 K = 32 bytes = 2 descriptor units
-                            mma_bf16(d_tmem, ad_hi + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+                            mma_bf16(d_hi, ad_hi + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
 #pragma unroll
                         for (int kk = 0; kk < TC_KATOM / 16; ++kk)
-                            mma_bf16(d_tmem, ad_mid + 2 * kk, bd + 2 * kk, idesc, 1u);
+                            mma_bf16(d_rest, ad_mid + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
 #pragma unroll
                         for (int kk = 0; kk < TC_KATOM / 16; ++kk)   // lo split, A from tensor memory
-                            mma_bf16_ta(d_tmem, ad_lo + (uint32_t)(kk * 8), bd + 2 * kk, idesc, 1u);
+                            mma_bf16_ta(d_rest, ad_lo + (uint32_t)(kk * 8), bd + 2 * kk, idesc, 1u);
                         mma_commit(smem_u32(&bar_b_empty[s]));
                         if (i == te - tb - 1) mma_commit(smem_u32(&bar_a_empty[kc]));   // last reader of this A chunk
                     }
                     __syncwarp();
                 }
                 if (!ok) break;
-                if (elect_one()) mma_commit(smem_u32(&bar_acc_full[acc]));
+                if (elect_one()) mma_commit(smem_u32(&bar_acc_full));
                 __syncwarp();
             }
             ++uc;
@@ -554,18 +572,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int i = 0; i < te - tb; ++i, ++tcount) {
                 const int tt = tile_at(u, tb, te, i);
                 const uint4 piece_w = (has_next && i < NP) ? alo_fetch(u + gridDim.x, i) : make_uint4(0u, 0u, 0u, 0u);
-                const int acc = tcount & 1;
-                const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
-                if (!mbar_wait_warp(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
+                const uint32_t use = (uint32_t)tcount & 1u;
+                if (!mbar_wait_warp(smem_u32(&bar_acc_full), use, &abort_flag, a.status)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const int n0 = tt * TC_N + col0;
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N + col0), v);
-                tc_fence_before();
-                mbar_arrive(smem_u32(&bar_acc_empty[acc]));   // the slice is in registers
+                {
+                    float vr[32];
+                    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
+                    tmem_ld32_pair(lane_base, lane_base + TC_REST_COL, v, vr);
+                    tc_fence_before();
+                    mbar_arrive(smem_u32(&bar_acc_empty));   // both slices are in registers
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        const float2 q = add2(make_float2(v[i], v[i + 1]), make_float2(vr[i], vr[i + 1]));
+                        v[i] = q.x;
+                        v[i + 1] = q.y;
+                    }
+                }
                 float tile_sum = 0.0f;
                 if (n0 < a.KD) {   // (columns past KD: the last tile's MMA did not write them)
                     int xmin = 0x7fffffff;   // smallest bit pattern of a log argument (sign included)
@@ -643,9 +670,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // work unit is one (chain tile, N tile) pair and A's K chunks are streamed with P's through a
 // 2-stage ring: stage = one 64-wide K chunk of A's hi, mid and lo splits (3 x 16 KB) and of
 // the P tile (256 projectors x 64 = 32 KB).  N tiles are 256 wide (M128 N256 K16 MMAs, both
-// operands from shared memory); TMEM holds two 256-column accumulators.  The epilogue is the
-// one above, on 64-column slices, with the weights read through L1 (they do not fit beside
-// the ring).
+// operands from shared memory); TMEM holds the hi and the mid + lo accumulators, 256 columns
+// each, as above.  The epilogue is the one above, on 64-column slices, with the weights read
+// through L1 (they do not fit beside the ring).
 constexpr int TCW_N = 256;
 constexpr int TCW_STAGES = 2;
 constexpr int TCW_STAGE_BYTES = 3 * TC_ATOM_BYTES + TCW_N * TC_KATOM * 2;   // 80 KB
@@ -657,8 +684,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ uint8_t dyn_smem[];
     __shared__ __align__(8) uint64_t bar_full[TCW_STAGES];
     __shared__ __align__(8) uint64_t bar_empty[TCW_STAGES];
-    __shared__ __align__(8) uint64_t bar_acc_full[2];
-    __shared__ __align__(8) uint64_t bar_acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_acc_full;
+    __shared__ __align__(8) uint64_t bar_acc_empty;
     __shared__ __align__(8) uint64_t bar_mma_done;
     __shared__ uint32_t tmem_base_s;
     __shared__ volatile int abort_flag;
@@ -674,10 +701,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(smem_u32(&bar_acc_full[s]), 1);
-            mbar_init(smem_u32(&bar_acc_empty[s]), 4 * TC_EPI_PER_QUAD * 32);
-        }
+        mbar_init(smem_u32(&bar_acc_full), 1);
+        mbar_init(smem_u32(&bar_acc_empty), 4 * TC_EPI_PER_QUAD * 32);
         mbar_init(smem_u32(&bar_mma_done), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -730,14 +755,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint64_t desc0 = sw128_desc(smem_u32(base));
         for (int64_t u = blockIdx.x; u < a.units && ok; u += gridDim.x, ++tcount) {
             const int t = (int)(u % a.ntiles);
-            const int acc = tcount & 1;
-            const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
-            if (!mbar_wait_warp(smem_u32(&bar_acc_empty[acc]), use ^ 1u, &abort_flag, a.status)) {
+            const uint32_t use = (uint32_t)tcount & 1u;
+            if (!mbar_wait_warp(smem_u32(&bar_acc_empty), use ^ 1u, &abort_flag, a.status)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t d_tmem = tmem + (uint32_t)(acc * TCW_N);
+            const uint32_t d_hi = tmem, d_rest = tmem + (uint32_t)TCW_N;
             const int n_valid = min(TCW_N, (a.KD - t * TCW_N + 15) / 16 * 16);
             const uint32_t idesc = mma_idesc(n_valid);
             for (int kc = 0; kc < nk; ++kc, ++it) {
@@ -752,18 +776,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint64_t bd = sd + (uint64_t)((3 * TC_ATOM_BYTES) >> 4);
                 if (elect_one()) {
 #pragma unroll
-                    for (int sp = 0; sp < 3; ++sp) {
+                    for (int sp = 0; sp < 3; ++sp) {   // hi into d_hi, mid and lo into d_rest
 #pragma unroll
                         for (int kk = 0; kk < TC_KATOM / 16; ++kk)
-                            mma_bf16(d_tmem, sd + (uint64_t)((sp * TC_ATOM_BYTES) >> 4) + 2 * kk, bd + 2 * kk, idesc,
-                                     (kc | sp | kk) != 0 ? 1u : 0u);
+                            mma_bf16(sp == 0 ? d_hi : d_rest, sd + (uint64_t)((sp * TC_ATOM_BYTES) >> 4) + 2 * kk,
+                                     bd + 2 * kk, idesc, (kc | (sp >> 1) | kk) != 0 ? 1u : 0u);
                     }
                     mma_commit(smem_u32(&bar_empty[s]));
                 }
                 __syncwarp();
             }
             if (!ok) break;
-            if (elect_one()) mma_commit(smem_u32(&bar_acc_full[acc]));
+            if (elect_one()) mma_commit(smem_u32(&bar_acc_full));
             __syncwarp();
         }
         if (!ok && lane == 0) {
@@ -786,24 +810,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float inv_t = (float)(1.0 / tr);
             const float t_hi = (float)tr;
             const float t_lo = (float)(tr - (double)t_hi);
-            const int acc = tcount & 1;
-            const uint32_t use = (uint32_t)(tcount >> 1) & 1u;
-            if (!mbar_wait_warp(smem_u32(&bar_acc_full[acc]), use, &abort_flag, a.status)) {
+            const uint32_t use = (uint32_t)tcount & 1u;
+            if (!mbar_wait_warp(smem_u32(&bar_acc_full), use, &abort_flag, a.status)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             float tile_sum = 0.0f;
             int xmin = 0x7fffffff;
-#pragma unroll 1
+            float vv[2][32];   // q of this warp's two 32-column settings: hi + (mid + lo)
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float vr[32];
+                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(col0 + 32 * half);
+                tmem_ld32_pair(ta, ta + (uint32_t)TCW_N, vv[half], vr);
+#pragma unroll
+                for (int i = 0; i < 32; i += 2) {
+                    const float2 q = add2(make_float2(vv[half][i], vv[half][i + 1]), make_float2(vr[i], vr[i + 1]));
+                    vv[half][i] = q.x;
+                    vv[half][i + 1] = q.y;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&bar_acc_empty));   // both accumulators' slices are in registers
+#pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int n0 = t * TCW_N + col0 + 32 * half;   // one setting of 32 outcomes
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TCW_N + col0 + 32 * half), v);
-                if (half == 1) {
-                    tc_fence_before();
-                    mbar_arrive(smem_u32(&bar_acc_empty[acc]));   // both halves are in registers
-                }
+                const float *v = vv[half];
                 if (n0 >= a.KD) continue;
                 const float pk = __ldg(a.ptot + n0 / D);
                 if (pk > 0.0f) {
