@@ -37,20 +37,19 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
             "Haar pure truth depolarised 0.02, beta0 0.02")
 
 # DRAM bytes per launch of each kernel from one ncu capture (bench.py --profile-case,
-# config 4 problem at `chains` chains, the second launch of the kernel), scaled to a launch
+# config 4 problem at `chains` chains, one pCN-step launch of the kernel), scaled to a launch
 # over the benchmark's chains in proportion to the chains processed.  The capture is only
 # used while the kernel's source file still has the recorded SHA-256.
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "d21a2f5d26a17c645dd1937b703b2bc87d330e4de2bfca5202fe0df052b35a3b",
-                "chains": 32768, "bytes": 134.682880e6 + 160.286208e6},
+                "sha256": "cc6013a5f5a51cb4f5d6e94851e28d22c32ce09f3a0ad3bad6d226ca8f6e34f5",
+                "chains": 32768, "bytes": 134.935296e6 + 162.193664e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "bc7718df75d75efe9cfe831466550380fc8063c876f6fc6e619876f7729e57c8",
-                "chains": 32768, "bytes": 51.390464e6 + 0.004608e6},
+                "sha256": "c2db208dc97367f3d48b6a86ab373cc6b5340ce7a8c02983c6f4f9aeea5a7cd7",
+                "chains": 32768, "bytes": 51.389184e6 + 0.004864e6},
 }
-
 
 def _sha256(path):
     with open(os.path.join(ROOT, path), "rb") as f:
@@ -64,7 +63,7 @@ def ncu_traffic(kernel, chains):
     return rec["bytes"] * chains / rec["chains"]
 
 
-# ---- algorithmic work per chain-step ("Kernels and rooflines") ------------------
+# ---- algorithmic work per chain-step ------------------------------------------------------
 
 def propose_flops(D):
     """FP32 FLOPs of Algorithm 1 + pCN as implemented (FMA = 2, no redundant work counted):

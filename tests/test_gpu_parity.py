@@ -1,6 +1,6 @@
 """GPU parity tests: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (derived from the arithmetic; DESIGN.md Sec. "Tolerances"):
+Tolerances (derived from the arithmetic of each step):
 * Philox words: bit-exact.
 * p_kl on identical latent x: 1e-6 absolute whenever cond(H) <= 1e3.  The FP32
   assembly's forward error in U is O(cond(H) * 2^-24), and p inherits it.
