@@ -65,24 +65,24 @@ typedef struct {
     int64_t num_chains;     /* R >= 1 */
     int64_t chain_offset;   /* global id of chain 0 (disjoint ranges shard one run) */
     uint64_t seed;          /* Philox4x32-10 key */
-    double beta0;           /* this problem's initial beta (Algorithm 2 l.1); 0 = the config's beta0 */
+    double beta0;           /* this problem's initial beta (Algorithm 2, initialisation); 0 = the config's beta0 */
 } qst_problem_desc;
 
 /* Sampler settings (Algorithm 2 and Sec. IV); qst_default_config fills the paper's values. */
 typedef struct {
-    double beta0;           /* initial pCN step beta (Algorithm 2 l.1: 0.1) */
+    double beta0;           /* initial pCN step beta (Algorithm 2 initialises it to 0.1) */
     int32_t adapt_interval; /* M_A (Sec. III: 500); 0 keeps beta fixed */
-    double acc_lo, acc_hi;  /* acceptance window [0.2, 0.6] (Algorithm 2 l.14, l.17) */
-    double adapt_factor;    /* 1.1 (Algorithm 2 l.15, l.18) */
+    double acc_lo, acc_hi;  /* acceptance window [0.2, 0.6] (Algorithm 2, adaptation tests) */
+    double adapt_factor;    /* 1.1 (Algorithm 2, adaptation) */
     double beta_max;        /* 1.0: clamp keeping sqrt(1 - beta^2) real (the paper is silent) */
-    int32_t thin;           /* T: keep every T-th state (Algorithm 2 l.22) */
+    int32_t thin;           /* T: keep every T-th state (Algorithm 2, thinning) */
     int32_t burn_in;        /* pool only steps j > burn_in (the paper uses none: 0) */
     int32_t diag_chains;    /* chains per problem whose kept states are stored for the ACF */
     int32_t traj_capacity;  /* kept states stored per diagnostic chain (Sec. IV: N = 2^10) */
     int32_t acf_lmax;       /* l_max of Eq. ACFrho / Eq. IACT (Fig. 2: 200) */
     int32_t trace_steps;    /* record the accept flag and log L(y') of the first trace_steps steps */
     int32_t precision;      /* qst_precision */
-    int32_t qr_passes;      /* modified Gram-Schmidt passes computing U of Algorithm 1 l.4-5: 1, or 2
+    int32_t qr_passes;      /* modified Gram-Schmidt passes computing U of Algorithm 1 (QR and phase fix): 1, or 2
                                (default) re-orthogonalising once, which cuts U's FP32 error ~10x */
     int32_t use_graph;      /* 1 (default): qst_run_chains replays one step captured as a CUDA graph
                                (the step counter lives on the device); 0: plain launches. Kernel
@@ -143,7 +143,7 @@ qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_prob
  * config's and every problem's own beta0 (0 meaning the config's);
  * for QST_PREC_BF16X3 every packed projector entry exactly representable in bf16),
  * packs the projectors, uploads everything into the workspace and enqueues the chains'
- * initial states y^0 ~ N(0, I) with rho(y^0) and log L(y^0) (Algorithm 2 l.1).
+ * initial states y^0 ~ N(0, I) with rho(y^0) and log L(y^0) (Algorithm 2, initialisation).
  * d_workspace: device memory of at least qst_workspace_size bytes, 256-byte aligned,
  * owned by the caller and kept alive until qst_destroy; NULL makes the library
  * allocate (and later free) it itself.  cuda_stream: a cudaStream_t (NULL = default).

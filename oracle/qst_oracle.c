@@ -12,7 +12,7 @@
  * Contents and the passages they follow:
  *   philox4x32_10     counter-based generator of Salmon, Moraes, Dror, Shaw,
  *                     "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
- *   normal draws      Box-Muller on the generator's uniforms (Algorithm 2 l.1, l.3).
+ *   normal draws      Box-Muller on the generator's uniforms (Algorithm 2: initial state and proposal noise).
  *   bures_rho         Algorithm 1 steps 2-6 (Householder QR, U = Q Lambda,
  *                     W = (U + I) G, rho = W W^dag / Tr W W^dag).
  *   probabilities     p_kl = Tr(Lambda_kl rho) as a direct complex trace (Sec. II).
@@ -106,7 +106,7 @@ void oracle_normals(uint64_t seed, uint32_t step, uint32_t chain, uint32_t tag, 
     }
 }
 
-/* alpha ~ U(0,1) for step j of a chain (Algorithm 2 l.6): word 0 of block 0. */
+/* alpha ~ U(0,1) for step j of a chain (Algorithm 2, accept test): word 0 of block 0. */
 double oracle_alpha(uint64_t seed, uint32_t step, uint32_t chain)
 {
     uint32_t w[4];
@@ -284,7 +284,7 @@ typedef struct {
     int64_t chain_begin;     /* global id of the first chain */
     int64_t num_chains;
     int64_t num_steps;       /* steps j = 1..num_steps */
-    double beta0;            /* initial beta (Algorithm 2 l.1) */
+    double beta0;            /* initial beta (Algorithm 2, initialisation) */
     int32_t adapt_interval;  /* M_A; 0 = fixed beta */
     double acc_lo, acc_hi;   /* adaptation window [0.2, 0.6] */
     double adapt_factor;     /* 1.1 */
@@ -324,7 +324,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
     cplx *rho = malloc(sizeof(cplx) * d2);
     cplx *rhop = malloc(sizeof(cplx) * d2);
 
-    /* l.1: A = 0, beta = beta0, y^0 ~ N(0, I) */
+    /* initialisation: A = 0, beta = beta0, y^0 ~ N(0, I) */
     int64_t A = 0, acc_total = 0, kept = 0;
     double beta = cfg->beta0;
     oracle_normals(cfg->seed, 0u, chain, TAG_INIT, nx, y);
@@ -333,15 +333,15 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
     double logl = oracle_loglik(KD, cfg->counts, p);
 
     for (int64_t j = 1; j <= cfg->num_steps; ++j) {
-        /* l.3-4: eta ~ N(0, I), y' = sqrt(1 - beta^2) y + beta eta */
+        /* proposal: eta ~ N(0, I), y' = sqrt(1 - beta^2) y + beta eta */
         oracle_normals(cfg->seed, (uint32_t)j, chain, TAG_PROPOSAL, nx, eta);
         double a = sqrt(1.0 - beta * beta);
         for (int e = 0; e < nx; ++e) yp[e] = a * y[e] + beta * eta[e];
-        /* l.5: rho(y') and L(y'); rho(y^{j-1}) and L(y^{j-1}) are kept from the last accept */
+        /* likelihood: rho(y') and L(y'); rho(y^{j-1}) and L(y^{j-1}) are kept from the last accept */
         oracle_bures_rho(D, yp, rhop);
         oracle_probabilities(D, KD, cfg->povm_re, cfg->povm_im, rhop, p);
         double loglp = oracle_loglik(KD, cfg->counts, p);
-        /* l.6-12: alpha ~ U(0,1); accept iff log alpha < log L(y') - log L(y) */
+        /* accept test: alpha ~ U(0,1); accept iff log alpha < log L(y') - log L(y) */
         double log_alpha = log(oracle_alpha(cfg->seed, (uint32_t)j, chain));
         int accept = log_alpha < loglp - logl;
         if (cfg->trace_steps > 0 && j <= cfg->trace_steps) {
@@ -358,7 +358,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
             A += 1;
             acc_total += 1;
         }
-        /* l.13-21: every M_A steps rescale beta to keep A/M_A in [lo, hi], then reset A */
+        /* adaptation: every M_A steps rescale beta to keep A/M_A in [lo, hi], then reset A */
         if (cfg->adapt_interval > 0 && j % cfg->adapt_interval == 0) {
             double rate = (double)A / (double)cfg->adapt_interval;
             if (rate > cfg->acc_hi) beta = cfg->adapt_factor * beta;
@@ -366,7 +366,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
             if (beta > cfg->beta_max) beta = cfg->beta_max;
             A = 0;
         }
-        /* l.22-24 with Eq. BME2: keep the current state every T steps and pool it */
+        /* thinning and pooling (Eq. BME2): keep the current state every T steps and pool it */
         if (j % cfg->thin == 0 && j > cfg->burn_in) {
             for (int e = 0; e < d2; ++e) {
                 pool_re_r[e] += creal(rho[e]);

@@ -1,4 +1,4 @@
-// Accept / reject, step-size adaptation, thinning and pooling (Algorithm 2 l.6-24,
+// Accept / reject, step-size adaptation, thinning and pooling (Algorithm 2,
 // Eq. BME2), the diagnostics reductions (Eq. ACFrho, Eq. IACT) and small test hooks.
 #include "qst_internal.cuh"
 
@@ -42,19 +42,26 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
             // stored FP32 rho, t its exact trace, p = q / t
             const double tr = p.trace_prop[c];
             itr = (float)(1.0 / tr);
-            double logl_prop = p.C0 - p.Ntot * log(tr);
+            // log t: t is the exact trace of an already normalised rho, so |t - 1| is a few ulps;
+            // three terms of log1p(t - 1) then leave less than (t - 1)^4 / 4, far below FP64
+            // rounding (FP64 log would cost ~30 of the scarce FP64 FMAs; it is kept for
+            // |t - 1| >= 2^-10)
+            const double dl = tr - 1.0;
+            double logl_prop = p.C0 - p.Ntot * (fabs(dl) < 0x1p-10 ? dl * (1.0 - dl * (0.5 - dl * (1.0 / 3.0))) : log(tr));
             for (int g = 0; g < p.ngroups; ++g) logl_prop += p.logl_part[(int64_t)g * p.R + c];
             if (a.mode == MODE_INIT) {
                 acc = 1;
                 p.logl_cur[c] = logl_prop;
                 p.cur[c] ^= 1;
             } else {
-                // l.6-7: alpha ~ U(0,1), accept iff log alpha < log L(y') - log L(y)
+                // accept test: alpha ~ U(0,1), accept iff log alpha < log L(y') - log L(y)
                 const uint32_t chain_id = (uint32_t)(p.chain_offset + c);
                 const uint4 w = Philox::block(make_uint4(0u, a.step, chain_id, TAG_ALPHA),
                                               (uint32_t)(p.seed & 0xffffffffu), (uint32_t)(p.seed >> 32));
                 const double alpha = ((double)(w.x >> 9) + 0.5) * 0x1p-23;
-                const double log_alpha = log(alpha);
+                // log alpha in FP32 (alpha is exact in FP32; error <= 2e-6, far inside the
+                // near-tie band); the log-ratio it is compared with stays FP64
+                const double log_alpha = (double)logf((float)alpha);
                 const double logl_cur = p.logl_cur[c];
                 acc = (log_alpha < logl_prop - logl_cur) ? 1 : 0;
                 int32_t win = p.acc_win[c];
@@ -69,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
                     p.trace_acc[t] = acc;
                     p.trace_logl[t] = logl_prop;
                 }
-                // l.13-21: every M_A steps rescale beta by the window's acceptance rate
+                // adaptation: every M_A steps rescale beta by the window's acceptance rate
                 if (a.sp.adapt_interval > 0 && a.step % (uint32_t)a.sp.adapt_interval == 0) {
                     const double rate = (double)win / (double)a.sp.adapt_interval;
                     double beta = p.beta[c];
@@ -104,27 +111,41 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
         const bool vthread = (V < kThreads) ? (lane_c < P) : (vv < V);
         float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
         if (vthread) {
-#pragma unroll 4
-            for (int k = (V < kThreads ? lane_c : 0); k < nc; k += (V < kThreads ? P : 1)) {
-                const int64_t c = c0 + k;
-                float4 val;
-                if (flag[k]) {
-                    const float4 q = reinterpret_cast<const float4 *>(p.rho_prop + c * p.d_pad)[vv];
-                    const float s_ = inv_tr[k];
-                    val = make_float4(q.x * s_, q.y * s_, q.z * s_, q.w * s_);
-                    reinterpret_cast<float4 *>(p.rho_cur + c * p.d_pad)[vv] = val;
-                } else if (pool_now) {
-                    val = reinterpret_cast<const float4 *>(p.rho_cur + c * p.d_pad)[vv];
-                } else {
-                    continue;
+            // chains k0, k0 + st, ...: four loads in flight per batch, one per chain (the new
+            // current state: rho' if accepted, else the stored rho, read only when pooling)
+            const int k0 = (V < kThreads ? lane_c : 0), st = (V < kThreads ? P : 1);
+            constexpr int B = 4;
+            for (int kb = k0; kb < nc; kb += B * st) {
+                float4 q[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int k = kb + u * st;
+                    q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (k < nc && (flag[k] || pool_now)) {
+                        const int64_t c = c0 + k;
+                        const float *row = flag[k] ? p.rho_prop : p.rho_cur;
+                        q[u] = reinterpret_cast<const float4 *>(row + c * p.d_pad)[vv];
+                    }
                 }
-                if (pool_now) {
-                    sum.x += val.x;
-                    sum.y += val.y;
-                    sum.z += val.z;
-                    sum.w += val.w;
-                    if (c < p.n_diag && a.kept_idx < p.traj_cap)
-                        reinterpret_cast<float4 *>(p.traj + ((int64_t)c * p.traj_cap + a.kept_idx) * d)[vv] = val;
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int k = kb + u * st;
+                    if (k >= nc) break;
+                    const int64_t c = c0 + k;
+                    float4 val = q[u];
+                    if (flag[k]) {
+                        const float s_ = inv_tr[k];
+                        val = make_float4(val.x * s_, val.y * s_, val.z * s_, val.w * s_);
+                        reinterpret_cast<float4 *>(p.rho_cur + c * p.d_pad)[vv] = val;
+                    }
+                    if (pool_now) {
+                        sum.x += val.x;
+                        sum.y += val.y;
+                        sum.z += val.z;
+                        sum.w += val.w;
+                        if (c < p.n_diag && a.kept_idx < p.traj_cap)
+                            reinterpret_cast<float4 *>(p.traj + ((int64_t)c * p.traj_cap + a.kept_idx) * d)[vv] = val;
+                    }
                 }
             }
         }

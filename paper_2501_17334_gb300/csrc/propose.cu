@@ -1,4 +1,4 @@
-// Proposal and density-matrix assembly (Algorithm 2 l.3-4, Algorithm 1 l.2-6).
+// Proposal and density-matrix assembly (the proposal of Algorithm 2, Algorithm 1).
 //
 // One chain is handled by D consecutive lanes; lane j owns column j of the D x D
 // blocks G and H (the latent layout is column-major, so a column is D contiguous
@@ -7,11 +7,11 @@
 //      Philox block (four entries) at a time; y' goes to the chain's other y buffer (the
 //      accept kernel flips to it); lane j keeps H's column j in registers.  G's column is
 //      read back from those same (own) global writes in step 3.
-//   2. QR of H (Algorithm 1 l.4-5).  Modified Gram-Schmidt: at step k lane k publishes its
+//   2. QR of H (Algorithm 1).  Modified Gram-Schmidt: at step k lane k publishes its
 //      (unnormalised) column v_k, and every lane j > k loads it, forms |v_k|^2 and v_k^dag h_j
 //      itself and removes the projection -- no lane works alone on a normalisation.  The
 //      columns are normalised at the end.  MGS yields the unitary factor whose R has a
-//      positive real diagonal, i.e. U = Q Lambda of Algorithm 1 l.5.  Its FP32 columns are
+//      positive real diagonal, i.e. U = Q Lambda of Algorithm 1.  Its FP32 columns are
 //      orthogonal only to O(cond(H) 2^-24); with PASSES = 2 they are re-orthogonalised once:
 //      Q1 = Q2 R2 with R2 = chol(Q1^dag Q1) = I + F + O(E^2), E = Q1^dag Q1 - I,
 //      F = strict upper part of E plus half its (real) diagonal, so Q2 = Q1 (I - F) is the
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         }
     }
 
-    // ---- 2a. modified Gram-Schmidt on the columns of H (Algorithm 1 l.4-5) ------------------
+    // ---- 2a. modified Gram-Schmidt on the columns of H (Algorithm 1) ---------------------------
     // Every lane loads the published column v_k and forms r = v_k^dag h with its own column h
     // (packed f32x2 products over pairs of rows).  Lane k's column is v_k itself, so its r is
     // |v_k|^2, which the other lanes take by shuffle.  Lanes j > k project; lane k keeps
