@@ -224,8 +224,9 @@ def time_form(qst, prob, precision, steps, warmup, world, chain_offset):
     return s, ms, launches, kernel_ms, ms_profiled
 
 
-def time_handle(qst, probs, precision, steps, warmup):
-    """ms per step of one handle over `probs` (device-timed, steps after warmup)."""
+def time_handle(qst, probs, precision, steps, warmup, keep=False):
+    """ms per step of one handle over `probs` (device-timed, steps after warmup); with `keep`
+    the sampler is returned too, still open."""
     import torch
     s = qst.Sampler(probs, precision=precision, diag_chains=0)
     s.run_chains(warmup)
@@ -237,19 +238,27 @@ def time_handle(qst, probs, precision, steps, warmup):
     stop.record(stream)
     torch.cuda.synchronize()
     ms = start.elapsed_time(stop) / steps
+    if keep:
+        return ms, s
     s.close()
     return ms
 
 
-def other_configs(qst, W):
-    """The other workloads, measured briefly (one handle each; chain state resident)."""
+def other_configs(qst, W, oracle):
+    """The other workloads, measured briefly (one handle each; chain state resident).  At
+    configuration 3 every form of the projection runs, each with its log L error against the
+    oracle on 1024 of its chains' current states."""
     out = {}
-    for c, form, steps in [(1, "fp32", 2000), (2, "fp32", 1000), (3, "fp32", 300), (3, "bf16x3", 300)]:
+    precs = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "tf32": qst.PREC_TF32, "tf32x2": qst.PREC_TF32X2}
+    for c, form, steps in [(1, "fp32", 2000), (2, "fp32", 1000), (3, "fp32", 300), (3, "bf16x3", 300),
+                           (3, "tf32", 300), (3, "tf32x2", 300)]:
         prob = W.config_problem(c)
-        prec = qst.PREC_FP32 if form == "fp32" else qst.PREC_BF16X3
-        ms = time_handle(qst, prob, prec, steps, 5)
+        ms, s = time_handle(qst, prob, precs[form], steps, 5, keep=True)
         out[f"config{c}_{form}"] = {"chains": prob.num_chains, "qubits": prob.num_qubits, "ms_per_step": ms,
                                     "chain_steps_per_s": prob.num_chains / (ms / 1000.0), "steps": steps}
+        if c == 3:
+            out[f"config{c}_{form}"]["logl_err"] = logl_error(qst, oracle, s, prob)
+        s.close()
     # configuration 5: 64 problems of 1..5 qubits with uneven chain counts in one handle (one
     # launch per kernel and problem per step, replayed as a CUDA graph), mixed form; the plain
     # FP32 form on the same batch for comparison (few steps: its 5-qubit projections are slow)
@@ -484,7 +493,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(oracle, prob)
     if world == 1 and not args.no_configs:
-        line["configs"] = other_configs(qst, W)
+        line["configs"] = other_configs(qst, W, oracle)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

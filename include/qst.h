@@ -49,9 +49,15 @@ typedef enum {
 
 /* Arithmetic of the projector contraction p = vec_h(rho) . P (Sec. II, p_kl = Tr Lambda_kl rho). */
 typedef enum {
-    QST_PREC_FP32 = 0,  /* plain FP32 SIMT contraction */
-    QST_PREC_BF16X3 = 1 /* tcgen05 tensor cores: rho split into three bf16 terms against the
-                           exactly-representable Pauli projector matrix, FP32 accumulation */
+    QST_PREC_FP32 = 0,   /* plain FP32 SIMT contraction */
+    QST_PREC_BF16X3 = 1, /* tcgen05 tensor cores: rho split into three bf16 terms against the
+                            exactly-representable Pauli projector matrix, FP32 accumulation
+                            (hi products and mid + lo products in two accumulators); 1..5 qubits */
+    QST_PREC_TF32 = 2,   /* tcgen05 kind::tf32: rho rounded once to TF32 (11 significant bits),
+                            FP32 accumulation; 1..4 qubits.  Its log L error is O(1) at 4 qubits:
+                            a comparison form, not an accurate one */
+    QST_PREC_TF32X2 = 3  /* tcgen05 kind::tf32: rho = hi + lo, both TF32 (22 significant bits),
+                            hi and lo products in two accumulators; 1..3 qubits */
 } qst_precision;
 
 /* One tomography problem (Sec. III Steps 1-4).  All pointers are host memory,
@@ -141,7 +147,9 @@ qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_prob
 /* Validates the problems (Sec. III Step 1: counts >= 0; each Lambda_kl Hermitian and
  * sum_l Lambda_kl = I to 1e-12; Q in 1..5; R >= 1; T >= 1; 0 < beta0 <= beta_max <= 1 for the
  * config's and every problem's own beta0 (0 meaning the config's);
- * for QST_PREC_BF16X3 every packed projector entry exactly representable in bf16),
+ * for the tensor-core precisions every packed projector entry exactly representable in
+ * bf16 (QST_PREC_BF16X3) or TF32 (QST_PREC_TF32, QST_PREC_TF32X2), and Q within the
+ * precision's range: QST_ERR_INVALID_ARG otherwise),
  * packs the projectors, uploads everything into the workspace and enqueues the chains'
  * initial states y^0 ~ N(0, I) with rho(y^0) and log L(y^0) (Algorithm 2, initialisation).
  * d_workspace: device memory of at least qst_workspace_size bytes, 256-byte aligned,

@@ -63,6 +63,25 @@ void pack_projectors(int D, int KD, const double *re, const double *im, double *
 
 // Is v a bf16 value up to FP64 round-off of its construction (relative 1e-12, the same
 // tolerance as the completeness check)?  Then the bf16 value is used.
+// operand kind of the tensor-core projection for a precision (TC_NONE: the plain FP32 form)
+int tc_kind_of(int32_t precision) {
+    switch (precision) {
+        case QST_PREC_BF16X3: return TC_BF16X3;
+        case QST_PREC_TF32: return TC_TF32;
+        case QST_PREC_TF32X2: return TC_TF32X2;
+        default: return TC_NONE;
+    }
+}
+
+// v is exactly a TF32 value: an FP32 value whose 13 low mantissa bits are zero
+bool tf32_exact(double v) {
+    const float f = (float)v;
+    if ((double)f != v) return false;
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return (u & 0x1FFFu) == 0u;
+}
+
 bool bf16_exact(double v) {
     const double r = (double)__bfloat162float(__float2bfloat16_rn((float)v));
     return std::fabs(r - v) <= 1e-12 * std::fabs(v);
@@ -72,7 +91,7 @@ bool bf16_exact(double v) {
 // Per-problem host record and workspace layout
 // ------------------------------------------------------------------------------------------
 struct Layout {
-    size_t P32, Pbf, cnt, invf, ptot, colw, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, coef,
+    size_t P32, Ptc, cnt, invf, ptot, colw, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, coef,
         acc_win,
         acc_total, pool, traj, trace_acc, trace_logl, red, acf, logl_eval, end;
 };
@@ -85,7 +104,8 @@ struct HostProblem {
     double beta0 = 0.0;
     Layout off{};
     std::vector<float> P32;
-    std::vector<__nv_bfloat16> Pbf;
+    std::vector<__nv_bfloat16> Pbf;   // tensor-core B operand, BF16x3
+    std::vector<float> Ptf;           // tensor-core B operand, TF32 forms
     std::vector<float> cnt, invf, ptot;
     TcPlan *tc = nullptr;
 };
@@ -109,7 +129,8 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
     if (cfg->burn_in < 0) return fail(QST_ERR_INVALID_ARG, "burn_in must be >= 0");
     if (cfg->diag_chains < 0 || cfg->traj_capacity < 0 || cfg->acf_lmax < 0 || cfg->trace_steps < 0)
         return fail(QST_ERR_INVALID_ARG, "diagnostic sizes must be >= 0");
-    if (cfg->precision != QST_PREC_FP32 && cfg->precision != QST_PREC_BF16X3)
+    if (cfg->precision != QST_PREC_FP32 && cfg->precision != QST_PREC_BF16X3 && cfg->precision != QST_PREC_TF32 &&
+        cfg->precision != QST_PREC_TF32X2)
         return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
     if (cfg->qr_passes != 1 && cfg->qr_passes != 2)
         return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1 or 2");
@@ -123,6 +144,9 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
         return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..5", idx, d.num_qubits);
     if (d.num_povms < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_povms must be >= 1", idx);
     if (!d.counts || !d.povm_re || !d.povm_im) return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
+    if (tc_kind_of(cfg->precision) != TC_NONE && !tc_supported(tc_kind_of(cfg->precision), 1 << d.num_qubits))
+        return fail(QST_ERR_INVALID_ARG, "problem %d: precision %d does not cover %d qubits (TF32: 1..4, TF32x2: 1..3)",
+                    idx, cfg->precision, d.num_qubits);
     if (d.num_chains < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_chains must be >= 1", idx);
     if (d.chain_offset < 0 || d.chain_offset + d.num_chains > (int64_t(1) << 32))
         return fail(QST_ERR_INVALID_ARG, "problem %d: chain ids must fit 32 bits", idx);
@@ -188,7 +212,9 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         v.chain_offset = d.chain_offset;
         v.seed = d.seed;
         hp.beta0 = d.beta0 > 0.0 ? d.beta0 : cfg->beta0;
-        const bool tc = cfg->precision == QST_PREC_BF16X3;
+        const int kind = tc_kind_of(cfg->precision);
+        const bool tc = kind != TC_NONE;
+        v.tc_kind = kind;
         if (tc) {
             const int nt = tc_column_tile(v.D, v.KD);
             if (nt <= 0) return fail(QST_ERR_UNSUPPORTED, "problem %d: no tensor-core column tile for %d projectors", i, v.KD);
@@ -203,7 +229,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         hp.P32.assign((size_t)v.d_pad * v.KD_pad, 0.0f);
         for (int r = 0; r < v.d; ++r)
             for (int m = 0; m < v.KD; ++m) hp.P32[(size_t)r * v.KD_pad + m] = (float)P[(size_t)r * v.KD + m];
-        if (tc) {
+        if (kind == TC_BF16X3) {
             hp.Pbf.assign((size_t)v.KD_tc * v.d_pad, __float2bfloat16_rn(0.0f));
             for (int r = 0; r < v.d; ++r)
                 for (int m = 0; m < v.KD; ++m) {
@@ -214,6 +240,17 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
                                     i, x);
                     hp.Pbf[(size_t)m * v.d_pad + r] = __float2bfloat16_rn((float)x);
                     hp.P32[(size_t)r * v.KD_pad + m] = __bfloat162float(hp.Pbf[(size_t)m * v.d_pad + r]);
+                }
+        } else if (tc) {
+            hp.Ptf.assign((size_t)v.KD_tc * v.d_pad, 0.0f);
+            for (int r = 0; r < v.d; ++r)
+                for (int m = 0; m < v.KD; ++m) {
+                    const double x = P[(size_t)r * v.KD + m];
+                    if (!tf32_exact(x))
+                        return fail(QST_ERR_INVALID_ARG,
+                                    "problem %d: packed projector entry %.17g is not exact in TF32; use QST_PREC_FP32",
+                                    i, x);
+                    hp.Ptf[(size_t)m * v.d_pad + r] = (float)x;
                 }
         }
         // deviance weights: log L = C0 + sum_{c>0} c log(p * invf), invf = P_k / c (as float)
@@ -265,7 +302,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         Layout &L = hp.off;
         const int64_t R = v.R;
         L.P32 = take(sizeof(float) * hp.P32.size());
-        L.Pbf = take(tc ? sizeof(__nv_bfloat16) * hp.Pbf.size() : 0);
+        L.Ptc = take(tc ? (size_t)tc_elem_bytes(kind) * v.KD_tc * v.d_pad : 0);
         L.cnt = take(sizeof(float) * hp.KDmax);
         L.invf = take(sizeof(float) * hp.KDmax);
         L.ptot = take(sizeof(float) * (hp.KDmax / v.D));
@@ -274,7 +311,7 @@ qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler
         L.cur = take(R);
         L.rho_cur = take(sizeof(float) * R * v.d_pad);
         L.rho_prop = take(sizeof(float) * R * v.d_pad);
-        L.rho_split = take(tc ? sizeof(__nv_bfloat16) * 3 * R * v.d_pad : 0);
+        L.rho_split = take(tc ? (size_t)tc_elem_bytes(kind) * tc_splits(kind) * R * v.d_pad : 0);
         L.trace_prop = take(sizeof(double) * R);
         L.logl_cur = take(sizeof(double) * R);
         L.logl_part = take(sizeof(double) * hp.part_slots * R);
@@ -390,7 +427,7 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     ProblemView &v = hp.v;
     const Layout &L = hp.off;
     v.P32 = reinterpret_cast<const float *>(b + L.P32);
-    v.Pbf = reinterpret_cast<const __nv_bfloat16 *>(b + L.Pbf);
+    v.Ptc = b + L.Ptc;
     v.cnt = reinterpret_cast<const float *>(b + L.cnt);
     v.invf = reinterpret_cast<const float *>(b + L.invf);
     v.ptot = reinterpret_cast<const float *>(b + L.ptot);
@@ -399,7 +436,7 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     v.cur = reinterpret_cast<uint8_t *>(b + L.cur);
     v.rho_cur = reinterpret_cast<float *>(b + L.rho_cur);
     v.rho_prop = reinterpret_cast<float *>(b + L.rho_prop);
-    v.rho_split = reinterpret_cast<__nv_bfloat16 *>(b + L.rho_split);
+    v.rho_split = b + L.rho_split;
     v.trace_prop = reinterpret_cast<double *>(b + L.trace_prop);
     v.logl_cur = reinterpret_cast<double *>(b + L.logl_cur);
     v.logl_part = reinterpret_cast<double *>(b + L.logl_part);
@@ -414,7 +451,7 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     return QST_OK;
 }
 
-bool is_tc(const qst_handle *h) { return h->cfg.precision == QST_PREC_BF16X3; }
+bool is_tc(const qst_handle *h) { return tc_kind_of(h->cfg.precision) != TC_NONE; }
 
 // proposal -> projection -> (accept) for one problem
 qst_status enqueue_projection(qst_handle *h, HostProblem &hp, int64_t rows, float *p_out) {
@@ -577,9 +614,12 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
         const Layout &L = hp.off;
         QST_CUDA(cudaMemcpyAsync(h->ws + L.P32, hp.P32.data(), sizeof(float) * hp.P32.size(), cudaMemcpyHostToDevice,
                                  h->stream), "upload P");
-        if (is_tc(h.get()))
-            QST_CUDA(cudaMemcpyAsync(h->ws + L.Pbf, hp.Pbf.data(), sizeof(__nv_bfloat16) * hp.Pbf.size(),
+        if (!hp.Pbf.empty())
+            QST_CUDA(cudaMemcpyAsync(h->ws + L.Ptc, hp.Pbf.data(), sizeof(__nv_bfloat16) * hp.Pbf.size(),
                                      cudaMemcpyHostToDevice, h->stream), "upload P (bf16)");
+        if (!hp.Ptf.empty())
+            QST_CUDA(cudaMemcpyAsync(h->ws + L.Ptc, hp.Ptf.data(), sizeof(float) * hp.Ptf.size(),
+                                     cudaMemcpyHostToDevice, h->stream), "upload P (TF32)");
         QST_CUDA(cudaMemcpyAsync(h->ws + L.cnt, hp.cnt.data(), sizeof(float) * hp.KDmax, cudaMemcpyHostToDevice,
                                  h->stream), "upload counts");
         QST_CUDA(cudaMemcpyAsync(h->ws + L.invf, hp.invf.data(), sizeof(float) * hp.KDmax, cudaMemcpyHostToDevice,
@@ -612,6 +652,7 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
         if (st != QST_OK) return st;
         std::vector<float>().swap(hp.P32);
         std::vector<__nv_bfloat16>().swap(hp.Pbf);
+        std::vector<float>().swap(hp.Ptf);
     }
     if (cfg->autotune) {
         st = autotune_groups(h.get());

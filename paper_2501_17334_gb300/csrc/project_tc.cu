@@ -59,20 +59,33 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_N = 128;
 constexpr int TC_KATOM = 64;                       // bf16 elements per 128-byte swizzle row
-constexpr int TC_ATOM_BYTES = TC_M * TC_KATOM * 2; // 16 KB: 128 rows x 128 B
+constexpr int TC_ATOM_BYTES = TC_M * 128;          // 16 KB: 128 rows x 128 B (64 bf16 or 32 TF32 of K)
 constexpr int TC_BSTAGES = 5;
 constexpr int TC_EPI_PER_QUAD = 4;                           // epilogue warps per lane quadrant
 constexpr int TC_EPI_COLS = TC_N / TC_EPI_PER_QUAD;           // columns per epilogue warp (32)
 constexpr int TC_FIRST_EPI = 3;                               // first epilogue warp
 constexpr int TC_THREADS = (TC_FIRST_EPI + 4 * TC_EPI_PER_QUAD) * 32;   // 608
-constexpr int TC_MAX_KCHUNK = 4;                              // d_pad <= 256
+constexpr int TC_MAX_KCHUNK = 8;                              // d_pad <= 256 at 32 TF32 per atom
 constexpr uint32_t TC_TMEM_COLS = 512;   // hi and mid + lo accumulators, 2 buffers of the lo split
 constexpr uint32_t TC_REST_COL = TC_N;         // first column of the mid + lo accumulator
 constexpr uint32_t TC_ALO_COL = 2 * TC_N;      // first column of the lo-split buffers
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;     // 1 s
 
+// What each operand kind keeps where (TcKind): K elements per 128-byte atom row, the A splits
+// resident in shared memory, whether a bf16 lo split goes through tensor memory, whether a
+// second accumulator takes the smaller splits, and the A/B format of the instruction
+// descriptor (BF16 = 1, TF32 = 2).
+template <int KIND>
+struct TcOps {
+    static constexpr int katom = 128 / tc_elem_bytes(KIND);
+    static constexpr int smem_splits = KIND == TC_TF32 ? 1 : 2;
+    static constexpr bool lo_in_tmem = KIND == TC_BF16X3;
+    static constexpr bool two_acc = KIND != TC_TF32;
+    static constexpr uint32_t fmt = KIND == TC_BF16X3 ? 1u : 2u;
+};
+
 struct TcArgs {
-    const __nv_bfloat16 *a_split;   // [rows][3 d_pad] hi, mid, lo (the lo part goes through TMEM)
+    const void *a_split;   // [rows][splits d_pad] the A operand (bf16 hi, mid, lo -- lo through TMEM -- or TF32 hi[, lo])
     const float4 *colw;    // [KD_tc / 2] per column pair (invf, invf, add, add): x = q invf + add
     const float *cnt;      // [KD_tc] counts as float
     const float *ptot;     // [KD_tc / D] shots per setting
@@ -83,7 +96,7 @@ struct TcArgs {
     int64_t rows;
     int64_t units;         // M tiles * ngroups
     int KD;
-    int n_katoms;          // d_pad / 64
+    int n_katoms;          // d_pad / (K elements per atom)
     int ntiles;            // KD_tc / 128
     int tiles_per_group;
     int ngroups;
@@ -167,10 +180,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
     return d;
 }
-// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128, N = n (a multiple
-// of 16, at most 128: the last N tile of a problem only covers its remaining columns).
-__host__ __device__ constexpr uint32_t mma_idesc(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+// Instruction descriptor of kind::f16 (fmt 1: A/B BF16) and kind::tf32 (fmt 2: A/B TF32): D F32,
+// both operands K-major, M = 128, N = n (a multiple of 16: the last N tile of a problem only
+// covers its remaining columns).
+__host__ __device__ constexpr uint32_t mma_idesc(int n, uint32_t fmt = 1u) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -179,7 +193,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
             d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
-// the same MMA with A read from tensor memory (row m = TMEM lane m, K packed two per column)
+// M128 Nn K8 TF32 MMA, both operands from shared memory (one 32-byte K step, as above)
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+template <int KIND>
+__device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    if constexpr (KIND == TC_BF16X3)
+        mma_bf16(d_tmem, a, b, idesc, accumulate);
+    else
+        mma_tf32(d_tmem, a, b, idesc, accumulate);
+}
+// the bf16 MMA with A read from tensor memory (row m = TMEM lane m, K packed two per column)
 __device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                             uint32_t accumulate) {
     asm volatile(
@@ -199,6 +227,20 @@ __device__ __forceinline__ bool elect_one() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float (&va)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) va[i] = __uint_as_float(r[i]);
+}
 // two 32-column slices (the same lanes), one wait for both
 __device__ __forceinline__ void tmem_ld32_pair(uint32_t ta, uint32_t tb, float (&va)[32], float (&vb)[32]) {
     uint32_t r[32], q[32];
@@ -314,9 +356,10 @@ __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&r)[NC])
 // Padded K (d_pad) of the packed rho for D: D^2 rounded up to 64.
 __host__ __device__ constexpr int tc_dpad(int D) { return (D * D + 63) / 64 * 64; }
 
-template <int D>
+template <int D, int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     project_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    using T = TcOps<KIND>;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ __align__(8) uint64_t bar_a_full[TC_MAX_KCHUNK];
     __shared__ __align__(8) uint64_t bar_a_empty[TC_MAX_KCHUNK];
@@ -334,8 +377,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // 1024-byte aligned, by pointer arithmetic on the shared array (so accesses stay ld.shared)
     uint8_t *base = dyn_smem + ((1024u - (smem_u32(dyn_smem) & 1023u)) & 1023u);
     const int nk = a.n_katoms;
-    uint8_t *smA = base;                                          // atom (split sp < 2, chunk kc) at sp * nk + kc
-    uint8_t *smB = base + (size_t)2 * nk * TC_ATOM_BYTES;
+    uint8_t *smA = base;                                          // atom (split sp, chunk kc) at sp * nk + kc
+    uint8_t *smB = base + (size_t)T::smem_splits * nk * TC_ATOM_BYTES;
     // the epilogue's per-column weights, staged once: (invf, invf, add, add) and (c, c) per column
     // pair, shots per setting
     const int kd_tc = a.ntiles * TC_N;
@@ -407,7 +450,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     if (elect_one()) {
                         mbar_expect_tx(smem_u32(&bar_b_full[s]), (uint32_t)TC_ATOM_BYTES);
-                        tma_load_2d(smem_u32(smB + (size_t)s * TC_ATOM_BYTES), &tmB, kc * TC_KATOM, t * TC_N,
+                        tma_load_2d(smem_u32(smB + (size_t)s * TC_ATOM_BYTES), &tmB, kc * T::katom, t * TC_N,
                                     smem_u32(&bar_b_full[s]));
                     }
                     __syncwarp();
@@ -436,10 +479,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 if (elect_one()) {
-                    mbar_expect_tx(smem_u32(&bar_a_full[kc]), (uint32_t)(2 * TC_ATOM_BYTES));
-                    for (int sp = 0; sp < 2; ++sp)
+                    mbar_expect_tx(smem_u32(&bar_a_full[kc]), (uint32_t)(T::smem_splits * TC_ATOM_BYTES));
+                    for (int sp = 0; sp < T::smem_splits; ++sp)
                         tma_load_2d(smem_u32(smA + (size_t)(sp * nk + kc) * TC_ATOM_BYTES), &tmA,
-                                    (sp * nk + kc) * TC_KATOM, m0, smem_u32(&bar_a_full[kc]));
+                                    (sp * nk + kc) * T::katom, m0, smem_u32(&bar_a_full[kc]));
                 }
                 __syncwarp();
             }
@@ -467,14 +510,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int t = tile_at(u, tb, te, i);
                 const uint32_t use = (uint32_t)tcount & 1u;   // the accumulators' use parity
                 if (!wait_all(smem_u32(&bar_acc_empty), use ^ 1u) ||
-                    (i == 0 && !wait_all(smem_u32(&bar_alo_full[uc & 1u]), (uc >> 1) & 1u))) {
+                    (T::lo_in_tmem && i == 0 && !wait_all(smem_u32(&bar_alo_full[uc & 1u]), (uc >> 1) & 1u))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d_hi = tmem, d_rest = tmem + TC_REST_COL;
                 const int n_valid = min(TC_N, (a.KD - t * TC_N + 15) / 16 * 16);
-                const uint32_t idesc = mma_idesc(n_valid);
+                const uint32_t idesc = mma_idesc(n_valid, T::fmt);
                 const uint32_t alo_tmem = tmem + TC_ALO_COL + (uc & 1u) * (uint32_t)TC_N;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int s = it % TC_BSTAGES;
@@ -487,18 +530,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint64_t bd = bdesc0 + (uint64_t)((s * TC_ATOM_BYTES) >> 4);
                     const uint64_t ad_hi = adesc0 + (uint64_t)((kc * TC_ATOM_BYTES) >> 4);
-                    const uint64_t ad_mid = adesc0 + (uint64_t)(((nk + kc) * TC_ATOM_BYTES) >> 4);
+                    const uint64_t ad_2 = adesc0 + (uint64_t)(((nk + kc) * TC_ATOM_BYTES) >> 4);   // mid / TF32 lo
                     const uint32_t ad_lo = alo_tmem + (uint32_t)(kc * TC_KATOM / 2);
                     if (elect_one()) {
+                        // four MMAs per 128-byte atom row: 32 bytes of K (16 bf16 or 8 TF32) each,
+                        // 2 descriptor units
 #pragma unroll
-                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)   // 16 K = 32 bytes = 2 descriptor units
-                            mma_bf16(d_hi, ad_hi + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_ss<KIND>(d_hi, ad_hi + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+                        if constexpr (T::smem_splits == 2) {
 #pragma unroll
-                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)
-                            mma_bf16(d_rest, ad_mid + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_ss<KIND>(d_rest, ad_2 + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0 ? 1u : 0u);
+                        }
+                        if constexpr (T::lo_in_tmem) {
 #pragma unroll
-                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)   // lo split, A from tensor memory
-                            mma_bf16_ta(d_rest, ad_lo + (uint32_t)(kk * 8), bd + 2 * kk, idesc, 1u);
+                            for (int kk = 0; kk < 4; ++kk)   // lo split, A from tensor memory
+                                mma_bf16_ta(d_rest, ad_lo + (uint32_t)(kk * 8), bd + 2 * kk, idesc, 1u);
+                        }
                         mma_commit(smem_u32(&bar_b_empty[s]));
                         if (i == te - tb - 1) mma_commit(smem_u32(&bar_a_empty[kc]));   // last reader of this A chunk
                     }
@@ -532,8 +581,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         auto alo_fetch = [&](int64_t u, int piece) {
             const int64_t row = (u / a.ngroups) * TC_M + quad * 32 + lane;
             if (row >= a.rows) return make_uint4(0u, 0u, 0u, 0u);
-            const uint4 *src =
-                reinterpret_cast<const uint4 *>(a.a_split + row * 3 * DP + 2 * DP + sub * (DP / TC_EPI_PER_QUAD));
+            const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(a.a_split) +
+                                                               row * 3 * DP + 2 * DP + sub * (DP / TC_EPI_PER_QUAD));
             return __ldg(src + piece);
         };
         auto alo_store = [&](uint32_t b, int piece, uint4 w) {
@@ -546,7 +595,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_before();
             mbar_arrive(smem_u32(&bar_alo_full[b]));
         };
-        if (blockIdx.x < a.units) {
+        if (T::lo_in_tmem && blockIdx.x < a.units) {
             for (int piece = 0; piece < NP; ++piece) alo_store(0u, piece, alo_fetch(blockIdx.x, piece));
             alo_done(0u);
         }
@@ -557,7 +606,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // the next unit's lo split goes into the other buffer: its last readers (the MMAs of
             // the unit before this one) completed before this warp received that unit's last
             // accumulator
-            const bool has_next = u + gridDim.x < a.units;
+            const bool has_next = T::lo_in_tmem && u + gridDim.x < a.units;
             const uint32_t nb_buf = (ucount + 1) & 1u;
             int tb, te;
             unit_tiles(u, tb, te);
@@ -580,9 +629,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const int n0 = tt * TC_N + col0;
                 float v[32];
-                {
+                const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
+                if constexpr (T::two_acc) {
                     float vr[32];
-                    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
                     tmem_ld32_pair(lane_base, lane_base + TC_REST_COL, v, vr);
                     tc_fence_before();
                     mbar_arrive(smem_u32(&bar_acc_empty));   // both slices are in registers
@@ -592,6 +641,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         v[i] = q.x;
                         v[i + 1] = q.y;
                     }
+                } else {
+                    tmem_ld32(lane_base, v);
+                    tc_fence_before();
+                    mbar_arrive(smem_u32(&bar_acc_empty));   // the slice is in registers
                 }
                 float tile_sum = 0.0f;
                 if (n0 < a.KD) {   // (columns past KD: the last tile's MMA did not write them)
@@ -893,24 +946,27 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-bool encode_bf16_2d(CUtensorMap *map, const void *ptr, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                    uint32_t box_outer) {
+// 2-D row-major map (inner elements contiguous) of bf16 or FP32 elements, 128-byte swizzle
+bool encode_2d(CUtensorMap *map, const void *ptr, int elem_bytes, uint64_t inner, uint64_t outer, uint32_t box_inner,
+               uint32_t box_outer) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint64_t strides[1] = {inner * (cuuint64_t)elem_bytes};
     const cuuint32_t box[2] = {box_inner, box_outer};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+    const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = enc(map, dt, 2, const_cast<void *>(ptr), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-// A (hi, mid), the P ring, then the epilogue's weights
-size_t tc_smem_bytes(int n_katoms, int kd_tc, int D) {
-    return 1024 + (size_t)(2 * n_katoms + TC_BSTAGES) * TC_ATOM_BYTES + (size_t)(kd_tc / 2) * (sizeof(float4) + sizeof(float2)) +
-           (size_t)(kd_tc / D) * sizeof(float);
+// A (the splits held in shared memory), the P ring, then the epilogue's weights
+size_t tc_smem_bytes(int kind, int n_katoms, int kd_tc, int D) {
+    const int splits = kind == TC_TF32 ? 1 : 2;
+    return 1024 + (size_t)(splits * n_katoms + TC_BSTAGES) * TC_ATOM_BYTES +
+           (size_t)(kd_tc / 2) * (sizeof(float4) + sizeof(float2)) + (size_t)(kd_tc / D) * sizeof(float);
 }
 
 }  // namespace
@@ -918,26 +974,50 @@ size_t tc_smem_bytes(int n_katoms, int kd_tc, int D) {
 struct TcPlan {
     CUtensorMap a;
     CUtensorMap b;
-    const __nv_bfloat16 *a_split;
+    const void *a_split;
+    int kind;
     int n_katoms;
     int ntiles;
 };
 
 namespace {
-template <int D>
-cudaError_t launch_tc_d(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
+template <int D, int KIND>
+cudaError_t launch_tc_dk(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(project_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(project_tc_kernel<D, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    project_tc_kernel<D><<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
+    project_tc_kernel<D, KIND><<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
     return cudaGetLastError();
+}
+template <int D>
+cudaError_t launch_tc_d(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
+    switch (plan->kind) {
+        case TC_BF16X3: return launch_tc_dk<D, TC_BF16X3>(plan, a, grid, smem, s);
+        case TC_TF32: return launch_tc_dk<D, TC_TF32>(plan, a, grid, smem, s);
+        case TC_TF32X2:
+            if constexpr (D <= 8) return launch_tc_dk<D, TC_TF32X2>(plan, a, grid, smem, s);
+            return cudaErrorNotSupported;
+        default: return cudaErrorNotSupported;
+    }
 }
 }  // namespace
 
 int tc_column_tile(int D, int KD) { return KD > 0 ? (D == 32 ? TCW_N : TC_N) : 0; }
+
+// BF16x3 to D = 32 (the streamed kernel above D = 16); TF32 keeps its one A split in shared
+// memory to D = 16 (128 KB at D = 16); TF32x2 keeps two, to D = 8.
+bool tc_supported(int kind, int D) {
+    switch (kind) {
+        case TC_BF16X3: return D >= 2 && D <= 32;
+        case TC_TF32: return D >= 2 && D <= 16;
+        case TC_TF32X2: return D >= 2 && D <= 8;
+        default: return false;
+    }
+}
 // (a setting's D outcome columns never straddle a tile: D divides the tile width)
 
 // Partial sums per chain: four column slices times the column groups that split the N tiles
@@ -951,23 +1031,28 @@ int tc_ngroups(const ProblemView &p, int64_t rows) {
     return 4 * (g > ntiles ? ntiles : g);
 }
 
-cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, int64_t rows, TcPlan **plan) {
+cudaError_t tc_plan_create(const ProblemView &p, const void *A_split, int64_t rows, TcPlan **plan) {
     *plan = nullptr;
-    const bool wide = p.D == 32;
+    const int kind = p.tc_kind;
+    if (!tc_supported(kind, p.D)) return cudaErrorNotSupported;
+    const bool wide = p.D == 32;   // BF16x3 only
     const int n_tile = wide ? TCW_N : TC_N;
-    if (p.d_pad % TC_KATOM != 0 || p.KD_tc % n_tile != 0 || p.KD_tc <= 0) return cudaErrorNotSupported;
-    const int n_katoms = p.d_pad / TC_KATOM;
+    const int eb = tc_elem_bytes(kind);
+    const int katom = 128 / eb;
+    if (p.d_pad % katom != 0 || p.KD_tc % n_tile != 0 || p.KD_tc <= 0) return cudaErrorNotSupported;
+    const int n_katoms = p.d_pad / katom;
     if (!wide && n_katoms > TC_MAX_KCHUNK) return cudaErrorNotSupported;
     if (p.d_pad != tc_dpad(p.D)) return cudaErrorNotSupported;
-    if (!wide && tc_smem_bytes(n_katoms, p.KD_tc, p.D) > 227 * 1024 - 256) return cudaErrorNotSupported;
-    if (reinterpret_cast<uintptr_t>(A_split) % 16 != 0 || reinterpret_cast<uintptr_t>(p.Pbf) % 16 != 0)
+    if (!wide && tc_smem_bytes(kind, n_katoms, p.KD_tc, p.D) > 227 * 1024 - 256) return cudaErrorNotSupported;
+    if (reinterpret_cast<uintptr_t>(A_split) % 16 != 0 || reinterpret_cast<uintptr_t>(p.Ptc) % 16 != 0)
         return cudaErrorMisalignedAddress;
     TcPlan *pl = new TcPlan();
+    pl->kind = kind;
     pl->n_katoms = n_katoms;
     pl->a_split = A_split;
     pl->ntiles = p.KD_tc / n_tile;
-    const bool ok_a = encode_bf16_2d(&pl->a, A_split, (uint64_t)3 * p.d_pad, (uint64_t)rows, TC_KATOM, TC_M);
-    const bool ok_b = encode_bf16_2d(&pl->b, p.Pbf, (uint64_t)p.d_pad, (uint64_t)p.KD_tc, TC_KATOM, n_tile);
+    const bool ok_a = encode_2d(&pl->a, A_split, eb, (uint64_t)tc_splits(kind) * p.d_pad, (uint64_t)rows, katom, TC_M);
+    const bool ok_b = encode_2d(&pl->b, p.Ptc, eb, (uint64_t)p.d_pad, (uint64_t)p.KD_tc, katom, n_tile);
     if (!ok_a || !ok_b) {
         delete pl;
         return cudaErrorInvalidValue;
@@ -1018,7 +1103,7 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
         project_tc_wide_kernel<<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
         return cudaGetLastError();
     }
-    const size_t smem = tc_smem_bytes(plan->n_katoms, plan->ntiles * TC_N, p.D);
+    const size_t smem = tc_smem_bytes(plan->kind, plan->n_katoms, plan->ntiles * TC_N, p.D);
     switch (p.D) {
         case 2: return launch_tc_d<2>(plan, a, grid, smem, s);
         case 4: return launch_tc_d<4>(plan, a, grid, smem, s);

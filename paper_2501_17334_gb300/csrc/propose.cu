@@ -128,6 +128,14 @@ __device__ __forceinline__ void store_column2(float *dst, const float2 (&v)[D / 
 
 __device__ __forceinline__ float hsum(float2 v) { return v.x + v.y; }
 
+// x rounded to TF32 (11 significant bits, nearest, ties away from zero), in an FP32 container
+// whose low 13 mantissa bits are zero; x - tf32_rna(x) is exact in FP32
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 template <int D>
 __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
@@ -162,7 +170,9 @@ struct ProposeArgs {
     const uint8_t *cur;         // [R]
     const float2 *coef;         // [R] (sqrt(1 - beta^2), beta) as floats
     float *rho_out;             // [rows][d_pad] packed rho (FP32-normalised)
-    __nv_bfloat16 *split_out;   // [rows][3][d_pad] or null
+    __nv_bfloat16 *split_out;   // [rows][3][d_pad] bf16 hi/mid/lo, or null
+    float *split_tf;            // [rows][tf_splits][d_pad] TF32 hi[, lo], or null
+    int tf_splits;              // 1 or 2
     double *trace_out;          // [rows] exact trace of the stored rho (1 up to rounding)
     float *rho_norm_out;        // MODE_EVAL, optional: [rows][d] copy of the packed rho
     int64_t rows;
@@ -602,6 +612,14 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                 *reinterpret_cast<uint2 *>(sp + a.d_pad) = *reinterpret_cast<const uint2 *>(ms);
                 *reinterpret_cast<uint2 *>(sp + 2 * a.d_pad) = *reinterpret_cast<const uint2 *>(ls);
             }
+            if (a.split_tf) {   // TF32 hi = v rounded to 11 significant bits, lo = TF32(v - hi)
+                const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+                float *sp = a.split_tf + c * (int64_t)a.tf_splits * a.d_pad + e;
+                *reinterpret_cast<float4 *>(sp) = hi;
+                if (a.tf_splits == 2)
+                    *reinterpret_cast<float4 *>(sp + a.d_pad) = make_float4(
+                        tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z), tf32_rna(v.w - hi.w));
+            }
         }
     }
 }
@@ -960,7 +978,10 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.cur = p.cur;
     a.coef = p.coef;
     a.rho_out = p.rho_prop;
-    a.split_out = want_split ? p.rho_split : nullptr;
+    a.split_out = (want_split && p.tc_kind == TC_BF16X3) ? static_cast<__nv_bfloat16 *>(p.rho_split) : nullptr;
+    a.split_tf = (want_split && (p.tc_kind == TC_TF32 || p.tc_kind == TC_TF32X2)) ? static_cast<float *>(p.rho_split)
+                                                                                   : nullptr;
+    a.tf_splits = tc_splits(p.tc_kind);
     a.trace_out = p.trace_prop;
     a.rho_norm_out = (mode == MODE_EVAL) ? rho_norm_out : nullptr;
     a.rows = rows;
@@ -972,6 +993,7 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.mode = mode;
     a.d_pad = p.d_pad;
     if constexpr (D == 32) {
+        if (a.split_tf) return cudaErrorNotSupported;   // the TF32 forms stop at D = 16
         return launch_propose_d32<PASSES>(a, s);
     } else {
         using S = Shape<D>;

@@ -87,8 +87,16 @@ struct StepState {
     int64_t kept_count;  // kept states so far, this step included
 };
 
+// Operand kind of the tensor-core projection (the mixed forms).  TC_BF16X3: rho split into
+// bf16 hi + mid + lo, P in bf16 (kind::f16).  TC_TF32: rho rounded to TF32 once, P in TF32
+// (kind::tf32).  TC_TF32X2: rho = hi + lo, both TF32 (kind::tf32).
+enum TcKind { TC_NONE = 0, TC_BF16X3 = 1, TC_TF32 = 2, TC_TF32X2 = 3 };
+__host__ __device__ constexpr int tc_splits(int kind) { return kind == TC_BF16X3 ? 3 : kind == TC_TF32X2 ? 2 : 1; }
+__host__ __device__ constexpr int tc_elem_bytes(int kind) { return kind == TC_BF16X3 ? 2 : 4; }
+
 struct ProblemView {
     int D, d, nx, KD, KD_pad, d_pad;
+    int tc_kind;                 // TcKind of the projection (TC_NONE: the plain FP32 form)
     int KD_tc;                   // columns of the tensor-core operand (multiple of its N tile)
     int64_t R;
     int64_t chain_offset;
@@ -98,7 +106,8 @@ struct ProblemView {
 
     // packed projector operands and per-column likelihood weights
     const float *P32;            // [d_pad][KD_pad]  (row = packed rho index, contiguous columns)
-    const __nv_bfloat16 *Pbf;    // [KD_tc][d_pad]   (row = projector, contiguous packed index)
+    const void *Ptc;             // [KD_tc][d_pad]   tensor-core B operand (row = projector, contiguous packed
+                                 //                  index): bf16, or FP32 holding TF32 values
     const float *cnt;            // [max(KD_pad, KD_tc)] counts as float, 0 on padding
     const float *invf;           // [max(KD_pad, KD_tc)] P_k / c_kl (1 where c_kl = 0)
     const float *ptot;           // [max(KD_pad, KD_tc) / D] shots P_k of each setting (0 on padding)
@@ -109,7 +118,8 @@ struct ProblemView {
     uint8_t *cur;                // [R] which y buffer holds the current state
     float *rho_cur;              // [R][d_pad] packed rho of the current state
     float *rho_prop;             // [R][d_pad] packed rho of the proposal (FP32 operand)
-    __nv_bfloat16 *rho_split;    // [R][3][d_pad] bf16 hi/mid/lo of the same (tensor operand)
+    void *rho_split;             // [R][tc_splits][d_pad] the same split for the tensor cores: bf16 hi/mid/lo,
+                                 //                  or FP32 TF32 hi[, lo]
     double *trace_prop;          // [R] exact FP64 sum of rho_prop's stored diagonal (1 up to rounding)
     double *logl_cur;            // [R]
     double *logl_part;           // [ngroups][R] partial deviance sums of the proposal
@@ -152,15 +162,16 @@ cudaError_t launch_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uin
                                  uint32_t block0, int32_t nblocks, uint32_t *out, cudaStream_t s);
 cudaError_t launch_inject_nan(const ProblemView &p, int64_t chain, cudaStream_t s);
 
-// tcgen05 BF16x3 projection (sm_103a).  Returns cudaErrorNotSupported if the shape is
-// outside what the kernel handles.
+// tcgen05 projection in the view's tc_kind (sm_103a).  Returns cudaErrorNotSupported if the
+// shape is outside what the kernel handles.
 struct TcPlan;
-cudaError_t tc_plan_create(const ProblemView &p, const __nv_bfloat16 *A_split, int64_t rows, TcPlan **plan);
+cudaError_t tc_plan_create(const ProblemView &p, const void *A_split, int64_t rows, TcPlan **plan);
 void tc_plan_destroy(TcPlan *plan);
 cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t rows, double *out_part,
                               float *p_out, uint32_t *status, cudaStream_t s);
 int tc_ngroups(const ProblemView &p, int64_t rows);
 int tc_column_tile(int D, int KD);       // N tile of the tensor-core contraction for KD columns (0 = unsupported)
+bool tc_supported(int kind, int D);      // the tensor-core kernels handle this operand kind at this D
 int fp32_ngroups(const ProblemView &p, int64_t rows);
 void set_last_error(const char *msg);   // message returned by qst_last_error()
 int accept_slots(int64_t R);

@@ -20,6 +20,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memo
                 5: "numeric", 6: "invalid state", 7: "unsupported"}
 PREC_FP32 = 0
 PREC_BF16X3 = 1
+PREC_TF32 = 2
+PREC_TF32X2 = 3
 KERNEL_PROPOSE, KERNEL_PROJECT, KERNEL_ACCEPT, KERNEL_DIAG = range(4)
 KERNEL_NAMES = {KERNEL_PROPOSE: "propose", KERNEL_PROJECT: "project", KERNEL_ACCEPT: "accept", KERNEL_DIAG: "diag"}
 

@@ -99,3 +99,36 @@ def test_packed_projectors_reproduce_direct_trace(qst, oracle_mod, q):
     # Pauli projector entries are 0 or +-2^-m: exact in bf16 (8-bit mantissa)
     vals = np.unique(np.abs(P[P != 0]))
     assert np.all(np.log2(vals) == np.round(np.log2(vals)))
+
+
+@pytest.mark.parametrize("q,tf32_ok,tf32x2_ok", [(1, True, True), (3, True, True), (4, True, False), (5, False, False)])
+def test_tensor_core_precisions_cover_their_qubit_ranges(qst, q, tf32_ok, tf32x2_ok):
+    """TF32 keeps one A split in shared memory (to 4 qubits), TF32x2 two (to 3 qubits);
+    outside its range a precision is refused before any allocation."""
+    prob = W.config_problem(q, num_chains=8) if q <= 4 else W.five_qubit_problem(num_chains=8, num_steps=1)
+    for prec, ok in ((qst.PREC_TF32, tf32_ok), (qst.PREC_TF32X2, tf32x2_ok)):
+        cfg = qst.default_config(precision=prec)
+        if ok:
+            assert qst.workspace_size([prob], cfg) > 0
+        else:
+            assert _status(lambda: qst.workspace_size([prob], cfg)) == 1
+    assert qst.workspace_size([prob], qst.default_config(precision=qst.PREC_BF16X3)) > 0
+
+
+def test_tf32_forms_need_projectors_exact_in_tf32(qst):
+    """A basis rotated by 0.3 rad has projector entries that TF32 (and bf16) cannot hold: the
+    tensor-core precisions refuse it, the FP32 form takes it."""
+    prob = W.config_problem(1, num_chains=8)
+    c, s_ = np.cos(0.3), np.sin(0.3)
+    u = np.array([c, s_])
+    v = np.array([-s_, c])
+    re = prob.povm_re.copy()
+    im = prob.povm_im.copy()
+    re[4] = np.outer(u, u)          # setting 2 (Z) replaced by the rotated basis
+    re[5] = np.outer(v, v)
+    im[4] = 0.0
+    im[5] = 0.0
+    prob.povm_re, prob.povm_im = re, im
+    assert qst.workspace_size([prob], qst.default_config(precision=qst.PREC_FP32)) > 0
+    for prec in (qst.PREC_TF32, qst.PREC_TF32X2, qst.PREC_BF16X3):
+        assert _status(lambda: qst.workspace_size([prob], qst.default_config(precision=prec))) == 1
