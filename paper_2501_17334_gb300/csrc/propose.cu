@@ -635,16 +635,16 @@ struct Wide {
     static constexpr int row_stride = D + 2;                // float2 per row of W
     static constexpr int qcol = D + 4;                      // floats per column of a Q plane
     static constexpr int pk_stride = D + 1;
-    static constexpr int area_a = 2 * D * qcol;             // >= 2 D row_stride
-    static constexpr int area_b = 2 * D * D;                // >= D pk_stride
+    static constexpr int area_a = 2 * D * qcol;             // Q planes, then W as two planes of stride qcol
+    static constexpr int area_b = 2 * D * D;                // F planes, then the staged rho (>= D pk_stride)
     static constexpr int smem_floats = (area_a + area_b + 31) / 32 * 32 + 16;
 };
-static_assert(Wide::area_a >= 2 * Wide::D * Wide::row_stride && Wide::area_b >= Wide::D * Wide::pk_stride, "areas");
+static_assert(Wide::area_b >= Wide::D * Wide::pk_stride, "areas");
 
 template <int PASSES>
 __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a) {
     using S = Wide;
-    constexpr int D = S::D, d = S::d, nx = 4 * d, RS = S::row_stride, QC = S::qcol, PK = S::pk_stride;
+    constexpr int D = S::D, d = S::d, nx = 4 * d, QC = S::qcol, PK = S::pk_stride;
     extern __shared__ __align__(16) float smem[];
     const int j = threadIdx.x % D;
     const int g = threadIdx.x / D;
@@ -652,10 +652,10 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
     const bool active = c < a.rows;
     const uint32_t step = (a.step_dev && a.mode == MODE_STEP) ? a.step_dev->step : a.step;
     float *sm = smem + g * S::smem_floats;
-    float *qre = sm, *qim = sm + D * QC;
-    float2 *wsm = reinterpret_cast<float2 *>(sm);
-    float2 *fsm = reinterpret_cast<float2 *>(sm + S::area_a);
-    float *packed = sm + S::area_a;
+    float *qre = sm, *qim = sm + D * QC;                 // Q planes (column stride QC)
+    float *wre = sm, *wim = sm + D * QC;                 // W planes (row stride QC), replace Q
+    float *fre = sm + S::area_a, *fim = fre + D * D;     // F column-major (stride D), re / im planes
+    float *packed = sm + S::area_a;                      // staged rho (row stride PK), replaces F
 
     // ---- 1. latent proposal (as in the D <= 16 kernel: lane j owns column j of each part) ------
     float coef_y = 1.0f, coef_eta = 0.0f;
@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
     const float *ysrc = a.y + ((int64_t)cur * a.R + cc) * nx;
     float *ydst = a.y + ((int64_t)(1 - cur) * a.R + cc) * nx;
     const float *gsrc = (a.mode == MODE_EVAL) ? a.x_eval + cc * nx : ydst;
-    float hr[D], hi[D];
+    float2 hr[D / 2], hi[D / 2];   // H's column j, entries (2p, 2p + 1) in pair p
 #pragma unroll 1
     for (int part = 0; part < 4; ++part) {
         const int e0 = part * d + j * D;
@@ -698,146 +698,149 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
                 if (active) *reinterpret_cast<float4 *>(ydst + e0 + 4 * q) = yn;
             }
             if (part == 2) {
-                hr[4 * q] = yn.x; hr[4 * q + 1] = yn.y; hr[4 * q + 2] = yn.z; hr[4 * q + 3] = yn.w;
+                hr[2 * q] = make_float2(yn.x, yn.y);
+                hr[2 * q + 1] = make_float2(yn.z, yn.w);
             } else if (part == 3) {
-                hi[4 * q] = yn.x; hi[4 * q + 1] = yn.y; hi[4 * q + 2] = yn.z; hi[4 * q + 3] = yn.w;
+                hi[2 * q] = make_float2(yn.x, yn.y);
+                hi[2 * q + 1] = make_float2(yn.z, yn.w);
             }
         }
     }
 
     // ---- 2a. modified Gram-Schmidt, the published column streamed in chunks --------------------
+    // As in the D <= 16 kernel: every lane forms r = v_k^dag h (lane k's is |v_k|^2, shuffled to
+    // the others), one uniform rsqrt, a branch-free projection (zero coefficient on lanes
+    // j <= k), and the lanes j < k form the Gram entries of the re-orthogonalisation.
+    float inv_own = 0.0f;
 #pragma unroll 1
     for (int k = 0; k < D; ++k) {
         if (j == k) {
-            store_column<D>(qre + k * QC, hr);
-            store_column<D>(qim + k * QC, hi);
+            store_column2<D>(qre + k * QC, hr);
+            store_column2<D>(qim + k * QC, hi);
         }
         __syncwarp();
-        if (j > k) {
-            const float *vre = qre + k * QC, *vim = qim + k * QC;
-            float n0 = 0.0f, n1 = 0.0f, rr0 = 0.0f, ri0 = 0.0f, rr1 = 0.0f, ri1 = 0.0f;
+        const float *vre = qre + k * QC, *vim = qim + k * QC;
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0, b0 = a0, b1 = a0, b2 = a0, b3 = a0;
 #pragma unroll
-            for (int i = 0; i < D; i += 4) {
-                const float4 vr = *reinterpret_cast<const float4 *>(vre + i);
-                const float4 vi = *reinterpret_cast<const float4 *>(vim + i);
-                n0 = __fmaf_rn(vr.x, vr.x, __fmaf_rn(vi.x, vi.x, n0));
-                n1 = __fmaf_rn(vr.y, vr.y, __fmaf_rn(vi.y, vi.y, n1));
-                n0 = __fmaf_rn(vr.z, vr.z, __fmaf_rn(vi.z, vi.z, n0));
-                n1 = __fmaf_rn(vr.w, vr.w, __fmaf_rn(vi.w, vi.w, n1));
-                rr0 = __fmaf_rn(vr.x, hr[i], __fmaf_rn(vi.x, hi[i], rr0));
-                ri0 = __fmaf_rn(vr.x, hi[i], __fmaf_rn(-vi.x, hr[i], ri0));
-                rr1 = __fmaf_rn(vr.y, hr[i + 1], __fmaf_rn(vi.y, hi[i + 1], rr1));
-                ri1 = __fmaf_rn(vr.y, hi[i + 1], __fmaf_rn(-vi.y, hr[i + 1], ri1));
-                rr0 = __fmaf_rn(vr.z, hr[i + 2], __fmaf_rn(vi.z, hi[i + 2], rr0));
-                ri0 = __fmaf_rn(vr.z, hi[i + 2], __fmaf_rn(-vi.z, hr[i + 2], ri0));
-                rr1 = __fmaf_rn(vr.w, hr[i + 3], __fmaf_rn(vi.w, hi[i + 3], rr1));
-                ri1 = __fmaf_rn(vr.w, hi[i + 3], __fmaf_rn(-vi.w, hr[i + 3], ri1));
-            }
-            const float inv_n = 1.0f / (n0 + n1);
-            const float sr = (rr0 + rr1) * inv_n, si = (ri0 + ri1) * inv_n;
+        for (int p = 0; p < D / 2; p += 2) {
+            const float4 vr4 = *reinterpret_cast<const float4 *>(vre + 2 * p);
+            const float4 vi4 = *reinterpret_cast<const float4 *>(vim + 2 * p);
+            const float2 vr0 = make_float2(vr4.x, vr4.y), vr1 = make_float2(vr4.z, vr4.w);
+            const float2 vi0 = make_float2(vi4.x, vi4.y), vi1 = make_float2(vi4.z, vi4.w);
+            a0 = __ffma2_rn(vr0, hr[p], a0);
+            a1 = __ffma2_rn(vi0, hi[p], a1);
+            b0 = __ffma2_rn(vr0, hi[p], b0);
+            b1 = __ffma2_rn(vi0, hr[p], b1);
+            a2 = __ffma2_rn(vr1, hr[p + 1], a2);
+            a3 = __ffma2_rn(vi1, hi[p + 1], a3);
+            b2 = __ffma2_rn(vr1, hi[p + 1], b2);
+            b3 = __ffma2_rn(vi1, hr[p + 1], b3);
+        }
+        const float rr = (hsum(a0) + hsum(a1)) + (hsum(a2) + hsum(a3));
+        const float ri = (hsum(b0) - hsum(b1)) + (hsum(b2) - hsum(b3));
+        const float nk = __shfl_sync(0xffffffffu, rr, k);   // |v_k|^2 from lane k
+        const float rs = rsqrtf(nk);
+        const float coef = (j > k) ? rs * rs : 0.0f;
+        const float sr = rr * coef, si = ri * coef;
+        const float2 msr = make_float2(-sr, -sr), psi = make_float2(si, si), msi = make_float2(-si, -si);
 #pragma unroll
-            for (int i = 0; i < D; i += 4) {
-                const float4 vr = *reinterpret_cast<const float4 *>(vre + i);
-                const float4 vi = *reinterpret_cast<const float4 *>(vim + i);
-                const float vrr[4] = {vr.x, vr.y, vr.z, vr.w}, vii[4] = {vi.x, vi.y, vi.z, vi.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    hr[i + u] = __fmaf_rn(-sr, vrr[u], __fmaf_rn(si, vii[u], hr[i + u]));
-                    hi[i + u] = __fmaf_rn(-sr, vii[u], __fmaf_rn(-si, vrr[u], hi[i + u]));
-                }
+        for (int p = 0; p < D / 2; p += 2) {
+            const float4 vr4 = *reinterpret_cast<const float4 *>(vre + 2 * p);
+            const float4 vi4 = *reinterpret_cast<const float4 *>(vim + 2 * p);
+            const float2 vr0 = make_float2(vr4.x, vr4.y), vr1 = make_float2(vr4.z, vr4.w);
+            const float2 vi0 = make_float2(vi4.x, vi4.y), vi1 = make_float2(vi4.z, vi4.w);
+            hr[p] = __ffma2_rn(msr, vr0, __ffma2_rn(psi, vi0, hr[p]));
+            hi[p] = __ffma2_rn(msr, vi0, __ffma2_rn(msi, vr0, hi[p]));
+            hr[p + 1] = __ffma2_rn(msr, vr1, __ffma2_rn(psi, vi1, hr[p + 1]));
+            hi[p + 1] = __ffma2_rn(msr, vi1, __ffma2_rn(msi, vr1, hi[p + 1]));
+        }
+        inv_own = (j == k) ? rs : inv_own;
+        if constexpr (PASSES == 2) {
+            if (j < k) {
+                const float sc = inv_own * rs;   // E_jk = conj(r) / (|v_j| |v_k|), j < k
+                fre[k * D + j] = rr * sc;
+                fim[k * D + j] = -ri * sc;
             }
         }
     }
-    {
-        float n0 = 0.0f, n1 = 0.0f;
+    {   // normalise the own column and publish it
+        const float2 sc = make_float2(inv_own, inv_own);
 #pragma unroll
-        for (int i = 0; i < D; i += 2) {
-            n0 = __fmaf_rn(hr[i], hr[i], __fmaf_rn(hi[i], hi[i], n0));
-            n1 = __fmaf_rn(hr[i + 1], hr[i + 1], __fmaf_rn(hi[i + 1], hi[i + 1], n1));
-        }
-        const float inv = 1.0f / sqrtf(n0 + n1);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            hr[i] *= inv;
-            hi[i] *= inv;
+        for (int p = 0; p < D / 2; ++p) {
+            hr[p] = __fmul2_rn(hr[p], sc);
+            hi[p] = __fmul2_rn(hi[p], sc);
         }
         __syncwarp();
-        store_column<D>(qre + j * QC, hr);
-        store_column<D>(qim + j * QC, hi);
+        store_column2<D>(qre + j * QC, hr);
+        store_column2<D>(qim + j * QC, hi);
         __syncwarp();
     }
 
     if constexpr (PASSES == 2) {
-        // ---- 2b. Q2 = Q1 (I - F): Gram entries (a, a + t), then row a of Q1 (I - F) ------------
-#pragma unroll 1
-        for (int t = 0; t <= D / 2; ++t) {
-            const int b = (j + t) & (D - 1);
-            if (t == D / 2 && j >= D / 2) continue;
-            const float *bre = qre + b * QC, *bim = qim + b * QC;
-            float er0 = 0.0f, ei0 = 0.0f, er1 = 0.0f, ei1 = 0.0f;
+        // ---- 2b. Q2 = Q1 (I - F): F's diagonal, then row a of Q1 (I - F) (as in D <= 16) ----------
+        {
+            float2 n = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < D; i += 4) {
-                const float4 br = *reinterpret_cast<const float4 *>(bre + i);
-                const float4 bi = *reinterpret_cast<const float4 *>(bim + i);
-                er0 = __fmaf_rn(hr[i], br.x, __fmaf_rn(hi[i], bi.x, er0));
-                ei0 = __fmaf_rn(hr[i], bi.x, __fmaf_rn(-hi[i], br.x, ei0));
-                er1 = __fmaf_rn(hr[i + 1], br.y, __fmaf_rn(hi[i + 1], bi.y, er1));
-                ei1 = __fmaf_rn(hr[i + 1], bi.y, __fmaf_rn(-hi[i + 1], br.y, ei1));
-                er0 = __fmaf_rn(hr[i + 2], br.z, __fmaf_rn(hi[i + 2], bi.z, er0));
-                ei0 = __fmaf_rn(hr[i + 2], bi.z, __fmaf_rn(-hi[i + 2], br.z, ei0));
-                er1 = __fmaf_rn(hr[i + 3], br.w, __fmaf_rn(hi[i + 3], bi.w, er1));
-                ei1 = __fmaf_rn(hr[i + 3], bi.w, __fmaf_rn(-hi[i + 3], br.w, ei1));
-            }
-            const float er = er0 + er1, ei = ei0 + ei1;
-            if (t == 0) {
-                fsm[j * D + j] = make_float2(0.5f * (er - 1.0f), 0.0f);
-                if (j + 1 < D) fsm[j * D + j + 1] = make_float2(0.0f, 0.0f);
-            } else if (j < b) {
-                fsm[b * D + j] = make_float2(er, ei);
-            } else {
-                fsm[j * D + b] = make_float2(er, -ei);
+            for (int p = 0; p < D / 2; ++p) n = __ffma2_rn(hr[p], hr[p], __ffma2_rn(hi[p], hi[p], n));
+            fre[j * D + j] = 0.5f * (hsum(n) - 1.0f);
+            fim[j * D + j] = 0.0f;
+            if (j + 1 < D) {
+                fre[j * D + j + 1] = 0.0f;
+                fim[j * D + j + 1] = 0.0f;
             }
         }
         __syncwarp();
         {
-            float xr[D], xi[D];
+            float2 xr[D / 2], xi[D / 2];
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                xr[i] = qre[i * QC + j];
-                xi[i] = qim[i * QC + j];
+            for (int p = 0; p < D / 2; ++p) {
+                xr[p] = make_float2(qre[(2 * p) * QC + j], qre[(2 * p + 1) * QC + j]);
+                xi[p] = make_float2(qim[(2 * p) * QC + j], qim[(2 * p + 1) * QC + j]);
             }
 #pragma unroll
             for (int m = D - 1; m >= 0; --m) {
-                float accr = xr[m], acci = xi[m];
+                float2 ca = make_float2(0.f, 0.f), cb = ca, cc2 = ca, cd = ca;
 #pragma unroll
-                for (int i = 0; i <= m; i += 2) {
-                    const float4 f = *reinterpret_cast<const float4 *>(fsm + m * D + i);
-                    accr = __fmaf_rn(-xr[i], f.x, __fmaf_rn(xi[i], f.y, accr));
-                    acci = __fmaf_rn(-xr[i], f.y, __fmaf_rn(-xi[i], f.x, acci));
-                    if (i + 1 <= m) {
-                        accr = __fmaf_rn(-xr[i + 1], f.z, __fmaf_rn(xi[i + 1], f.w, accr));
-                        acci = __fmaf_rn(-xr[i + 1], f.w, __fmaf_rn(-xi[i + 1], f.z, acci));
+                for (int p = 0; 2 * p <= m; ++p) {
+                    float2 fx, fy;   // F[2p][m], F[2p+1][m]
+                    if ((p & 1) == 0) {
+                        const float4 f4x = *reinterpret_cast<const float4 *>(fre + m * D + 2 * p);
+                        const float4 f4y = *reinterpret_cast<const float4 *>(fim + m * D + 2 * p);
+                        fx = make_float2(f4x.x, f4x.y);
+                        fy = make_float2(f4y.x, f4y.y);
+                    } else {
+                        fx = *reinterpret_cast<const float2 *>(fre + m * D + 2 * p);
+                        fy = *reinterpret_cast<const float2 *>(fim + m * D + 2 * p);
                     }
+                    ca = __ffma2_rn(xr[p], fx, ca);
+                    cb = __ffma2_rn(xi[p], fy, cb);
+                    cc2 = __ffma2_rn(xr[p], fy, cc2);
+                    cd = __ffma2_rn(xi[p], fx, cd);
                 }
-                xr[m] = accr;
-                xi[m] = acci;
+                const float dr = hsum(ca) - hsum(cb), di = hsum(cc2) + hsum(cd);
+                if (m & 1) {
+                    xr[m / 2].y -= dr;
+                    xi[m / 2].y -= di;
+                } else {
+                    xr[m / 2].x -= dr;
+                    xi[m / 2].x -= di;
+                }
             }
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                qre[i * QC + j] = xr[i];
-                qim[i * QC + j] = xi[i];
+            for (int p = 0; p < D / 2; ++p) {
+                qre[(2 * p) * QC + j] = xr[p].x;
+                qre[(2 * p + 1) * QC + j] = xr[p].y;
+                qim[(2 * p) * QC + j] = xi[p].x;
+                qim[(2 * p + 1) * QC + j] = xi[p].y;
             }
         }
         __syncwarp();
     }
 
-    // ---- 3. W[:, j] = G[:, j] + sum_k U[:, k] G[k, j], U streamed, G read back four rows at a time
-    float wr[D], wi[D];
+    // ---- 3. W[:, j] = G[:, j] + sum_k U[:, k] G[k, j]: pairs of rows, U streamed, G[k, j] broadcast
+    float2 wr[D / 2], wi[D / 2];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        wr[i] = 0.0f;
-        wi[i] = 0.0f;
-    }
+    for (int p = 0; p < D / 2; ++p) wr[p] = wi[p] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int k0 = 0; k0 < D; k0 += 4) {
         float4 g4r = make_float4(0.f, 0.f, 0.f, 0.f), g4i = g4r;
@@ -849,75 +852,96 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const float *ure = qre + (k0 + u) * QC, *uim = qim + (k0 + u) * QC;
+            const float2 pgr = make_float2(gkr[u], gkr[u]), pgi = make_float2(gki[u], gki[u]);
+            const float2 mgi = make_float2(-gki[u], -gki[u]);
 #pragma unroll
-            for (int i = 0; i < D; i += 4) {
-                const float4 ur = *reinterpret_cast<const float4 *>(ure + i);
-                const float4 ui = *reinterpret_cast<const float4 *>(uim + i);
-                const float urr[4] = {ur.x, ur.y, ur.z, ur.w}, uii[4] = {ui.x, ui.y, ui.z, ui.w};
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    wr[i + v] = __fmaf_rn(urr[v], gkr[u], __fmaf_rn(-uii[v], gki[u], wr[i + v]));
-                    wi[i + v] = __fmaf_rn(urr[v], gki[u], __fmaf_rn(uii[v], gkr[u], wi[i + v]));
-                }
+            for (int p = 0; p < D / 2; p += 2) {
+                const float4 ur = *reinterpret_cast<const float4 *>(ure + 2 * p);
+                const float4 ui = *reinterpret_cast<const float4 *>(uim + 2 * p);
+                const float2 ur0 = make_float2(ur.x, ur.y), ur1 = make_float2(ur.z, ur.w);
+                const float2 ui0 = make_float2(ui.x, ui.y), ui1 = make_float2(ui.z, ui.w);
+                wr[p] = __ffma2_rn(ur0, pgr, __ffma2_rn(ui0, mgi, wr[p]));
+                wi[p] = __ffma2_rn(ur0, pgi, __ffma2_rn(ui0, pgr, wi[p]));
+                wr[p + 1] = __ffma2_rn(ur1, pgr, __ffma2_rn(ui1, mgi, wr[p + 1]));
+                wi[p + 1] = __ffma2_rn(ur1, pgi, __ffma2_rn(ui1, pgr, wi[p + 1]));
             }
         }
     }
     if (active) {   // + G[:, j]
 #pragma unroll
-        for (int i = 0; i < D; i += 4) {
-            const float4 gr4 = *reinterpret_cast<const float4 *>(gsrc + j * D + i);
-            const float4 gi4 = *reinterpret_cast<const float4 *>(gsrc + d + j * D + i);
-            wr[i] += gr4.x; wr[i + 1] += gr4.y; wr[i + 2] += gr4.z; wr[i + 3] += gr4.w;
-            wi[i] += gi4.x; wi[i + 1] += gi4.y; wi[i + 2] += gi4.z; wi[i + 3] += gi4.w;
+        for (int p = 0; p < D / 2; p += 2) {
+            const float4 gr4 = *reinterpret_cast<const float4 *>(gsrc + j * D + 2 * p);
+            const float4 gi4 = *reinterpret_cast<const float4 *>(gsrc + d + j * D + 2 * p);
+            wr[p] = __fadd2_rn(wr[p], make_float2(gr4.x, gr4.y));
+            wr[p + 1] = __fadd2_rn(wr[p + 1], make_float2(gr4.z, gr4.w));
+            wi[p] = __fadd2_rn(wi[p], make_float2(gi4.x, gi4.y));
+            wi[p + 1] = __fadd2_rn(wi[p + 1], make_float2(gi4.z, gi4.w));
         }
     }
     __syncwarp();
 #pragma unroll
-    for (int i = 0; i < D; ++i) wsm[i * RS + j] = make_float2(wr[i], wi[i]);
+    for (int p = 0; p < D / 2; ++p) {   // W row-major, real and imaginary planes (replace Q)
+        wre[(2 * p) * QC + j] = wr[p].x;
+        wre[(2 * p + 1) * QC + j] = wr[p].y;
+        wim[(2 * p) * QC + j] = wi[p].x;
+        wim[(2 * p + 1) * QC + j] = wi[p].y;
+    }
     __syncwarp();
 
     // ---- 4. rho = W W^dag / Tr, lane a: entries (a, a + t mod D), row b streamed --------------
+    // Re (W W^dag)_ab = sum Re W_am Re W_bm + Im W_am Im W_bm and Im = sum Im W_am Re W_bm -
+    // Re W_am Im W_bm, on pairs of columns m.  For t = D/2 lanes a and a + D/2 both form the pair
+    // {a, a + D/2}; the results are bitwise equal (the same products in the same order), so both
+    // stores may stand.
     const int arow = j;
-    float war[D], wai[D];
+    float2 war[D / 2], wai[D / 2];
 #pragma unroll
-    for (int jj = 0; jj < D; jj += 2) {
-        const float4 v = *reinterpret_cast<const float4 *>(wsm + arow * RS + jj);
-        war[jj] = v.x;
-        wai[jj] = v.y;
-        war[jj + 1] = v.z;
-        wai[jj + 1] = v.w;
+    for (int p = 0; p < D / 2; p += 2) {
+        const float4 r4 = *reinterpret_cast<const float4 *>(wre + arow * QC + 2 * p);
+        const float4 i4 = *reinterpret_cast<const float4 *>(wim + arow * QC + 2 * p);
+        war[p] = make_float2(r4.x, r4.y);
+        war[p + 1] = make_float2(r4.z, r4.w);
+        wai[p] = make_float2(i4.x, i4.y);
+        wai[p + 1] = make_float2(i4.z, i4.w);
     }
-    float diag = 0.0f;
+    float diag;
+    {
+        float2 d0 = make_float2(0.f, 0.f), d1 = d0;
 #pragma unroll
-    for (int jj = 0; jj < D; ++jj) diag = __fmaf_rn(war[jj], war[jj], __fmaf_rn(wai[jj], wai[jj], diag));
+        for (int p = 0; p < D / 2; ++p) {
+            d0 = __ffma2_rn(war[p], war[p], d0);
+            d1 = __ffma2_rn(wai[p], wai[p], d1);
+        }
+        diag = hsum(d0) + hsum(d1);
+    }
     const float inv_tr = 1.0f / group_sum<D>(diag);
     const float diag_n = diag * inv_tr;
     float tr_hi, tr_lo;
     group_sum_exact<D>(diag_n, tr_hi, tr_lo);
-    __syncwarp();
+    __syncwarp();   // every lane holds its W row before F's area becomes the staged rho
     packed[arow * PK + arow] = diag_n;
 #pragma unroll 1
     for (int t = 1; t <= D / 2; ++t) {
         const int b = (arow + t) & (D - 1);
-        if (t == D / 2 && arow >= D / 2) continue;
-        float re0 = 0.0f, im0 = 0.0f, re1 = 0.0f, im1 = 0.0f;
+        float2 re = make_float2(0.f, 0.f), ima = re, imb = re;
 #pragma unroll
-        for (int jj = 0; jj < D; jj += 2) {
-            const float4 wb = *reinterpret_cast<const float4 *>(wsm + b * RS + jj);
-            re0 = __fmaf_rn(war[jj], wb.x, __fmaf_rn(wai[jj], wb.y, re0));
-            im0 = __fmaf_rn(wai[jj], wb.x, __fmaf_rn(-war[jj], wb.y, im0));
-            re1 = __fmaf_rn(war[jj + 1], wb.z, __fmaf_rn(wai[jj + 1], wb.w, re1));
-            im1 = __fmaf_rn(wai[jj + 1], wb.z, __fmaf_rn(-war[jj + 1], wb.w, im1));
+        for (int p = 0; p < D / 2; p += 2) {
+            const float4 r4 = *reinterpret_cast<const float4 *>(wre + b * QC + 2 * p);
+            const float4 i4 = *reinterpret_cast<const float4 *>(wim + b * QC + 2 * p);
+            const float2 br0 = make_float2(r4.x, r4.y), br1 = make_float2(r4.z, r4.w);
+            const float2 bi0 = make_float2(i4.x, i4.y), bi1 = make_float2(i4.z, i4.w);
+            re = __ffma2_rn(wai[p], bi0, __ffma2_rn(war[p], br0, re));
+            ima = __ffma2_rn(wai[p], br0, ima);
+            imb = __ffma2_rn(war[p], bi0, imb);
+            re = __ffma2_rn(wai[p + 1], bi1, __ffma2_rn(war[p + 1], br1, re));
+            ima = __ffma2_rn(wai[p + 1], br1, ima);
+            imb = __ffma2_rn(war[p + 1], bi1, imb);
         }
-        const float re = (re0 + re1) * inv_tr;
-        const float im = (im0 + im1) * inv_tr;
-        if (arow < b) {
-            packed[arow * PK + b] = re;
-            packed[b * PK + arow] = -im;
-        } else {
-            packed[arow * PK + b] = im;
-            packed[b * PK + arow] = re;
-        }
+        const float rv = hsum(re) * inv_tr;
+        const float iv = (hsum(ima) - hsum(imb)) * inv_tr;
+        const bool upper = arow < b;
+        packed[arow * PK + b] = upper ? rv : iv;
+        packed[b * PK + arow] = upper ? -iv : rv;
     }
     if (active && j == 0) a.trace_out[c] = (double)tr_hi + (double)tr_lo;
     __syncwarp();
