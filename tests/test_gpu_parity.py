@@ -31,12 +31,7 @@ def _prec(qst, name):
 
 
 def _sampler(qst, prob, prec="fp32", **kw):
-    try:
-        return qst.Sampler(prob, precision=_prec(qst, prec), **kw)
-    except qst.QstError as e:
-        if e.status == 7:
-            pytest.skip(f"{prec} not supported by this build: {e}")
-        raise
+    return qst.Sampler(prob, precision=_prec(qst, prec), **kw)
 
 
 # ------------------------------------------------------------------------------- Philox
