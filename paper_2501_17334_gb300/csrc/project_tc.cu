@@ -94,7 +94,8 @@ struct TcArgs {
     float *p_out;          // [rows][KD] or null
     uint32_t *status;
     int64_t rows;
-    int64_t units;         // M tiles * ngroups
+    int64_t units;         // full_units + (M tiles - full_units) * ngroups
+    int64_t full_units;    // the first full_units units are whole chain tiles (all N tiles)
     int KD;
     int n_katoms;          // d_pad / (K elements per atom)
     int ntiles;            // KD_tc / 128
@@ -390,10 +391,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         w_c[i] = __ldg(reinterpret_cast<const float2 *>(a.cnt) + i);
     }
     for (int i = threadIdx.x; i < kd_tc / D; i += blockDim.x) w_p[i] = __ldg(a.ptot + i);
-    // N tiles of work unit u: [tb, te), a balanced split of the tiles over the column groups
-    // (never empty: ngroups <= ntiles)
+    // Work unit u: the first full_units units (whole rounds of the grid) are whole chain tiles;
+    // every later chain tile is split into ngroups units, each a balanced range of its N tiles
+    // (never empty: ngroups <= ntiles), so the last round still occupies every SM.
+    auto unit_mtile = [&](int64_t u) -> int64_t {
+        return u < a.full_units ? u : a.full_units + (u - a.full_units) / a.ngroups;
+    };
+    auto unit_group = [&](int64_t u) -> int { return u < a.full_units ? 0 : (int)((u - a.full_units) % a.ngroups); };
     auto unit_tiles = [&](int64_t u, int &tb, int &te) {
-        const int g = (int)(u % a.ngroups);
+        if (u < a.full_units) {
+            tb = 0;
+            te = a.ntiles;
+            return;
+        }
+        const int g = unit_group(u);
         tb = g * a.ntiles / a.ngroups;
         te = (g + 1) * a.ntiles / a.ngroups;
     };
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // side by side read different P tiles from L2 instead of all the same lines at once
     auto tile_at = [&](int64_t u, int tb, int te, int i) {
         const int len = te - tb;
-        int j = i + (int)((u / a.ngroups) % len);
+        int j = i + (int)(unit_mtile(u) % len);
         if (j >= len) j -= len;
         return tb + j;
     };
@@ -472,7 +483,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int tb, te;
             unit_tiles(u, tb, te);
             if (te <= tb) continue;
-            const int m0 = (int)((u / a.ngroups) * TC_M);
+            const int m0 = (int)(unit_mtile(u) * TC_M);
             for (int kc = 0; kc < nk; ++kc) {
                 if (!mbar_wait_warp(smem_u32(&bar_a_empty[kc]), (uc & 1u) ^ 1u, &abort_flag, a.status)) {
                     ok = false;
@@ -579,7 +590,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // loads never stall the epilogue.
         constexpr int NP = NCW / 4;
         auto alo_fetch = [&](int64_t u, int piece) {
-            const int64_t row = (u / a.ngroups) * TC_M + quad * 32 + lane;
+            const int64_t row = unit_mtile(u) * TC_M + quad * 32 + lane;
             if (row >= a.rows) return make_uint4(0u, 0u, 0u, 0u);
             const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(a.a_split) +
                                                                row * 3 * DP + 2 * DP + sub * (DP / TC_EPI_PER_QUAD));
@@ -610,8 +621,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t nb_buf = (ucount + 1) & 1u;
             int tb, te;
             unit_tiles(u, tb, te);
-            const int g = (int)(u % a.ngroups);
-            const int64_t grow = (u / a.ngroups) * TC_M + quad * 32 + lane;
+            const int g = unit_group(u);
+            const int64_t grow = unit_mtile(u) * TC_M + quad * 32 + lane;
             const bool valid = grow < a.rows;
             const double t = valid ? a.trace[grow] : 1.0;
             const float inv_t = (float)(1.0 / t);
@@ -705,7 +716,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
             }
-            if (ok && valid) a.out[(int64_t)(g * 4 + sub) * a.rows + grow] = total;
+            if (ok && valid) {
+                a.out[(int64_t)(g * 4 + sub) * a.rows + grow] = total;
+                if (u < a.full_units)   // a whole chain tile: its other groups' partials are zero
+                    for (int g2 = 1; g2 < a.ngroups; ++g2) a.out[(int64_t)(g2 * 4 + sub) * a.rows + grow] = 0.0;
+            }
         }
     }
 
@@ -1027,6 +1042,11 @@ int tc_ngroups(const ProblemView &p, int64_t rows) {
     const int64_t mt = (rows + TC_M - 1) / TC_M;
     const int ntiles = p.KD_tc / TC_N;
     int g = 1;
+    if (mt >= 152) {   // whole rounds run undivided (tc_full_units); split the last round's tiles
+        const int64_t rem = mt % 152;
+        if (rem > 0) g = (int)std::min<int64_t>(ntiles, std::max<int64_t>(1, 152 / rem));
+        return 4 * g;
+    }
     while (g < ntiles && mt * g < 152) g *= 2;
     return 4 * (g > ntiles ? ntiles : g);
 }
@@ -1083,7 +1103,6 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     const int groups = p.ngroups / 4;   // the epilogue writes four column-slice partials per group
     a.ngroups = groups;
     a.tiles_per_group = (plan->ntiles + groups - 1) / groups;
-    a.units = ((rows + TC_M - 1) / TC_M) * groups;
     static int num_sms = 0;
     if (num_sms == 0) {
         int dev = 0;
@@ -1091,6 +1110,10 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
         if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms <= 0)
             num_sms = 148;
     }
+    const int64_t mtiles = (rows + TC_M - 1) / TC_M;
+    // whole rounds of the grid take whole chain tiles; the rest are split into `groups` units
+    a.full_units = (p.D == 32) ? 0 : (mtiles / num_sms) * num_sms;
+    a.units = (p.D == 32) ? mtiles * groups : a.full_units + (mtiles - a.full_units) * groups;
     dim3 grid((unsigned)std::min<int64_t>(a.units, num_sms));
     if (p.D == 32) {   // units: (chain tile, N tile) pairs
         const size_t smem = 1024 + (size_t)TCW_STAGES * TCW_STAGE_BYTES;
