@@ -47,8 +47,8 @@ NCU_TRAFFIC = {
                 "chains": 32768, "bytes": 134.972160e6 + 162.235648e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "493dbda321cb27cfd8fa6733136abe2e15079dfecff422c287eb08f5f9786591",
-                "chains": 32768, "bytes": 51.388928e6 + 0.006656e6},
+                "sha256": "d7fd759acb602c1896bc5dfc87e7c945c815e82b7e5eb278b2c3b402d9d5ca0d",
+                "chains": 32768, "bytes": 51.399424e6 + 0.016384e6},
 }
 
 def _sha256(path):
