@@ -249,6 +249,16 @@ qst_status qst_pack_projectors(int32_t num_qubits, int32_t num_povms, const doub
  * pooling) its last valid rho.  Device-side only, asynchronous. */
 qst_status qst_inject_nan(qst_handle *h, int32_t problem, int64_t chain);
 
+/* Failure-path probe (test hook): runs, on the handle's stream, one warp that waits through
+ * the kernels' own bounded mbarrier wait on a barrier nothing ever completes, with a limit of
+ * wait_ms milliseconds (1..2000) instead of the kernels' 1 s.  The wait gives up, sets the
+ * device status word's time-out bit and the kernel returns, so the context stays usable.
+ * Synchronises; returns what the next synchronising call would report, QST_ERR_TIMEOUT, then
+ * clears the bit it set.  If the status word already holds a failure, that failure is
+ * returned and nothing is cleared.  QST_ERR_INVALID_ARG for a NULL handle or wait_ms out of
+ * range. */
+qst_status qst_probe_wait_timeout(qst_handle *h, int32_t wait_ms);
+
 /* ---- evaluation without device allocation ---------------------------------------------------- */
 
 /* The paper has no counterpart to this entry point: it serves callers that must not

@@ -1069,6 +1069,20 @@ qst_status qst_pack_projectors(int32_t num_qubits, int32_t num_povms, const doub
     return QST_OK;
 }
 
+qst_status qst_probe_wait_timeout(qst_handle *h, int32_t wait_ms) {
+    if (!h) return fail(QST_ERR_INVALID_ARG, "NULL handle");
+    if (wait_ms < 1 || wait_ms > 2000) return fail(QST_ERR_INVALID_ARG, "wait_ms must be in 1..2000");
+    QST_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    uint32_t before = 0;
+    QST_CUDA(cudaMemcpy(&before, h->d_status, sizeof(before), cudaMemcpyDeviceToHost), "read status");
+    if (before != 0) return check_status(h);   // a real failure is pending: report it, clear nothing
+    QST_CUDA(launch_wait_timeout_probe(h->d_status, (uint64_t)wait_ms * 1000000ull, h->stream), "probe launch");
+    const qst_status st = check_status(h);
+    const uint32_t zero = 0;
+    QST_CUDA(cudaMemcpy(h->d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice), "clear status");
+    return st;
+}
+
 qst_status qst_inject_nan(qst_handle *h, int32_t problem, int64_t chain) {
     HostProblem *hp;
     qst_status st = get_problem(h, problem, &hp);

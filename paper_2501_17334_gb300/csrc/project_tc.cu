@@ -136,7 +136,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // false on abort or after about 1 s (then the status word's TIMEOUT bit is set and every role
 // stops).  Every lane polls and the warp votes, so the loop and everything after it stay
 // warp-uniform (values the issuing warps derive there can live in uniform registers).
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t *status) {
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint32_t *status,
+                                               uint64_t limit_ns = TC_WAIT_NS) {
     uint64_t t0 = 0;
     for (uint32_t it = 0; it < (1u << 28); ++it) {
         if (__all_sync(0xffffffffu, mbar_try(bar, parity))) return true;
@@ -145,7 +146,7 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, vo
             const uint64_t now = __shfl_sync(0xffffffffu, global_timer(), 0);
             if (t0 == 0) {
                 t0 = now;
-            } else if (now - t0 > TC_WAIT_NS) {
+            } else if (now - t0 > limit_ns) {
                 break;
             }
         }
@@ -948,6 +949,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// Test hook for the failure path: one warp waits, through the same bounded wait as the kernels
+// above, on an mbarrier that nothing ever arrives on.  After limit_ns the wait gives up, sets
+// the status word's TIMEOUT bit and returns, and the kernel exits with nothing in flight.
+__global__ void wait_timeout_probe_kernel(uint32_t *status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    mbar_wait_warp(smem_u32(&bar), 0u, &abort_flag, status, limit_ns);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -1022,6 +1038,11 @@ cudaError_t launch_tc_d(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t s
 }  // namespace
 
 int tc_column_tile(int D, int KD) { return KD > 0 ? (D == 32 ? TCW_N : TC_N) : 0; }
+
+cudaError_t launch_wait_timeout_probe(uint32_t *status, uint64_t limit_ns, cudaStream_t s) {
+    wait_timeout_probe_kernel<<<1, 32, 0, s>>>(status, limit_ns);
+    return cudaGetLastError();
+}
 
 // BF16x3 to D = 32 (the streamed kernel above D = 16); TF32 keeps its one A split in shared
 // memory to D = 16 (128 KB at D = 16); TF32x2 keeps two, to D = 8.

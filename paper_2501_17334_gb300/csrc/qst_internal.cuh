@@ -172,6 +172,8 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
 int tc_ngroups(const ProblemView &p, int64_t rows);
 int tc_column_tile(int D, int KD);       // N tile of the tensor-core contraction for KD columns (0 = unsupported)
 bool tc_supported(int kind, int D);      // the tensor-core kernels handle this operand kind at this D
+// test hook: one bounded mbarrier wait that nothing satisfies (sets STATUS_TIMEOUT after limit_ns)
+cudaError_t launch_wait_timeout_probe(uint32_t *status, uint64_t limit_ns, cudaStream_t s);
 int fp32_ngroups(const ProblemView &p, int64_t rows);
 void set_last_error(const char *msg);   // message returned by qst_last_error()
 int accept_slots(int64_t R);

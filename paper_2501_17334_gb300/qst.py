@@ -89,6 +89,7 @@ _SIGS = {
                                          ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, _P, _P]),
     "qst_pack_projectors": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "qst_inject_nan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
+    "qst_probe_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int32]),
     "qst_loglik_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
 }
 
@@ -309,6 +310,11 @@ class Sampler:
 
     def inject_nan(self, chain: int, problem: int = 0):
         _check(self.lib.qst_inject_nan(self.handle, problem, chain))
+
+    def probe_wait_timeout(self, wait_ms: int = 50):
+        """Failure-path probe: a bounded device wait that runs out (raises QstError with
+        status QST_ERR_TIMEOUT); the handle stays usable afterwards."""
+        _check(self.lib.qst_probe_wait_timeout(self.handle, int(wait_ms)))
 
 
 # ---- free functions with the ABI's names

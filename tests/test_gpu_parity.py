@@ -372,3 +372,26 @@ def test_config4_full_size_sampled_chains(qst, oracle_mod, cuda_ok, prec):
             assert np.abs(st["y"][c] - ref["final_y"][0]).max() < 1e-3
             assert abs(st["logl"][c] - ref["final_logl"][0]) < 1e-3 * max(1.0, abs(ref["final_logl"][0]) * 1e-6) + 5e-3
     assert agree >= len(sample) - 1
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(qst, cuda_ok):
+    """The kernels' bounded mbarrier wait, on a barrier nothing completes, gives up after its
+    limit, reports QST_ERR_TIMEOUT through the status word, and leaves the context and the
+    handle working (no trap, no fault)."""
+    import time
+    prob = W.config_problem(2, num_chains=256, num_steps=10)
+    s = _sampler(qst, prob, "bf16x3", diag_chains=0)
+    s.run_chains(5)
+    t0 = time.perf_counter()
+    with pytest.raises(qst.QstError) as err:
+        s.probe_wait_timeout(50)
+    waited = time.perf_counter() - t0
+    assert err.value.status == 4                      # QST_ERR_TIMEOUT
+    assert 0.04 <= waited < 5.0
+    s.run_chains(5)                                    # the same handle keeps sampling
+    s.synchronize()
+    rho, n = s.posterior_mean()
+    assert n == 256 * 10 and np.isfinite(rho).all()
+    with pytest.raises(qst.QstError):
+        s.probe_wait_timeout(0)                        # out of range: refused on the host
+    s.close()
