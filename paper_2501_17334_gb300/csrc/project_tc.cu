@@ -12,10 +12,14 @@
 // that much smaller too.  The epilogue adds the two: q carries one FP32 rounding instead
 // of one per MMA (a single accumulator rounds, one-sidedly, at the scale of q after each
 // of the 3 d_pad / 16 MMAs), which halves the log L error of the contraction.
+// The same kernel runs the TF32 forms (kind::tf32, K8 per MMA): rho rounded once to TF32
+// (one accumulator), or split hi + lo (two), every split of A in shared memory.
 //
 // Persistent CTAs (one per SM) loop over work units: a tile of 128 chains (M = 128) times a
-// group of 128-column N tiles.
-//   warp 0 (one lane)  TMA producer of P tiles (128 projectors x 64 K) through a 6-stage ring;
+// range of its 128-column N tiles.  Whole rounds of the grid take whole chain tiles; the
+// tiles of the last, partial round are split into column groups so that it still covers
+// the SMs (a uniform split would reload A in every round).
+//   warp 0 (one lane)  TMA producer of P tiles (128 projectors x 64 K) through a 5-stage ring;
 //   warp 1             allocates all 512 TMEM columns (the hi and the mid + lo FP32
 //                      accumulators, 128 columns each, and two buffers for the lo split of
 //                      A); one lane issues tcgen05.mma (M128 N128 K16) and commits;
@@ -35,7 +39,7 @@
 //                      FP32 per tile, FP64 across tiles.  At the start of a unit the same
 //                      warps copy the next unit's lo split from global memory into the idle
 //                      TMEM buffer (tcgen05.st), where the lo-split MMAs read A.  Keeping a
-//                      third of A out of shared memory leaves room for six P stages, enough to
+//                      third of A out of shared memory leaves room for five P stages, enough to
 //                      cover the L2 latency of the P tiles.
 // Renormalising every setting by its own computed sum S_k (instead of the trace t) is exact
 // for a complete POVM (sum_l Lambda_kl = I gives S_k = t in real arithmetic) and cancels any

@@ -632,7 +632,6 @@ struct Wide {
     static constexpr int D = 32;
     static constexpr int d = D * D;
     static constexpr int chains_per_block = kThreads / D;   // 4
-    static constexpr int row_stride = D + 2;                // float2 per row of W
     static constexpr int qcol = D + 4;                      // floats per column of a Q plane
     static constexpr int pk_stride = D + 1;
     static constexpr int area_a = 2 * D * qcol;             // Q planes, then W as two planes of stride qcol
