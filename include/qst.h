@@ -66,7 +66,9 @@ typedef struct {
     int32_t num_qubits;     /* Q, 1..5 (D = 2^Q) */
     int32_t num_povms;      /* K, the number of measurement settings (3^Q for Pauli) */
     const int32_t *counts;  /* [K*D] outcome counts c_kl >= 0, setting-major */
-    const double *povm_re;  /* [K*D][D][D] row-major real parts of Lambda_kl */
+    const double *povm_re;  /* [K*D][D][D] row-major real parts of Lambda_kl; NULL together with
+                               povm_im selects the built-in Pauli POVMs (qst_pauli_povms; K must
+                               then be 3^Q) */
     const double *povm_im;  /* [K*D][D][D] imaginary parts */
     int64_t num_chains;     /* R >= 1 */
     int64_t chain_offset;   /* global id of chain 0 (disjoint ranges shard one run) */
@@ -237,6 +239,13 @@ int64_t qst_launch_count(const qst_handle *h);
  * Counter = (block, step, chain, tag), key = (seed low, seed high). */
 qst_status qst_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uint32_t chain0, int64_t nchains,
                              uint32_t block0, int32_t nblocks, uint32_t *out, void *cuda_stream);
+
+/* The built-in Pauli POVMs of Q qubits (1..5), written to host arrays povm_re, povm_im of
+ * [3^Q 2^Q][2^Q][2^Q] doubles (caller-owned): setting k = sum_q s_q 3^(Q-1-q) with s = 0, 1, 2
+ * for X, Y, Z; outcome l = sum_q b_q 2^(Q-1-q) with b = 0 for the +1 eigenvalue; qubit 0 is the
+ * most significant Kronecker factor (Sec. IV: all 3^Q Pauli settings).  Host-only.
+ * QST_ERR_INVALID_ARG for Q outside 1..5 or a NULL array. */
+qst_status qst_pauli_povms(int32_t num_qubits, double *povm_re, double *povm_im);
 
 /* Packs the POVM elements into the real [D^2][K D] matrix P with p = vec_h(rho) . P:
  * P[(i,i), kl] = Re Lambda_ii, P[(i,j), kl] = 2 Re Lambda_ij (i < j), 2 Im Lambda_ij (i > j).

@@ -182,10 +182,65 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
     return QST_OK;
 }
 
-qst_status make_plan(const qst_problem_desc *probs, int32_t n, const qst_sampler_cfg *cfg, Plan &plan) {
-    if (!probs || n < 1) return fail(QST_ERR_INVALID_ARG, "need at least one problem");
+// The built-in Pauli POVMs of Q qubits, [3^Q * 2^Q][2^Q][2^Q] real and imaginary parts: setting
+// k = sum_q s_q 3^(Q-1-q) (s = 0, 1, 2 for X, Y, Z), outcome l = sum_q b_q 2^(Q-1-q) (b = 0 for
+// the +1 eigenvalue), qubit 0 the most significant Kronecker factor.  Every entry is 0 or
+// +-2^-m (times 1 or i), exact in double.
+void pauli_povms(int Q, std::vector<double> &re, std::vector<double> &im) {
+    const int D = 1 << Q, K = (int)std::lround(std::pow(3.0, Q));
+    // single-qubit eigenprojectors [setting][outcome][row][col] as (re, im)
+    static const double pr[3][2][2][2] = {{{{0.5, 0.5}, {0.5, 0.5}}, {{0.5, -0.5}, {-0.5, 0.5}}},
+                                          {{{0.5, 0.0}, {0.0, 0.5}}, {{0.5, 0.0}, {0.0, 0.5}}},
+                                          {{{1.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 1.0}}}};
+    static const double pi[3][2][2][2] = {{{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}},
+                                          {{{0.0, -0.5}, {0.5, 0.0}}, {{0.0, 0.5}, {-0.5, 0.0}}},
+                                          {{{0.0, 0.0}, {0.0, 0.0}}, {{0.0, 0.0}, {0.0, 0.0}}}};
+    re.assign((size_t)K * D * D * D, 0.0);
+    im.assign((size_t)K * D * D * D, 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int l = 0; l < D; ++l)
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    double ar = 1.0, ai = 0.0;   // product over qubits of the factors' (i_q, j_q) entries
+                    for (int q = 0; q < Q; ++q) {
+                        int kk = k;
+                        for (int t = q + 1; t < Q; ++t) kk /= 3;
+                        const int sq = kk % 3, bq = (l >> (Q - 1 - q)) & 1;
+                        const int iq = (i >> (Q - 1 - q)) & 1, jq = (j >> (Q - 1 - q)) & 1;
+                        const double fr = pr[sq][bq][iq][jq], fi = pi[sq][bq][iq][jq];
+                        const double nr = ar * fr - ai * fi, ni = ar * fi + ai * fr;
+                        ar = nr;
+                        ai = ni;
+                    }
+                    const size_t e = (((size_t)(k * D + l) * D + i) * D + j);
+                    re[e] = ar;
+                    im[e] = ai;
+                }
+}
+
+qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_sampler_cfg *cfg, Plan &plan) {
+    if (!probs_in || n < 1) return fail(QST_ERR_INVALID_ARG, "need at least one problem");
     qst_status st = validate_cfg(cfg);
     if (st != QST_OK) return st;
+    // NULL POVM arrays select the built-in Pauli POVMs (num_povms must then be 3^Q)
+    std::vector<qst_problem_desc> probs_v(probs_in, probs_in + n);
+    std::vector<std::vector<double>> pauli_store;
+    pauli_store.reserve(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        qst_problem_desc &d = probs_v[i];
+        if (d.povm_re || d.povm_im) continue;
+        if (d.num_qubits < 1 || d.num_qubits > 5)
+            return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..5", i, d.num_qubits);
+        if (d.num_povms != (int32_t)std::lround(std::pow(3.0, d.num_qubits)))
+            return fail(QST_ERR_INVALID_ARG, "problem %d: the built-in Pauli POVMs need num_povms = 3^Q", i);
+        pauli_store.emplace_back();
+        pauli_store.emplace_back();
+        std::vector<double> &re = pauli_store[pauli_store.size() - 2], &im = pauli_store.back();
+        pauli_povms(d.num_qubits, re, im);
+        d.povm_re = re.data();
+        d.povm_im = im.data();
+    }
+    const qst_problem_desc *probs = probs_v.data();
     plan.probs.clear();
     plan.probs.resize(n);
     size_t off = 0;
@@ -1066,6 +1121,16 @@ qst_status qst_pack_projectors(int32_t num_qubits, int32_t num_povms, const doub
     std::vector<double> P((size_t)D * D * KD);
     pack_projectors(D, KD, povm_re, povm_im, P.data(), KD);
     for (size_t i = 0; i < P.size(); ++i) P_out[i] = (float)P[i];
+    return QST_OK;
+}
+
+qst_status qst_pauli_povms(int32_t num_qubits, double *povm_re, double *povm_im) {
+    if (num_qubits < 1 || num_qubits > 5) return fail(QST_ERR_INVALID_ARG, "num_qubits %d outside 1..5", num_qubits);
+    if (!povm_re || !povm_im) return fail(QST_ERR_INVALID_ARG, "NULL output");
+    std::vector<double> re, im;
+    pauli_povms(num_qubits, re, im);
+    std::memcpy(povm_re, re.data(), sizeof(double) * re.size());
+    std::memcpy(povm_im, im.data(), sizeof(double) * im.size());
     return QST_OK;
 }
 

@@ -90,6 +90,7 @@ _SIGS = {
     "qst_pack_projectors": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "qst_inject_nan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
     "qst_probe_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "qst_pauli_povms": (ctypes.c_int, [ctypes.c_int32, _P, _P]),
     "qst_loglik_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int64, _P, _P]),
 }
 
@@ -155,15 +156,20 @@ class _Descs:
         self.descs = (ProblemDesc * len(problems))()
         for i, p in enumerate(problems):
             counts = np.ascontiguousarray(p.counts, dtype=np.int32)
-            re = np.ascontiguousarray(p.povm_re, dtype=np.float64)
-            im = np.ascontiguousarray(p.povm_im, dtype=np.float64)
-            self.arrays += [counts, re, im]
+            self.arrays.append(counts)
             d = self.descs[i]
             d.num_qubits = p.num_qubits
             d.num_povms = p.num_povms
             d.counts = counts.ctypes.data
-            d.povm_re = re.ctypes.data
-            d.povm_im = im.ctypes.data
+            if p.povm_re is None and p.povm_im is None:   # the built-in Pauli POVMs
+                d.povm_re = None
+                d.povm_im = None
+            else:
+                re = np.ascontiguousarray(p.povm_re, dtype=np.float64)
+                im = np.ascontiguousarray(p.povm_im, dtype=np.float64)
+                self.arrays += [re, im]
+                d.povm_re = re.ctypes.data
+                d.povm_im = im.ctypes.data
             d.num_chains = p.num_chains
             d.chain_offset = 0 if chain_offsets is None else int(chain_offsets[i])
             d.seed = p.seed
@@ -333,6 +339,16 @@ def loglik_noalloc(num_qubits: int, num_povms: int, P, counts, x, logl, stream=N
     c = np.ascontiguousarray(counts, dtype=np.int32)
     _check(load().qst_loglik_noalloc(num_qubits, num_povms, _ptr(P), c.ctypes.data, _ptr(x), int(x.shape[0]),
                                      _ptr(logl), _stream_ptr(stream)))
+
+
+def pauli_povms(num_qubits: int):
+    """The library's built-in Pauli POVMs (what NULL POVM arrays select): real and imaginary
+    [3^Q 2^Q, 2^Q, 2^Q] float64 arrays."""
+    D = 1 << num_qubits
+    re = np.empty((3 ** num_qubits * D, D, D))
+    im = np.empty_like(re)
+    _check(load().qst_pauli_povms(num_qubits, re.ctypes.data, im.ctypes.data))
+    return re, im
 
 
 def pack_projectors(num_qubits: int, povm_re: np.ndarray, povm_im: np.ndarray) -> np.ndarray:

@@ -132,3 +132,26 @@ def test_tf32_forms_need_projectors_exact_in_tf32(qst):
     assert qst.workspace_size([prob], qst.default_config(precision=qst.PREC_FP32)) > 0
     for prec in (qst.PREC_TF32, qst.PREC_TF32X2, qst.PREC_BF16X3):
         assert _status(lambda: qst.workspace_size([prob], qst.default_config(precision=prec))) == 1
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5])
+def test_builtin_pauli_povms_are_the_workload_ones(qst, q):
+    """NULL POVM arrays select the library's Pauli POVMs: the same elements, bit for bit, as the
+    seeded-input module builds (same setting and outcome order)."""
+    re, im = qst.pauli_povms(q)
+    wre, wim = W.pauli_povms(q)
+    assert np.array_equal(re, wre) and np.array_equal(im, wim)
+
+
+def test_null_povms_select_the_builtin_pauli_set(qst):
+    import copy
+    prob = W.config_problem(3, num_chains=64)
+    null = copy.copy(prob)
+    null.povm_re = None
+    null.povm_im = None
+    cfg = qst.default_config(precision=qst.PREC_BF16X3)
+    assert qst.workspace_size([null], cfg) == qst.workspace_size([prob], cfg)
+    from types import SimpleNamespace
+    wrong = SimpleNamespace(num_qubits=3, num_povms=26, counts=prob.counts[:26 * 8], povm_re=None,
+                            povm_im=None, num_chains=64, seed=1, beta0=0.0)   # the built-in set has 3^Q
+    assert _status(lambda: qst.workspace_size([wrong], cfg)) == 1

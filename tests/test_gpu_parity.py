@@ -395,3 +395,21 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable(qst, cuda_ok):
     with pytest.raises(qst.QstError):
         s.probe_wait_timeout(0)                        # out of range: refused on the host
     s.close()
+
+
+def test_builtin_pauli_povms_give_the_same_chains(qst, cuda_ok):
+    """NULL POVM arrays (the built-in Pauli set) and the explicit Pauli arrays give bitwise the
+    same chains."""
+    import copy
+    prob = W.config_problem(3, num_chains=256, num_steps=20)
+    null = copy.copy(prob)
+    null.povm_re = None
+    null.povm_im = None
+    out = []
+    for p in (prob, null):
+        s = _sampler(qst, p, "bf16x3", diag_chains=0)
+        s.run_chains(20)
+        out.append(s.get_state())
+        s.close()
+    assert np.array_equal(out[0]["y"], out[1]["y"])
+    assert np.array_equal(out[0]["logl"], out[1]["logl"])
