@@ -43,12 +43,12 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "04e11727baa73864a7612d29d8b45bcc8a6ef64faf9a31f74e22fcbe35a80893",
-                "chains": 32768, "bytes": 134.972160e6 + 162.235648e6},
+                "sha256": "44591e26432ac5fc54cb5ee01019972cc46124e7d2f7647d3b3608e077413b72",
+                "chains": 32768, "bytes": 134.877440e6 + 162.219520e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "d7fd759acb602c1896bc5dfc87e7c945c815e82b7e5eb278b2c3b402d9d5ca0d",
-                "chains": 32768, "bytes": 51.399424e6 + 0.016384e6},
+                "sha256": "422eeb992a1c60056f12d67addd42ec9f536e3f9c701ebc9a6323947bf0ab1bb",
+                "chains": 32768, "bytes": 51.399424e6 + 0.023808e6},
 }
 
 def _sha256(path):
