@@ -249,9 +249,10 @@ def other_configs(qst, W, oracle):
     configuration 3 every form of the projection runs, each with its log L error against the
     oracle on 1024 of its chains' current states."""
     out = {}
-    precs = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "tf32": qst.PREC_TF32, "tf32x2": qst.PREC_TF32X2}
+    precs = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "tf32": qst.PREC_TF32, "tf32x2": qst.PREC_TF32X2,
+             "pauli": qst.PREC_PAULI}
     for c, form, steps in [(1, "fp32", 2000), (2, "fp32", 1000), (3, "fp32", 300), (3, "bf16x3", 300),
-                           (3, "tf32", 300), (3, "tf32x2", 300)]:
+                           (3, "tf32", 300), (3, "tf32x2", 300), (3, "pauli", 300)]:
         prob = W.config_problem(c)
         ms, s = time_handle(qst, prob, precs[form], steps, 5, keep=True)
         out[f"config{c}_{form}"] = {"chains": prob.num_chains, "qubits": prob.num_qubits, "ms_per_step": ms,
@@ -266,11 +267,13 @@ def other_configs(qst, W, oracle):
     chains = sum(p.num_chains for p in batch)
     ms_mixed = time_handle(qst, batch, qst.PREC_BF16X3, 20, 3)
     ms_plain = time_handle(qst, batch, qst.PREC_FP32, 3, 1)
+    ms_pauli = time_handle(qst, batch, qst.PREC_PAULI, 20, 3)
     out["config5_heterogeneous"] = {
         "problems": len(batch), "chains": chains,
         "qubits_hist": [sum(p.num_qubits == q for p in batch) for q in range(1, 6)],
         "ms_per_step_bf16x3": ms_mixed, "chain_steps_per_s_bf16x3": chains / (ms_mixed / 1000.0),
-        "ms_per_step_fp32": ms_plain, "chain_steps_per_s_fp32": chains / (ms_plain / 1000.0)}
+        "ms_per_step_fp32": ms_plain, "chain_steps_per_s_fp32": chains / (ms_plain / 1000.0),
+        "ms_per_step_pauli": ms_pauli, "chain_steps_per_s_pauli": chains / (ms_pauli / 1000.0)}
     return out
 
 
@@ -343,7 +346,7 @@ def run_profile_case(args):
     import torch
     from paper_2501_17334_gb300 import qst, workload as W
     qst.load()
-    prec = qst.PREC_FP32 if args.form == "fp32" else qst.PREC_BF16X3
+    prec = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "pauli": qst.PREC_PAULI}[args.form]
     # the fixed column-group rule (no autotuner timing pass): a profiler distorts the timings
     # the autotuner compares, and with it the captured kernel's schedule
     s = qst.Sampler(W.config_problem(CONFIG_INDEX, num_chains=args.chains), precision=prec, diag_chains=0,
@@ -361,10 +364,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chains", type=int, default=CHAINS)
-    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp32", "pauli"])
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-pauli", action="store_true", help="skip the structured Pauli form")
     ap.add_argument("--no-configs", action="store_true", help="skip the brief runs of the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -394,6 +398,8 @@ def main():
     forms = [("bf16x3", qst.PREC_BF16X3)]
     if not args.no_plain:
         forms.append(("fp32", qst.PREC_FP32))
+    if not args.no_pauli:
+        forms.append(("pauli", qst.PREC_PAULI))
 
     clocks = Clocks(local)
     results = {}
@@ -448,6 +454,9 @@ def main():
     err_plain = None
     if "fp32" in results:
         err_plain = logl_error(qst, oracle, results["fp32"]["sampler"], prob)
+    err_pauli = None
+    if "pauli" in results:
+        err_pauli = logl_error(qst, oracle, results["pauli"]["sampler"], prob)
 
     # end to end through the C ABI with host buffers: qst_create from host counts and
     # projectors (H2D), run, read the posterior mean back (D2H)
@@ -493,6 +502,8 @@ def main():
     if err_plain is not None:
         line["forms"]["fp32"]["logl_err"] = err_plain
         line["speedup_vs_plain_fp32"] = results["fp32"]["ms"] / head["ms"]
+    if err_pauli is not None:
+        line["forms"]["pauli"]["logl_err"] = err_pauli
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(oracle, prob)
     if world == 1 and not args.no_configs:

@@ -56,8 +56,13 @@ typedef enum {
     QST_PREC_TF32 = 2,   /* tcgen05 kind::tf32: rho rounded once to TF32 (11 significant bits),
                             FP32 accumulation; 1..4 qubits.  Its log L error is O(1) at 4 qubits:
                             a comparison form, not an accurate one */
-    QST_PREC_TF32X2 = 3  /* tcgen05 kind::tf32: rho = hi + lo, both TF32 (22 significant bits),
+    QST_PREC_TF32X2 = 3, /* tcgen05 kind::tf32: rho = hi + lo, both TF32 (22 significant bits),
                             hi and lo products in two accumulators; 1..3 qubits */
+    QST_PREC_PAULI = 4   /* structured FP32 form for the Pauli POVMs only (NULL POVM arrays or
+                            arrays equal to qst_pauli_povms): no projector matrix; the 6^Q
+                            probabilities come from rho by one split per qubit, each a few FP32
+                            adds of the parent block's entries (about 3.5 * 6^Q adds per chain
+                            against 2 * 24^Q FLOPs dense); 1..5 qubits */
 } qst_precision;
 
 /* One tomography problem (Sec. III Steps 1-4).  All pointers are host memory,
@@ -151,7 +156,8 @@ qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_prob
  * config's and every problem's own beta0 (0 meaning the config's);
  * for the tensor-core precisions every packed projector entry exactly representable in
  * bf16 (QST_PREC_BF16X3) or TF32 (QST_PREC_TF32, QST_PREC_TF32X2), and Q within the
- * precision's range: QST_ERR_INVALID_ARG otherwise),
+ * precision's range; for QST_PREC_PAULI the 3^Q Pauli settings of qst_pauli_povms:
+ * QST_ERR_INVALID_ARG otherwise),
  * packs the projectors, uploads everything into the workspace and enqueues the chains'
  * initial states y^0 ~ N(0, I) with rho(y^0) and log L(y^0) (Algorithm 2, initialisation).
  * d_workspace: device memory of at least qst_workspace_size bytes, 256-byte aligned,

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
             // log L(y') = C0 + sum_{c>0} c log(q invf) - N log t: q = vec_h(rho) . P for the
             // stored FP32 rho, t its exact trace, p = q / t
             const double tr = p.trace_prop[c];
-            itr = (float)(1.0 / tr);
+            itr = 1.0f / (float)tr;
             // log t: t is the exact trace of an already normalised rho, so |t - 1| is a few ulps;
             // three terms of log1p(t - 1) then leave less than (t - 1)^4 / 4, far below FP64
             // rounding (FP64 log would cost ~30 of the scarce FP64 FMAs; it is kept for
@@ -58,10 +58,10 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
                 const uint32_t chain_id = (uint32_t)(p.chain_offset + c);
                 const uint4 w = Philox::block(make_uint4(0u, a.step, chain_id, TAG_ALPHA),
                                               (uint32_t)(p.seed & 0xffffffffu), (uint32_t)(p.seed >> 32));
-                const double alpha = ((double)(w.x >> 9) + 0.5) * 0x1p-23;
+                const float alpha = ((float)(w.x >> 9) + 0.5f) * 0x1p-23f;
                 // log alpha in FP32 (alpha is exact in FP32; error <= 2e-6, far inside the
                 // near-tie band); the log-ratio it is compared with stays FP64
-                const double log_alpha = (double)logf((float)alpha);
+                const double log_alpha = (double)logf(alpha);
                 const double logl_cur = p.logl_cur[c];
                 acc = (log_alpha < logl_prop - logl_cur) ? 1 : 0;
                 int32_t win = p.acc_win[c];
@@ -181,12 +181,25 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
     }
 }
 
-// Sums the pool slots in slot order (deterministic) -> out[d].
-__global__ void pool_reduce_kernel(const double *pool, int n_slots, int d, double *out) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d; e += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < n_slots; ++b) s += pool[(int64_t)b * d + e];
-        out[e] = s;
+// Sums the pool slots -> out[d] (deterministic): a CTA owns 32 consecutive entries; its warp w
+// adds slots [w n/32, (w + 1) n/32) in slot order, and the 32 partial sums are added in warp order.
+constexpr int kReduceWarps = 32;
+__global__ void __launch_bounds__(32 * kReduceWarps) pool_reduce_kernel(const double *pool, int n_slots, int d,
+                                                                          double *out) {
+    __shared__ double part[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    const int per = (n_slots + kReduceWarps - 1) / kReduceWarps;
+    const int b0 = w * per, b1 = min(n_slots, b0 + per);
+    double s = 0.0;
+    if (e < d)
+        for (int b = b0; b < b1; ++b) s += pool[(int64_t)b * d + e];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && e < d) {
+        double t = 0.0;
+        for (int k = 0; k < kReduceWarps; ++k) t += part[k][lane];
+        out[e] = t;
     }
 }
 
@@ -292,7 +305,7 @@ cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mod
 int accept_slots(int64_t R) { return (int)((R + kChainsPerCta - 1) / kChainsPerCta); }
 
 cudaError_t launch_pool_reduce(const ProblemView &p, double *out, cudaStream_t s) {
-    pool_reduce_kernel<<<(p.d + 255) / 256, 256, 0, s>>>(p.pool, p.n_slots, p.d, out);
+    pool_reduce_kernel<<<(p.d + 31) / 32, 32 * kReduceWarps, 0, s>>>(p.pool, p.n_slots, p.d, out);
     return cudaGetLastError();
 }
 

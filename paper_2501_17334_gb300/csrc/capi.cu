@@ -91,7 +91,7 @@ bool bf16_exact(double v) {
 // Per-problem host record and workspace layout
 // ------------------------------------------------------------------------------------------
 struct Layout {
-    size_t P32, Ptc, cnt, invf, ptot, colw, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, coef,
+    size_t P32, Ptc, cnt, invf, ptot, colw, pauli_wq, pauli_wc, pauli_perm, y, cur, rho_cur, rho_prop, rho_split, trace_prop, logl_cur, logl_part, beta, coef,
         acc_win,
         acc_total, pool, traj, trace_acc, trace_logl, red, acf, logl_eval, end;
 };
@@ -107,6 +107,9 @@ struct HostProblem {
     std::vector<__nv_bfloat16> Pbf;   // tensor-core B operand, BF16x3
     std::vector<float> Ptf;           // tensor-core B operand, TF32 forms
     std::vector<float> cnt, invf, ptot;
+    std::vector<float4> pauli_wq;     // structured Pauli form: deviance weights per output pair
+    std::vector<float2> pauli_wc;     // and counts
+    std::vector<int32_t> pauli_perm;  // tree order -> setting-major projector index
     TcPlan *tc = nullptr;
 };
 
@@ -130,7 +133,7 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
     if (cfg->diag_chains < 0 || cfg->traj_capacity < 0 || cfg->acf_lmax < 0 || cfg->trace_steps < 0)
         return fail(QST_ERR_INVALID_ARG, "diagnostic sizes must be >= 0");
     if (cfg->precision != QST_PREC_FP32 && cfg->precision != QST_PREC_BF16X3 && cfg->precision != QST_PREC_TF32 &&
-        cfg->precision != QST_PREC_TF32X2)
+        cfg->precision != QST_PREC_TF32X2 && cfg->precision != QST_PREC_PAULI)
         return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
     if (cfg->qr_passes != 1 && cfg->qr_passes != 2)
         return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1 or 2");
@@ -138,6 +141,8 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
     if (cfg->autotune != 0 && cfg->autotune != 1) return fail(QST_ERR_INVALID_ARG, "autotune must be 0 or 1");
     return QST_OK;
 }
+
+void pauli_povms(int Q, std::vector<double> &re, std::vector<double> &im);
 
 qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sampler_cfg *cfg) {
     if (d.num_qubits < 1 || d.num_qubits > 5)
@@ -179,6 +184,15 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
                 if (std::fabs(sr - (i == j ? 1.0 : 0.0)) > 1e-12 || std::fabs(si) > 1e-12)
                     return fail(QST_ERR_INVALID_ARG, "problem %d: setting %d does not sum to the identity", idx, k);
             }
+    if (cfg->precision == QST_PREC_PAULI) {   // the structured form assumes the Pauli POVMs
+        if (d.num_povms != (int32_t)std::lround(std::pow(3.0, d.num_qubits)))
+            return fail(QST_ERR_INVALID_ARG, "problem %d: QST_PREC_PAULI needs the 3^Q Pauli settings", idx);
+        std::vector<double> pre, pim;
+        pauli_povms(d.num_qubits, pre, pim);
+        for (size_t e = 0; e < pre.size(); ++e)
+            if (std::fabs(d.povm_re[e] - pre[e]) > 1e-12 || std::fabs(d.povm_im[e] - pim[e]) > 1e-12)
+                return fail(QST_ERR_INVALID_ARG, "problem %d: QST_PREC_PAULI needs the built-in Pauli POVMs", idx);
+    }
     return QST_OK;
 }
 
@@ -269,7 +283,9 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         hp.beta0 = d.beta0 > 0.0 ? d.beta0 : cfg->beta0;
         const int kind = tc_kind_of(cfg->precision);
         const bool tc = kind != TC_NONE;
+        const bool pauli = cfg->precision == QST_PREC_PAULI;
         v.tc_kind = kind;
+        v.pauli = pauli ? 1 : 0;
         if (tc) {
             const int nt = tc_column_tile(v.D, v.KD);
             if (nt <= 0) return fail(QST_ERR_UNSUPPORTED, "problem %d: no tensor-core column tile for %d projectors", i, v.KD);
@@ -279,11 +295,14 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         }
         hp.KDmax = std::max(v.KD_pad, v.KD_tc);
         // packed projectors
-        std::vector<double> P((size_t)v.d * v.KD);
-        pack_projectors(v.D, v.KD, d.povm_re, d.povm_im, P.data(), v.KD);
-        hp.P32.assign((size_t)v.d_pad * v.KD_pad, 0.0f);
-        for (int r = 0; r < v.d; ++r)
-            for (int m = 0; m < v.KD; ++m) hp.P32[(size_t)r * v.KD_pad + m] = (float)P[(size_t)r * v.KD + m];
+        std::vector<double> P;
+        if (!pauli) {   // the structured form never reads a projector matrix
+            P.resize((size_t)v.d * v.KD);
+            pack_projectors(v.D, v.KD, d.povm_re, d.povm_im, P.data(), v.KD);
+            hp.P32.assign((size_t)v.d_pad * v.KD_pad, 0.0f);
+            for (int r = 0; r < v.d; ++r)
+                for (int m = 0; m < v.KD; ++m) hp.P32[(size_t)r * v.KD_pad + m] = (float)P[(size_t)r * v.KD + m];
+        }
         if (kind == TC_BF16X3) {
             hp.Pbf.assign((size_t)v.KD_tc * v.d_pad, __float2bfloat16_rn(0.0f));
             for (int r = 0; r < v.d; ++r)
@@ -330,8 +349,15 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         }
         v.C0 = C0;
         v.Ntot = Ntot;
+        if (pauli) {
+            pauli_tree_order(hp.Q, hp.pauli_perm);
+            pauli_weights(hp.Q, hp.pauli_perm, hp.cnt.data(), hp.invf.data(), hp.pauli_wq, hp.pauli_wc);
+        }
         // column groups: a fixed rule, and the candidates the autotuner may time instead
-        if (tc) {
+        if (pauli) {
+            v.ngroups = 1;
+            hp.group_choices = {1};
+        } else if (tc) {
             v.ngroups = tc_ngroups(v, v.R);
             const int ntiles = v.KD_tc / tc_column_tile(v.D, v.KD);
             if (v.D == 32) {
@@ -362,6 +388,9 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         L.invf = take(sizeof(float) * hp.KDmax);
         L.ptot = take(sizeof(float) * (hp.KDmax / v.D));
         L.colw = take(sizeof(float4) * (hp.KDmax / 2));
+        L.pauli_wq = take(sizeof(float4) * hp.pauli_wq.size());
+        L.pauli_wc = take(sizeof(float2) * hp.pauli_wc.size());
+        L.pauli_perm = take(sizeof(int32_t) * hp.pauli_perm.size());
         L.y = take(sizeof(float) * 2 * R * v.nx);
         L.cur = take(R);
         L.rho_cur = take(sizeof(float) * R * v.d_pad);
@@ -487,6 +516,9 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     v.invf = reinterpret_cast<const float *>(b + L.invf);
     v.ptot = reinterpret_cast<const float *>(b + L.ptot);
     v.colw = reinterpret_cast<const float4 *>(b + L.colw);
+    v.pauli_wq = v.pauli ? reinterpret_cast<const float4 *>(b + L.pauli_wq) : nullptr;
+    v.pauli_wc = v.pauli ? reinterpret_cast<const float2 *>(b + L.pauli_wc) : nullptr;
+    v.pauli_perm = v.pauli ? reinterpret_cast<const int32_t *>(b + L.pauli_perm) : nullptr;
     v.y = reinterpret_cast<float *>(b + L.y);
     v.cur = reinterpret_cast<uint8_t *>(b + L.cur);
     v.rho_cur = reinterpret_cast<float *>(b + L.rho_cur);
@@ -511,6 +543,11 @@ bool is_tc(const qst_handle *h) { return tc_kind_of(h->cfg.precision) != TC_NONE
 // proposal -> projection -> (accept) for one problem
 qst_status enqueue_projection(qst_handle *h, HostProblem &hp, int64_t rows, float *p_out) {
     ProblemView &v = hp.v;
+    if (v.pauli) {
+        return launch(h, QST_KERNEL_PROJECT, "projection (structured Pauli)", [&] {
+            return launch_project_pauli(v, v.rho_prop, rows, v.logl_part, p_out, h->stream);
+        });
+    }
     if (is_tc(h)) {
         return launch(h, QST_KERNEL_PROJECT, "projection (tcgen05)", [&] {
             return launch_project_tc(hp.tc, v, rows, v.logl_part, p_out, h->d_status, h->stream);
@@ -669,6 +706,15 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
         const Layout &L = hp.off;
         QST_CUDA(cudaMemcpyAsync(h->ws + L.P32, hp.P32.data(), sizeof(float) * hp.P32.size(), cudaMemcpyHostToDevice,
                                  h->stream), "upload P");
+        if (v.pauli) {
+            QST_CUDA(cudaMemcpyAsync(h->ws + L.pauli_wq, hp.pauli_wq.data(), sizeof(float4) * hp.pauli_wq.size(),
+                                     cudaMemcpyHostToDevice, h->stream), "upload deviance weights");
+            QST_CUDA(cudaMemcpyAsync(h->ws + L.pauli_wc, hp.pauli_wc.data(), sizeof(float2) * hp.pauli_wc.size(),
+                                     cudaMemcpyHostToDevice, h->stream), "upload counts (pairs)");
+            QST_CUDA(cudaMemcpyAsync(h->ws + L.pauli_perm, hp.pauli_perm.data(),
+                                     sizeof(int32_t) * hp.pauli_perm.size(), cudaMemcpyHostToDevice, h->stream),
+                     "upload tree order");
+        }
         if (!hp.Pbf.empty())
             QST_CUDA(cudaMemcpyAsync(h->ws + L.Ptc, hp.Pbf.data(), sizeof(__nv_bfloat16) * hp.Pbf.size(),
                                      cudaMemcpyHostToDevice, h->stream), "upload P (bf16)");

@@ -1,0 +1,69 @@
+// Packed FP32 pairs (f32x2: one instruction, two IEEE operations), and the logarithm of the
+// likelihood epilogues on such pairs.  Shared by the tensor-core and the structured Pauli projections.
+#pragma once
+
+#include "log_poly.h"
+#include <cuda_runtime.h>
+
+namespace qst {
+
+// The pair is packed into a 64-bit register inside the asm (mov.b64 {lo, hi}), so no float2
+// is ever reinterpreted through memory.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n add.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mul.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+
+// qst_log_poly (log_poly.h) on two arguments at once, operation for operation, so each
+// result has the same bits as the scalar function; arguments must be positive normal finite
+// (the caller checks that separately).
+__device__ __forceinline__ float2 log_poly2(float2 x) {
+    const int ix0 = __float_as_int(x.x), ix1 = __float_as_int(x.y);
+    const int k0 = (ix0 - 0x3f3504f3) >> 23, k1 = (ix1 - 0x3f3504f3) >> 23;
+    const float2 m = make_float2(__int_as_float(ix0 - (k0 << 23)), __int_as_float(ix1 - (k1 << 23)));
+    const float2 f = add2(m, splat2(-1.0f));
+    const float2 kf = make_float2((float)k0, (float)k1);
+    float2 q = splat2(-0.08064694682313636f);
+    q = fma2(q, f, splat2(0.1291790293475221f));
+    q = fma2(q, f, splat2(-0.13072555472249744f));
+    q = fma2(q, f, splat2(0.14173450906326862f));
+    q = fma2(q, f, splat2(-0.16628919666247013f));
+    q = fma2(q, f, splat2(0.20002695649848323f));
+    q = fma2(q, f, splat2(-0.25000751231191953f));
+    q = fma2(q, f, splat2(0.33333312940994586f));
+    q = fma2(q, f, splat2(-0.49999997733204976f));
+    const float2 f2 = mul2(f, f);
+    const float2 r = fma2(f2, q, fma2(kf, splat2(1.42860677e-06f), f));
+    return fma2(kf, splat2(0.693145751953125f), r);
+}
+
+}  // namespace qst

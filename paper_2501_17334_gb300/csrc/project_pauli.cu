@@ -1,0 +1,317 @@
+// Structured form of the projector contraction for the Pauli POVMs (Sec. II, p_kl = Tr Lambda_kl
+// rho, with Lambda_kl the Kronecker product over qubits of single-qubit eigenprojectors
+// (1 +- P_q) / 2, P_q in {X, Y, Z}; Sec. IV uses all 3^Q settings), fused with the likelihood
+// (Eq. likelihood) in the deviance form of the FP32 form.
+//
+// Because each projector is a product over qubits, the probabilities follow from rho by a tree
+// over the qubits instead of a dense contraction.  Fixing the outcome of the most significant
+// remaining qubit of a Hermitian block M = [[A, B], [B^dag, C]] (A: that qubit's bit 0 in row
+// and column) leaves, on the other qubits, the Hermitian block Tr_q((Pi ⊗ 1) M):
+//     X+-: (A + C +- (B + B^dag)) / 2,   Y+-: (A + C +- i (B - B^dag)) / 2,   Z+: A,   Z-: C.
+// After Q such splits the 6^Q scalars are q_kl = Tr(Lambda_kl rho) of every setting and outcome.
+// In the packed layout (Re rho_ij on and above the diagonal, Im rho_ij below it) a block's packed
+// form is the same sub-block of its parent's packed form, and each entry of a child is a few
+// real adds of parent entries (Re B_uv = TR_uv, Im B_uv = -BL_vu):
+//     u <= v:  Re (B + B^dag)_uv = TR_uv + TR_vu,   Re i(B - B^dag)_uv = BL_uv + BL_vu
+//     u >  v:  Im (B + B^dag)_uv = BL_uv - BL_vu,   Im i(B - B^dag)_uv = TR_uv - TR_vu
+// with TR = the top-right and BL = the bottom-left quarter of the parent's packed form.  The tree
+// costs about 3.5 * 6^Q adds per chain against the 2 * 24^Q FLOPs of the dense contraction;
+// every add is one FP32 rounding and each value passes through Q of them.
+//
+// Work split: a chain's levels t = 0 .. Q-2 (6^t blocks of 2^(Q-t) x 2^(Q-t) packed floats, block
+// index o = sum over split qubits of (2 s + b) 6^(...), the first split most significant) live
+// in two shared-memory buffers (even levels in one, odd in the other).  A split task takes an
+// entry pair (u, v), (v, u) of one parent (8 loads, 12 stores) or a diagonal entry.  The last
+// two splits run in registers: one thread per 4 x 4 block of level Q-2 forms its 36 outputs
+// (tree indices 36 p .. 36 p + 35) and their deviance terms, so a chain has 6^(Q-2) threads.
+// The deviance terms run on packed FP32 pairs (the outputs X+-, Y+-, Z+- of one split), with
+// weights per pair: x = q w + a (w = P_k / count, halved for the X and Y pairs whose factor 1/2
+// is left out of q, and w = 0, a = 1 for an outcome without counts, whose term is then 0); they
+// are stored pair-major ([18][6^(Q-2)]) so that the threads of a warp read them coalesced.
+#include "qst_internal.cuh"
+#include "f32x2.cuh"
+
+namespace qst {
+namespace {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+template <int Q>
+struct PauliShape {
+    static constexpr int D = 1 << Q, d = D * D;
+    static constexpr int level(int t) { return ipow(6, t) * ipow(4, Q - t); }   // floats of level t
+    static constexpr int max_level(int parity) {   // over the stored levels t <= Q - 2 of that parity
+        int m = 0;
+        for (int t = parity; t <= Q - 2; t += 2) m = cmax(m, level(t));
+        return m;
+    }
+    static constexpr int bufA = Q == 1 ? 4 : max_level(0);   // even levels (0: the packed rho)
+    static constexpr int bufB = Q >= 3 ? max_level(1) : 0;   // odd levels
+    static constexpr int floats = (bufA + bufB + 3) / 4 * 4; // per chain
+    static constexpr int TPC = Q >= 2 ? ipow(6, Q - 2) : 1;  // threads per chain: one per 4 x 4 block
+    static constexpr int CPB = Q <= 2 ? 128 : (Q == 3 ? 48 : (Q == 4 ? 8 : 1));   // chains per CTA
+    static constexpr int threads = TPC * CPB;                // 128, 128, 288, 288, 216
+    static constexpr int min_ctas = Q <= 2 ? 8 : (Q <= 4 ? 4 : 6);   // per SM (a register cap)
+};
+
+struct PauliArgs {
+    const float *A;          // [rows][d_pad] packed rho
+    const float4 *wq;        // [18][6^(Q-2)] (w, w, a, a) of output pair 2 j, 2 j + 1 of block p at [j][p]
+    const float2 *wc;        // [18][6^(Q-2)] their counts
+    const int32_t *perm;     // [6^Q] tree order -> setting-major projector index
+    double *out;             // [rows] the deviance sum (one column group)
+    float *p_out;            // [rows][KD] (P_OUT only): p = q / t
+    const double *trace;     // [rows] exact trace of the stored rho (P_OUT only)
+    int64_t rows;
+    int d_pad, KD;
+};
+
+// The six children of one split at an entry: s = A + C, x = B + B^dag, y = i(B - B^dag) there.
+__device__ __forceinline__ void six(float s, float x, float y, float a, float c, float o[6]) {
+    o[0] = 0.5f * (s + x);
+    o[1] = 0.5f * (s - x);
+    o[2] = 0.5f * (s + y);
+    o[3] = 0.5f * (s - y);
+    o[4] = a;
+    o[5] = c;
+}
+
+// One split of a level in shared memory: every parent (n x n) of `in` into its six children
+// (h x h, h = n / 2) in `out`; tasks are the entry pairs u < v and the diagonal entries of the
+// children, folded so that task r of h (h + 1) / 2 maps to row i = r / (h + 1) of the upper
+// triangle and its complement row h - 1 - i.
+template <int N>
+__device__ __forceinline__ void split_level(const float *in, float *out, int parents, int lt, int tpc) {
+    constexpr int h = N / 2, hh = h * h, tasks = h * (h + 1) / 2;
+    for (int idx = lt; idx < parents * tasks; idx += tpc) {
+        const int p = idx / tasks, r = idx - p * tasks;
+        const int i = r / (h + 1), j = r - i * (h + 1);
+        const int u = (j < h - i) ? i : h - 1 - i;
+        const int v = (j < h - i) ? i + j : h - 1 - i + (j - (h - i));
+        const float *M = in + p * N * N;
+        float *O = out + 6 * p * hh;
+        const float tl_uv = M[u * N + v], br_uv = M[(h + u) * N + h + v];
+        const float tr_uv = M[u * N + h + v], bl_uv = M[(h + u) * N + v];
+        float o[6];
+        if (u == v) {
+            six(tl_uv + br_uv, 2.0f * tr_uv, 2.0f * bl_uv, tl_uv, br_uv, o);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) O[c * hh + u * h + v] = o[c];
+        } else {
+            const float tl_vu = M[v * N + u], br_vu = M[(h + v) * N + h + u];
+            const float tr_vu = M[v * N + h + u], bl_vu = M[(h + v) * N + u];
+            six(tl_uv + br_uv, tr_uv + tr_vu, bl_uv + bl_vu, tl_uv, br_uv, o);          // (u, v): real parts
+#pragma unroll
+            for (int c = 0; c < 6; ++c) O[c * hh + u * h + v] = o[c];
+            six(tl_vu + br_vu, bl_vu - bl_uv, tr_vu - tr_uv, tl_vu, br_vu, o);          // (v, u): imaginary parts
+#pragma unroll
+            for (int c = 0; c < 6; ++c) O[c * hh + v * h + u] = o[c];
+        }
+    }
+}
+
+// The last split of one 2 x 2 block [[e00, Re b], [Im b*, e11]] and the deviance terms of its
+// six outputs, pairs j0 .. j0 + 2 of this thread's weights: (S +- 2 Re b), (S +- 2 Im b*) are
+// 2 q of X+- and Y+- (the 1/2 sits in their weights), (e00, e11) are q of Z+-.
+template <bool P_OUT>
+__device__ __forceinline__ void last_split(float e00, float e01, float e10, float e11, const PauliArgs &a, int j0,
+                                           int stride, int lt, float2 &dev, int &xmin, float *p_row, int o0,
+                                           float inv_t) {
+    const float S = e00 + e11;
+    const float2 q2[3] = {fma2(splat2(e01), make_float2(2.0f, -2.0f), splat2(S)),
+                          fma2(splat2(e10), make_float2(2.0f, -2.0f), splat2(S)), make_float2(e00, e11)};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float4 w = a.wq[(j0 + j) * stride + lt];
+        const float2 cnt = a.wc[(j0 + j) * stride + lt];
+        const float2 x = fma2(q2[j], make_float2(w.x, w.y), make_float2(w.z, w.w));
+        xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
+        dev = fma2(cnt, log_poly2(x), dev);
+        if constexpr (P_OUT) {
+            if (p_row) {
+                const float h = j < 2 ? 0.5f : 1.0f;
+                p_row[a.perm[o0 + 2 * j]] = h * q2[j].x * inv_t;
+                p_row[a.perm[o0 + 2 * j + 1]] = h * q2[j].y * inv_t;
+            }
+        }
+    }
+}
+
+template <int Q, bool P_OUT>
+__global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_ctas) project_pauli_kernel(PauliArgs a) {
+    using S = PauliShape<Q>;
+    constexpr int D = S::D, d = S::d, TPC = S::TPC, CPB = S::CPB;
+    extern __shared__ __align__(16) float smem[];
+    __shared__ float part[S::threads];
+    const int g = threadIdx.x / TPC, lt = threadIdx.x - g * TPC;
+    const int64_t c = (int64_t)blockIdx.x * CPB + g;
+    const bool active = c < a.rows;
+    float *bufA = smem + g * S::floats;
+    float *bufB = bufA + S::bufA;
+
+    if (active)
+        for (int e = 4 * lt; e < d; e += 4 * TPC)
+            *reinterpret_cast<float4 *>(bufA + e) = *reinterpret_cast<const float4 *>(a.A + c * a.d_pad + e);
+    if constexpr (TPC > 1) __syncthreads();
+
+    // splits of the stored levels 0 .. Q-3
+    if constexpr (Q >= 3) {
+        split_level<D>(bufA, bufB, 1, lt, TPC);
+        __syncthreads();
+    }
+    if constexpr (Q >= 4) {
+        split_level<D / 2>(bufB, bufA, 6, lt, TPC);
+        __syncthreads();
+    }
+    if constexpr (Q >= 5) {
+        split_level<D / 4>(bufA, bufB, 36, lt, TPC);
+        __syncthreads();
+    }
+
+    float2 dev = splat2(0.0f);
+    int xmin = 0x7fffffff;   // smallest bit pattern of a log argument (sign included)
+    float inv_t = 0.0f;
+    float *p_row = nullptr;
+    if constexpr (P_OUT) {
+        inv_t = active ? (float)(1.0 / a.trace[c]) : 0.0f;
+        p_row = active ? a.p_out + c * a.KD : nullptr;
+    }
+    if constexpr (Q == 1) {
+        const float4 m = *reinterpret_cast<const float4 *>(bufA);   // [[a, Re b], [Im b*, e]]
+        last_split<P_OUT>(m.x, m.y, m.z, m.w, a, 0, 1, 0, dev, xmin, p_row, 0, inv_t);
+    } else {
+        // the last two splits of this thread's 4 x 4 block of level Q - 2 (block lt)
+        const float *Mb = ((Q - 2) & 1 ? bufB : bufA) + 16 * lt;
+        float M[16];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float4 v = *reinterpret_cast<const float4 *>(Mb + 4 * r);
+            M[4 * r] = v.x;
+            M[4 * r + 1] = v.y;
+            M[4 * r + 2] = v.z;
+            M[4 * r + 3] = v.w;
+        }
+        // first of the two: the 2 x 2 children at entries (0,0), (0,1), (1,0), (1,1)
+        float e00[6], e01[6], e10[6], e11[6];
+        six(M[0] + M[10], 2.0f * M[2], 2.0f * M[8], M[0], M[10], e00);
+        six(M[1] + M[11], M[3] + M[6], M[9] + M[12], M[1], M[11], e01);
+        six(M[4] + M[14], M[12] - M[9], M[6] - M[3], M[4], M[14], e10);
+        six(M[5] + M[15], 2.0f * M[7], 2.0f * M[13], M[5], M[15], e11);
+        // second: child c1 gives the outputs 36 lt + 6 c1 .. + 5, weight pairs 3 c1 .. 3 c1 + 2
+#pragma unroll
+        for (int c1 = 0; c1 < 6; ++c1)
+            last_split<P_OUT>(e00[c1], e01[c1], e10[c1], e11[c1], a, 3 * c1, TPC, lt, dev, xmin, p_row,
+                              36 * lt + 6 * c1, inv_t);
+    }
+    // a counted outcome with q <= 0 (or below the normal range): log L = -inf
+    const float acc = (xmin < 0x00800000) ? -INFINITY : dev.x + dev.y;
+
+    // the chain's threads' FP32 sums, added in thread order as an unevaluated FP32 pair (hi, lo)
+    // by one thread per chain; the CTA's chains sit in its first threads, so the FP64 result
+    // (scarce FP64 instructions, each costing its warp the same however many lanes are active)
+    // takes a few warp instructions per CTA
+    if constexpr (TPC == 1) {
+        if (active) a.out[c] = (double)acc;
+    } else {
+        part[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < CPB) {
+            const int64_t cc = (int64_t)blockIdx.x * CPB + threadIdx.x;
+            float hi = 0.0f, lo = 0.0f;
+            for (int t = 0; t < TPC; ++t) {   // two-sum: hi + lo = the exact running sum, up to lo's rounding
+                const float x = part[threadIdx.x * TPC + t];
+                const float sum = hi + x, bp = sum - hi;
+                lo += (hi - (sum - bp)) + (x - bp);
+                hi = sum;
+            }
+            if (cc < a.rows) a.out[cc] = (double)hi + (double)lo;
+        }
+    }
+}
+
+template <int Q, bool P_OUT>
+cudaError_t launch_qp(const PauliArgs &a, cudaStream_t s) {
+    using S = PauliShape<Q>;
+    const size_t smem = sizeof(float) * (size_t)S::floats * S::CPB;
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(project_pauli_kernel<Q, P_OUT>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t blocks = (a.rows + S::CPB - 1) / S::CPB;
+    project_pauli_kernel<Q, P_OUT><<<(unsigned)blocks, S::threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t launch_q(const PauliArgs &a, cudaStream_t s) {
+    return a.p_out ? launch_qp<Q, true>(a, s) : launch_qp<Q, false>(a, s);
+}
+
+}  // namespace
+
+void pauli_tree_order(int Q, std::vector<int32_t> &perm) {
+    const int D = 1 << Q, n = ipow(6, Q);
+    perm.assign(n, 0);
+    for (int o = 0; o < n; ++o) {
+        int k = 0, l = 0, rest = o;
+        for (int q = Q - 1; q >= 0; --q) {   // digit of qubit q: (o / 6^(Q-1-q)) % 6 = 2 s_q + b_q
+            const int digit = rest % 6;
+            rest /= 6;
+            k += (digit / 2) * ipow(3, Q - 1 - q);
+            l += (digit % 2) << (Q - 1 - q);
+        }
+        perm[o] = k * D + l;
+    }
+}
+
+void pauli_weights(int Q, const std::vector<int32_t> &perm, const float *cnt, const float *invf,
+                   std::vector<float4> &wq, std::vector<float2> &wc) {
+    const int npb = Q >= 2 ? ipow(6, Q - 2) : 1;
+    const int n = ipow(6, Q);
+    wq.assign(n / 2, make_float4(0.f, 0.f, 1.f, 1.f));
+    wc.assign(n / 2, make_float2(0.f, 0.f));
+    for (int o = 0; o < n; ++o) {
+        const int p = o / 36, k = o % 36;                 // block, output within the block
+        const int j = k / 2, e = k % 2;                   // pair, element
+        const int idx = j * npb + p;
+        const float half = ((k % 6) < 4) ? 0.5f : 1.0f;   // X and Y outputs carry their 1/2 here
+        const int m = perm[o];
+        const bool counted = cnt[m] > 0.0f;
+        float *q = reinterpret_cast<float *>(&wq[idx]);
+        float *c = reinterpret_cast<float *>(&wc[idx]);
+        q[e] = counted ? invf[m] * half : 0.0f;
+        q[2 + e] = counted ? 0.0f : 1.0f;
+        c[e] = cnt[m];
+    }
+}
+
+cudaError_t launch_project_pauli(const ProblemView &p, const float *A, int64_t rows, double *out, float *p_out,
+                                 cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    if (!p.pauli_wq || !p.pauli_wc || !p.pauli_perm) return cudaErrorInvalidValue;
+    PauliArgs a;
+    a.A = A;
+    a.wq = p.pauli_wq;
+    a.wc = p.pauli_wc;
+    a.perm = p.pauli_perm;
+    a.out = out;
+    a.p_out = p_out;
+    a.trace = p.trace_prop;
+    a.rows = rows;
+    a.d_pad = p.d_pad;
+    a.KD = p.KD;
+    switch (p.D) {
+        case 2: return launch_q<1>(a, s);
+        case 4: return launch_q<2>(a, s);
+        case 8: return launch_q<3>(a, s);
+        case 16: return launch_q<4>(a, s);
+        case 32: return launch_q<5>(a, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace qst

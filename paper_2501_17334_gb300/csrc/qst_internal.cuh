@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace qst {
 
 // Device status bits (read back by synchronising calls).
@@ -112,6 +114,10 @@ struct ProblemView {
     const float *invf;           // [max(KD_pad, KD_tc)] P_k / c_kl (1 where c_kl = 0)
     const float *ptot;           // [max(KD_pad, KD_tc) / D] shots P_k of each setting (0 on padding)
     const float4 *colw;          // [max(KD_pad, KD_tc) / 2] per column pair (invf, invf, add, add), tensor epilogue
+    int pauli;                   // the structured Pauli form of the projection (project_pauli.cu)
+    const float4 *pauli_wq;      // [KD / 2] deviance weights per output pair in the structured form's order
+    const float2 *pauli_wc;      // [KD / 2] and their counts (pauli_weights)
+    const int32_t *pauli_perm;   // [KD] tree order -> setting-major projector index
 
     // chain state
     float *y;                    // [2][R][nx] double-buffered latent states
@@ -175,6 +181,13 @@ bool tc_supported(int kind, int D);      // the tensor-core kernels handle this 
 // test hook: one bounded mbarrier wait that nothing satisfies (sets STATUS_TIMEOUT after limit_ns)
 cudaError_t launch_wait_timeout_probe(uint32_t *status, uint64_t limit_ns, cudaStream_t s);
 int fp32_ngroups(const ProblemView &p, int64_t rows);
+// Structured Pauli form: log L partials [rows] (one column group) and optionally p [rows][KD].
+cudaError_t launch_project_pauli(const ProblemView &p, const float *A, int64_t rows, double *out, float *p_out,
+                                 cudaStream_t s);
+void pauli_tree_order(int Q, std::vector<int32_t> &perm);   // perm[o] = k D + l of tree output o
+// the structured form's per-pair weights from the setting-major counts and P_k / c
+void pauli_weights(int Q, const std::vector<int32_t> &perm, const float *cnt, const float *invf,
+                   std::vector<float4> &wq, std::vector<float2> &wc);
 void set_last_error(const char *msg);   // message returned by qst_last_error()
 int accept_slots(int64_t R);
 

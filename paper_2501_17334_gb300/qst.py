@@ -22,6 +22,7 @@ PREC_FP32 = 0
 PREC_BF16X3 = 1
 PREC_TF32 = 2
 PREC_TF32X2 = 3
+PREC_PAULI = 4   # structured FP32 form, Pauli POVMs only
 KERNEL_PROPOSE, KERNEL_PROJECT, KERNEL_ACCEPT, KERNEL_DIAG = range(4)
 KERNEL_NAMES = {KERNEL_PROPOSE: "propose", KERNEL_PROJECT: "project", KERNEL_ACCEPT: "accept", KERNEL_DIAG: "diag"}
 

@@ -15,11 +15,11 @@ from paper_2501_17334_gb300 import workload as W
 from tests._helpers import unpack_rho
 
 pytestmark = pytest.mark.gpu
-PRECISIONS = ["fp32", "bf16x3"]
+PRECISIONS = ["fp32", "bf16x3", "pauli"]
 
 
 def _prec(qst, name):
-    return qst.PREC_FP32 if name == "fp32" else qst.PREC_BF16X3
+    return {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "pauli": qst.PREC_PAULI}[name]
 
 
 @pytest.fixture(scope="module")

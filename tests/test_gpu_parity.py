@@ -23,11 +23,11 @@ def _torch():
     return torch
 
 
-PRECISIONS = ["fp32", "bf16x3"]
+PRECISIONS = ["fp32", "bf16x3", "pauli"]
 
 
 def _prec(qst, name):
-    return qst.PREC_FP32 if name == "fp32" else qst.PREC_BF16X3
+    return {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "pauli": qst.PREC_PAULI}[name]
 
 
 def _sampler(qst, prob, prec="fp32", **kw):
