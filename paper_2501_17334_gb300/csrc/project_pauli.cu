@@ -28,6 +28,16 @@
 // weights per pair: x = q w + a (w = P_k / count, halved for the X and Y pairs whose factor 1/2
 // is left out of q, and w = 0, a = 1 for an outcome without counts, whose term is then 0); they
 // are stored pair-major ([18][6^(Q-2)]) so that the threads of a warp read them coalesced.
+//
+// Every setting is renormalised by its own sum, log L = C0 + sum_k [sum_l c_kl log(q_kl / f_kl)
+// - P_k log S_k], S_k = sum_l q_kl (the caller adds C0 - N log t, so the kernel adds
+// -P_k log(S_k / t)).  For a complete POVM S_k = Tr rho = t in real arithmetic, so this is the
+// likelihood of Eq. likelihood; in FP32 it cancels the part of each q's rounding error that is
+// proportional to q, which near the posterior (c_kl ~ P_k p_kl) is most of its effect on log L.
+// S_k - t is formed exactly: each q is split at 2^-20 (2^-19 for the doubled X, Y outputs) by
+// adding and removing a constant, the high parts add without rounding and the low parts are
+// tiny.  A thread sums the outcomes of the last two qubits for its 9 settings of them; the
+// 2^(Q-2) threads of one setting prefix are combined in shared memory.
 #include "qst_internal.cuh"
 #include "f32x2.cuh"
 
@@ -36,11 +46,14 @@ namespace {
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int row_stride(int n) { return n >= 8 ? n + 1 : n; }   // of an n x n block
 
 template <int Q>
 struct PauliShape {
     static constexpr int D = 1 << Q, d = D * D;
-    static constexpr int level(int t) { return ipow(6, t) * ipow(4, Q - t); }   // floats of level t
+    // floats of level t: 6^t blocks of n x n, n = 2^(Q-t), rows padded to n + 1 from n = 8 on so
+    // that the transposed reads of a split hit distinct banks
+    static constexpr int level(int t) { return ipow(6, t) * (1 << (Q - t)) * row_stride(1 << (Q - t)); }
     static constexpr int max_level(int parity) {   // over the stored levels t <= Q - 2 of that parity
         int m = 0;
         for (int t = parity; t <= Q - 2; t += 2) m = cmax(m, level(t));
@@ -49,10 +62,11 @@ struct PauliShape {
     static constexpr int bufA = Q == 1 ? 4 : max_level(0);   // even levels (0: the packed rho)
     static constexpr int bufB = Q >= 3 ? max_level(1) : 0;   // odd levels
     static constexpr int floats = (bufA + bufB + 3) / 4 * 4; // per chain
+    static_assert(bufA % 4 == 0, "the odd levels' 4 x 4 blocks are read as float4 rows");
     static constexpr int TPC = Q >= 2 ? ipow(6, Q - 2) : 1;  // threads per chain: one per 4 x 4 block
     static constexpr int CPB = Q <= 2 ? 128 : (Q == 3 ? 48 : (Q == 4 ? 8 : 1));   // chains per CTA
     static constexpr int threads = TPC * CPB;                // 128, 128, 288, 288, 216
-    static constexpr int min_ctas = Q <= 2 ? 8 : (Q <= 4 ? 4 : 6);   // per SM (a register cap)
+    static constexpr int min_ctas = Q <= 2 ? 8 : (Q <= 4 ? 4 : 5);   // per SM (a register cap)
 };
 
 struct PauliArgs {
@@ -60,6 +74,7 @@ struct PauliArgs {
     const float4 *wq;        // [18][6^(Q-2)] (w, w, a, a) of output pair 2 j, 2 j + 1 of block p at [j][p]
     const float2 *wc;        // [18][6^(Q-2)] their counts
     const int32_t *perm;     // [6^Q] tree order -> setting-major projector index
+    const float *ptot;       // [3^Q] shots P_k of setting k
     double *out;             // [rows] the deviance sum (one column group)
     float *p_out;            // [rows][KD] (P_OUT only): p = q / t
     const double *trace;     // [rows] exact trace of the stored rho (P_OUT only)
@@ -83,30 +98,31 @@ __device__ __forceinline__ void six(float s, float x, float y, float a, float c,
 // triangle and its complement row h - 1 - i.
 template <int N>
 __device__ __forceinline__ void split_level(const float *in, float *out, int parents, int lt, int tpc) {
-    constexpr int h = N / 2, hh = h * h, tasks = h * (h + 1) / 2;
+    constexpr int h = N / 2, tasks = h * (h + 1) / 2;
+    constexpr int PS = row_stride(N), CS = row_stride(h), hh = h * CS;   // row strides, child block size
     for (int idx = lt; idx < parents * tasks; idx += tpc) {
         const int p = idx / tasks, r = idx - p * tasks;
         const int i = r / (h + 1), j = r - i * (h + 1);
         const int u = (j < h - i) ? i : h - 1 - i;
         const int v = (j < h - i) ? i + j : h - 1 - i + (j - (h - i));
-        const float *M = in + p * N * N;
+        const float *M = in + p * N * PS;
         float *O = out + 6 * p * hh;
-        const float tl_uv = M[u * N + v], br_uv = M[(h + u) * N + h + v];
-        const float tr_uv = M[u * N + h + v], bl_uv = M[(h + u) * N + v];
+        const float tl_uv = M[u * PS + v], br_uv = M[(h + u) * PS + h + v];
+        const float tr_uv = M[u * PS + h + v], bl_uv = M[(h + u) * PS + v];
         float o[6];
         if (u == v) {
             six(tl_uv + br_uv, 2.0f * tr_uv, 2.0f * bl_uv, tl_uv, br_uv, o);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) O[c * hh + u * h + v] = o[c];
+            for (int c = 0; c < 6; ++c) O[c * hh + u * CS + v] = o[c];
         } else {
-            const float tl_vu = M[v * N + u], br_vu = M[(h + v) * N + h + u];
-            const float tr_vu = M[v * N + h + u], bl_vu = M[(h + v) * N + u];
+            const float tl_vu = M[v * PS + u], br_vu = M[(h + v) * PS + h + u];
+            const float tr_vu = M[v * PS + h + u], bl_vu = M[(h + v) * PS + u];
             six(tl_uv + br_uv, tr_uv + tr_vu, bl_uv + bl_vu, tl_uv, br_uv, o);          // (u, v): real parts
 #pragma unroll
-            for (int c = 0; c < 6; ++c) O[c * hh + u * h + v] = o[c];
+            for (int c = 0; c < 6; ++c) O[c * hh + u * CS + v] = o[c];
             six(tl_vu + br_vu, bl_vu - bl_uv, tr_vu - tr_uv, tl_vu, br_vu, o);          // (v, u): imaginary parts
 #pragma unroll
-            for (int c = 0; c < 6; ++c) O[c * hh + v * h + u] = o[c];
+            for (int c = 0; c < 6; ++c) O[c * hh + v * CS + u] = o[c];
         }
     }
 }
@@ -116,8 +132,8 @@ __device__ __forceinline__ void split_level(const float *in, float *out, int par
 // 2 q of X+- and Y+- (the 1/2 sits in their weights), (e00, e11) are q of Z+-.
 template <bool P_OUT>
 __device__ __forceinline__ void last_split(float e00, float e01, float e10, float e11, const PauliArgs &a, int j0,
-                                           int stride, int lt, float2 &dev, int &xmin, float *p_row, int o0,
-                                           float inv_t) {
+                                           int stride, int lt, float2 &dev, int &xmin, float (&sh)[3],
+                                           float (&sl)[3], float *p_row, int o0, float inv_t) {
     const float S = e00 + e11;
     const float2 q2[3] = {fma2(splat2(e01), make_float2(2.0f, -2.0f), splat2(S)),
                           fma2(splat2(e10), make_float2(2.0f, -2.0f), splat2(S)), make_float2(e00, e11)};
@@ -128,6 +144,11 @@ __device__ __forceinline__ void last_split(float e00, float e01, float e10, floa
         const float2 x = fma2(q2[j], make_float2(w.x, w.y), make_float2(w.z, w.w));
         xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
         dev = fma2(cnt, log_poly2(x), dev);
+        // the setting sum of this pair's q (2 q for X, Y): high parts on the grid, exactly
+        const float2 C = splat2(j < 2 ? 24.0f : 12.0f);
+        const float2 hq = sub2(add2(q2[j], C), C), lq = sub2(q2[j], hq);
+        sh[j] += hq.x + hq.y;
+        sl[j] += lq.x + lq.y;
         if constexpr (P_OUT) {
             if (p_row) {
                 const float h = j < 2 ? 0.5f : 1.0f;
@@ -142,18 +163,36 @@ template <int Q, bool P_OUT>
 __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_ctas) project_pauli_kernel(PauliArgs a) {
     using S = PauliShape<Q>;
     constexpr int D = S::D, d = S::d, TPC = S::TPC, CPB = S::CPB;
+    constexpr int NS = Q == 1 ? 3 : 9;   // settings of the last one or two qubits
     extern __shared__ __align__(16) float smem[];
     __shared__ float part[S::threads];
+    __shared__ float4 tinfo[CPB];                                   // (t_hi, t_lo, 1 / t_hi) per chain
+    __shared__ float2 spart[Q >= 3 ? CPB * NS * TPC : 1];          // setting sums (hi, lo) per thread
     const int g = threadIdx.x / TPC, lt = threadIdx.x - g * TPC;
     const int64_t c = (int64_t)blockIdx.x * CPB + g;
     const bool active = c < a.rows;
     float *bufA = smem + g * S::floats;
     float *bufB = bufA + S::bufA;
 
+    // t = t_hi + t_lo exactly (t is an FP64 sum of FP32 values, a few ulps from 1); the CTA's
+    // chains in its first threads, so the few FP64 instructions fill their warps
+    if (threadIdx.x < CPB) {
+        const int64_t cc = (int64_t)blockIdx.x * CPB + threadIdx.x;
+        const double t = cc < a.rows ? a.trace[cc] : 1.0;
+        const float t_hi = (float)t;
+        tinfo[threadIdx.x] = make_float4(t_hi, (float)(t - (double)t_hi), 1.0f / t_hi, 0.0f);
+    }
+
     if (active)
-        for (int e = 4 * lt; e < d; e += 4 * TPC)
-            *reinterpret_cast<float4 *>(bufA + e) = *reinterpret_cast<const float4 *>(a.A + c * a.d_pad + e);
-    if constexpr (TPC > 1) __syncthreads();
+        for (int e = 4 * lt; e < d; e += 4 * TPC) {
+            const float4 r = *reinterpret_cast<const float4 *>(a.A + c * a.d_pad + e);
+            float *row = bufA + (e / D) * row_stride(D) + e % D;   // (four entries of one row)
+            row[0] = r.x;
+            row[1] = r.y;
+            row[2] = r.z;
+            row[3] = r.w;
+        }
+    __syncthreads();
 
     // splits of the stored levels 0 .. Q-3
     if constexpr (Q >= 3) {
@@ -177,9 +216,25 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
         inv_t = active ? (float)(1.0 / a.trace[c]) : 0.0f;
         p_row = active ? a.p_out + c * a.KD : nullptr;
     }
+    const float4 ti = tinfo[g];
+    // -P_k log(S_k / t) of a setting whose sums are (hi, lo) in units of `unit` q
+    auto renorm = [&](float sh, float sl, float unit, int k) {
+        const float rel = ((unit * sh - ti.x) + (unit * sl - ti.y)) * ti.z;
+        // log1p(rel): |rel| is a few ulps, where three terms are exact to 2^-40
+        const float l1p = fabsf(rel) < 0x1p-10f ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
+                                                : log1pf(rel);
+        return -__ldg(a.ptot + k) * l1p;
+    };
+    float extra = 0.0f;   // this thread's renormalisation terms
+    float sh[3], sl[3];   // setting sums of the current child pair, per last-qubit setting j
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sh[j] = sl[j] = 0.0f;
     if constexpr (Q == 1) {
         const float4 m = *reinterpret_cast<const float4 *>(bufA);   // [[a, Re b], [Im b*, e]]
-        last_split<P_OUT>(m.x, m.y, m.z, m.w, a, 0, 1, 0, dev, xmin, p_row, 0, inv_t);
+        last_split<P_OUT>(m.x, m.y, m.z, m.w, a, 0, 1, 0, dev, xmin, sh, sl, p_row, 0, inv_t);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            extra += renorm(sh[j], sl[j], j < 2 ? 0.5f : 1.0f, j);
     } else {
         // the last two splits of this thread's 4 x 4 block of level Q - 2 (block lt)
         const float *Mb = ((Q - 2) & 1 ? bufB : bufA) + 16 * lt;
@@ -199,13 +254,51 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
         six(M[4] + M[14], M[12] - M[9], M[6] - M[3], M[4], M[14], e10);
         six(M[5] + M[15], 2.0f * M[7], 2.0f * M[13], M[5], M[15], e11);
         // second: child c1 gives the outputs 36 lt + 6 c1 .. + 5, weight pairs 3 c1 .. 3 c1 + 2
+        // children 2 s and 2 s + 1 share the setting s of qubit Q - 2: after each such pair the
+        // sums of settings (s, j) are complete for this thread
 #pragma unroll
-        for (int c1 = 0; c1 < 6; ++c1)
-            last_split<P_OUT>(e00[c1], e01[c1], e10[c1], e11[c1], a, 3 * c1, TPC, lt, dev, xmin, p_row,
+        for (int c1 = 0; c1 < 6; ++c1) {
+            last_split<P_OUT>(e00[c1], e01[c1], e10[c1], e11[c1], a, 3 * c1, TPC, lt, dev, xmin, sh, sl, p_row,
                               36 * lt + 6 * c1, inv_t);
+            if (c1 & 1) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float2 v = make_float2(sh[j], sl[j]);
+                    if constexpr (Q == 2) {
+                        extra += renorm(v.x, v.y, j < 2 ? 0.5f : 1.0f, 3 * (c1 >> 1) + j);
+                    } else {
+                        spart[(g * NS + 3 * (c1 >> 1) + j) * TPC + lt] = v;
+                    }
+                    sh[j] = sl[j] = 0.0f;
+                }
+            }
+        }
+    }
+    if constexpr (Q >= 3) {
+        // the 2^(Q-2) threads of a setting prefix (same s_q, every b_q for q < Q - 2), in b order
+        __syncthreads();
+        constexpr int K3 = ipow(3, Q), NB = 1 << (Q - 2);
+        for (int k = lt; k < K3; k += TPC) {
+            const int slot = k % 9, pre = k / 9;   // (s_{Q-2}, s_{Q-1}) and the prefix's settings
+            int base = 0;                           // thread of the prefix with every b_q = 0
+#pragma unroll
+            for (int q = 0; q < Q - 2; ++q) base += 2 * ((pre / ipow(3, Q - 3 - q)) % 3) * ipow(6, Q - 3 - q);
+            const float2 *sp = spart + (g * NS + slot) * TPC + base;
+            float vh = 0.0f, vl = 0.0f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                int off = 0;   // + sum_q b_q 6^(Q-3-q), a constant
+#pragma unroll
+                for (int q = 0; q < Q - 2; ++q) off += ((b >> (Q - 3 - q)) & 1) * ipow(6, Q - 3 - q);
+                const float2 v = sp[off];
+                vh += v.x;
+                vl += v.y;
+            }
+            extra += renorm(vh, vl, slot % 3 < 2 ? 0.5f : 1.0f, k);
+        }
     }
     // a counted outcome with q <= 0 (or below the normal range): log L = -inf
-    const float acc = (xmin < 0x00800000) ? -INFINITY : dev.x + dev.y;
+    const float acc = (xmin < 0x00800000) ? -INFINITY : (dev.x + dev.y) + extra;
 
     // the chain's threads' FP32 sums, added in thread order as an unevaluated FP32 pair (hi, lo)
     // by one thread per chain; the CTA's chains sit in its first threads, so the FP64 result
@@ -298,6 +391,7 @@ cudaError_t launch_project_pauli(const ProblemView &p, const float *A, int64_t r
     a.wq = p.pauli_wq;
     a.wc = p.pauli_wc;
     a.perm = p.pauli_perm;
+    a.ptot = p.ptot;
     a.out = out;
     a.p_out = p_out;
     a.trace = p.trace_prop;

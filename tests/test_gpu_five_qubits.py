@@ -48,7 +48,7 @@ def test_five_qubit_evaluate_matches_oracle(qst, oracle_mod, cuda_ok, prob5, pre
     assert np.abs(p_gpu - p_ref).max(axis=1)[ok].max() < 1e-6
     c = prob5.counts.astype(np.float64)
     p_used = p_gpu
-    if prec == "bf16x3":
+    if prec in ("bf16x3", "pauli"):   # both renormalise every setting by its own sum
         p_used = (p_gpu.reshape(n, -1, 32) / p_gpu.reshape(n, -1, 32).sum(-1, keepdims=True)).reshape(n, -1)
     ll_own = np.array([oracle_mod.loglik(prob5.counts, p_used[i]) for i in range(n)])
     fin = np.isfinite(ll_own)

@@ -78,11 +78,11 @@ def test_evaluate_matches_oracle(qst, oracle_mod, cuda_ok, prec, q, n):
     # rho and p on identical x
     assert np.abs(rho_gpu - rho_ref).max(axis=(1, 2))[ok].max() < 2e-6
     assert np.abs(p_gpu - p_ref).max(axis=1)[ok].max() < 1e-6
-    # log-likelihood reduction on the GPU's own p (the tensor-core form renormalises every
+    # log-likelihood reduction on the GPU's own p (the tensor-core and Pauli forms renormalise every
     # setting by its own sum, p_kl / sum_l p_kl, which is exact for a complete POVM)
     c = prob.counts.astype(np.float64)
     p_used = p_gpu
-    if prec == "bf16x3":
+    if prec in ("bf16x3", "pauli"):   # both renormalise every setting by its own sum
         p_used = (p_gpu.reshape(n, -1, D) / p_gpu.reshape(n, -1, D).sum(-1, keepdims=True)).reshape(n, -1)
     ll_own = np.array([oracle_mod.loglik(prob.counts, p_used[i]) for i in range(n)])
     bound = np.sum(c) * 6 * 2.0 ** -24
