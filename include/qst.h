@@ -62,13 +62,14 @@ typedef enum {
                             arrays equal to qst_pauli_povms): no projector matrix; the 6^Q
                             probabilities come from rho by one split per qubit, each a few FP32
                             adds of the parent block's entries (about 3.5 * 6^Q adds per chain
-                            against 2 * 24^Q FLOPs dense); 1..5 qubits */
+                            against 2 * 24^Q FLOPs dense), every setting renormalised by its own
+                            sum; 1..6 qubits (6 only with NULL POVM arrays) */
 } qst_precision;
 
 /* One tomography problem (Sec. III Steps 1-4).  All pointers are host memory,
  * read during qst_create only. */
 typedef struct {
-    int32_t num_qubits;     /* Q, 1..5 (D = 2^Q) */
+    int32_t num_qubits;     /* Q, 1..5 (D = 2^Q); 6 with QST_PREC_PAULI and the built-in POVMs (NULL) */
     int32_t num_povms;      /* K, the number of measurement settings (3^Q for Pauli) */
     const int32_t *counts;  /* [K*D] outcome counts c_kl >= 0, setting-major */
     const double *povm_re;  /* [K*D][D][D] row-major real parts of Lambda_kl; NULL together with

@@ -84,7 +84,7 @@ def _ptr(a):
 
 
 def _c(a, dtype):
-    return np.ascontiguousarray(a, dtype=dtype)
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
 
 
 # --------------------------------------------------------------------------- primitives
@@ -178,7 +178,9 @@ def run(problem, num_chains=None, num_steps=None, chain_begin=0, trace_steps=0, 
     pr = _c(problem.povm_re, np.float64); pi = _c(problem.povm_im, np.float64)
     cnt = _c(problem.counts, np.int32)
     keep += [pr, pi, cnt]
-    cfg = OracleCfg(D=D, KD=KD, povm_re=pr.ctypes.data, povm_im=pi.ctypes.data, counts=cnt.ctypes.data,
+    # no POVM arrays: the Pauli projectors, each entry built from the single-qubit ones
+    cfg = OracleCfg(D=D, KD=KD, povm_re=None if pr is None else pr.ctypes.data,
+                    povm_im=None if pi is None else pi.ctypes.data, counts=cnt.ctypes.data,
                     seed=int(problem.seed), chain_begin=int(chain_begin), num_chains=R, num_steps=S,
                     beta0=float(opts["beta0"]), adapt_interval=int(opts["adapt_interval"]),
                     acc_lo=float(opts["acc_lo"]), acc_hi=float(opts["acc_hi"]),

@@ -15,7 +15,9 @@
  *   normal draws      Box-Muller on the generator's uniforms (Algorithm 2: initial state and proposal noise).
  *   bures_rho         Algorithm 1 steps 2-6 (Householder QR, U = Q Lambda,
  *                     W = (U + I) G, rho = W W^dag / Tr W W^dag).
- *   probabilities     p_kl = Tr(Lambda_kl rho) as a direct complex trace (Sec. II).
+ *   probabilities     p_kl = Tr(Lambda_kl rho) as a direct complex trace (Sec. II); with no
+ *                     POVM arrays, Lambda_kl is the Pauli projector of setting k and outcome l,
+ *                     each entry the product of the qubits' eigenprojector entries.
  *   loglik            log L = sum_kl c_kl log p_kl (Eq. likelihood).
  *   oracle_run        Algorithm 2 for chains [chain_begin, chain_begin+num_chains)
  *                     with step-size adaptation and thinning, pooled as in
@@ -213,10 +215,49 @@ void oracle_bures_rho(int D, const double *x, cplx *rho)
 /* Likelihood (Sec. III Step 4, Eq. likelihood)                          */
 /* ------------------------------------------------------------------ */
 
-/* p_kl = Re Tr(Lambda_kl rho) = Re sum_{a,b} Lambda[a,b] rho[b,a]; Lambda is row-major [KD][D][D]. */
+/* Entry (i, j) of the single-qubit eigenprojector of setting s (0 X, 1 Y, 2 Z) with outcome b
+ * (0: eigenvalue +1): (1 + X)/2, (1 - X)/2, (1 + Y)/2, (1 - Y)/2, |0><0|, |1><1| (Sec. II). */
+static cplx pauli_entry(int s, int b, int i, int j)
+{
+    const double sg = b ? -1.0 : 1.0;
+    if (s == 0) return (i == j) ? 0.5 : 0.5 * sg;                          /* X = [[0, 1], [1, 0]] */
+    if (s == 1) return (i == j) ? 0.5 : (i == 0 ? -0.5 * I * sg : 0.5 * I * sg);   /* Y = [[0, -i], [i, 0]] */
+    return (i == b && j == b) ? 1.0 : 0.0;
+}
+
+/* Lambda_kl[a, b] of Q qubits: setting k = sum_q s_q 3^(Q-1-q), outcome l = sum_q b_q 2^(Q-1-q),
+ * row a and column b split into qubit bits the same way (qubit 0 most significant). */
+static cplx pauli_projector_entry(int Q, int k, int l, int a, int b)
+{
+    cplx v = 1.0;
+    for (int q = Q - 1; q >= 0; --q) {   /* qubit q is digit Q-1-q from the right */
+        const int s = k % 3, o = l & 1, i = a & 1, j = b & 1;
+        k /= 3; l >>= 1; a >>= 1; b >>= 1;
+        v *= pauli_entry(s, o, i, j);
+        if (v == 0.0) return 0.0;
+    }
+    return v;
+}
+
+/* p_kl = Re Tr(Lambda_kl rho) = Re sum_{a,b} Lambda[a,b] rho[b,a]; Lambda is row-major [KD][D][D],
+ * or, with povm_re == NULL, the Pauli projector of pauli_projector_entry (KD = 6^Q). */
 void oracle_probabilities(int D, int KD, const double *povm_re, const double *povm_im, const cplx *rho,
                           double *p)
 {
+    if (!povm_re) {
+        int Q = 0;
+        while ((1 << Q) < D) ++Q;
+        for (int m = 0; m < KD; ++m) {
+            cplx s = 0.0;
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) {
+                    const cplx lam = pauli_projector_entry(Q, m / D, m % D, a, b);
+                    if (lam != 0.0) s += lam * rho[b * D + a];
+                }
+            p[m] = creal(s);
+        }
+        return;
+    }
     for (int m = 0; m < KD; ++m) {
         const double *lr = povm_re + (size_t)m * D * D;
         const double *li = povm_im + (size_t)m * D * D;

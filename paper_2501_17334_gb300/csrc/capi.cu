@@ -144,11 +144,18 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
 
 void pauli_povms(int Q, std::vector<double> &re, std::vector<double> &im);
 
+// Qubits the forms cover: 1..5, and 6 for the structured Pauli form with the built-in POVMs
+// (NULL arrays: as dense [K*D][D][D] arrays they would take 3 GB).
+int max_qubits(const qst_sampler_cfg *cfg, bool builtin) { return cfg->precision == QST_PREC_PAULI && builtin ? 6 : 5; }
+
 qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sampler_cfg *cfg) {
-    if (d.num_qubits < 1 || d.num_qubits > 5)
-        return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..5", idx, d.num_qubits);
+    const bool builtin = !d.povm_re && !d.povm_im;   // only the Pauli form keeps them unmaterialised
+    if (d.num_qubits < 1 || d.num_qubits > max_qubits(cfg, builtin))
+        return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..%d", idx, d.num_qubits,
+                    max_qubits(cfg, builtin));
     if (d.num_povms < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_povms must be >= 1", idx);
-    if (!d.counts || !d.povm_re || !d.povm_im) return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
+    if (!d.counts || (!builtin && (!d.povm_re || !d.povm_im)))
+        return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
     if (tc_kind_of(cfg->precision) != TC_NONE && !tc_supported(tc_kind_of(cfg->precision), 1 << d.num_qubits))
         return fail(QST_ERR_INVALID_ARG, "problem %d: precision %d does not cover %d qubits (TF32: 1..4, TF32x2: 1..3)",
                     idx, cfg->precision, d.num_qubits);
@@ -162,6 +169,10 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
     const int D = 1 << d.num_qubits, KD = d.num_povms * D;
     for (int m = 0; m < KD; ++m)
         if (d.counts[m] < 0) return fail(QST_ERR_INVALID_ARG, "problem %d: negative count at %d", idx, m);
+    if (builtin) {   // the built-in Pauli set (make_plan checked num_povms = 3^Q)
+        if (cfg->precision != QST_PREC_PAULI) return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
+        return QST_OK;
+    }
     // Hermitian elements, completeness per setting
     for (int m = 0; m < KD; ++m) {
         const double *re = d.povm_re + (size_t)m * D * D, *im = d.povm_im + (size_t)m * D * D;
@@ -243,10 +254,12 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
     for (int i = 0; i < n; ++i) {
         qst_problem_desc &d = probs_v[i];
         if (d.povm_re || d.povm_im) continue;
-        if (d.num_qubits < 1 || d.num_qubits > 5)
-            return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..5", i, d.num_qubits);
+        if (d.num_qubits < 1 || d.num_qubits > max_qubits(cfg, true))
+            return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..%d", i, d.num_qubits,
+                        max_qubits(cfg, true));
         if (d.num_povms != (int32_t)std::lround(std::pow(3.0, d.num_qubits)))
             return fail(QST_ERR_INVALID_ARG, "problem %d: the built-in Pauli POVMs need num_povms = 3^Q", i);
+        if (cfg->precision == QST_PREC_PAULI) continue;   // never reads the arrays
         pauli_store.emplace_back();
         pauli_store.emplace_back();
         std::vector<double> &re = pauli_store[pauli_store.size() - 2], &im = pauli_store.back();

@@ -59,14 +59,20 @@ struct PauliShape {
         for (int t = parity; t <= Q - 2; t += 2) m = cmax(m, level(t));
         return m;
     }
+    static constexpr int NB = Q >= 2 ? ipow(6, Q - 2) : 1;   // 4 x 4 blocks of level Q - 2 per chain
+    static constexpr int TPC = NB > 648 ? 648 : NB;          // threads per chain (each takes NB / TPC blocks)
+    static constexpr int CPB = Q <= 2 ? 128 : (Q == 3 ? 48 : (Q == 4 ? 8 : 1));   // chains per CTA
+    static constexpr int threads = TPC * CPB;                // 128, 128, 288, 288, 216, 648
+    static constexpr int min_ctas = Q <= 2 ? 8 : (Q <= 4 ? 4 : (Q == 5 ? 5 : 1));   // per SM (a register cap)
+    static constexpr int NS = Q == 1 ? 3 : 9;                // settings of the last one or two qubits
+    // the setting sums (NS x NB (hi, lo) pairs per chain) take the odd-level buffer when the last
+    // stored level is even (Q = 4, 6): it is dead by then
+    static constexpr bool alias_spart = Q >= 4 && (Q % 2 == 0);
     static constexpr int bufA = Q == 1 ? 4 : max_level(0);   // even levels (0: the packed rho)
-    static constexpr int bufB = Q >= 3 ? max_level(1) : 0;   // odd levels
+    static constexpr int bufB = cmax(Q >= 3 ? max_level(1) : 0, alias_spart ? 2 * NS * NB : 0);   // odd levels
     static constexpr int floats = (bufA + bufB + 3) / 4 * 4; // per chain
     static_assert(bufA % 4 == 0, "the odd levels' 4 x 4 blocks are read as float4 rows");
-    static constexpr int TPC = Q >= 2 ? ipow(6, Q - 2) : 1;  // threads per chain: one per 4 x 4 block
-    static constexpr int CPB = Q <= 2 ? 128 : (Q == 3 ? 48 : (Q == 4 ? 8 : 1));   // chains per CTA
-    static constexpr int threads = TPC * CPB;                // 128, 128, 288, 288, 216
-    static constexpr int min_ctas = Q <= 2 ? 8 : (Q <= 4 ? 4 : 5);   // per SM (a register cap)
+    static_assert(NB % TPC == 0, "whole blocks per thread");
 };
 
 struct PauliArgs {
@@ -132,15 +138,15 @@ __device__ __forceinline__ void split_level(const float *in, float *out, int par
 // 2 q of X+- and Y+- (the 1/2 sits in their weights), (e00, e11) are q of Z+-.
 template <bool P_OUT>
 __device__ __forceinline__ void last_split(float e00, float e01, float e10, float e11, const PauliArgs &a, int j0,
-                                           int stride, int lt, float2 &dev, int &xmin, float (&sh)[3],
+                                           int stride, int blk, float2 &dev, int &xmin, float (&sh)[3],
                                            float (&sl)[3], float *p_row, int o0, float inv_t) {
     const float S = e00 + e11;
     const float2 q2[3] = {fma2(splat2(e01), make_float2(2.0f, -2.0f), splat2(S)),
                           fma2(splat2(e10), make_float2(2.0f, -2.0f), splat2(S)), make_float2(e00, e11)};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float4 w = a.wq[(j0 + j) * stride + lt];
-        const float2 cnt = a.wc[(j0 + j) * stride + lt];
+        const float4 w = a.wq[(j0 + j) * stride + blk];
+        const float2 cnt = a.wc[(j0 + j) * stride + blk];
         const float2 x = fma2(q2[j], make_float2(w.x, w.y), make_float2(w.z, w.w));
         xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
         dev = fma2(cnt, log_poly2(x), dev);
@@ -162,17 +168,19 @@ __device__ __forceinline__ void last_split(float e00, float e01, float e10, floa
 template <int Q, bool P_OUT>
 __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_ctas) project_pauli_kernel(PauliArgs a) {
     using S = PauliShape<Q>;
-    constexpr int D = S::D, d = S::d, TPC = S::TPC, CPB = S::CPB;
-    constexpr int NS = Q == 1 ? 3 : 9;   // settings of the last one or two qubits
+    constexpr int D = S::D, d = S::d, TPC = S::TPC, CPB = S::CPB, NB = S::NB;
+    constexpr int NS = S::NS;
     extern __shared__ __align__(16) float smem[];
     __shared__ float part[S::threads];
     __shared__ float4 tinfo[CPB];                                   // (t_hi, t_lo, 1 / t_hi) per chain
-    __shared__ float2 spart[Q >= 3 ? CPB * NS * TPC : 1];          // setting sums (hi, lo) per thread
+    __shared__ float2 spart_s[(Q >= 3 && !S::alias_spart) ? CPB * NS * NB : 1];   // setting sums (hi, lo) per block
     const int g = threadIdx.x / TPC, lt = threadIdx.x - g * TPC;
     const int64_t c = (int64_t)blockIdx.x * CPB + g;
     const bool active = c < a.rows;
     float *bufA = smem + g * S::floats;
     float *bufB = bufA + S::bufA;
+    // setting sums of chain g's blocks: [NS][NB] (hi, lo)
+    float2 *spart = S::alias_spart ? reinterpret_cast<float2 *>(bufB) : spart_s + g * NS * NB;
 
     // t = t_hi + t_lo exactly (t is an FP64 sum of FP32 values, a few ulps from 1); the CTA's
     // chains in its first threads, so the few FP64 instructions fill their warps
@@ -207,6 +215,10 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
         split_level<D / 4>(bufA, bufB, 36, lt, TPC);
         __syncthreads();
     }
+    if constexpr (Q >= 6) {
+        split_level<D / 8>(bufB, bufA, 216, lt, TPC);
+        __syncthreads();
+    }
 
     float2 dev = splat2(0.0f);
     int xmin = 0x7fffffff;   // smallest bit pattern of a log argument (sign included)
@@ -236,40 +248,44 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
         for (int j = 0; j < 3; ++j)
             extra += renorm(sh[j], sl[j], j < 2 ? 0.5f : 1.0f, j);
     } else {
-        // the last two splits of this thread's 4 x 4 block of level Q - 2 (block lt)
-        const float *Mb = ((Q - 2) & 1 ? bufB : bufA) + 16 * lt;
-        float M[16];
+        // the last two splits of this thread's 4 x 4 blocks of level Q - 2 (blocks lt, lt + TPC, ..)
+#pragma unroll 1
+        for (int ib = 0; ib < NB / TPC; ++ib) {
+            const int blk = lt + ib * TPC;
+            const float *Mb = ((Q - 2) & 1 ? bufB : bufA) + 16 * blk;
+            float M[16];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float4 v = *reinterpret_cast<const float4 *>(Mb + 4 * r);
-            M[4 * r] = v.x;
-            M[4 * r + 1] = v.y;
-            M[4 * r + 2] = v.z;
-            M[4 * r + 3] = v.w;
-        }
-        // first of the two: the 2 x 2 children at entries (0,0), (0,1), (1,0), (1,1)
-        float e00[6], e01[6], e10[6], e11[6];
-        six(M[0] + M[10], 2.0f * M[2], 2.0f * M[8], M[0], M[10], e00);
-        six(M[1] + M[11], M[3] + M[6], M[9] + M[12], M[1], M[11], e01);
-        six(M[4] + M[14], M[12] - M[9], M[6] - M[3], M[4], M[14], e10);
-        six(M[5] + M[15], 2.0f * M[7], 2.0f * M[13], M[5], M[15], e11);
-        // second: child c1 gives the outputs 36 lt + 6 c1 .. + 5, weight pairs 3 c1 .. 3 c1 + 2
-        // children 2 s and 2 s + 1 share the setting s of qubit Q - 2: after each such pair the
-        // sums of settings (s, j) are complete for this thread
+            for (int r = 0; r < 4; ++r) {
+                const float4 v = *reinterpret_cast<const float4 *>(Mb + 4 * r);
+                M[4 * r] = v.x;
+                M[4 * r + 1] = v.y;
+                M[4 * r + 2] = v.z;
+                M[4 * r + 3] = v.w;
+            }
+            // first of the two: the 2 x 2 children at entries (0,0), (0,1), (1,0), (1,1)
+            float e00[6], e01[6], e10[6], e11[6];
+            six(M[0] + M[10], 2.0f * M[2], 2.0f * M[8], M[0], M[10], e00);
+            six(M[1] + M[11], M[3] + M[6], M[9] + M[12], M[1], M[11], e01);
+            six(M[4] + M[14], M[12] - M[9], M[6] - M[3], M[4], M[14], e10);
+            six(M[5] + M[15], 2.0f * M[7], 2.0f * M[13], M[5], M[15], e11);
+            // second: child c1 gives the outputs 36 blk + 6 c1 .. + 5, weight pairs 3 c1 .. 3 c1 + 2;
+            // children 2 s and 2 s + 1 share the setting s of qubit Q - 2: after each such pair the
+            // sums of settings (s, j) are complete for this block
 #pragma unroll
-        for (int c1 = 0; c1 < 6; ++c1) {
-            last_split<P_OUT>(e00[c1], e01[c1], e10[c1], e11[c1], a, 3 * c1, TPC, lt, dev, xmin, sh, sl, p_row,
-                              36 * lt + 6 * c1, inv_t);
-            if (c1 & 1) {
+            for (int c1 = 0; c1 < 6; ++c1) {
+                last_split<P_OUT>(e00[c1], e01[c1], e10[c1], e11[c1], a, 3 * c1, NB, blk, dev, xmin, sh, sl, p_row,
+                                  36 * blk + 6 * c1, inv_t);
+                if (c1 & 1) {
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const float2 v = make_float2(sh[j], sl[j]);
-                    if constexpr (Q == 2) {
-                        extra += renorm(v.x, v.y, j < 2 ? 0.5f : 1.0f, 3 * (c1 >> 1) + j);
-                    } else {
-                        spart[(g * NS + 3 * (c1 >> 1) + j) * TPC + lt] = v;
+                    for (int j = 0; j < 3; ++j) {
+                        const float2 v = make_float2(sh[j], sl[j]);
+                        if constexpr (Q == 2) {
+                            extra += renorm(v.x, v.y, j < 2 ? 0.5f : 1.0f, 3 * (c1 >> 1) + j);
+                        } else {
+                            spart[(3 * (c1 >> 1) + j) * NB + blk] = v;
+                        }
+                        sh[j] = sl[j] = 0.0f;
                     }
-                    sh[j] = sl[j] = 0.0f;
                 }
             }
         }
@@ -277,16 +293,16 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
     if constexpr (Q >= 3) {
         // the 2^(Q-2) threads of a setting prefix (same s_q, every b_q for q < Q - 2), in b order
         __syncthreads();
-        constexpr int K3 = ipow(3, Q), NB = 1 << (Q - 2);
+        constexpr int K3 = ipow(3, Q), NPRE = 1 << (Q - 2);   // settings; b-prefixes of a setting prefix
         for (int k = lt; k < K3; k += TPC) {
             const int slot = k % 9, pre = k / 9;   // (s_{Q-2}, s_{Q-1}) and the prefix's settings
             int base = 0;                           // thread of the prefix with every b_q = 0
 #pragma unroll
             for (int q = 0; q < Q - 2; ++q) base += 2 * ((pre / ipow(3, Q - 3 - q)) % 3) * ipow(6, Q - 3 - q);
-            const float2 *sp = spart + (g * NS + slot) * TPC + base;
+            const float2 *sp = spart + slot * NB + base;
             float vh = 0.0f, vl = 0.0f;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
+            for (int b = 0; b < NPRE; ++b) {
                 int off = 0;   // + sum_q b_q 6^(Q-3-q), a constant
 #pragma unroll
                 for (int q = 0; q < Q - 2; ++q) off += ((b >> (Q - 3 - q)) & 1) * ipow(6, Q - 3 - q);
@@ -404,6 +420,7 @@ cudaError_t launch_project_pauli(const ProblemView &p, const float *A, int64_t r
         case 8: return launch_q<3>(a, s);
         case 16: return launch_q<4>(a, s);
         case 32: return launch_q<5>(a, s);
+        case 64: return launch_q<6>(a, s);
         default: return cudaErrorNotSupported;
     }
 }

@@ -973,6 +973,328 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// D = 64 (six qubits): one 128-thread CTA per chain, two threads per column (thread 2 j + h holds
+// rows 32 h .. 32 h + 31 of column j).  The same steps as the kernels above, with CTA barriers
+// where those use warp ones: the latent proposal and H's column half in registers; modified
+// Gram-Schmidt with each column normalised by its owner pair and published to shared memory
+// (the others project it out; pairs whose column is final form the Gram entries); the
+// first-order re-orthogonalisation Q1 (I - F) (R21) by rows; W = (U + I) G by column halves;
+// the Hermitian half of W W^dag by rows, the two threads of a row splitting its columns.
+// ---------------------------------------------------------------------------------------
+struct Wide64 {
+    static constexpr int D = 64;
+    static constexpr int d = D * D;
+    static constexpr int threads = 128;
+    static constexpr int qcol = D + 4;                  // floats per column of a Q plane (per row of W)
+    static constexpr int pk_stride = D + 1;
+    static constexpr int area_a = 2 * D * qcol;         // Q planes, then W as two planes of row stride qcol
+    static constexpr int area_b = 2 * D * D;            // F planes (column-major), then the staged rho
+    static constexpr int smem_floats = area_a + area_b + 2 * D + 32;
+};
+static_assert(Wide64::area_b >= Wide64::D * Wide64::pk_stride, "areas");
+
+template <int PASSES>
+__global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(ProposeArgs a) {
+    using S = Wide64;
+    constexpr int D = S::D, d = S::d, nx = 4 * d, QC = S::qcol, PK = S::pk_stride, H2 = D / 2;
+    extern __shared__ __align__(16) float smem[];
+    float *qre = smem, *qim = smem + D * QC;             // Q planes (column stride QC)
+    float *wre = smem, *wim = smem + D * QC;             // W planes (row stride QC), replace Q
+    float *fre = smem + S::area_a, *fim = fre + D * D;   // F column-major (F[p][m] at m D + p)
+    float *packed = smem + S::area_a;                    // staged rho (row stride PK), replaces F
+    float *rowv = smem + S::area_a + S::area_b;          // [D] per-row values (diagonal of W W^dag)
+    const int t = threadIdx.x;
+    const int j = t >> 1, hh = t & 1, r0 = H2 * hh;      // column (or row) j, half hh
+    const unsigned pair_mask = 3u << ((t & 31) & ~1);
+    const int64_t c = blockIdx.x;                        // one chain per CTA; the grid is exactly rows
+    const uint32_t step = (a.step_dev && a.mode == MODE_STEP) ? a.step_dev->step : a.step;
+
+    // ---- 1. latent proposal: this thread's 32 entries of column j of each part -----------------
+    float coef_y = 1.0f, coef_eta = 0.0f;
+    int cur = 0;
+    if (a.mode == MODE_STEP) {
+        cur = a.cur[c];
+        const float2 cf = a.coef[c];
+        coef_y = cf.x;
+        coef_eta = cf.y;
+    } else if (a.mode == MODE_INIT) {
+        coef_y = 0.0f;
+        coef_eta = 1.0f;
+    }
+    const uint32_t chain_id = (uint32_t)(a.chain_offset + c);
+    const uint32_t tag = (a.mode == MODE_INIT) ? TAG_INIT : TAG_PROPOSAL;
+    const uint32_t key_lo = (uint32_t)(a.seed & 0xffffffffu), key_hi = (uint32_t)(a.seed >> 32);
+    const float *ysrc = a.y + ((int64_t)cur * a.R + c) * nx;
+    float *ydst = a.y + ((int64_t)(1 - cur) * a.R + c) * nx;
+    const float *gsrc = (a.mode == MODE_EVAL) ? a.x_eval + c * nx : ydst;
+    float2 hr[H2 / 2], hi[H2 / 2];   // rows r0 + 2p, r0 + 2p + 1 of H's column j in pair p
+#pragma unroll 1
+    for (int part = 0; part < 4; ++part) {
+        const int e0 = part * d + j * D + r0;
+#pragma unroll
+        for (int q = 0; q < H2 / 4; ++q) {
+            float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.mode == MODE_STEP) y0 = *reinterpret_cast<const float4 *>(ysrc + e0 + 4 * q);
+            if (a.mode == MODE_EVAL) y0 = *reinterpret_cast<const float4 *>(a.x_eval + c * nx + e0 + 4 * q);
+            float4 yn = y0;
+            if (a.mode != MODE_EVAL) {
+                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), key_lo, key_hi);
+                float z0, z1, z2, z3;
+                gaussian_pair_fast(w.x, w.y, z0, z1);
+                gaussian_pair_fast(w.z, w.w, z2, z3);
+                yn.x = __fmaf_rn(coef_y, y0.x, coef_eta * z0);
+                yn.y = __fmaf_rn(coef_y, y0.y, coef_eta * z1);
+                yn.z = __fmaf_rn(coef_y, y0.z, coef_eta * z2);
+                yn.w = __fmaf_rn(coef_y, y0.w, coef_eta * z3);
+                *reinterpret_cast<float4 *>(ydst + e0 + 4 * q) = yn;
+            }
+            if (part == 2) {
+                hr[2 * q] = make_float2(yn.x, yn.y);
+                hr[2 * q + 1] = make_float2(yn.z, yn.w);
+            } else if (part == 3) {
+                hi[2 * q] = make_float2(yn.x, yn.y);
+                hi[2 * q + 1] = make_float2(yn.z, yn.w);
+            }
+        }
+    }
+    __syncthreads();   // y' (read back as G) is written
+
+    // ---- 2a. modified Gram-Schmidt: q_k = v_k / |v_k| published by its pair, projected out ------
+#pragma unroll 1
+    for (int k = 0; k < D; ++k) {
+        if (j == k) {
+            float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < H2 / 2; ++p) n2 = __ffma2_rn(hr[p], hr[p], __ffma2_rn(hi[p], hi[p], n2));
+            float n = hsum(n2);
+            n += __shfl_xor_sync(pair_mask, n, 1);
+            const float2 rs = make_float2(rsqrtf(n), rsqrtf(n));
+#pragma unroll
+            for (int p = 0; p < H2 / 2; ++p) {
+                hr[p] = __fmul2_rn(hr[p], rs);
+                hi[p] = __fmul2_rn(hi[p], rs);
+            }
+            store_column2<H2>(qre + k * QC + r0, hr);
+            store_column2<H2>(qim + k * QC + r0, hi);
+        }
+        __syncthreads();
+        // r = q_k^dag h over this half, then both halves
+        const float *vre = qre + k * QC + r0, *vim = qim + k * QC + r0;
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+#pragma unroll
+        for (int p = 0; p < H2 / 2; p += 2) {
+            const float4 vr4 = *reinterpret_cast<const float4 *>(vre + 2 * p);
+            const float4 vi4 = *reinterpret_cast<const float4 *>(vim + 2 * p);
+            const float2 vr0 = make_float2(vr4.x, vr4.y), vr1 = make_float2(vr4.z, vr4.w);
+            const float2 vi0 = make_float2(vi4.x, vi4.y), vi1 = make_float2(vi4.z, vi4.w);
+            a0 = __ffma2_rn(vr0, hr[p], __ffma2_rn(vr1, hr[p + 1], a0));
+            a1 = __ffma2_rn(vi0, hi[p], __ffma2_rn(vi1, hi[p + 1], a1));
+            b0 = __ffma2_rn(vr0, hi[p], __ffma2_rn(vr1, hi[p + 1], b0));
+            b1 = __ffma2_rn(vi0, hr[p], __ffma2_rn(vi1, hr[p + 1], b1));
+        }
+        float rr = hsum(a0) + hsum(a1), ri = hsum(b0) - hsum(b1);
+        rr += __shfl_xor_sync(0xffffffffu, rr, 1);
+        ri += __shfl_xor_sync(0xffffffffu, ri, 1);
+        if (j > k) {   // h -= r q_k
+            const float2 msr = make_float2(-rr, -rr), psi = make_float2(ri, ri), msi = make_float2(-ri, -ri);
+#pragma unroll
+            for (int p = 0; p < H2 / 2; p += 2) {
+                const float4 vr4 = *reinterpret_cast<const float4 *>(vre + 2 * p);
+                const float4 vi4 = *reinterpret_cast<const float4 *>(vim + 2 * p);
+                const float2 vr0 = make_float2(vr4.x, vr4.y), vr1 = make_float2(vr4.z, vr4.w);
+                const float2 vi0 = make_float2(vi4.x, vi4.y), vi1 = make_float2(vi4.z, vi4.w);
+                hr[p] = __ffma2_rn(msr, vr0, __ffma2_rn(psi, vi0, hr[p]));
+                hi[p] = __ffma2_rn(msr, vi0, __ffma2_rn(msi, vr0, hi[p]));
+                hr[p + 1] = __ffma2_rn(msr, vr1, __ffma2_rn(psi, vi1, hr[p + 1]));
+                hi[p + 1] = __ffma2_rn(msr, vi1, __ffma2_rn(msi, vr1, hi[p + 1]));
+            }
+        } else if (PASSES == 2 && j < k && hh == 0) {   // E_jk = q_j^dag q_k = conj(q_k^dag q_j)
+            fre[k * D + j] = rr;
+            fim[k * D + j] = -ri;
+        }
+    }
+
+    if constexpr (PASSES == 2) {
+        {   // F's diagonal: (|q_j|^2 - 1) / 2
+            float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < H2 / 2; ++p) n2 = __ffma2_rn(hr[p], hr[p], __ffma2_rn(hi[p], hi[p], n2));
+            float n = hsum(n2);
+            n += __shfl_xor_sync(0xffffffffu, n, 1);
+            if (hh == 0) {
+                fre[j * D + j] = 0.5f * (n - 1.0f);
+                fim[j * D + j] = 0.0f;
+            }
+        }
+        __syncthreads();
+        // ---- 2b. Q2 = Q1 (I - F): row a = j, the columns m of parity hh ------------------------
+        float2 q2[H2];   // (re, im) of Q2[a][2 mm + hh]
+#pragma unroll 1
+        for (int mm = 0; mm < H2; ++mm) {
+            const int m = 2 * mm + hh;
+            float2 acc = make_float2(0.f, 0.f), acc2 = acc;   // sum_p Q1[a][p] F[p][m] as (re, im) pairs
+            for (int p = 0; p <= m; ++p) {
+                const float xr = qre[p * QC + j], xi = qim[p * QC + j];
+                const float fr = fre[m * D + p], fi = fim[m * D + p];
+                acc = __ffma2_rn(make_float2(xr, xr), make_float2(fr, fi), acc);     // (xr fr, xr fi)
+                acc2 = __ffma2_rn(make_float2(xi, xi), make_float2(fi, fr), acc2);   // (xi fi, xi fr)
+            }
+            q2[mm] = make_float2(qre[m * QC + j] - (acc.x - acc2.x), qim[m * QC + j] - (acc.y + acc2.y));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int mm = 0; mm < H2; ++mm) {
+            qre[(2 * mm + hh) * QC + j] = q2[mm].x;
+            qim[(2 * mm + hh) * QC + j] = q2[mm].y;
+        }
+        __syncthreads();
+    } else {
+        __syncthreads();
+    }
+
+    // ---- 3. W[:, j] = G[:, j] + sum_k U[:, k] G[k, j] over this half's rows --------------------
+    float2 wr[H2 / 2], wi[H2 / 2];
+#pragma unroll
+    for (int p = 0; p < H2 / 2; ++p) wr[p] = wi[p] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int k0 = 0; k0 < D; k0 += 4) {
+        const float4 g4r = *reinterpret_cast<const float4 *>(gsrc + j * D + k0);
+        const float4 g4i = *reinterpret_cast<const float4 *>(gsrc + d + j * D + k0);
+        const float gkr[4] = {g4r.x, g4r.y, g4r.z, g4r.w}, gki[4] = {g4i.x, g4i.y, g4i.z, g4i.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float *ure = qre + (k0 + u) * QC + r0, *uim = qim + (k0 + u) * QC + r0;
+            const float2 pgr = make_float2(gkr[u], gkr[u]), pgi = make_float2(gki[u], gki[u]);
+            const float2 mgi = make_float2(-gki[u], -gki[u]);
+#pragma unroll
+            for (int p = 0; p < H2 / 2; p += 2) {
+                const float4 ur = *reinterpret_cast<const float4 *>(ure + 2 * p);
+                const float4 ui = *reinterpret_cast<const float4 *>(uim + 2 * p);
+                const float2 ur0 = make_float2(ur.x, ur.y), ur1 = make_float2(ur.z, ur.w);
+                const float2 ui0 = make_float2(ui.x, ui.y), ui1 = make_float2(ui.z, ui.w);
+                wr[p] = __ffma2_rn(ur0, pgr, __ffma2_rn(ui0, mgi, wr[p]));
+                wi[p] = __ffma2_rn(ur0, pgi, __ffma2_rn(ui0, pgr, wi[p]));
+                wr[p + 1] = __ffma2_rn(ur1, pgr, __ffma2_rn(ui1, mgi, wr[p + 1]));
+                wi[p + 1] = __ffma2_rn(ur1, pgi, __ffma2_rn(ui1, pgr, wi[p + 1]));
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < H2 / 2; p += 2) {   // + G[:, j]
+        const float4 gr4 = *reinterpret_cast<const float4 *>(gsrc + j * D + r0 + 2 * p);
+        const float4 gi4 = *reinterpret_cast<const float4 *>(gsrc + d + j * D + r0 + 2 * p);
+        wr[p] = __fadd2_rn(wr[p], make_float2(gr4.x, gr4.y));
+        wr[p + 1] = __fadd2_rn(wr[p + 1], make_float2(gr4.z, gr4.w));
+        wi[p] = __fadd2_rn(wi[p], make_float2(gi4.x, gi4.y));
+        wi[p + 1] = __fadd2_rn(wi[p + 1], make_float2(gi4.z, gi4.w));
+    }
+    __syncthreads();   // U is read by every thread before W replaces it
+#pragma unroll
+    for (int p = 0; p < H2 / 2; ++p) {   // W row-major, real and imaginary planes
+        wre[(r0 + 2 * p) * QC + j] = wr[p].x;
+        wre[(r0 + 2 * p + 1) * QC + j] = wr[p].y;
+        wim[(r0 + 2 * p) * QC + j] = wi[p].x;
+        wim[(r0 + 2 * p + 1) * QC + j] = wi[p].y;
+    }
+    __syncthreads();
+
+    // ---- 4. rho = W W^dag / Tr: row a = j, this thread's half of the columns m ------------------
+    const int arow = j;
+    float2 war[H2 / 2], wai[H2 / 2];
+#pragma unroll
+    for (int p = 0; p < H2 / 2; p += 2) {
+        const float4 r4 = *reinterpret_cast<const float4 *>(wre + arow * QC + r0 + 2 * p);
+        const float4 i4 = *reinterpret_cast<const float4 *>(wim + arow * QC + r0 + 2 * p);
+        war[p] = make_float2(r4.x, r4.y);
+        war[p + 1] = make_float2(r4.z, r4.w);
+        wai[p] = make_float2(i4.x, i4.y);
+        wai[p + 1] = make_float2(i4.z, i4.w);
+    }
+    {
+        float2 d0 = make_float2(0.f, 0.f), d1 = d0;
+#pragma unroll
+        for (int p = 0; p < H2 / 2; ++p) {
+            d0 = __ffma2_rn(war[p], war[p], d0);
+            d1 = __ffma2_rn(wai[p], wai[p], d1);
+        }
+        float diag = hsum(d0) + hsum(d1);
+        diag += __shfl_xor_sync(0xffffffffu, diag, 1);
+        if (hh == 0) rowv[arow] = diag;
+    }
+    __syncthreads();
+    float tr = 0.0f;   // Tr W W^dag in row order (every thread alike)
+    for (int r = 0; r < D; ++r) tr += rowv[r];
+    const float inv_tr = 1.0f / tr;
+    if (hh == 0) packed[arow * PK + arow] = rowv[arow] * inv_tr;
+#pragma unroll 1
+    for (int s = 1; s <= D / 2; ++s) {
+        const int b = (arow + s) & (D - 1);
+        float2 re = make_float2(0.f, 0.f), ima = re, imb = re;
+#pragma unroll
+        for (int p = 0; p < H2 / 2; p += 2) {
+            const float4 r4 = *reinterpret_cast<const float4 *>(wre + b * QC + r0 + 2 * p);
+            const float4 i4 = *reinterpret_cast<const float4 *>(wim + b * QC + r0 + 2 * p);
+            const float2 br0 = make_float2(r4.x, r4.y), br1 = make_float2(r4.z, r4.w);
+            const float2 bi0 = make_float2(i4.x, i4.y), bi1 = make_float2(i4.z, i4.w);
+            re = __ffma2_rn(wai[p], bi0, __ffma2_rn(war[p], br0, re));
+            ima = __ffma2_rn(wai[p], br0, ima);
+            imb = __ffma2_rn(war[p], bi0, imb);
+            re = __ffma2_rn(wai[p + 1], bi1, __ffma2_rn(war[p + 1], br1, re));
+            ima = __ffma2_rn(wai[p + 1], br1, ima);
+            imb = __ffma2_rn(war[p + 1], bi1, imb);
+        }
+        // both halves, in the same order for both threads of the pair
+        float rs = hsum(re), is = hsum(ima) - hsum(imb);
+        const float rs_o = __shfl_xor_sync(0xffffffffu, rs, 1), is_o = __shfl_xor_sync(0xffffffffu, is, 1);
+        const float rv = (hh == 0 ? rs + rs_o : rs_o + rs) * inv_tr;
+        const float iv = (hh == 0 ? is + is_o : is_o + is) * inv_tr;
+        if (hh == 0) {
+            const bool upper = arow < b;
+            packed[arow * PK + b] = upper ? rv : iv;
+            packed[b * PK + arow] = upper ? -iv : rv;
+        }
+    }
+    if (t == 0) {   // the exact trace of the stored (normalised) diagonal, in row order
+        float th = 0.0f, tl = 0.0f;
+        for (int r = 0; r < D; ++r) {
+            const float x = rowv[r] * inv_tr;
+            const float sum = th + x, bp = sum - th;
+            tl += (th - (sum - bp)) + (x - bp);
+            th = sum;
+        }
+        a.trace_out[c] = (double)th + (double)tl;
+    }
+    __syncthreads();
+
+    // ---- 5. store packed rho (FP32) -----------------------------------------------------------
+    float *dst = a.rho_out + c * a.d_pad;
+    for (int e = 4 * t; e < d; e += 4 * S::threads) {
+        auto staged = [&](int ee) { return packed[(ee / D) * PK + (ee % D)]; };
+        const float4 v = make_float4(staged(e), staged(e + 1), staged(e + 2), staged(e + 3));
+        *reinterpret_cast<float4 *>(dst + e) = v;
+        if (a.rho_norm_out) *reinterpret_cast<float4 *>(a.rho_norm_out + c * d + e) = v;
+    }
+}
+
+template <int PASSES>
+cudaError_t launch_propose_d64(const ProposeArgs &a, cudaStream_t s) {
+    using S = Wide64;
+    const size_t smem = sizeof(float) * S::smem_floats;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(propose_kernel_d64<PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(propose_kernel_d64<PASSES>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.rows <= 0) return cudaSuccess;
+    propose_kernel_d64<PASSES><<<(unsigned)a.rows, S::threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int PASSES>
 cudaError_t launch_propose_d32(const ProposeArgs &a, cudaStream_t s) {
     using S = Wide;
@@ -1015,7 +1337,10 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.step_dev = step_dev;
     a.mode = mode;
     a.d_pad = p.d_pad;
-    if constexpr (D == 32) {
+    if constexpr (D == 64) {
+        if (a.split_out || a.split_tf) return cudaErrorNotSupported;   // no tensor-core form at D = 64
+        return launch_propose_d64<PASSES>(a, s);
+    } else if constexpr (D == 32) {
         if (a.split_tf) return cudaErrorNotSupported;   // the TF32 forms stop at D = 16
         return launch_propose_d32<PASSES>(a, s);
     } else {
@@ -1057,6 +1382,7 @@ cudaError_t launch_propose(const ProblemView &p, int mode, uint32_t step, const 
         case 8: return launch_propose_d<8>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
         case 16: return launch_propose_d<16>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
         case 32: return launch_propose_d<32>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+        case 64: return launch_propose_d<64>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
         default: return cudaErrorInvalidValue;
     }
 }

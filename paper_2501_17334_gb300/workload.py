@@ -207,6 +207,18 @@ def five_qubit_problem(num_chains: int = 256, num_steps: int = 100, seed: int = 
     return make_problem(5, truth, 1000, num_chains, num_steps, 0.05, seed + 1000, seed + 2000, name="five_qubits")
 
 
+def six_qubit_problem(num_chains: int = 64, num_steps: int = 50, seed: int = 1007) -> Problem:
+    """A 6-qubit problem (D = 64, 729 bases x 64 outcomes = 46656 projectors): Ginibre truth of
+    rank 3 mixed with I/D at weight 0.05, 1000 shots per basis, beta0 0.02.  Its POVM arrays are
+    left out (``None``: the built-in Pauli set) -- as dense [K*D, D, D] arrays they would take
+    3 GB."""
+    rng = np.random.default_rng(seed)
+    truth = depolarise(ginibre_state(64, 3, rng), 0.05)
+    counts = sample_counts(truth, 6, 1000, np.random.default_rng(seed + 1000))
+    return Problem(6, None, None, counts, truth, int(num_chains), int(num_steps), 0.02, seed + 2000,
+                   name="six_qubits")
+
+
 def heterogeneous_batch(num_problems: int = 64, seed: int = 1005, max_qubits: int = 5,
                         chain_scale: float = 1.0) -> List[Problem]:
     """Batch of independent problems of uneven size (configuration 5).

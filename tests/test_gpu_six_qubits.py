@@ -1,0 +1,77 @@
+"""GPU parity at six qubits (D = 64, 729 settings x 64 outcomes = 46656 Pauli projectors): the
+D = 64 proposal kernel (one CTA per chain) with the structured Pauli contraction, the only
+form that covers six qubits (the dense projector matrix would be 764 MB in FP32 and the dense
+POVM arrays 3 GB).  Against the FP64 oracle, which builds each projector entry from the
+single-qubit eigenprojectors: rho and p on identical latent rows, the log-likelihood, the
+first accept decisions of a few chains and the pooled mean."""
+import numpy as np
+import pytest
+
+from paper_2501_17334_gb300 import workload as W
+from tests._helpers import unpack_rho
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def prob6():
+    return W.six_qubit_problem(num_chains=8, num_steps=10)   # (the oracle takes seconds per rho at 6 qubits)
+
+
+def _cond(x, D):
+    d = D * D
+    H = (x[:, 2 * d:3 * d] + 1j * x[:, 3 * d:]).reshape(-1, D, D).transpose(0, 2, 1)
+    return np.linalg.cond(H)
+
+
+def test_six_qubit_evaluate_matches_oracle(qst, oracle_mod, cuda_ok, prob6):
+    import torch
+    n = 8
+    s = qst.Sampler(prob6, precision=qst.PREC_PAULI, diag_chains=0)
+    x32 = W.latent_batch(n, 6, seed=606).astype(np.float32)
+    rho_p, p_gpu, ll_gpu = s.evaluate(torch.from_numpy(x32).cuda())
+    torch.cuda.synchronize()
+    s.close()
+    rho_gpu = unpack_rho(rho_p.cpu().numpy(), 64)
+    p_gpu = p_gpu.cpu().numpy().astype(np.float64)
+    ll_gpu = ll_gpu.cpu().numpy()
+    rho_ref, p_ref, ll_ref = oracle_mod.evaluate(prob6, x32.astype(np.float64))
+    ok = _cond(x32.astype(np.float64), 64) <= 1e3
+    assert ok.mean() >= 0.75
+    # the FP32 assembly of a 64 x 64 rho: entries ~1/64, errors a few 1e-7
+    assert np.abs(rho_gpu - rho_ref).max(axis=(1, 2))[ok].max() < 2e-6
+    assert np.all(np.isfinite(rho_gpu)) and np.abs(np.trace(rho_gpu, axis1=1, axis2=2) - 1).max() < 1e-5
+    assert np.abs(p_gpu - p_ref).max(axis=1)[ok].max() < 1e-6
+    # the FP64 reduction on the GPU's own p (renormalised per setting, as the form does)
+    D = 64
+    p_used = (p_gpu.reshape(n, -1, D) / p_gpu.reshape(n, -1, D).sum(-1, keepdims=True)).reshape(n, -1)
+    ll_own = np.array([oracle_mod.loglik(prob6.counts, p_used[i]) for i in range(n)])
+    fin = np.isfinite(ll_own)
+    assert np.abs(ll_gpu[fin] - ll_own[fin]).max() < np.sum(prob6.counts.astype(np.float64)) * 6 * 2.0 ** -24
+    rel = np.abs(ll_gpu - ll_ref) / np.abs(ll_ref)
+    assert np.nanmax(rel[ok]) < 1e-5
+
+
+def test_six_qubit_decisions_match_oracle(qst, oracle_mod, cuda_ok, prob6):
+    R, S = prob6.num_chains, prob6.num_steps
+    s = qst.Sampler(prob6, precision=qst.PREC_PAULI, trace_steps=S, diag_chains=0)
+    s.run_chains(S)
+    acc_gpu, _ = s.get_trace()
+    mean, n = s.posterior_mean()
+    s.close()
+    ref = oracle_mod.run(prob6, num_steps=S, trace_steps=S, want_final=True)
+    margin = ref["trace_log_alpha"] - (ref["trace_logl_prop"] - ref["trace_logl_cur"])
+    mism = 0
+    for r in range(R):
+        bad = np.nonzero(acc_gpu.T[r] != ref["trace_accept"][r])[0]
+        if bad.size:
+            assert abs(margin[r, bad[0]]) < 5e-2, (r, bad[0], margin[r, bad[0]])
+            mism += 1
+    assert mism <= 1
+    assert ref["trace_accept"].mean() > 0.05   # the chains move
+    assert n == ref["num_pooled"] == R * S
+    assert abs(np.trace(mean).real - 1) < 1e-6
+    assert np.linalg.eigvalsh(mean).min() > -1e-7
+    same = np.all(acc_gpu.T == ref["trace_accept"], axis=1)
+    if same.all():
+        assert np.abs(mean - ref["mean"]).max() < 1e-5
