@@ -268,6 +268,13 @@ def other_configs(qst, W, oracle):
     ms_mixed = time_handle(qst, batch, qst.PREC_BF16X3, 20, 3)
     ms_plain = time_handle(qst, batch, qst.PREC_FP32, 3, 1)
     ms_pauli = time_handle(qst, batch, qst.PREC_PAULI, 20, 3)
+    # six qubits (D = 64, 46656 projectors): the structured Pauli form is the one that covers it
+    p6 = W.six_qubit_problem(num_chains=4096, num_steps=20)
+    ms6, s6 = time_handle(qst, p6, qst.PREC_PAULI, 10, 3, keep=True)
+    out["six_qubits_pauli"] = {"chains": p6.num_chains, "qubits": 6, "ms_per_step": ms6,
+                               "chain_steps_per_s": p6.num_chains / (ms6 / 1000.0), "steps": 10,
+                               "logl_err": logl_error(qst, oracle, s6, p6, nsample=8)}
+    s6.close()
     out["config5_heterogeneous"] = {
         "problems": len(batch), "chains": chains,
         "qubits_hist": [sum(p.num_qubits == q for p in batch) for q in range(1, 6)],
