@@ -134,3 +134,26 @@ def test_capi_takes_the_pauli_form_for_pauli_povms_only(qst):
     assert qst.workspace_size([rot], qst.default_config(precision=qst.PREC_FP32)) > 0
     with pytest.raises(Exception):
         qst.workspace_size([rot], cfg)
+
+
+def test_six_qubits_only_in_the_pauli_form_with_builtin_povms(qst):
+    """Six qubits run only in the structured form, and only with the built-in (NULL) POVM arrays,
+    which the library then never materialises; every other combination is refused before any
+    allocation."""
+    import copy
+    p6 = W.six_qubit_problem(num_chains=4, num_steps=1)
+    assert p6.povm_re is None and p6.povm_im is None
+    assert qst.workspace_size([p6], qst.default_config(precision=qst.PREC_PAULI)) > 0
+    for prec in (qst.PREC_FP32, qst.PREC_BF16X3, qst.PREC_TF32, qst.PREC_TF32X2):
+        with pytest.raises(Exception):
+            qst.workspace_size([p6], qst.default_config(precision=prec))
+    # five qubits with NULL arrays still work in the dense forms (materialised there)
+    p5 = copy.copy(W.five_qubit_problem(num_chains=4, num_steps=1))
+    p5.povm_re = p5.povm_im = None
+    assert qst.workspace_size([p5], qst.default_config(precision=qst.PREC_FP32)) > 0
+    assert qst.workspace_size([p5], qst.default_config(precision=qst.PREC_PAULI)) > 0
+    # seven qubits: refused in every form
+    p7 = copy.copy(p6)
+    p7.num_qubits = 7
+    with pytest.raises(Exception):
+        qst.workspace_size([p7], qst.default_config(precision=qst.PREC_PAULI))
