@@ -66,6 +66,15 @@ typedef enum {
                             sum; 1..6 qubits (6 only with NULL POVM arrays) */
 } qst_precision;
 
+/* Prior of rho, i.e. the map from the latent Gaussian vector x to rho (Algorithm 1 is the
+ * Bures one; the method leaves the prior open). */
+typedef enum {
+    QST_PRIOR_BURES = 0, /* Algorithm 1: W = (U + I) G with U the unitary QR factor of H (positive
+                            real diagonal of R), rho = W W^dag / Tr */
+    QST_PRIOR_HS = 1     /* Hilbert-Schmidt (Ginibre) prior: W = G, rho = G G^dag / Tr; the QR of H
+                            is skipped (H's entries are still drawn and carried, unused) */
+} qst_prior;
+
 /* One tomography problem (Sec. III Steps 1-4).  All pointers are host memory,
  * read during qst_create only. */
 typedef struct {
@@ -104,7 +113,7 @@ typedef struct {
     int32_t autotune;       /* 1 (default): qst_create times the projection of every problem with
                                each candidate number of column groups (the split of its N tiles
                                over CTAs) and keeps the fastest; 0: a fixed rule */
-    int32_t reserved[1];    /* zero */
+    int32_t prior;          /* qst_prior: QST_PRIOR_BURES (0, the default) or QST_PRIOR_HS */
 } qst_sampler_cfg;
 
 /* Diagnostics of one problem (Sec. IV). */

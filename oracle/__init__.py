@@ -43,6 +43,7 @@ class OracleCfg(ctypes.Structure):
         ("acc_lo", ctypes.c_double), ("acc_hi", ctypes.c_double), ("adapt_factor", ctypes.c_double),
         ("beta_max", ctypes.c_double), ("thin", ctypes.c_int32), ("burn_in", ctypes.c_int32),
         ("trace_steps", ctypes.c_int32), ("traj_chains", ctypes.c_int32), ("traj_capacity", ctypes.c_int32),
+        ("prior", ctypes.c_int32),
     ]
 
 
@@ -71,7 +72,8 @@ def lib():
         L.oracle_probabilities_split.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P]
         L.oracle_loglik.argtypes = [ctypes.c_int, P, P]
         L.oracle_loglik.restype = ctypes.c_double
-        L.oracle_evaluate_batch.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int64, P, P, P, P, P]
+        L.oracle_evaluate_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int64, P, P,
+                                            P, P, P]
         L.oracle_run.argtypes = [ctypes.POINTER(OracleCfg), ctypes.POINTER(OracleOut)]
         L.oracle_run.restype = ctypes.c_int
         L.oracle_num_threads.restype = ctypes.c_int
@@ -125,7 +127,10 @@ def qr_unitary(H: np.ndarray):
     return (ur + 1j * ui).T, rr + 1j * ri
 
 
-def evaluate(problem, x: np.ndarray, want_rho=True, want_p=True):
+PRIOR_BURES, PRIOR_HS = 0, 1   # Algorithm 1; Hilbert-Schmidt (rho = G G^dag / Tr)
+
+
+def evaluate(problem, x: np.ndarray, want_rho=True, want_p=True, prior=PRIOR_BURES):
     """rho(x), p(x) and log L(x) for rows of ``x`` (``[n, 4D^2]``), all FP64."""
     D, KD = problem.dim, problem.num_povms * problem.dim
     x = _c(np.atleast_2d(x), np.float64)
@@ -136,7 +141,7 @@ def evaluate(problem, x: np.ndarray, want_rho=True, want_p=True):
     ll = np.zeros(n)
     pr = _c(problem.povm_re, np.float64); pi = _c(problem.povm_im, np.float64)
     cnt = _c(problem.counts, np.int32)
-    lib().oracle_evaluate_batch(D, KD, _ptr(pr), _ptr(pi), _ptr(cnt), n, _ptr(x), _ptr(rr), _ptr(ri), _ptr(p),
+    lib().oracle_evaluate_batch(D, int(prior), KD, _ptr(pr), _ptr(pi), _ptr(cnt), n, _ptr(x), _ptr(rr), _ptr(ri), _ptr(p),
                                 _ptr(ll))
     rho = (rr + 1j * ri) if want_rho else None
     return rho, p, ll
@@ -163,7 +168,7 @@ DEFAULTS = dict(beta0=0.1, adapt_interval=500, acc_lo=0.2, acc_hi=0.6, adapt_fac
 
 
 def run(problem, num_chains=None, num_steps=None, chain_begin=0, trace_steps=0, traj_chains=0,
-        traj_capacity=0, want_final=False, want_chain_pool=False, **overrides):
+        traj_capacity=0, want_final=False, want_chain_pool=False, prior=PRIOR_BURES, **overrides):
     """Algorithm 2 on every chain of ``problem`` (or the given counts), pooled as Eq. BME2.
 
     Returns a dict with the pooled sum and mean, the sample count and any requested traces.
@@ -186,7 +191,7 @@ def run(problem, num_chains=None, num_steps=None, chain_begin=0, trace_steps=0, 
                     acc_lo=float(opts["acc_lo"]), acc_hi=float(opts["acc_hi"]),
                     adapt_factor=float(opts["adapt_factor"]), beta_max=float(opts["beta_max"]),
                     thin=int(opts["thin"]), burn_in=int(opts["burn_in"]), trace_steps=int(trace_steps),
-                    traj_chains=int(traj_chains), traj_capacity=int(traj_capacity))
+                    traj_chains=int(traj_chains), traj_capacity=int(traj_capacity), prior=int(prior))
     res = {}
 
     def buf(name, shape, dtype):

@@ -15,6 +15,8 @@
  *   normal draws      Box-Muller on the generator's uniforms (Algorithm 2: initial state and proposal noise).
  *   bures_rho         Algorithm 1 steps 2-6 (Householder QR, U = Q Lambda,
  *                     W = (U + I) G, rho = W W^dag / Tr W W^dag).
+ *   hs_rho            the Hilbert-Schmidt prior, rho = G G^dag / Tr G G^dag (G as in
+ *                     Algorithm 1; H unused), a prior the method admits in place of Bures.
  *   probabilities     p_kl = Tr(Lambda_kl rho) as a direct complex trace (Sec. II); with no
  *                     POVM arrays, Lambda_kl is the Pauli projector of setting k and outcome l,
  *                     each entry the product of the qubits' eigenprojector entries.
@@ -211,6 +213,29 @@ void oracle_bures_rho(int D, const double *x, cplx *rho)
     free(G); free(H); free(U); free(W); free(rd);
 }
 
+/* The Hilbert-Schmidt (Ginibre) prior: rho = G G^dag / Tr(G G^dag), G from the first 2 D^2
+ * entries of x exactly as in Algorithm 1. */
+void oracle_hs_rho(int D, const double *x, cplx *rho)
+{
+    const int d2 = D * D;
+    double tr = 0.0;
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+            cplx s = 0.0;
+            for (int j = 0; j < D; ++j) s += (x[a + D * j] + I * x[d2 + a + D * j]) * conj(x[b + D * j] + I * x[d2 + b + D * j]);
+            rho[a * D + b] = s;
+            if (a == b) tr += creal(s);
+        }
+    for (int e = 0; e < d2; ++e) rho[e] /= tr;
+}
+
+/* rho(x) under the prior: 0 Bures (Algorithm 1), 1 Hilbert-Schmidt. */
+static void rho_of_x(int D, int prior, const double *x, cplx *rho)
+{
+    if (prior == 1) oracle_hs_rho(D, x, rho);
+    else oracle_bures_rho(D, x, rho);
+}
+
 /* ------------------------------------------------------------------ */
 /* Likelihood (Sec. III Step 4, Eq. likelihood)                          */
 /* ------------------------------------------------------------------ */
@@ -282,12 +307,12 @@ double oracle_loglik(int KD, const int32_t *counts, const double *p)
 }
 
 /* rho(x) followed by its log-likelihood, for one latent vector. */
-double oracle_loglik_of_x(int D, int KD, const double *povm_re, const double *povm_im, const int32_t *counts,
+double oracle_loglik_of_x(int D, int prior, int KD, const double *povm_re, const double *povm_im, const int32_t *counts,
                           const double *x, double *rho_re, double *rho_im, double *p_out)
 {
     cplx *rho = malloc(sizeof(cplx) * D * D);
     double *p = malloc(sizeof(double) * KD);
-    oracle_bures_rho(D, x, rho);
+    rho_of_x(D, prior, x, rho);
     oracle_probabilities(D, KD, povm_re, povm_im, rho, p);
     double ll = oracle_loglik(KD, counts, p);
     if (rho_re)
@@ -299,13 +324,14 @@ double oracle_loglik_of_x(int D, int KD, const double *povm_re, const double *po
 }
 
 /* Batched helper: rows of x [n][4D^2] -> rho, p, logL (each output optional). */
-void oracle_evaluate_batch(int D, int KD, const double *povm_re, const double *povm_im, const int32_t *counts,
-                           int64_t n, const double *x, double *rho_re, double *rho_im, double *p, double *logl)
+void oracle_evaluate_batch(int D, int prior, int KD, const double *povm_re, const double *povm_im,
+                           const int32_t *counts, int64_t n, const double *x, double *rho_re, double *rho_im,
+                           double *p, double *logl)
 {
     const int64_t nx = 4 * (int64_t)D * D, d2 = (int64_t)D * D;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < n; ++i) {
-        double ll = oracle_loglik_of_x(D, KD, povm_re, povm_im, counts, x + i * nx,
+        double ll = oracle_loglik_of_x(D, prior, KD, povm_re, povm_im, counts, x + i * nx,
                                        rho_re ? rho_re + i * d2 : NULL, rho_im ? rho_im + i * d2 : NULL,
                                        p ? p + i * KD : NULL);
         if (logl) logl[i] = ll;
@@ -335,6 +361,7 @@ typedef struct {
     int32_t trace_steps;     /* record the first trace_steps steps of every chain */
     int32_t traj_chains;     /* store the pooled trajectory of the first traj_chains chains */
     int32_t traj_capacity;   /* ... up to this many kept samples each */
+    int32_t prior;           /* 0 Bures (Algorithm 1), 1 Hilbert-Schmidt */
 } oracle_cfg;
 
 typedef struct {
@@ -369,7 +396,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
     int64_t A = 0, acc_total = 0, kept = 0;
     double beta = cfg->beta0;
     oracle_normals(cfg->seed, 0u, chain, TAG_INIT, nx, y);
-    oracle_bures_rho(D, y, rho);
+    rho_of_x(D, cfg->prior, y, rho);
     oracle_probabilities(D, KD, cfg->povm_re, cfg->povm_im, rho, p);
     double logl = oracle_loglik(KD, cfg->counts, p);
 
@@ -379,7 +406,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
         double a = sqrt(1.0 - beta * beta);
         for (int e = 0; e < nx; ++e) yp[e] = a * y[e] + beta * eta[e];
         /* likelihood: rho(y') and L(y'); rho(y^{j-1}) and L(y^{j-1}) are kept from the last accept */
-        oracle_bures_rho(D, yp, rhop);
+        rho_of_x(D, cfg->prior, yp, rhop);
         oracle_probabilities(D, KD, cfg->povm_re, cfg->povm_im, rhop, p);
         double loglp = oracle_loglik(KD, cfg->counts, p);
         /* accept test: alpha ~ U(0,1); accept iff log alpha < log L(y') - log L(y) */

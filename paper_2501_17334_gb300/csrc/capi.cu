@@ -137,6 +137,8 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
         return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
     if (cfg->qr_passes != 1 && cfg->qr_passes != 2)
         return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1 or 2");
+    if (cfg->prior != QST_PRIOR_BURES && cfg->prior != QST_PRIOR_HS)
+        return fail(QST_ERR_INVALID_ARG, "unknown prior %d", cfg->prior);
     if (cfg->use_graph != 0 && cfg->use_graph != 1) return fail(QST_ERR_INVALID_ARG, "use_graph must be 0 or 1");
     if (cfg->autotune != 0 && cfg->autotune != 1) return fail(QST_ERR_INVALID_ARG, "autotune must be 0 or 1");
     return QST_OK;
@@ -387,7 +389,7 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         }
         hp.part_slots = v.ngroups;
         for (int g : hp.group_choices) hp.part_slots = std::max(hp.part_slots, g);
-        v.qr_passes = cfg->qr_passes;
+        v.qr_passes = cfg->prior == QST_PRIOR_HS ? 0 : cfg->qr_passes;   // 0: no QR, W = G
         v.n_slots = accept_slots(v.R);
         v.n_diag = (int)std::min<int64_t>(cfg->diag_chains, v.R);
         v.traj_cap = cfg->traj_capacity;

@@ -305,6 +305,8 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     // Gram entry E_jk = q_j^dag q_k of the normalised columns for the re-orthogonalisation --
     // the entries become available exactly as lanes fall idle, so the Gram matrix costs no
     // separate pass.
+    // PASSES = 0 (the Hilbert-Schmidt prior) skips steps 2 and the U term of step 3: W = G
+    if constexpr (PASSES > 0) {
     float inv_own = 0.0f;   // 1 / |v_j| of this lane's final column
 #pragma unroll 1
     for (int k = 0; k < D; ++k) {
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         store_column2<D>(qim + j * QC, hi);
         __syncwarp();
     }
+    }   // PASSES > 0
 
     if constexpr (PASSES == 2) {
         // ---- 2b. re-orthogonalisation Q2 = Q1 (I - F), F = strict upper part of E (formed in
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
             wi[r][1] = make_float2(g4i.z, g4i.w);
         }
 #pragma unroll 4
-        for (int k = 0; k < D; ++k) {
+        for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {
             const float4 ur4 = *reinterpret_cast<const float4 *>(qre + k * QC + 4 * bi);
             const float4 ui4 = *reinterpret_cast<const float4 *>(qim + k * QC + 4 * bi);
             const float4 g4r = *reinterpret_cast<const float4 *>(gsr + k * D + 4 * bj);
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
             wi[i] = gi[i];
         }
     #pragma unroll
-        for (int k = 0; k < D; ++k) {
+        for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {
             float ur[D], ui[D];
             load_column<D>(qre + k * QC, ur);
             load_column<D>(qim + k * QC, ui);
@@ -712,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
     // j <= k), and the lanes j < k form the Gram entries of the re-orthogonalisation.
     float inv_own = 0.0f;
 #pragma unroll 1
-    for (int k = 0; k < D; ++k) {
+    for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {   // (PASSES = 0, the Hilbert-Schmidt prior: no QR)
         if (j == k) {
             store_column2<D>(qre + k * QC, hr);
             store_column2<D>(qim + k * QC, hi);
@@ -762,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
             }
         }
     }
-    {   // normalise the own column and publish it
+    if constexpr (PASSES > 0) {   // normalise the own column and publish it
         const float2 sc = make_float2(inv_own, inv_own);
 #pragma unroll
         for (int p = 0; p < D / 2; ++p) {
@@ -841,7 +844,7 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
 #pragma unroll
     for (int p = 0; p < D / 2; ++p) wr[p] = wi[p] = make_float2(0.f, 0.f);
 #pragma unroll 1
-    for (int k0 = 0; k0 < D; k0 += 4) {
+    for (int k0 = 0; k0 < (PASSES > 0 ? D : 0); k0 += 4) {
         float4 g4r = make_float4(0.f, 0.f, 0.f, 0.f), g4i = g4r;
         if (active) {
             g4r = *reinterpret_cast<const float4 *>(gsrc + j * D + k0);
@@ -1062,7 +1065,7 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
 
     // ---- 2a. modified Gram-Schmidt: q_k = v_k / |v_k| published by its pair, projected out ------
 #pragma unroll 1
-    for (int k = 0; k < D; ++k) {
+    for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {   // (PASSES = 0, the Hilbert-Schmidt prior: no QR)
         if (j == k) {
             float2 n2 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -1158,7 +1161,7 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
 #pragma unroll
     for (int p = 0; p < H2 / 2; ++p) wr[p] = wi[p] = make_float2(0.f, 0.f);
 #pragma unroll 1
-    for (int k0 = 0; k0 < D; k0 += 4) {
+    for (int k0 = 0; k0 < (PASSES > 0 ? D : 0); k0 += 4) {
         const float4 g4r = *reinterpret_cast<const float4 *>(gsrc + j * D + k0);
         const float4 g4i = *reinterpret_cast<const float4 *>(gsrc + d + j * D + k0);
         const float gkr[4] = {g4r.x, g4r.y, g4r.z, g4r.w}, gki[4] = {g4i.x, g4i.y, g4i.z, g4i.w};
@@ -1366,6 +1369,7 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
 template <int D>
 cudaError_t launch_propose_d(const ProblemView &p, int mode, uint32_t step, const StepState *step_dev, const float *x_eval,
                              int64_t rows, bool want_split, float *rho_norm_out, cudaStream_t s) {
+    if (p.qr_passes == 0) return launch_propose_pd<D, 0>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
     if (p.qr_passes == 1) return launch_propose_pd<D, 1>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
     return launch_propose_pd<D, 2>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
 }

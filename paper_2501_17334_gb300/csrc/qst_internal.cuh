@@ -142,7 +142,7 @@ struct ProblemView {
     double *trace_logl;          // [trace_steps][R]
     int trace_steps;
     int ngroups;                 // column groups of the projection (partial sums per group)
-    int qr_passes;               // 1 or 2 modified Gram-Schmidt passes
+    int qr_passes;               // 1 or 2 modified Gram-Schmidt passes; 0: no QR (Hilbert-Schmidt prior, W = G)
 };
 
 struct SamplerParams {

@@ -23,6 +23,8 @@ PREC_BF16X3 = 1
 PREC_TF32 = 2
 PREC_TF32X2 = 3
 PREC_PAULI = 4   # structured FP32 form, Pauli POVMs only
+PRIOR_BURES = 0  # Algorithm 1
+PRIOR_HS = 1     # Hilbert-Schmidt: rho = G G^dag / Tr
 KERNEL_PROPOSE, KERNEL_PROJECT, KERNEL_ACCEPT, KERNEL_DIAG = range(4)
 KERNEL_NAMES = {KERNEL_PROPOSE: "propose", KERNEL_PROJECT: "project", KERNEL_ACCEPT: "accept", KERNEL_DIAG: "diag"}
 
@@ -45,7 +47,7 @@ class SamplerCfg(ctypes.Structure):
                 ("thin", ctypes.c_int32), ("burn_in", ctypes.c_int32), ("diag_chains", ctypes.c_int32),
                 ("traj_capacity", ctypes.c_int32), ("acf_lmax", ctypes.c_int32), ("trace_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("qr_passes", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("autotune", ctypes.c_int32), ("prior", ctypes.c_int32)]
 
 
 class Diag(ctypes.Structure):
