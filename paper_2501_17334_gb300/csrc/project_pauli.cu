@@ -47,13 +47,16 @@ namespace {
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int row_stride(int n) { return n >= 8 ? n + 1 : n; }   // of an n x n block
+// floats per stored n x n block: the 4 x 4 blocks that one thread reads as four float4 rows sit
+// 20 floats apart, so the 8 threads of a quarter warp cover all 32 banks
+__host__ __device__ constexpr int block_floats(int n) { return n == 4 ? 20 : n * row_stride(n); }
 
 template <int Q>
 struct PauliShape {
     static constexpr int D = 1 << Q, d = D * D;
     // floats of level t: 6^t blocks of n x n, n = 2^(Q-t), rows padded to n + 1 from n = 8 on so
     // that the transposed reads of a split hit distinct banks
-    static constexpr int level(int t) { return ipow(6, t) * (1 << (Q - t)) * row_stride(1 << (Q - t)); }
+    static constexpr int level(int t) { return ipow(6, t) * block_floats(1 << (Q - t)); }
     static constexpr int max_level(int parity) {   // over the stored levels t <= Q - 2 of that parity
         int m = 0;
         for (int t = parity; t <= Q - 2; t += 2) m = cmax(m, level(t));
@@ -105,13 +108,13 @@ __device__ __forceinline__ void six(float s, float x, float y, float a, float c,
 template <int N>
 __device__ __forceinline__ void split_level(const float *in, float *out, int parents, int lt, int tpc) {
     constexpr int h = N / 2, tasks = h * (h + 1) / 2;
-    constexpr int PS = row_stride(N), CS = row_stride(h), hh = h * CS;   // row strides, child block size
+    constexpr int PS = row_stride(N), CS = row_stride(h), hh = block_floats(h);   // row strides, child block size
     for (int idx = lt; idx < parents * tasks; idx += tpc) {
         const int p = idx / tasks, r = idx - p * tasks;
         const int i = r / (h + 1), j = r - i * (h + 1);
         const int u = (j < h - i) ? i : h - 1 - i;
         const int v = (j < h - i) ? i + j : h - 1 - i + (j - (h - i));
-        const float *M = in + p * N * PS;
+        const float *M = in + p * block_floats(N);
         float *O = out + 6 * p * hh;
         const float tl_uv = M[u * PS + v], br_uv = M[(h + u) * PS + h + v];
         const float tr_uv = M[u * PS + h + v], bl_uv = M[(h + u) * PS + v];
@@ -140,13 +143,20 @@ template <bool P_OUT>
 __device__ __forceinline__ void last_split(float e00, float e01, float e10, float e11, const PauliArgs &a, int j0,
                                            int stride, int blk, float2 &dev, int &xmin, float (&sh)[3],
                                            float (&sl)[3], float *p_row, int o0, float inv_t) {
+    float4 wq[3];   // the three pairs' weights, requested before the arithmetic that needs them
+    float2 wc[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        wq[j] = a.wq[(j0 + j) * stride + blk];
+        wc[j] = a.wc[(j0 + j) * stride + blk];
+    }
     const float S = e00 + e11;
     const float2 q2[3] = {fma2(splat2(e01), make_float2(2.0f, -2.0f), splat2(S)),
                           fma2(splat2(e10), make_float2(2.0f, -2.0f), splat2(S)), make_float2(e00, e11)};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float4 w = a.wq[(j0 + j) * stride + blk];
-        const float2 cnt = a.wc[(j0 + j) * stride + blk];
+        const float4 w = wq[j];
+        const float2 cnt = wc[j];
         const float2 x = fma2(q2[j], make_float2(w.x, w.y), make_float2(w.z, w.w));
         xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
         dev = fma2(cnt, log_poly2(x), dev);
@@ -252,7 +262,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
 #pragma unroll 1
         for (int ib = 0; ib < NB / TPC; ++ib) {
             const int blk = lt + ib * TPC;
-            const float *Mb = ((Q - 2) & 1 ? bufB : bufA) + 16 * blk;
+            const float *Mb = ((Q - 2) & 1 ? bufB : bufA) + block_floats(4) * blk;
             float M[16];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
