@@ -43,8 +43,8 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "44591e26432ac5fc54cb5ee01019972cc46124e7d2f7647d3b3608e077413b72",
-                "chains": 32768, "bytes": 134.877440e6 + 162.219520e6},
+                "sha256": "0cf7b2a2199018151cdc430c9d9c5ff8b8d1bb9d400e0e46ed55595eaf97a141",
+                "chains": 32768, "bytes": 134.850304e6 + 162.057472e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
                 "sha256": "bb4a32a10fe520cdc1c9caa95f8de77b913b4d73f1f31d3887f71ab37c249eeb",
