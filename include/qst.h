@@ -162,7 +162,8 @@ qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_prob
                               const qst_sampler_cfg *cfg, size_t *bytes);
 
 /* Validates the problems (Sec. III Step 1: counts >= 0; each Lambda_kl Hermitian and
- * sum_l Lambda_kl = I to 1e-12; Q in 1..5; R >= 1; T >= 1; 0 < beta0 <= beta_max <= 1 for the
+ * sum_l Lambda_kl = I to 1e-12; Q in 1..5, or 6 for QST_PREC_PAULI with NULL POVM arrays; R >= 1;
+ * T >= 1; 0 < beta0 <= beta_max <= 1 for the
  * config's and every problem's own beta0 (0 meaning the config's);
  * for the tensor-core precisions every packed projector entry exactly representable in
  * bf16 (QST_PREC_BF16X3) or TF32 (QST_PREC_TF32, QST_PREC_TF32X2), and Q within the
@@ -256,7 +257,7 @@ int64_t qst_launch_count(const qst_handle *h);
 qst_status qst_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uint32_t chain0, int64_t nchains,
                              uint32_t block0, int32_t nblocks, uint32_t *out, void *cuda_stream);
 
-/* The built-in Pauli POVMs of Q qubits (1..5), written to host arrays povm_re, povm_im of
+/* The built-in Pauli POVMs of Q qubits (1..5; at 6 the arrays would take 3 GB), written to host arrays povm_re, povm_im of
  * [3^Q 2^Q][2^Q][2^Q] doubles (caller-owned): setting k = sum_q s_q 3^(Q-1-q) with s = 0, 1, 2
  * for X, Y, Z; outcome l = sum_q b_q 2^(Q-1-q) with b = 0 for the +1 eigenvalue; qubit 0 is the
  * most significant Kronecker factor (Sec. IV: all 3^Q Pauli settings).  Host-only.
