@@ -183,6 +183,7 @@ struct ProposeArgs {
     const StepState *step_dev;   // MODE_STEP: when not null the step is read from here
     int mode;
     int d_pad;
+    Philox::RoundKeys rk;        // the generator's round keys for `seed`
 };
 
 template <int D, int PASSES>
@@ -221,7 +222,6 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     const int64_t cc = active ? c : 0;
     const uint32_t chain_id = (uint32_t)(a.chain_offset + cc);
     const uint32_t tag = (a.mode == MODE_INIT) ? TAG_INIT : TAG_PROPOSAL;
-    const uint32_t key_lo = (uint32_t)(a.seed & 0xffffffffu), key_hi = (uint32_t)(a.seed >> 32);
     const float *ysrc = a.y + ((int64_t)cur * a.R + cc) * nx;
     float *ydst = a.y + ((int64_t)(1 - cur) * a.R + cc) * nx;
     // where G's column j is read back in step 3: this lane's own y' writes, or the input row
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
             for (int q = 0; q < D / 4; ++q) {
                 float4 yn = y0[q];
                 if (a.mode != MODE_EVAL) {
-                    const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), key_lo, key_hi);
+                    const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), a.rk);
                     float z0, z1, z2, z3;
                     gaussian_pair_fast(w.x, w.y, z0, z1);
                     gaussian_pair_fast(w.z, w.w, z2, z3);
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                     y1v = a.x_eval[cc * nx + e + 1];
                 }
             } else {
-                const uint4 w = Philox::block(make_uint4((uint32_t)part, step, chain_id, tag), key_lo, key_hi);
+                const uint4 w = Philox::block(make_uint4((uint32_t)part, step, chain_id, tag), a.rk);
                 float z0, z1;
                 gaussian_pair_fast(j == 0 ? w.x : w.z, j == 0 ? w.y : w.w, z0, z1);
                 float o0 = 0.0f, o1 = 0.0f;
@@ -674,7 +674,6 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
     const int64_t cc = active ? c : 0;
     const uint32_t chain_id = (uint32_t)(a.chain_offset + cc);
     const uint32_t tag = (a.mode == MODE_INIT) ? TAG_INIT : TAG_PROPOSAL;
-    const uint32_t key_lo = (uint32_t)(a.seed & 0xffffffffu), key_hi = (uint32_t)(a.seed >> 32);
     const float *ysrc = a.y + ((int64_t)cur * a.R + cc) * nx;
     float *ydst = a.y + ((int64_t)(1 - cur) * a.R + cc) * nx;
     const float *gsrc = (a.mode == MODE_EVAL) ? a.x_eval + cc * nx : ydst;
@@ -689,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
             if (active && a.mode == MODE_EVAL) y0 = *reinterpret_cast<const float4 *>(a.x_eval + cc * nx + e0 + 4 * q);
             float4 yn = y0;
             if (a.mode != MODE_EVAL) {
-                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), key_lo, key_hi);
+                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), a.rk);
                 float z0, z1, z2, z3;
                 gaussian_pair_fast(w.x, w.y, z0, z1);
                 gaussian_pair_fast(w.z, w.w, z2, z3);
@@ -1027,7 +1026,6 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
     }
     const uint32_t chain_id = (uint32_t)(a.chain_offset + c);
     const uint32_t tag = (a.mode == MODE_INIT) ? TAG_INIT : TAG_PROPOSAL;
-    const uint32_t key_lo = (uint32_t)(a.seed & 0xffffffffu), key_hi = (uint32_t)(a.seed >> 32);
     const float *ysrc = a.y + ((int64_t)cur * a.R + c) * nx;
     float *ydst = a.y + ((int64_t)(1 - cur) * a.R + c) * nx;
     const float *gsrc = (a.mode == MODE_EVAL) ? a.x_eval + c * nx : ydst;
@@ -1042,7 +1040,7 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
             if (a.mode == MODE_EVAL) y0 = *reinterpret_cast<const float4 *>(a.x_eval + c * nx + e0 + 4 * q);
             float4 yn = y0;
             if (a.mode != MODE_EVAL) {
-                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), key_lo, key_hi);
+                const uint4 w = Philox::block(make_uint4((uint32_t)(e0 / 4 + q), step, chain_id, tag), a.rk);
                 float z0, z1, z2, z3;
                 gaussian_pair_fast(w.x, w.y, z0, z1);
                 gaussian_pair_fast(w.z, w.w, z2, z3);
@@ -1336,6 +1334,7 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.R = p.R;
     a.chain_offset = p.chain_offset;
     a.seed = p.seed;
+    a.rk = Philox::round_keys(p.seed);
     a.step = step;
     a.step_dev = step_dev;
     a.mode = mode;

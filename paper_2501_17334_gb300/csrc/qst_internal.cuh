@@ -48,6 +48,34 @@ struct Philox {
         return ctr;
     }
 
+    // The same block with the ten round keys (key + r (kWeylA, kWeylB)) given: a kernel that
+    // takes them as launch parameters reads them as constant operands instead of forming them.
+    struct RoundKeys {
+        uint32_t k[20];   // (lo, hi) of rounds 0..9
+    };
+    __host__ __device__ static RoundKeys round_keys(uint64_t seed) {
+        RoundKeys rk;
+        uint32_t lo = (uint32_t)(seed & 0xffffffffu), hi = (uint32_t)(seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            rk.k[2 * r] = lo;
+            rk.k[2 * r + 1] = hi;
+            lo += kWeylA;
+            hi += kWeylB;
+        }
+        return rk;
+    }
+    __device__ __forceinline__ static uint4 block(uint4 ctr, const RoundKeys &rk) {
+#pragma unroll
+        for (int round = 0; round < 10; ++round) {
+            const uint32_t pa_hi = __umulhi(kMulA, ctr.x);
+            const uint32_t pa_lo = kMulA * ctr.x;
+            const uint32_t pb_hi = __umulhi(kMulB, ctr.z);
+            const uint32_t pb_lo = kMulB * ctr.z;
+            ctr = make_uint4(pb_hi ^ ctr.y ^ rk.k[2 * round], pb_lo, pa_hi ^ ctr.w ^ rk.k[2 * round + 1], pa_lo);
+        }
+        return ctr;
+    }
+
     // Open-interval uniform from the top 23 bits: (2 m + 1) 2^-24, exact in float.
     __device__ __forceinline__ static float uniform(uint32_t word) {
         return __fmaf_rn((float)(word >> 9), 0x1p-23f, 0x1p-24f);
