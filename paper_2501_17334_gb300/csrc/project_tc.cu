@@ -570,11 +570,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int g = unit_group(u);
             const int64_t grow = unit_mtile(u) * TC_M + quad * 32 + lane;
             const bool valid = grow < a.rows;
+            // t = t_hi + t_lo exactly (an FP64 sum of FP32 values, a few ulps from 1); 1 / t in FP32
+            // (it scales rel, itself a few ulps, and p), so the unit's FP64 work is these two
+            // conversions and the final sum: on this part an FP64 instruction is scarce
             const double t = valid ? a.trace[grow] : 1.0;
-            const float inv_t = (float)(1.0 / t);
             const float t_hi = (float)t;
             const float t_lo = (float)(t - (double)t_hi);
-            double total = 0.0;
+            const float inv_t = 1.0f / t_hi;
+            float tot_hi = 0.0f, tot_lo = 0.0f;   // the unit's tile sums as an FP32 pair (two-sum)
+            bool neg_inf = false;
             for (int i = 0; i < te - tb; ++i, ++tcount) {
                 const int tt = tile_at(u, tb, te, i);
                 const uint4 piece_w = (has_next && i < NP) ? alo_fetch(u + gridDim.x, i) : make_uint4(0u, 0u, 0u, 0u);
@@ -652,7 +656,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
                     }
                 }
-                total += (double)tile_sum;
+                if (tile_sum == -INFINITY) {
+                    neg_inf = true;
+                } else {
+                    const float sum = tot_hi + tile_sum, bp = sum - tot_hi;
+                    tot_lo += (tot_hi - (sum - bp)) + (tile_sum - bp);
+                    tot_hi = sum;
+                }
                 if (has_next) {
                     if (i < NP) alo_store(nb_buf, i, piece_w);
                     if (i == te - tb - 1) {   // last tile of the unit: whatever is left, then publish
@@ -663,7 +673,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             if (ok && valid) {
-                a.out[(int64_t)(g * 4 + sub) * a.rows + grow] = total;
+                a.out[(int64_t)(g * 4 + sub) * a.rows + grow] = neg_inf ? -INFINITY : (double)tot_hi + (double)tot_lo;
                 if (u < a.full_units)   // a whole chain tile: its other groups' partials are zero
                     for (int g2 = 1; g2 < a.ngroups; ++g2) a.out[(int64_t)(g2 * 4 + sub) * a.rows + grow] = 0.0;
             }
@@ -821,9 +831,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int64_t grow = (u / a.ntiles) * TC_M + quad * 32 + lane;
             const bool valid = grow < a.rows;
             const double tr = valid ? a.trace[grow] : 1.0;
-            const float inv_t = (float)(1.0 / tr);
             const float t_hi = (float)tr;
             const float t_lo = (float)(tr - (double)t_hi);
+            const float inv_t = 1.0f / t_hi;
             const uint32_t use = (uint32_t)tcount & 1u;
             if (!mbar_wait_warp(smem_u32(&bar_acc_full), use, &abort_flag, a.status)) {
                 ok = false;
