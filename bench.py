@@ -43,12 +43,12 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "0cf7b2a2199018151cdc430c9d9c5ff8b8d1bb9d400e0e46ed55595eaf97a141",
-                "chains": 32768, "bytes": 134.850304e6 + 162.057472e6},
+                "sha256": "75962df8497970c7be7848220496d84eb5c19233da551da049c648e6fa667e88",
+                "chains": 32768, "bytes": 134.872832e6 + 162.136832e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "bb4a32a10fe520cdc1c9caa95f8de77b913b4d73f1f31d3887f71ab37c249eeb",
-                "chains": 32768, "bytes": 51.399680e6 + 3.328000e6},
+                "sha256": "0f046db29f097b38ad8e2df865cad9b5f22ad35179d1616de5154f68f2e5df19",
+                "chains": 32768, "bytes": 51.399680e6 + 3.840000e6},
 }
 
 def _sha256(path):
