@@ -413,3 +413,30 @@ def test_builtin_pauli_povms_give_the_same_chains(qst, cuda_ok):
         s.close()
     assert np.array_equal(out[0]["y"], out[1]["y"])
     assert np.array_equal(out[0]["logl"], out[1]["logl"])
+
+
+def test_config5_full_batch_sampled_chains(qst, oracle_mod, cuda_ok):
+    """Configuration 5 as the benchmark runs it (64 problems of 1-5 qubits, 552,149 chains, one
+    handle, graph replay, autotuned, mixed form): chains sampled from four problems, including
+    the largest five-qubit one, re-run alone by the oracle give the same accept decisions
+    (chains are independent and keyed by their problem's seed and global id)."""
+    batch = W.heterogeneous_batch(64)
+    S = 12
+    s = qst.Sampler(batch, precision=qst.PREC_BF16X3, trace_steps=S, diag_chains=0)
+    s.run_chains(S)
+    five = [i for i, p in enumerate(batch) if p.num_qubits == 5]
+    picks = [0, 1, five[0], max(five, key=lambda i: batch[i].num_chains)]
+    rng = np.random.default_rng(5)
+    checked = agree = 0
+    for i in picks:
+        p = batch[i]
+        acc, _ = s.get_trace(i)
+        for c in [0, p.num_chains - 1] + list(rng.choice(p.num_chains, 2, replace=False)):
+            ref = oracle_mod.run(p, num_chains=1, chain_begin=int(c), num_steps=S, trace_steps=S)
+            checked += 1
+            agree += int(np.array_equal(acc[:, c], ref["trace_accept"][0]))
+        rho, n = s.posterior_mean(i)
+        assert n == p.num_chains * S
+        assert abs(np.trace(rho).real - 1) < 1e-6
+    s.close()
+    assert agree >= checked - 1, f"{agree} of {checked} sampled chains agree"
