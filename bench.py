@@ -349,19 +349,22 @@ def run_reference(args):
 
 
 def run_profile_case(args):
-    """A short run of the headline form for ncu captures (no timing)."""
+    """A short run of the headline form (or, with --qubits 6, the six-qubit problem) for ncu
+    captures (no timing)."""
     import torch
     from paper_2501_17334_gb300 import qst, workload as W
     qst.load()
     prec = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "pauli": qst.PREC_PAULI}[args.form]
     # the fixed column-group rule (no autotuner timing pass): a profiler distorts the timings
     # the autotuner compares, and with it the captured kernel's schedule
-    s = qst.Sampler(W.config_problem(CONFIG_INDEX, num_chains=args.chains), precision=prec, diag_chains=0,
-                    autotune=0)
+    prob = W.six_qubit_problem(num_chains=args.chains) if args.qubits == 6 else \
+        W.config_problem(CONFIG_INDEX, num_chains=args.chains)
+    s = qst.Sampler(prob, precision=prec, diag_chains=0, autotune=0)
     s.run_chains(args.steps)
     s.synchronize()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": True, "chains": args.chains, "steps": args.steps, "form": args.form}))
+    print(json.dumps({"profile_case": True, "chains": args.chains, "steps": args.steps, "form": args.form,
+                      "qubits": prob.num_qubits}))
 
 
 def main():
@@ -373,6 +376,8 @@ def main():
     ap.add_argument("--chains", type=int, default=CHAINS)
     ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp32", "pauli"])
     ap.add_argument("--profile-case", action="store_true")
+    ap.add_argument("--qubits", type=int, default=4, choices=[4, 6], help="profile case: the 4-qubit "
+                    "workload or the six-qubit problem (structured Pauli form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-pauli", action="store_true", help="skip the structured Pauli form")
