@@ -988,7 +988,10 @@ struct Wide64 {
     static constexpr int D = 64;
     static constexpr int d = D * D;
     static constexpr int threads = 128;
-    static constexpr int qcol = D + 4;                  // floats per column of a Q plane (per row of W)
+    // floats per column of a Q plane (per row of W): entry i sits at i + 4 (i / 32), so the two
+    // halves a thread pair works on fall in different 16-byte bank groups and the eight float4
+    // accesses of a quarter warp in distinct ones (72 = 18 groups of 4 floats per column)
+    static constexpr int qcol = D + 8;
     static constexpr int pk_stride = D + 1;
     static constexpr int area_a = 2 * D * qcol;         // Q planes, then W as two planes of row stride qcol
     static constexpr int area_b = 2 * D * D;            // F planes (column-major), then the staged rho
@@ -1008,6 +1011,8 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
     float *rowv = smem + S::area_a + S::area_b;          // [D] per-row values (diagonal of W W^dag)
     const int t = threadIdx.x;
     const int j = t >> 1, hh = t & 1, r0 = H2 * hh;      // column (or row) j, half hh
+    const int r0s = r0 + 4 * hh;                         // where half hh starts within a column (row)
+    const int js = j + 4 * (j >> 5);                     // where entry j sits within a column (row)
     const unsigned pair_mask = 3u << ((t & 31) & ~1);
     const int64_t c = blockIdx.x;                        // one chain per CTA; the grid is exactly rows
     const uint32_t step = (a.step_dev && a.mode == MODE_STEP) ? a.step_dev->step : a.step;
@@ -1076,12 +1081,12 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
                 hr[p] = __fmul2_rn(hr[p], rs);
                 hi[p] = __fmul2_rn(hi[p], rs);
             }
-            store_column2<H2>(qre + k * QC + r0, hr);
-            store_column2<H2>(qim + k * QC + r0, hi);
+            store_column2<H2>(qre + k * QC + r0s, hr);
+            store_column2<H2>(qim + k * QC + r0s, hi);
         }
         __syncthreads();
         // r = q_k^dag h over this half, then both halves
-        const float *vre = qre + k * QC + r0, *vim = qim + k * QC + r0;
+        const float *vre = qre + k * QC + r0s, *vim = qim + k * QC + r0s;
         float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
 #pragma unroll
         for (int p = 0; p < H2 / 2; p += 2) {
@@ -1136,18 +1141,18 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
             const int m = 2 * mm + hh;
             float2 acc = make_float2(0.f, 0.f), acc2 = acc;   // sum_p Q1[a][p] F[p][m] as (re, im) pairs
             for (int p = 0; p <= m; ++p) {
-                const float xr = qre[p * QC + j], xi = qim[p * QC + j];
+                const float xr = qre[p * QC + js], xi = qim[p * QC + js];
                 const float fr = fre[m * D + p], fi = fim[m * D + p];
                 acc = __ffma2_rn(make_float2(xr, xr), make_float2(fr, fi), acc);     // (xr fr, xr fi)
                 acc2 = __ffma2_rn(make_float2(xi, xi), make_float2(fi, fr), acc2);   // (xi fi, xi fr)
             }
-            q2[mm] = make_float2(qre[m * QC + j] - (acc.x - acc2.x), qim[m * QC + j] - (acc.y + acc2.y));
+            q2[mm] = make_float2(qre[m * QC + js] - (acc.x - acc2.x), qim[m * QC + js] - (acc.y + acc2.y));
         }
         __syncthreads();
 #pragma unroll
         for (int mm = 0; mm < H2; ++mm) {
-            qre[(2 * mm + hh) * QC + j] = q2[mm].x;
-            qim[(2 * mm + hh) * QC + j] = q2[mm].y;
+            qre[(2 * mm + hh) * QC + js] = q2[mm].x;
+            qim[(2 * mm + hh) * QC + js] = q2[mm].y;
         }
         __syncthreads();
     } else {
@@ -1165,7 +1170,7 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
         const float gkr[4] = {g4r.x, g4r.y, g4r.z, g4r.w}, gki[4] = {g4i.x, g4i.y, g4i.z, g4i.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float *ure = qre + (k0 + u) * QC + r0, *uim = qim + (k0 + u) * QC + r0;
+            const float *ure = qre + (k0 + u) * QC + r0s, *uim = qim + (k0 + u) * QC + r0s;
             const float2 pgr = make_float2(gkr[u], gkr[u]), pgi = make_float2(gki[u], gki[u]);
             const float2 mgi = make_float2(-gki[u], -gki[u]);
 #pragma unroll
@@ -1193,10 +1198,10 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
     __syncthreads();   // U is read by every thread before W replaces it
 #pragma unroll
     for (int p = 0; p < H2 / 2; ++p) {   // W row-major, real and imaginary planes
-        wre[(r0 + 2 * p) * QC + j] = wr[p].x;
-        wre[(r0 + 2 * p + 1) * QC + j] = wr[p].y;
-        wim[(r0 + 2 * p) * QC + j] = wi[p].x;
-        wim[(r0 + 2 * p + 1) * QC + j] = wi[p].y;
+        wre[(r0 + 2 * p) * QC + js] = wr[p].x;
+        wre[(r0 + 2 * p + 1) * QC + js] = wr[p].y;
+        wim[(r0 + 2 * p) * QC + js] = wi[p].x;
+        wim[(r0 + 2 * p + 1) * QC + js] = wi[p].y;
     }
     __syncthreads();
 
@@ -1205,8 +1210,8 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
     float2 war[H2 / 2], wai[H2 / 2];
 #pragma unroll
     for (int p = 0; p < H2 / 2; p += 2) {
-        const float4 r4 = *reinterpret_cast<const float4 *>(wre + arow * QC + r0 + 2 * p);
-        const float4 i4 = *reinterpret_cast<const float4 *>(wim + arow * QC + r0 + 2 * p);
+        const float4 r4 = *reinterpret_cast<const float4 *>(wre + arow * QC + r0s + 2 * p);
+        const float4 i4 = *reinterpret_cast<const float4 *>(wim + arow * QC + r0s + 2 * p);
         war[p] = make_float2(r4.x, r4.y);
         war[p + 1] = make_float2(r4.z, r4.w);
         wai[p] = make_float2(i4.x, i4.y);
@@ -1234,8 +1239,8 @@ __global__ void __launch_bounds__(Wide64::threads, 3) propose_kernel_d64(Propose
         float2 re = make_float2(0.f, 0.f), ima = re, imb = re;
 #pragma unroll
         for (int p = 0; p < H2 / 2; p += 2) {
-            const float4 r4 = *reinterpret_cast<const float4 *>(wre + b * QC + r0 + 2 * p);
-            const float4 i4 = *reinterpret_cast<const float4 *>(wim + b * QC + r0 + 2 * p);
+            const float4 r4 = *reinterpret_cast<const float4 *>(wre + b * QC + r0s + 2 * p);
+            const float4 i4 = *reinterpret_cast<const float4 *>(wim + b * QC + r0s + 2 * p);
             const float2 br0 = make_float2(r4.x, r4.y), br1 = make_float2(r4.z, r4.w);
             const float2 bi0 = make_float2(i4.x, i4.y), bi1 = make_float2(i4.z, i4.w);
             re = __ffma2_rn(wai[p], bi0, __ffma2_rn(war[p], br0, re));
