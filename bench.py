@@ -43,8 +43,8 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "75962df8497970c7be7848220496d84eb5c19233da551da049c648e6fa667e88",
-                "chains": 32768, "bytes": 134.872832e6 + 162.136832e6},
+                "sha256": "788fb450d44d69a82b7b449dc9222407116b644f164f8f337849f60c51ec0273",
+                "chains": 32768, "bytes": 134.882304e6 + 162.290432e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
                 "sha256": "0f046db29f097b38ad8e2df865cad9b5f22ad35179d1616de5154f68f2e5df19",
