@@ -20,10 +20,12 @@
 //
 // Work split: a chain's levels t = 0 .. Q-2 (6^t blocks of 2^(Q-t) x 2^(Q-t) packed floats, block
 // index o = sum over split qubits of (2 s + b) 6^(...), the first split most significant) live
-// in two shared-memory buffers (even levels in one, odd in the other).  A split task takes an
-// entry pair (u, v), (v, u) of one parent (8 loads, 12 stores) or a diagonal entry.  The last
-// two splits run in registers: one thread per 4 x 4 block of level Q-2 forms its 36 outputs
-// (tree indices 36 p .. 36 p + 35) and their deviance terms, so a chain has 6^(Q-2) threads.
+// in two shared-memory buffers (even levels in one, odd in the other; rows padded to n + 1 from
+// n = 8 on, 4 x 4 blocks 20 floats apart).  A split task takes an entry pair (u, v), (v, u) of
+// one parent (8 loads, 12 stores) or a diagonal entry.  The last two splits run in registers: a
+// thread takes a 4 x 4 block of level Q-2 and forms its 36 outputs (tree indices 36 p .. 36 p +
+// 35) and their deviance terms; a chain has one thread per block up to five qubits and 648
+// threads with two blocks each at six.
 // The deviance terms run on packed FP32 pairs (the outputs X+-, Y+-, Z+- of one split), with
 // weights per pair: x = q w + a (w = P_k / count, halved for the X and Y pairs whose factor 1/2
 // is left out of q, and w = 0, a = 1 for an outcome without counts, whose term is then 0); they
