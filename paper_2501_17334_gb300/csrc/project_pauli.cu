@@ -73,8 +73,11 @@ struct PauliShape {
     // the setting sums (NS x NB (hi, lo) pairs per chain) take the odd-level buffer when the last
     // stored level is even (Q = 4, 6): it is dead by then
     static constexpr bool alias_spart = Q >= 4 && (Q % 2 == 0);
+    // (hi, lo) pairs per setting slot of the sums: NB + 1, so that the 9 slots a warp's
+    // consecutive settings read fall in different banks
+    static constexpr int slot_stride = NB + 1;
     static constexpr int bufA = Q == 1 ? 4 : max_level(0);   // even levels (0: the packed rho)
-    static constexpr int bufB = cmax(Q >= 3 ? max_level(1) : 0, alias_spart ? 2 * NS * NB : 0);   // odd levels
+    static constexpr int bufB = cmax(Q >= 3 ? max_level(1) : 0, alias_spart ? 2 * NS * slot_stride : 0);   // odd levels
     static constexpr int floats = (bufA + bufB + 3) / 4 * 4; // per chain
     static_assert(bufA % 4 == 0, "the odd levels' 4 x 4 blocks are read as float4 rows");
     static_assert(NB % TPC == 0, "whole blocks per thread");
@@ -185,14 +188,14 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
     extern __shared__ __align__(16) float smem[];
     __shared__ float part[S::threads];
     __shared__ float4 tinfo[CPB];                                   // (t_hi, t_lo, 1 / t_hi) per chain
-    __shared__ float2 spart_s[(Q >= 3 && !S::alias_spart) ? CPB * NS * NB : 1];   // setting sums (hi, lo) per block
+    __shared__ float2 spart_s[(Q >= 3 && !S::alias_spart) ? CPB * NS * S::slot_stride : 1];   // setting sums per block
     const int g = threadIdx.x / TPC, lt = threadIdx.x - g * TPC;
     const int64_t c = (int64_t)blockIdx.x * CPB + g;
     const bool active = c < a.rows;
     float *bufA = smem + g * S::floats;
     float *bufB = bufA + S::bufA;
-    // setting sums of chain g's blocks: [NS][NB] (hi, lo)
-    float2 *spart = S::alias_spart ? reinterpret_cast<float2 *>(bufB) : spart_s + g * NS * NB;
+    // setting sums of chain g's blocks: [NS][NB + 1] (hi, lo)
+    float2 *spart = S::alias_spart ? reinterpret_cast<float2 *>(bufB) : spart_s + g * NS * S::slot_stride;
 
     // t = t_hi + t_lo exactly (t is an FP64 sum of FP32 values, a few ulps from 1); the CTA's
     // chains in its first threads, so the few FP64 instructions fill their warps
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
                         if constexpr (Q == 2) {
                             extra += renorm(v.x, v.y, j < 2 ? 0.5f : 1.0f, 3 * (c1 >> 1) + j);
                         } else {
-                            spart[(3 * (c1 >> 1) + j) * NB + blk] = v;
+                            spart[(3 * (c1 >> 1) + j) * S::slot_stride + blk] = v;
                         }
                         sh[j] = sl[j] = 0.0f;
                     }
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
             int base = 0;                           // thread of the prefix with every b_q = 0
 #pragma unroll
             for (int q = 0; q < Q - 2; ++q) base += 2 * ((pre / ipow(3, Q - 3 - q)) % 3) * ipow(6, Q - 3 - q);
-            const float2 *sp = spart + slot * NB + base;
+            const float2 *sp = spart + slot * S::slot_stride + base;
             float vh = 0.0f, vl = 0.0f;
 #pragma unroll
             for (int b = 0; b < NPRE; ++b) {
