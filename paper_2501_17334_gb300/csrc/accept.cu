@@ -5,7 +5,7 @@
 namespace qst {
 namespace {
 
-constexpr int kChainsPerCta = 128;
+constexpr int kChainsPerCta = 128;   // the most chains one accept CTA takes (ProblemView::accept_cpc)
 constexpr int kThreads = 256;
 
 struct AcceptArgs {
@@ -18,7 +18,7 @@ struct AcceptArgs {
     const StepState *step_dev;   // when not null: step, kept and kept_idx come from here
 };
 
-// One CTA owns chains [128 b, 128 b + 128) and pool slot b.
+// One CTA owns chains [C b, C b + C) and pool slot b, C = p.accept_cpc <= 128.
 __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
     const ProblemView &p = a.p;
     if (a.step_dev) {   // (a is this thread's copy of the parameters)
@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
     __shared__ uint8_t flag[kChainsPerCta];
     __shared__ float inv_tr[kChainsPerCta];
     const int tid = threadIdx.x;
-    const int64_t c0 = (int64_t)blockIdx.x * kChainsPerCta;
-    const int nc = (int)min((int64_t)kChainsPerCta, p.R - c0);
+    const int64_t c0 = (int64_t)blockIdx.x * p.accept_cpc;
+    const int nc = (int)min((int64_t)p.accept_cpc, p.R - c0);
 
     // ---- phase 1: one thread per chain -------------------------------------------------
     if (tid < kChainsPerCta) {
@@ -297,12 +297,30 @@ cudaError_t launch_accept(const ProblemView &p, const SamplerParams &sp, int mod
     a.kept = kept ? 1 : 0;
     a.kept_idx = kept_idx;
     a.step_dev = step_dev;
-    const int64_t blocks = (p.R + kChainsPerCta - 1) / kChainsPerCta;
+    const int64_t blocks = (p.R + p.accept_cpc - 1) / p.accept_cpc;
     accept_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-int accept_slots(int64_t R) { return (int)((R + kChainsPerCta - 1) / kChainsPerCta); }
+// Up to 256 packed floats per chain (D <= 16) a CTA takes 128 chains, which moves its 256
+// threads' float4 lanes over several chains at once.  From D = 32 on, each chain alone fills
+// the CTA's lanes and a CTA walks its chains in turn, so 128 chains per CTA leave most SMs
+// idle (4096 six-qubit chains: 32 CTAs) and the copy latency-bound: halve the chains per CTA
+// until the grid covers the SMs twice, down to 8 (more pool slots, each read and written
+// once per kept step).
+int accept_chains_per_cta(int64_t R, int d) {
+    if (d < 4 * kThreads) return kChainsPerCta;
+    static int num_sms = 0;
+    if (num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms <= 0)
+            num_sms = 148;
+    }
+    int c = kChainsPerCta;
+    while (c > 8 && (R + c - 1) / c < 2 * (int64_t)num_sms) c /= 2;
+    return c;
+}
 
 cudaError_t launch_pool_reduce(const ProblemView &p, double *out, cudaStream_t s) {
     pool_reduce_kernel<<<(p.d + 31) / 32, 32 * kReduceWarps, 0, s>>>(p.pool, p.n_slots, p.d, out);

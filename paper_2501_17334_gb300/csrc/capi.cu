@@ -390,7 +390,8 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         hp.part_slots = v.ngroups;
         for (int g : hp.group_choices) hp.part_slots = std::max(hp.part_slots, g);
         v.qr_passes = cfg->prior == QST_PRIOR_HS ? 0 : cfg->qr_passes;   // 0: no QR, W = G
-        v.n_slots = accept_slots(v.R);
+        v.accept_cpc = accept_chains_per_cta(v.R, v.d);
+        v.n_slots = (int)((v.R + v.accept_cpc - 1) / v.accept_cpc);
         v.n_diag = (int)std::min<int64_t>(cfg->diag_chains, v.R);
         v.traj_cap = cfg->traj_capacity;
         if (v.traj_cap == 0) v.n_diag = 0;

@@ -163,6 +163,7 @@ struct ProblemView {
     int64_t *acc_total;          // [R]
     double *pool;                // [n_slots][d] FP64 pooled sums, one slot per accept CTA
     int n_slots;
+    int accept_cpc;              // chains per accept CTA (n_slots = ceil(R / accept_cpc))
     float *traj;                 // [n_diag][traj_cap][d] kept states of the diagnostic chains
     int n_diag;
     int traj_cap;
@@ -217,6 +218,7 @@ void pauli_tree_order(int Q, std::vector<int32_t> &perm);   // perm[o] = k D + l
 void pauli_weights(int Q, const std::vector<int32_t> &perm, const float *cnt, const float *invf,
                    std::vector<float4> &wq, std::vector<float2> &wc);
 void set_last_error(const char *msg);   // message returned by qst_last_error()
-int accept_slots(int64_t R);
+// chains per accept CTA for R chains of d packed floats each (a power of two, 8..128)
+int accept_chains_per_cta(int64_t R, int d);
 
 }  // namespace qst
