@@ -38,7 +38,7 @@ def _problem(Q, dense):
     return SimpleNamespace(dim=D, num_povms=3 ** Q, povm_re=re, povm_im=im)
 
 
-@pytest.mark.parametrize("q", [1, 2, 3])
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
 def test_builtin_pauli_projectors_match_the_dense_arrays(oracle_mod, q):
     rho = _random_rho(1 << q, np.random.default_rng(60 + q))
     p_dense = oracle_mod.probabilities(_problem(q, True), rho)
