@@ -1,8 +1,9 @@
-"""The pooled mean (Eq. BME2) summed over many accept CTAs at five and six qubits, where a CTA
-takes as few as 8 chains and so owns as few pool slots' worth of chains, with a ragged last
-CTA.  With a single kept step (thinning 1, burn-in S - 1) the pooled mean is the mean over
-the chains of their current rho, which the test forms independently of the pool: from the
-chains' own latent states, read back and passed through the evaluation entry point."""
+"""The pooled mean (Eq. BME2) summed over many accept CTAs, each with its own FP64 pool slot:
+at two and four qubits (128 chains per CTA) and at five and six qubits (as few as 8), each
+with a ragged last CTA.  With a single kept step (thinning 1, burn-in S - 1) the pooled
+mean is the mean over the chains of their current rho, which the test forms independently
+of the pool: from the chains' own latent states, read back and passed through the
+evaluation entry point."""
 import numpy as np
 import pytest
 
@@ -12,12 +13,16 @@ from tests._helpers import unpack_rho
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("q,R", [(5, 2001), (6, 300)])
+@pytest.mark.parametrize("q,R", [(2, 3001), (4, 1000), (5, 2001), (6, 300)])
 def test_pooled_mean_over_many_accept_ctas(qst, cuda_ok, q, R):
     import torch
     S = 4
-    make = W.five_qubit_problem if q == 5 else W.six_qubit_problem
-    prob = make(num_chains=R, num_steps=S)
+    if q <= 4:
+        prob = W.config_problem(q, num_chains=R, num_steps=S)   # configurations 2 and 4
+    else:
+        make = W.five_qubit_problem if q == 5 else W.six_qubit_problem
+        prob = make(num_chains=R, num_steps=S)
+    assert prob.dim == 1 << q
     s = qst.Sampler(prob, precision=qst.PREC_PAULI, diag_chains=0, thin=1, burn_in=S - 1)
     s.run_chains(S)
     mean, n = s.posterior_mean()
