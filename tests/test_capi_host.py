@@ -155,3 +155,32 @@ def test_null_povms_select_the_builtin_pauli_set(qst):
     wrong = SimpleNamespace(num_qubits=3, num_povms=26, counts=prob.counts[:26 * 8], povm_re=None,
                             povm_im=None, num_chains=64, seed=1, beta0=0.0)   # the built-in set has 3^Q
     assert _status(lambda: qst.workspace_size([wrong], cfg)) == 1
+
+
+class _HugeProblem:
+    """A problem whose POVM count would make K * D (and K * D^3) wrap a 32-bit int: the
+    arrays are tiny because validation must reject the size before reading them."""
+    num_qubits = 4
+    num_povms = 1 << 28
+    counts = np.zeros(16, np.int32)
+    povm_re = np.zeros((1, 16, 16))
+    povm_im = np.zeros((1, 16, 16))
+    num_chains = 8
+    seed = 1
+    beta0 = 0.02
+
+
+def test_huge_povm_count_is_rejected_before_any_product_wraps(qst):
+    lib = qst.load()
+    # qst_create's validation (through qst_workspace_size, which runs the same checks)
+    assert _status(lambda: qst.workspace_size([_HugeProblem()], qst.default_config())) == 1
+    # qst_pack_projectors
+    re = np.zeros((16, 16, 16))
+    out = np.zeros(16, np.float32)
+    assert lib.qst_pack_projectors(4, 1 << 28, re.ctypes.data, re.ctypes.data, out.ctypes.data) == 1
+    # qst_loglik_noalloc: rejected on the host, before any CUDA call (no GPU here)
+    counts = np.zeros(16, np.int32)
+    for k in (1 << 28, (1 << 31) // 16, 89, -1, 0):
+        st = lib.qst_loglik_noalloc(4, k, None, counts.ctypes.data, None, 1, None, None)
+        assert st == 1, (k, st)
+    assert lib.qst_loglik_noalloc(4, 81, None, counts.ctypes.data, None, 1, None, None) == 1   # NULL P
