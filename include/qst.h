@@ -105,8 +105,13 @@ typedef struct {
     int32_t acf_lmax;       /* l_max of Eq. ACFrho / Eq. IACT (Fig. 2: 200) */
     int32_t trace_steps;    /* record the accept flag and log L(y') of the first trace_steps steps */
     int32_t precision;      /* qst_precision */
-    int32_t qr_passes;      /* modified Gram-Schmidt passes computing U of Algorithm 1 (QR and phase fix): 1, or 2
-                               (default) re-orthogonalising once, which cuts U's FP32 error ~10x */
+    int32_t qr_passes;      /* how U of Algorithm 1 (QR and phase fix) is computed: 1, one FP32 modified
+                               Gram-Schmidt pass (U off by about cond(H) 2^-24); 2, that pass plus a
+                               first-order FP32 re-orthogonalisation (orthogonal to ~2^-24, still off
+                               by cond(H) 2^-24); 3 (default), the pass plus a first-order refinement
+                               to the exact QR factor from Q1^dag H and Q1^dag Q1 formed without
+                               rounding error (U within ~2^-24 of the exact factor).  Five and six
+                               qubits take 2 when 3 is asked for */
     int32_t use_graph;      /* 1 (default): qst_run_chains replays one step captured as a CUDA graph
                                (the step counter lives on the device); 0: plain launches. Kernel
                                timing (qst_set_profiling) always uses plain launches */
@@ -194,6 +199,14 @@ qst_status qst_run_chains(qst_handle *h, int64_t num_steps);
  * Synchronises the stream.  Errors: QST_ERR_STATE if nothing has been pooled yet. */
 qst_status qst_posterior_mean(qst_handle *h, int32_t problem, double *rho_re, double *rho_im,
                               int64_t *num_pooled);
+
+/* The sum behind that mean, unnormalised: the FP64 sum over every kept state of one problem of
+ * its packed vec_h(rho) (Eq. BME2's numerator), sum_packed host [D*D] doubles in the packed
+ * layout of the header comment (caller-owned), and the count N R.  Sums from runs over
+ * disjoint chain ranges add to the sum of one run over all of them (each state is summed in
+ * FP64 once), which is how replicas on several GPUs are merged.  Synchronises the stream.
+ * Errors as qst_posterior_mean. */
+qst_status qst_posterior_sum(qst_handle *h, int32_t problem, double *sum_packed, int64_t *num_pooled);
 
 /* Diagnostics of one problem (Sec. IV): acceptance, beta statistics, the chain-averaged
  * ACF c[0..l_max] of Eq. ACFrho into acf (host, l_max+1 doubles, may be NULL) and the
@@ -292,31 +305,33 @@ qst_status qst_probe_wait_timeout(qst_handle *h, int32_t wait_ms);
  * owns the device memory through its own allocator, or an asynchronous pipeline that
  * cannot afford cudaMalloc/cudaFree, which may synchronise the whole device.
  *
- * qst_loglik_noalloc computes log L(x) of Eq. likelihood for n latent vectors x exactly as
- * qst_evaluate does with QST_PREC_FP32 (Algorithm 1 with two Gram-Schmidt passes, the FP32
- * projector contraction, the deviance-form FP64 reduction), but needs no handle and no
- * workspace: its intermediates live in one device array of QST_NOALLOC_SCRATCH_BYTES
- * (about 5.8 MiB) defined in the library, which every GPU that loads the library holds
- * until the process exits.
+ * qst_loglik_noalloc returns, for n latent vectors x, the same log-likelihood that
+ * qst_evaluate returns with QST_PREC_FP32 and the default configuration (the same
+ * density-matrix assembly, FP32 projector contraction and FP64 reduction), but needs
+ * no handle and no workspace: its intermediates live in one device array of
+ * QST_NOALLOC_SCRATCH_BYTES (about 5.8 MiB) defined in the library, which every GPU that
+ * loads the library holds until the process exits.
  *   num_qubits  Q, 1..4
  *   num_povms   K, with K * 2^Q <= 1408 (all 81 Pauli settings of 4 qubits fit)
  *   P           device [D^2][K D] float: the packed projector matrix, as qst_pack_projectors
- *               produces it; caller-owned, read during the call
+ *               produces it; caller-owned, read by the enqueued work
  *   counts      host [K D] int32 outcome counts c_kl >= 0; read before the call returns
  *   x           device [n][4 D^2] float latent vectors (layout as in the header comment)
  *   n           0 <= n <= QST_NOALLOC_MAX_ROWS rows per call (larger batches: call again)
  *   logl        device [n] double, written
  *   cuda_stream cudaStream_t the work is enqueued on (NULL = default stream)
  * Returns QST_ERR_INVALID_ARG for a size beyond these limits, a NULL pointer or a negative
- * count, QST_ERR_CUDA for a CUDA failure (message in qst_last_error()).  It calls no
- * cudaMalloc, cudaFree or other allocating routine.  The first call on a device (with
- * that device current) looks up the scratch array's device address once; make that first
- * call before any stream capture.  All calls share the one scratch array, which keeps the
- * previous call's contents (each call rewrites what it reads): calls that can overlap on
+ * count, before anything is enqueued; QST_ERR_CUDA for a CUDA failure (message in
+ * qst_last_error()).  It calls no cudaMalloc, cudaFree or other allocating routine and does
+ * not wait for the device: the weights formed from the counts travel as kernel launch
+ * parameters, so no host buffer is read after the call returns.  The first call on a device
+ * (with that device current) looks up the scratch array's device address once; make that
+ * first call before any stream capture.  All calls share the one scratch array, which keeps
+ * the previous call's contents (each call rewrites what it reads): calls that can overlap on
  * the GPU -- on different streams without ordering between them -- race and must be
  * serialised by the caller. */
 #define QST_NOALLOC_MAX_ROWS 4096
-#define QST_NOALLOC_SCRATCH_BYTES 6040576
+#define QST_NOALLOC_SCRATCH_BYTES 6043392
 qst_status qst_loglik_noalloc(int32_t num_qubits, int32_t num_povms, const float *P, const int32_t *counts,
                               const float *x, int64_t n, double *logl, void *cuda_stream);
 

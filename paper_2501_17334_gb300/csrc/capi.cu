@@ -135,14 +135,17 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
     if (cfg->precision != QST_PREC_FP32 && cfg->precision != QST_PREC_BF16X3 && cfg->precision != QST_PREC_TF32 &&
         cfg->precision != QST_PREC_TF32X2 && cfg->precision != QST_PREC_PAULI)
         return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
-    if (cfg->qr_passes != 1 && cfg->qr_passes != 2)
-        return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1 or 2");
+    if (cfg->qr_passes < 1 || cfg->qr_passes > 3) return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1, 2 or 3");
     if (cfg->prior != QST_PRIOR_BURES && cfg->prior != QST_PRIOR_HS)
         return fail(QST_ERR_INVALID_ARG, "unknown prior %d", cfg->prior);
     if (cfg->use_graph != 0 && cfg->use_graph != 1) return fail(QST_ERR_INVALID_ARG, "use_graph must be 0 or 1");
     if (cfg->autotune != 0 && cfg->autotune != 1) return fail(QST_ERR_INVALID_ARG, "autotune must be 0 or 1");
     return QST_OK;
 }
+
+// Upper bound on the POVM elements K D of one problem (2^20; six-qubit Pauli tomography has
+// 46,656): keeps K D, K D D^2 and the padded sizes far from int and size_t limits.
+constexpr int kMaxPovmElements = 1 << 20;
 
 void pauli_povms(int Q, std::vector<double> &re, std::vector<double> &im);
 
@@ -155,7 +158,9 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
     if (d.num_qubits < 1 || d.num_qubits > max_qubits(cfg, builtin))
         return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..%d", idx, d.num_qubits,
                     max_qubits(cfg, builtin));
-    if (d.num_povms < 1) return fail(QST_ERR_INVALID_ARG, "problem %d: num_povms must be >= 1", idx);
+    // bounded before any product with D is formed (K D and K D D^2 must not wrap)
+    if (d.num_povms < 1 || d.num_povms > kMaxPovmElements >> d.num_qubits)
+        return fail(QST_ERR_INVALID_ARG, "problem %d: num_povms must be in 1..2^20 / 2^Q", idx);
     if (!d.counts || (!builtin && (!d.povm_re || !d.povm_im)))
         return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
     if (tc_kind_of(cfg->precision) != TC_NONE && !tc_supported(tc_kind_of(cfg->precision), 1 << d.num_qubits))
@@ -626,7 +631,7 @@ void qst_default_config(qst_sampler_cfg *cfg) {
     cfg->acf_lmax = 200;
     cfg->trace_steps = 0;
     cfg->precision = QST_PREC_FP32;
-    cfg->qr_passes = 2;
+    cfg->qr_passes = 3;
     cfg->use_graph = 1;
     cfg->autotune = 1;
 }
@@ -894,22 +899,43 @@ static qst_status get_problem(qst_handle *h, int32_t problem, HostProblem **hp) 
     return QST_OK;
 }
 
-qst_status qst_posterior_mean(qst_handle *h, int32_t problem, double *rho_re, double *rho_im, int64_t *num_pooled) {
+// The FP64 sum of the kept packed states of one problem (d doubles, host) and their count.
+static qst_status pooled_sum(qst_handle *h, int32_t problem, std::vector<double> &sum, int64_t &n, int &D) {
     HostProblem *hp;
     qst_status st = get_problem(h, problem, &hp);
     if (st != QST_OK) return st;
     const ProblemView &v = hp->v;
-    const int64_t n = h->kept * v.R;
-    if (num_pooled) *num_pooled = n;
+    n = h->kept * v.R;
+    D = v.D;
     if (n == 0) return fail(QST_ERR_STATE, "no state has been pooled yet");
     double *red = reinterpret_cast<double *>(h->ws + hp->off.red);
     st = launch(h, QST_KERNEL_DIAG, "pool reduce", [&] { return launch_pool_reduce(v, red, h->stream); });
     if (st != QST_OK) return st;
-    std::vector<double> sum(v.d);
+    sum.assign(v.d, 0.0);
     QST_CUDA(cudaMemcpyAsync(sum.data(), red, sizeof(double) * v.d, cudaMemcpyDeviceToHost, h->stream), "read pool");
-    st = check_status(h);
+    return check_status(h);
+}
+
+qst_status qst_posterior_sum(qst_handle *h, int32_t problem, double *sum_packed, int64_t *num_pooled) {
+    std::vector<double> sum;
+    int64_t n = 0;
+    int D = 0;
+    if (num_pooled) *num_pooled = 0;
+    qst_status st = pooled_sum(h, problem, sum, n, D);
+    if (num_pooled) *num_pooled = n;
     if (st != QST_OK) return st;
-    const int D = v.D;
+    if (sum_packed) std::memcpy(sum_packed, sum.data(), sizeof(double) * sum.size());
+    return QST_OK;
+}
+
+qst_status qst_posterior_mean(qst_handle *h, int32_t problem, double *rho_re, double *rho_im, int64_t *num_pooled) {
+    std::vector<double> sum;
+    int64_t n = 0;
+    int D = 0;
+    if (num_pooled) *num_pooled = 0;
+    qst_status st = pooled_sum(h, problem, sum, n, D);
+    if (num_pooled) *num_pooled = n;
+    if (st != QST_OK) return st;
     for (int i = 0; i < D; ++i)
         for (int j = i; j < D; ++j) {
             const double re = sum[i * D + j] / (double)n;
@@ -1177,7 +1203,8 @@ qst_status qst_philox_blocks(uint64_t seed, uint32_t step, uint32_t tag, uint32_
 
 qst_status qst_pack_projectors(int32_t num_qubits, int32_t num_povms, const double *povm_re, const double *povm_im,
                                float *P_out) {
-    if (num_qubits < 1 || num_qubits > 5 || num_povms < 1 || !povm_re || !povm_im || !P_out)
+    if (num_qubits < 1 || num_qubits > 5 || num_povms < 1 || num_povms > kMaxPovmElements >> num_qubits || !povm_re ||
+        !povm_im || !P_out)
         return fail(QST_ERR_INVALID_ARG, "bad arguments");
     const int D = 1 << num_qubits, KD = num_povms * D;
     std::vector<double> P((size_t)D * D * KD);

@@ -43,6 +43,35 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
 
+// Compensated (Kahan) accumulation on a packed pair: sum += c v, with the rounding error of
+// every add carried in comp (the sum is sum - comp).  The log-likelihood terms of one setting
+// are O(c) far from the posterior, so their plain FP32 sum would lose ~2^-24 of it per add.
+__device__ __forceinline__ void kahan_fma2(float2 &sum, float2 &comp, float2 c, float2 v) {
+    const float2 y = fma2(c, v, make_float2(-comp.x, -comp.y));
+    const float2 t = add2(sum, y);
+    comp = sub2(sub2(t, sum), y);
+    sum = t;
+}
+
+// s + e = a + b exactly (Knuth's two-sum; no assumption on the magnitudes)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Adds one measurement setting's log-likelihood term, (sum - comp) summed over both halves of
+// the pair minus `sub`, to the running pair (hi, lo): hi takes the large part exactly (two-sum),
+// lo the errors and the small terms.
+__device__ __forceinline__ void add_setting(float &hi, float &lo, float2 sum, float2 comp, float sub) {
+    float s, e;
+    two_sum(sum.x, sum.y, s, e);
+    float h, e2;
+    two_sum(hi, s, h, e2);
+    hi = h;
+    lo += (e2 + e) - ((comp.x + comp.y) + sub);
+}
+
 // qst_log_poly (log_poly.h) on two arguments at once, operation for operation, so each
 // result has the same bits as the scalar function; arguments must be positive normal finite
 // (the caller checks that separately).

@@ -4,12 +4,14 @@
 // p = A . P with A = packed vec_h(rho) rows [rows][d_pad] and P the packed projector
 // matrix [d_pad][KD_pad].  A CTA owns 128 chains and sweeps a group of 128-column
 // tiles; each thread keeps an 8 x 8 register tile.  The epilogue evaluates the
-// likelihood in deviance form,
-//     log L = C0 - N log t + sum_{c_kl > 0} c_kl log(q_kl * invf_kl),   invf_kl = P_k / c_kl,
-// (q = vec_h(rho) . P, t the exact trace of the stored rho, p = q / t), which equals
-// sum c log p exactly in real arithmetic (C0 = -sum c log invf) but keeps every FP32
-// term O(1); each thread sums its terms in FP32, the 16 threads sharing a chain
-// combine in FP64, and one FP64 partial per (column group, chain) is written.  The
+// likelihood in deviance form, every setting k renormalised by its own sum S_k = sum_l q_kl,
+//     log L = C0 - N log t + sum_k [ sum_{c_kl > 0} c_kl log(q_kl invf_kl) - P_k log(S_k / t) ],
+// invf_kl = P_k / c_kl (q = vec_h(rho) . P, t the exact trace of the stored rho), which equals
+// sum c log p exactly in real arithmetic (C0 = -sum c log invf; S_k = t for a complete POVM)
+// and cancels the rounding the FP32 sums of a setting share.  S_k is summed exactly as a
+// hi + lo pair over the four threads that hold the setting's 16 columns; each thread sums its
+// deviance terms with a compensated (Kahan) sum carried as a pair into the FP64 combine of the
+// 16 threads sharing a chain, and one FP64 partial per (column group, chain) is written.  The
 // constant and trace terms are added by the accept kernel.
 #include "qst_internal.cuh"
 
@@ -23,11 +25,13 @@ struct ProjectArgs {
     const float *P;      // [d_pad][KD_pad]
     const float *cnt;    // [KD_pad]
     const float *invf;   // [KD_pad]
+    const float *ptot;   // [KD_pad / D] shots P_k of each setting
     double *out;         // [ngroups][rows]
     float *p_out;        // [rows][KD] or null: p = q / t
     const double *trace; // [rows] t, the exact trace of the stored rho (used only for p_out)
     int64_t rows;
     int d_pad, KD, KD_pad;
+    int D;               // outcomes per setting (a setting's columns are consecutive)
     int tiles_per_group;
 };
 
@@ -43,9 +47,19 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
     const int t_begin = blockIdx.y * a.tiles_per_group;
     const int t_end = min(t_begin + a.tiles_per_group, n_tiles_total);
 
-    float rowsum[8];
+    // per row: the compensated deviance sum (sum - comp) and the small renormalisation terms
+    float rowsum[8], rowcomp[8], rowsmall[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) rowsum[i] = 0.0f;
+    for (int i = 0; i < 8; ++i) rowsum[i] = rowcomp[i] = rowsmall[i] = 0.0f;
+    float trace_hi[8], trace_lo[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+        const int64_t row = m0 + r;
+        const double t = (row < a.rows) ? a.trace[row] : 1.0;
+        trace_hi[i] = (float)t;
+        trace_lo[i] = (float)(t - (double)trace_hi[i]);
+    }
 
     const int k_steps = a.d_pad / BK;
     for (int nt = t_begin; nt < t_end; ++nt) {
@@ -113,19 +127,59 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
             __syncthreads();
         }
 
-        // epilogue: deviance terms of this tile
+        // epilogue: deviance terms of this tile, and the renormalisation of its settings.  The
+        // four columns jj = 4h .. 4h + 3 of this thread belong to one setting, whose other twelve
+        // columns are held by the threads tx ^ 1, tx ^ 2, tx ^ 3 (16 columns per setting, D = 16;
+        // for D < 16 a group of four columns holds whole settings, for D = 32 two groups of
+        // threads form one setting)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
             const int64_t row = m0 + r;
             const float inv_tr = (a.p_out && row < a.rows) ? (float)(1.0 / a.trace[row]) : 0.0f;
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const int col = (jj < 4) ? tx * 4 + jj : 64 + tx * 4 + (jj - 4);
-                const float pv = acc[i][jj];
-                const float cv = cnt_s[col];
-                if (cv > 0.0f) rowsum[i] += cv * deviance_log(pv * invf_s[col]);
-                if (a.p_out && row < a.rows && n0 + col < a.KD) a.p_out[row * a.KD + n0 + col] = pv * inv_tr;
+            for (int h = 0; h < 2; ++h) {
+                float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int jj = 4 * h + u;
+                    const int col = (jj < 4) ? tx * 4 + jj : 64 + tx * 4 + (jj - 4);
+                    const float pv = acc[i][jj];
+                    const float cv = cnt_s[col];
+                    if (cv > 0.0f) {   // Kahan: rowsum - rowcomp
+                        const float y = __fmaf_rn(cv, deviance_log(pv * invf_s[col]), -rowcomp[i]);
+                        const float tt = rowsum[i] + y;
+                        rowcomp[i] = (tt - rowsum[i]) - y;
+                        rowsum[i] = tt;
+                    }
+                    // S_k as an exact pair: every q in (-4, 4) split at 2^-20 (the hi parts add exactly)
+                    const float hq = (pv + 12.0f) - 12.0f;
+                    sh += hq;
+                    sl += pv - hq;
+                    if (a.p_out && row < a.rows && n0 + col < a.KD) a.p_out[row * a.KD + n0 + col] = pv * inv_tr;
+                }
+                // the setting's sum over the threads holding its columns (exact for the hi parts)
+                const int col0 = (h == 0) ? tx * 4 : 64 + tx * 4;
+                // threads per setting: D / 4 (1 .. 16, consecutive tx); at D = 2 a thread's four
+                // columns hold two settings and the renormalisation is left out (the plain
+                // deviance form alone is exact too)
+                const int per = a.D / 4;
+#pragma unroll
+                for (int off = 1; off < 16; off <<= 1) {
+                    if (off < per) {
+                        sh += __shfl_xor_sync(0xffffffffu, sh, off);
+                        sl += __shfl_xor_sync(0xffffffffu, sl, off);
+                    }
+                }
+                // one thread per setting adds -P_k log(S_k / t)
+                if (per >= 1 && (tx & (per - 1)) == 0 && n0 + col0 < a.KD) {
+                    const float pk = a.ptot[(n0 + col0) / a.D];
+                    const float rel = ((sh - trace_hi[i]) + (sl - trace_lo[i])) / trace_hi[i];
+                    const float l1p = fabsf(rel) < 0x1p-10f
+                                          ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
+                                          : log1pf(rel);
+                    rowsmall[i] -= pk * l1p;
+                }
             }
         }
         __syncthreads();   // cnt_s / invf_s reuse
@@ -134,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
     // combine the 16 threads (tx) that share each row, in FP64
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        double v = (double)rowsum[i];
+        double v = ((double)rowsum[i] - (double)rowcomp[i]) + (double)rowsmall[i];
 #pragma unroll
         for (int off = 8; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
@@ -163,6 +217,8 @@ cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t ro
     a.P = p.P32;
     a.cnt = p.cnt;
     a.invf = p.invf;
+    a.ptot = p.ptot;
+    a.D = p.D;
     a.out = out_part;
     a.p_out = p_out;
     a.trace = p.trace_prop;

@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_before();
                     mbar_arrive(smem_u32(&bar_acc_empty));   // the slice is in registers
                 }
-                float tile_sum = 0.0f;
+                bool tile_neg_inf = false;
                 if (n0 < a.KD) {   // (columns past KD: the last tile's MMA did not write them)
                     int xmin = 0x7fffffff;   // smallest bit pattern of a log argument (sign included)
 #pragma unroll
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             // S_k = sum_l q_kl exactly as hi + lo: every q in (-4, 4) is split at
                             // 2^-20 by adding and removing 12 (so the hi parts add exactly), the
                             // lo parts are below 2^-21
-                            float2 sh = splat2(0.0f), sl = splat2(0.0f), dev = splat2(0.0f);
+                            float2 sh = splat2(0.0f), sl = splat2(0.0f), dev = splat2(0.0f), comp = splat2(0.0f);
                             float4 w_next = w_q[nb / 2];
                             float2 c_next = w_c[nb / 2];
 #pragma unroll
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 // deviance terms c log(q invf); columns without counts get x = 1
                                 const float2 x = fma2(q, make_float2(w.x, w.y), make_float2(w.z, w.w));
                                 xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
-                                dev = fma2(c, log_poly2(x), dev);
+                                kahan_fma2(dev, comp, c, log_poly2(x));
                             }
                             const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;   // (s_hi exact)
                             // log(S_k / t), S_k - t formed from the exact pairs (Sterbenz: s_hi - t_hi exact)
@@ -645,24 +645,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const float l1p = fabsf(rel) < 0x1p-10f
                                                   ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
                                                   : log1pf(rel);
-                            tile_sum += (dev.x + dev.y) - pk * l1p;
+                            // the setting's term goes straight into the unit's pair
+                            add_setting(tot_hi, tot_lo, dev, comp, pk * l1p);
                         }
                     }
                     // a counted outcome with q <= 0 (or below the normal range): log L = -inf
-                    if (xmin < 0x00800000) tile_sum = -INFINITY;
+                    if (xmin < 0x00800000) tile_neg_inf = true;
                     if (a.p_out && valid) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i)
                             if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
                     }
                 }
-                if (tile_sum == -INFINITY) {
-                    neg_inf = true;
-                } else {
-                    const float sum = tot_hi + tile_sum, bp = sum - tot_hi;
-                    tot_lo += (tot_hi - (sum - bp)) + (tile_sum - bp);
-                    tot_hi = sum;
-                }
+                if (tile_neg_inf) neg_inf = true;
                 if (has_next) {
                     if (i < NP) alo_store(nb_buf, i, piece_w);
                     if (i == te - tb - 1) {   // last tile of the unit: whatever is left, then publish
@@ -840,7 +835,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            float tile_sum = 0.0f;
+            float tile_hi = 0.0f, tile_lo = 0.0f;   // the tile's settings, summed as a pair
             int xmin = 0x7fffffff;
             float vv[2][32];   // q of this warp's two 32-column settings: hi + (mid + lo)
 #pragma unroll
@@ -864,7 +859,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (n0 >= a.KD) continue;
                 const float pk = __ldg(a.ptot + n0 / D);
                 if (pk > 0.0f) {
-                    float2 sh = splat2(0.0f), sl = splat2(0.0f), dev = splat2(0.0f);
+                    float2 sh = splat2(0.0f), sl = splat2(0.0f), dev = splat2(0.0f), comp = splat2(0.0f);
 #pragma unroll
                     for (int l = 0; l < D; l += 2) {
                         const float2 q = make_float2(v[l], v[l + 1]);
@@ -875,14 +870,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const float2 c = __ldg(reinterpret_cast<const float2 *>(a.cnt + n0 + l));
                         const float2 x = fma2(q, make_float2(w.x, w.y), make_float2(w.z, w.w));
                         xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
-                        dev = fma2(c, log_poly2(x), dev);
+                        kahan_fma2(dev, comp, c, log_poly2(x));
                     }
                     const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;
                     const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
                     const float l1p = fabsf(rel) < 0x1p-10f
                                           ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
                                           : log1pf(rel);
-                    tile_sum += (dev.x + dev.y) - pk * l1p;
+                    add_setting(tile_hi, tile_lo, dev, comp, pk * l1p);
                 }
                 if (a.p_out && valid) {
 #pragma unroll
@@ -890,8 +885,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (n0 + i < a.KD) a.p_out[grow * a.KD + n0 + i] = v[i] * inv_t;
                 }
             }
-            if (xmin < 0x00800000) tile_sum = -INFINITY;
-            if (valid) a.out[(int64_t)(t * 4 + sub) * a.rows + grow] = (double)tile_sum;
+            if (valid)
+                a.out[(int64_t)(t * 4 + sub) * a.rows + grow] =
+                    xmin < 0x00800000 ? -INFINITY : (double)tile_hi + (double)tile_lo;
         }
     }
 

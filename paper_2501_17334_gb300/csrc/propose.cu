@@ -30,6 +30,7 @@
 //   5. the packed row is stored as FP32 and, for the tensor-core contraction, as the
 //      exact three-term bf16 split hi + mid + lo.
 #include "qst_internal.cuh"
+#include "f32x2.cuh"
 
 namespace qst {
 namespace {
@@ -45,16 +46,22 @@ constexpr int kThreads = 128;
 //           rho (row stride D + 1).
 // The per-chain stride is an odd multiple of 16 floats, so the two chains of a warp that
 // read the same offset in their own areas use opposite halves of the banks.
-template <int D>
+//   area R (PASSES = 3 only): the upper triangle of R from the Gram-Schmidt sweep, packed
+//           (column c, row k <= c at c (c + 1) / 2 + k, complex), which the refinement's
+//           triangular solve reads; area B then holds H's original columns during the
+//           refinement's products.  At D = 16 the Q planes are unpadded there (area A stays at
+//           W's 576 floats), which keeps five CTAs on an SM.
+template <int D, int PASSES = 2>
 struct Shape {
     static constexpr int d = D * D;
     static constexpr int chains_per_block = kThreads / D;
     static constexpr int row_stride = D + 2;                    // float2 per row of W (padded)
-    static constexpr int qcol = D + 4;                          // floats per column of a Q plane
+    static constexpr int qcol = (PASSES == 3 && D == 16) ? D : D + 4;   // floats per column of a Q plane
     static constexpr int pk_stride = D + 1;                     // floats per row of the staged rho
     static constexpr int area_a = (2 * D * qcol > 2 * D * row_stride) ? 2 * D * qcol : 2 * D * row_stride;
     static constexpr int area_b = (2 * D * D > D * pk_stride) ? 2 * D * D : D * pk_stride;
-    static constexpr int raw = area_a + area_b;
+    static constexpr int area_r = (PASSES == 3) ? D * (D + 1) : 0;
+    static constexpr int raw = area_a + area_b + area_r;
     static constexpr int smem_floats = (raw + 31) / 32 * 32 + 16;
 };
 
@@ -164,6 +171,56 @@ __device__ __forceinline__ void group_sum_exact(float v, float &hi, float &lo) {
     lo = err;
 }
 
+// q^dag p for the lane's own column q = (qr, qi) (pairs of rows, in registers) and a column p
+// in shared memory (real and imaginary planes), without rounding error in the products and
+// the sum: each product is accumulated into s1, which carries the offset `offset` = 1.5 2^(e+1)
+// and so holds its running sum rounded to multiples of 2^(e-22) exactly (every partial sum of
+// one accumulator must stay below 2^e); the FMA's rounding error x y - (s1' - s1) is formed
+// exactly by a second FMA and summed in s2, where it is at most 2^(e-23).  The result is
+// returned as (re, im), minus `sub` on the real part (subtracted while the sum is still
+// exact); its error is about 2^(e-45) per product.
+template <int D>
+__device__ __forceinline__ float2 sum_products_exact(const float2 (&qr)[D / 2], const float2 (&qi)[D / 2],
+                                                     const float *pre, const float *pim, float offset, float sub) {
+    // four accumulators: qr pr + qi pi (real part), qr pi and qi pr (imaginary part, subtracted
+    // at the end); each a grid sum s1 and an error sum s2
+    float2 a1 = make_float2(offset, offset), b1 = a1, c1 = a1;
+    float2 a2 = make_float2(0.f, 0.f), b2 = a2, c2 = a2;
+    auto step = [](float2 &s1, float2 &s2, float2 x, float2 y) {
+        const float2 n = __ffma2_rn(x, y, s1);
+        s2 = __fadd2_rn(s2, __ffma2_rn(x, y, sub2(s1, n)));   // + (x y - (n - s1)): the rounding error
+        s1 = n;
+    };
+    // the column p is read two row pairs (one 128-bit load per plane) at a time
+#pragma unroll
+    for (int p0 = 0; p0 < D / 2; p0 += (D >= 4 ? 2 : 1)) {
+        float2 pr[2], pi[2];
+        if constexpr (D >= 4) {
+            const float4 r4 = *reinterpret_cast<const float4 *>(pre + 2 * p0);
+            const float4 i4 = *reinterpret_cast<const float4 *>(pim + 2 * p0);
+            pr[0] = make_float2(r4.x, r4.y);
+            pr[1] = make_float2(r4.z, r4.w);
+            pi[0] = make_float2(i4.x, i4.y);
+            pi[1] = make_float2(i4.z, i4.w);
+        } else {
+            pr[0] = *reinterpret_cast<const float2 *>(pre);
+            pi[0] = *reinterpret_cast<const float2 *>(pim);
+        }
+#pragma unroll
+        for (int u = 0; u < (D >= 4 ? 2 : 1); ++u) {
+            const int p = p0 + u;
+            step(a1, a2, qr[p], pr[u]);   // Re: qr pr + qi pi
+            step(a1, a2, qi[p], pi[u]);
+            step(b1, b2, qr[p], pi[u]);   // Im: qr pi - qi pr
+            step(c1, c2, qi[p], pr[u]);
+        }
+    }
+    // the grid parts minus their offsets are exact, and so are their sums and differences
+    const float re_grid = ((a1.x - offset) + (a1.y - offset)) - sub;
+    const float im_grid = ((b1.x - offset) + (b1.y - offset)) - ((c1.x - offset) + (c1.y - offset));
+    return make_float2(re_grid + (a2.x + a2.y), im_grid + ((b2.x + b2.y) - (c2.x + c2.y)));
+}
+
 struct ProposeArgs {
     const float *x_eval;        // MODE_EVAL: [rows][nx] latent vectors
     float *y;                   // [2][R][nx]
@@ -188,7 +245,7 @@ struct ProposeArgs {
 
 template <int D, int PASSES>
 __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
-    using S = Shape<D>;
+    using S = Shape<D, PASSES>;
     constexpr int d = S::d;
     constexpr int nx = 4 * d;
     constexpr int RS = S::row_stride;
@@ -206,6 +263,8 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
     float2 *wsm = reinterpret_cast<float2 *>(sm);        // W row-major (row stride RS), replaces Q
     float *fre = sm + S::area_a, *fim = fre + D * D;     // F column-major (stride D), re / im planes
     float *packed = sm + S::area_a;                      // staged rho (row stride PK), replaces F
+    float *hre = sm + S::area_a, *him = hre + D * D;     // PASSES = 3: H's columns (stride D), in area B
+    float2 *rpk = reinterpret_cast<float2 *>(sm + S::area_a + S::area_b);   // PASSES = 3: packed R
 
     // ---- 1. latent proposal --------------------------------------------------------------
     float coef_y = 1.0f, coef_eta = 0.0f;
@@ -297,6 +356,11 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         }
     }
 
+    if constexpr (PASSES == 3) {   // H's original columns, for the refinement after the sweep
+        store_column2<D>(hre + j * D, hr);
+        store_column2<D>(him + j * D, hi);
+    }
+
     // ---- 2a. modified Gram-Schmidt on the columns of H (Algorithm 1) ---------------------------
     // Every lane loads the published column v_k and forms r = v_k^dag h with its own column h
     // (packed f32x2 products over pairs of rows).  Lane k's column is v_k itself, so its r is
@@ -352,6 +416,12 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
                 fim[k * D + j] = -ri * sc;
             }
         }
+        if constexpr (PASSES == 3) {
+            // the triangular factor the refinement solves with (FP32 suffices there): R_kj =
+            // v_k^dag h_j / |v_k| above the diagonal; the diagonal slot holds (|v_k|, 1 / |v_k|)
+            if (j > k) rpk[j * (j + 1) / 2 + k] = make_float2(rr * rs, ri * rs);
+            if (j == k) rpk[k * (k + 1) / 2 + k] = make_float2(nk * rs, rs);
+        }
     }
     {   // normalise the own column and publish it
         const float2 sc = make_float2(inv_own, inv_own);
@@ -366,6 +436,119 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         __syncwarp();
     }
     }   // PASSES > 0
+
+    if constexpr (PASSES == 3) {
+        // ---- 2b. refinement of Q1 to the QR factor of H beyond FP32 ----------------------------
+        // An FP32 Gram-Schmidt factor Q1 is the exact factor of a matrix within 2^-24 of H, so it
+        // misses U by about cond(H) 2^-24 -- and near the posterior U + I is nearly singular, so
+        // that error reaches rho.  With Q1 = U V, V = I + X small: N = Q1^dag Q1 = I + X + X^dag
+        // (first order) and M = Q1^dag H = V^dag R, whose strictly lower part is that of X^dag R.
+        // So X^dag (called Y below) has: strictly lower part from the triangular system
+        // lower(Y R) = lower(M), upper part N - conj(lower part)^T, real diagonal (N_jj - 1) / 2,
+        // imaginary diagonal from the real diagonal of R; and U = Q1 V^-1 = Q1 (I - Y^dag) to
+        // first order (second order: (cond(H) 2^-24)^2, below FP32 rounding for cond(H) < 10^3).
+        // The lower part of M and N - I are tiny differences of O(1) products, so they are formed
+        // without rounding error: lane j forms row j (c < j: M_jc = q_j^dag h_c; c > j: N_jc =
+        // q_j^dag q_c) with error-free products (sum_products_exact), its own q_j in (hr, hi) and
+        // the other vector read from shared memory -- the lanes take different vectors at the
+        // same step only through their addresses, so every lane does useful work at every step.
+        // Lanes c > j then solve row j of the lower system as M_jc arrives (R from the sweep).
+        // C[j][c] (row j = lane j) is kept in area B: step c frees H's column c, whose 2 D floats
+        // take the D lanes' results of that step -- element (r, c) at c D + (r ^ c) of the real
+        // (hre) and imaginary (him) planes, so that the lanes' writes of a step, a lane's reads
+        // of its row and the reads of a column all hit distinct banks.
+        auto cidx = [](int r, int cc) { return cc * D + (r ^ cc); };
+#pragma unroll 1
+        for (int cc = 0; cc < D; ++cc) {
+            const bool lower = cc < j;   // M_jc = q_j^dag h_c; at c = j (and above) N_jc = q_j^dag q_c
+            const float *pre = lower ? hre + cc * D : qre + cc * QC;
+            const float *pim = lower ? him + cc * D : qim + cc * QC;
+            // every partial sum of M stays below 2^6 (|h| < 64), of N below 2^1
+            const float2 res = sum_products_exact<D>(hr, hi, pre, pim, lower ? 192.0f : 6.0f, cc == j ? 1.0f : 0.0f);
+            __syncwarp();   // every lane is done with column c of H
+            hre[cidx(j, cc)] = res.x;
+            him[cidx(j, cc)] = res.y;
+        }
+        // M_jj, the one entry of the row not formed above: its column of H now holds C, so h_j is
+        // read again from the proposal's own y' (or the evaluated row; for an inactive lane the
+        // first chain's row, in bounds, whose result is not used)
+        const float2 mjj = sum_products_exact<D>(hr, hi, gsrc + 2 * d + j * D, gsrc + 3 * d + j * D, 192.0f, 0.0f);
+        __syncwarp();
+        // Y, row j, in registers: y[c] = Y[j][c].  Forward substitution, right-looking: after
+        // Y[j][c0] = (M_jc0 - ...) / R_c0c0 every later entry of the row takes its share
+        // -Y[j][c0] R[c0][c] at once, so each R entry is read once for all lanes; entries at
+        // c >= j stay zero (the lane's row has no such unknowns) until the upper part below.
+        float2 y[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            y[c] = (c < j) ? make_float2(hre[cidx(j, c)], him[cidx(j, c)]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c0 = 0; c0 < D - 1; ++c0) {
+            const float inv_r = rpk[c0 * (c0 + 1) / 2 + c0].y;
+            y[c0] = make_float2(y[c0].x * inv_r, y[c0].y * inv_r);
+#pragma unroll
+            for (int c = c0 + 1; c < D - 1; ++c) {
+                const float2 r = rpk[c * (c + 1) / 2 + c0];   // R[c0][c]
+                y[c].x -= y[c0].x * r.x - y[c0].y * r.y;
+                y[c].y -= y[c0].x * r.y + y[c0].y * r.x;
+            }
+        }
+        // diagonal: Re Y_jj = (N_jj - 1) / 2; Im Y_jj makes R_jj real
+        float ydi = mjj.y;
+#pragma unroll
+        for (int k = 0; k < D - 1; ++k) {
+            const float2 r = rpk[j * (j + 1) / 2 + (k < j ? k : 0)];   // R[k][j] (k < j)
+            if (k < j) ydi -= y[k].x * r.y + y[k].y * r.x;
+        }
+        const float2 ydiag = make_float2(0.5f * hre[cidx(j, j)], ydi * rpk[j * (j + 1) / 2 + j].y);
+        // upper part: Y[j][c] = N_jc - conj(Y[c][j]), c > j, through area B
+#pragma unroll
+        for (int c = 0; c < D - 1; ++c)
+            if (c < j) {
+                hre[cidx(j, c)] = y[c].x;
+                him[cidx(j, c)] = y[c].y;
+            }
+        __syncwarp();   // every lane's lower row is in place
+#pragma unroll
+        for (int c = 1; c < D; ++c)
+            if (c > j) y[c] = make_float2(hre[cidx(j, c)] - hre[cidx(c, j)], him[cidx(j, c)] + him[cidx(c, j)]);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (c == j) y[c] = ydiag;
+        // U = Q1 - Q1 Y^dag: column j is q_j - sum_k q_k conj(Y[j][k]); the correction is summed
+        // on its own (it is small) and subtracted once.  Rows go in two halves: a half is
+        // overwritten only after every lane has read that half of every column.
+        constexpr int HP = (D >= 4) ? D / 4 : 1;   // row pairs per half
+#pragma unroll
+        for (int half = 0; half < (D >= 4 ? 2 : 1); ++half) {
+            float2 cr[HP], ci[HP];
+#pragma unroll
+            for (int p = 0; p < HP; ++p) cr[p] = ci[p] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float2 yx = make_float2(y[k].x, y[k].x), yy = make_float2(y[k].y, y[k].y);
+                const float2 myy = make_float2(-y[k].y, -y[k].y);   // conj(y) = (y.x, -y.y)
+#pragma unroll
+                for (int p = 0; p < HP; ++p) {   // (vr + i vi)(y.x - i y.y)
+                    const int row = 2 * (half * HP + p);
+                    const float2 vr = *reinterpret_cast<const float2 *>(qre + k * QC + row);
+                    const float2 vi = *reinterpret_cast<const float2 *>(qim + k * QC + row);
+                    cr[p] = __ffma2_rn(vr, yx, __ffma2_rn(vi, yy, cr[p]));
+                    ci[p] = __ffma2_rn(vi, yx, __ffma2_rn(vr, myy, ci[p]));
+                }
+            }
+            __syncwarp();   // every lane has read this half of every q_k
+#pragma unroll
+            for (int p = 0; p < HP; ++p) {
+                const int row = 2 * (half * HP + p);
+                float2 *ur = reinterpret_cast<float2 *>(qre + j * QC + row);
+                float2 *ui = reinterpret_cast<float2 *>(qim + j * QC + row);
+                *ur = sub2(*ur, cr[p]);
+                *ui = sub2(*ui, ci[p]);
+            }
+            __syncwarp();
+        }
+    }
 
     if constexpr (PASSES == 2) {
         // ---- 2b. re-orthogonalisation Q2 = Q1 (I - F), F = strict upper part of E (formed in
@@ -460,35 +643,56 @@ __global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
         }
         __syncwarp();
         const int bi = j >> 2, bj = j & 3;
-        float2 wr[4][2], wi[4][2];   // W[4bi + r][4bj + 2h .. 4bj + 2h + 1]
+        // W[4bi + r][4bj + 2h .. 4bj + 2h + 1], two rows at a time: the products of Re U (and G
+        // itself, the identity's term) in one pair of chains (wr, wi), those of Im U in another
+        // (xr, xi), added at the end -- each chain half as long, with the rounding of the two
+        // sums kept apart until the one final add (the assembly's log L error grows with the
+        // length of the chains that form W).  The first two rows wait in registers until
+        // every lane is done with U, whose storage W takes.
+        float2 wr[4][2], wi[4][2];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float4 g4r = *reinterpret_cast<const float4 *>(gsr + (4 * bi + r) * D + 4 * bj);
-            const float4 g4i = *reinterpret_cast<const float4 *>(gsi + (4 * bi + r) * D + 4 * bj);
-            wr[r][0] = make_float2(g4r.x, g4r.y);
-            wr[r][1] = make_float2(g4r.z, g4r.w);
-            wi[r][0] = make_float2(g4i.x, g4i.y);
-            wi[r][1] = make_float2(g4i.z, g4i.w);
-        }
+        for (int hb = 0; hb < 2; ++hb) {
+            float2 ar[2][2], ai[2][2], xr[2][2], xi[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int row = 4 * bi + 2 * hb + r;
+                const float4 g4r = *reinterpret_cast<const float4 *>(gsr + row * D + 4 * bj);
+                const float4 g4i = *reinterpret_cast<const float4 *>(gsi + row * D + 4 * bj);
+                ar[r][0] = make_float2(g4r.x, g4r.y);
+                ar[r][1] = make_float2(g4r.z, g4r.w);
+                ai[r][0] = make_float2(g4i.x, g4i.y);
+                ai[r][1] = make_float2(g4i.z, g4i.w);
+                xr[r][0] = xr[r][1] = xi[r][0] = xi[r][1] = make_float2(0.f, 0.f);
+            }
 #pragma unroll 4
-        for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {
-            const float4 ur4 = *reinterpret_cast<const float4 *>(qre + k * QC + 4 * bi);
-            const float4 ui4 = *reinterpret_cast<const float4 *>(qim + k * QC + 4 * bi);
-            const float4 g4r = *reinterpret_cast<const float4 *>(gsr + k * D + 4 * bj);
-            const float4 g4i = *reinterpret_cast<const float4 *>(gsi + k * D + 4 * bj);
-            const float2 gr2[2] = {make_float2(g4r.x, g4r.y), make_float2(g4r.z, g4r.w)};
-            const float2 gi2[2] = {make_float2(g4i.x, g4i.y), make_float2(g4i.z, g4i.w)};
-            const float ur[4] = {ur4.x, ur4.y, ur4.z, ur4.w}, ui[4] = {ui4.x, ui4.y, ui4.z, ui4.w};
+            for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {
+                const float2 ur2 = *reinterpret_cast<const float2 *>(qre + k * QC + 4 * bi + 2 * hb);
+                const float2 ui2 = *reinterpret_cast<const float2 *>(qim + k * QC + 4 * bi + 2 * hb);
+                const float4 g4r = *reinterpret_cast<const float4 *>(gsr + k * D + 4 * bj);
+                const float4 g4i = *reinterpret_cast<const float4 *>(gsi + k * D + 4 * bj);
+                const float2 gr2[2] = {make_float2(g4r.x, g4r.y), make_float2(g4r.z, g4r.w)};
+                const float2 gi2[2] = {make_float2(g4i.x, g4i.y), make_float2(g4i.z, g4i.w)};
+                const float ur[2] = {ur2.x, ur2.y}, ui[2] = {ui2.x, ui2.y};
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float2 pu = make_float2(ur[r], ur[r]), pi = make_float2(ui[r], ui[r]);
-                const float2 mi = make_float2(-ui[r], -ui[r]);
+                for (int r = 0; r < 2; ++r) {
+                    const float2 pu = make_float2(ur[r], ur[r]), pi = make_float2(ui[r], ui[r]);
+                    const float2 mi = make_float2(-ui[r], -ui[r]);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    wr[r][h] = __ffma2_rn(pu, gr2[h], __ffma2_rn(mi, gi2[h], wr[r][h]));
-                    wi[r][h] = __ffma2_rn(pu, gi2[h], __ffma2_rn(pi, gr2[h], wi[r][h]));
+                    for (int h = 0; h < 2; ++h) {
+                        ar[r][h] = __ffma2_rn(pu, gr2[h], ar[r][h]);
+                        xr[r][h] = __ffma2_rn(mi, gi2[h], xr[r][h]);
+                        ai[r][h] = __ffma2_rn(pu, gi2[h], ai[r][h]);
+                        xi[r][h] = __ffma2_rn(pi, gr2[h], xi[r][h]);
+                    }
                 }
             }
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    wr[2 * hb + r][h] = __fadd2_rn(ar[r][h], xr[r][h]);
+                    wi[2 * hb + r][h] = __fadd2_rn(ai[r][h], xi[r][h]);
+                }
         }
         __syncwarp();
 #pragma unroll
@@ -1344,14 +1548,16 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.step_dev = step_dev;
     a.mode = mode;
     a.d_pad = p.d_pad;
+    // the five- and six-qubit kernels have no refinement: they take the FP32 re-orthogonalisation
+    constexpr int WIDE_PASSES = PASSES == 3 ? 2 : PASSES;
     if constexpr (D == 64) {
         if (a.split_out || a.split_tf) return cudaErrorNotSupported;   // no tensor-core form at D = 64
-        return launch_propose_d64<PASSES>(a, s);
+        return launch_propose_d64<WIDE_PASSES>(a, s);
     } else if constexpr (D == 32) {
         if (a.split_tf) return cudaErrorNotSupported;   // the TF32 forms stop at D = 16
-        return launch_propose_d32<PASSES>(a, s);
+        return launch_propose_d32<WIDE_PASSES>(a, s);
     } else {
-        using S = Shape<D>;
+        using S = Shape<D, PASSES>;
         const size_t smem = sizeof(float) * S::smem_floats * S::chains_per_block;
         static bool attr_set = false;
         if (!attr_set) {
@@ -1375,7 +1581,8 @@ cudaError_t launch_propose_d(const ProblemView &p, int mode, uint32_t step, cons
                              int64_t rows, bool want_split, float *rho_norm_out, cudaStream_t s) {
     if (p.qr_passes == 0) return launch_propose_pd<D, 0>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
     if (p.qr_passes == 1) return launch_propose_pd<D, 1>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
-    return launch_propose_pd<D, 2>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+    if (p.qr_passes == 2) return launch_propose_pd<D, 2>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
+    return launch_propose_pd<D, 3>(p, mode, step, step_dev, x_eval, rows, want_split, rho_norm_out, s);
 }
 
 }  // namespace

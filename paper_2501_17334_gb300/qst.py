@@ -75,6 +75,7 @@ _SIGS = {
                                   ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "qst_run_chains": (ctypes.c_int, [_P, ctypes.c_int64]),
     "qst_posterior_mean": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "qst_posterior_sum": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int64)]),
     "qst_diagnostics": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Diag), _P, _P]),
     "qst_synchronize": (ctypes.c_int, [_P]),
     "qst_destroy": (None, [_P]),
@@ -248,6 +249,15 @@ class Sampler:
         n = ctypes.c_int64()
         _check(self.lib.qst_posterior_mean(self.handle, problem, re.ctypes.data, im.ctypes.data, ctypes.byref(n)))
         return re + 1j * im, n.value
+
+    def posterior_sum(self, problem: int = 0):
+        """qst_posterior_sum: the FP64 sum of the kept packed states ([D*D], packed layout) and
+        their count."""
+        D = self.problems[problem].dim
+        out = np.zeros(D * D)
+        n = ctypes.c_int64()
+        _check(self.lib.qst_posterior_sum(self.handle, problem, out.ctypes.data, ctypes.byref(n)))
+        return out, n.value
 
     def diagnostics(self, problem: int = 0):
         d = Diag()

@@ -5,9 +5,10 @@ every random draw holds the chain's global id, so a chain gives the same traject
 rank. A run over R chains on N processes gives each rank one contiguous range of global
 chain ids (``chain_range``). The pooled estimate of Eq. BME2 is a sum over chains and kept
 steps divided by the number of kept states. It is merged once, at the end, by
-``merge_posterior_mean``: every rank's FP64 sum and count are gathered and added on the host
-in rank order. The result is the same on every rank and independent of the reduction
-schedule. Nothing is exchanged while the chains run.
+``merge_posterior_sum``: every rank's raw FP64 sum (``Sampler.posterior_sum``, the C ABI's
+``qst_posterior_sum``) and count are gathered, added on the host in rank order and divided
+once. The result is the same on every rank and independent of the reduction schedule.
+Nothing is exchanged while the chains run.
 """
 from __future__ import annotations
 
@@ -28,28 +29,41 @@ def chain_range(rank: int, world: int, num_chains: int) -> Tuple[int, int]:
     return begin, base + (1 if rank < extra else 0)
 
 
-def merge_posterior_mean(mean: np.ndarray, num_pooled: int, group=None):
-    """Merge per-rank posterior means into the mean over every rank's kept states.
+def packed_to_matrix(packed: np.ndarray, D: int) -> np.ndarray:
+    """The Hermitian D x D matrix of a packed vec_h array: Re rho_ii on the diagonal, Re rho_ij
+    above it (i < j), Im rho_ij below it (i > j), as include/qst.h lays it out."""
+    v = np.asarray(packed, dtype=np.float64).reshape(D, D)
+    m = np.zeros((D, D), dtype=np.complex128)
+    iu = np.triu_indices(D, 1)
+    m[np.diag_indices(D)] = np.diag(v)
+    m[iu] = v[iu] - 1j * v.T[iu]          # Im rho_ij = -Im rho_ji, stored at [j, i]
+    m[(iu[1], iu[0])] = np.conj(m[iu])
+    return m
 
-    ``mean`` is this rank's complex D x D mean of ``num_pooled`` kept states (what
-    ``Sampler.posterior_mean`` returns). The sums mean * n are gathered from all ranks of
-    the default process group (or ``group``) and added in rank order in FP64. Returns
-    ``(merged mean, total count)`` on every rank. A rank with no kept states contributes
-    zero. Works with the gloo backend (host tensors) and with NCCL (device tensors).
+
+def merge_posterior_sum(sum_packed: np.ndarray, num_pooled: int, group=None):
+    """Merge per-rank pooled sums into the posterior mean over every rank's kept states.
+
+    ``sum_packed`` is this rank's FP64 sum of its kept packed states and ``num_pooled`` their
+    count (what ``Sampler.posterior_sum`` returns). The sums and counts of all ranks of the
+    default process group (or ``group``) are gathered and added in rank order in FP64, and
+    the total is divided once. Returns ``(merged mean as a complex D x D matrix, total
+    count)`` on every rank, or ``(None, 0)`` when nothing was kept. A rank with no kept
+    states contributes zero. Works with the gloo backend (host tensors) and with NCCL
+    (device tensors).
     """
     import torch
     import torch.distributed as dist
 
-    mean = np.asarray(mean, dtype=np.complex128)
-    D = mean.shape[0]
+    s = np.asarray(sum_packed, dtype=np.float64).ravel()
+    d = s.size
+    D = int(round(np.sqrt(d)))
     world = dist.get_world_size(group)
     backend = dist.get_backend(group)
     device = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
-    local = np.zeros(2 * D * D + 1, dtype=np.float64)
+    local = np.zeros(d + 1, dtype=np.float64)
     if num_pooled > 0:
-        s = mean * float(num_pooled)
-        local[:D * D] = s.real.ravel()
-        local[D * D:2 * D * D] = s.imag.ravel()
+        local[:d] = s
     local[-1] = float(num_pooled)
     send = torch.from_numpy(local).to(device)
     parts = [torch.empty_like(send) for _ in range(world)]
@@ -60,5 +74,4 @@ def merge_posterior_mean(mean: np.ndarray, num_pooled: int, group=None):
     n = int(round(total[-1]))
     if n == 0:
         return None, 0
-    merged = (total[:D * D] + 1j * total[D * D:2 * D * D]).reshape(D, D) / n
-    return merged, n
+    return packed_to_matrix(total[:d] / n, D), n

@@ -1,9 +1,9 @@
 """Multi-process path on the CPU: chain ranges per rank and the final merge of Eq. BME2.
 
 Two gloo ranks each run their own contiguous range of global chain ids (the oracle
-stands in for the GPU sampler, which computes the same chains) and merge the pooled
-sums with ``shard.merge_posterior_mean``.  The merged mean must equal a single run over
-all chains up to FP64 summation order, and both ranks must hold the same result.
+stands in for the GPU sampler, which computes the same chains) and merge their raw FP64
+pooled sums with ``shard.merge_posterior_sum``.  The merged mean must equal a single run
+over all chains up to FP64 summation order, and every rank must hold the same result.
 """
 import os
 import socket
@@ -39,6 +39,15 @@ def test_chain_range_rejects_bad_rank():
         shard.chain_range(0, 0, 10)
 
 
+@pytest.mark.parametrize("D", [1, 2, 4, 16])
+def test_packed_to_matrix_inverts_the_packed_layout(D):
+    from tests._helpers import pack_rho
+    rng = np.random.default_rng(D)
+    g = rng.normal(size=(D, D)) + 1j * rng.normal(size=(D, D))
+    rho = g @ g.conj().T
+    assert np.array_equal(shard.packed_to_matrix(pack_rho(rho), D), rho - 1j * np.diag(np.diag(rho).imag))
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -57,7 +66,8 @@ def _rank_main(rank, world, port, num_chains, num_steps, out_dir):
         prob = WL.config_problem(1, num_chains=num_chains, num_steps=num_steps)
         begin, count = S.chain_range(rank, world, num_chains)
         res = oracle.run(prob, num_chains=count, num_steps=num_steps, chain_begin=begin)
-        merged, n = S.merge_posterior_mean(res["mean"], res["num_pooled"])
+        from tests._helpers import pack_rho
+        merged, n = S.merge_posterior_sum(pack_rho(res["pool"]), res["num_pooled"])
         np.save(os.path.join(out_dir, f"rank{rank}.npy"), np.concatenate([merged.ravel(), [n]]))
     finally:
         dist.destroy_process_group()
