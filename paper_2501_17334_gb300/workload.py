@@ -152,7 +152,8 @@ class Problem:
 
     @property
     def num_povms(self) -> int:
-        return 3 ** self.num_qubits
+        """Measurement settings K (3^Q for the Pauli problems): the counts hold K D outcomes."""
+        return len(self.counts) // self.dim
 
 
 def make_problem(
@@ -240,6 +241,86 @@ def heterogeneous_batch(num_problems: int = 64, seed: int = 1005, max_qubits: in
                                   int(rng.integers(1 << 31)), int(rng.integers(1 << 31)),
                                   name=f"batch{i}"))
     return probs
+
+
+# ---- problems with other measurements (any complete POVM; the method only needs Lambda_kl) ----
+
+def _haar_unitary(dim: int, rng: np.random.Generator) -> np.ndarray:
+    """A Haar-random unitary: the Q factor of a complex Gaussian matrix, columns rephased so
+    that R has a positive diagonal."""
+    z = (rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+# Two-qubit orthonormal bases (columns) whose projectors have dyadic entries (exact in bf16),
+# none of them a product of Pauli eigenbases: the Bell basis, the Bell basis with a phase i on
+# the second component, and a basis of real vectors with entries +-1/2.
+_B = 1.0 / math.sqrt(2.0)
+_TWO_QUBIT_BASES = (
+    np.array([[_B, _B, 0, 0], [0, 0, _B, _B], [0, 0, _B, -_B], [_B, -_B, 0, 0]], dtype=np.complex128),
+    np.array([[_B, _B, 0, 0], [0, 0, _B, _B], [0, 0, 1j * _B, -1j * _B], [1j * _B, -1j * _B, 0, 0]],
+             dtype=np.complex128),
+    0.5 * np.array([[1, 1, 1, -1], [1, -1, 1, 1], [1, 1, -1, 1], [-1, 1, 1, 1]], dtype=np.complex128),
+)
+
+
+def basis_problem(num_qubits: int, bases: np.ndarray, truth: np.ndarray, shots_per_setting: int, num_chains: int,
+                  num_steps: int, beta0: float, data_seed: int, chain_seed: int, name: str = "",
+                  dyadic: bool = False) -> Problem:
+    """A problem measured in K orthonormal bases: ``bases`` is ``[K, D, D]`` with the outcome
+    vectors as columns, ``Lambda_kl = |b_kl><b_kl|`` (each setting sums to the identity).
+    Counts are multinomial over the Born probabilities of ``truth``.  With ``dyadic`` the
+    projector entries, dyadic rationals up to the rounding of 1/sqrt(2) products, are set to
+    those exact values (multiples of 2^-30)."""
+    d = 1 << num_qubits
+    bases = np.asarray(bases, dtype=np.complex128)
+    k_count = bases.shape[0]
+    if bases.shape != (k_count, d, d):
+        raise ValueError("bases must be [K, D, D]")
+    phi = bases.transpose(0, 2, 1).reshape(k_count * d, d)   # row k D + l = column l of basis k
+    povm = phi[:, :, None] * phi.conj()[:, None, :]
+    if dyadic:
+        povm = np.round(povm.real * 2.0 ** 30) / 2.0 ** 30 + 1j * (np.round(povm.imag * 2.0 ** 30) / 2.0 ** 30)
+    rng = np.random.default_rng(data_seed)
+    born = np.clip(np.einsum("ia,ab,ib->i", phi.conj(), truth, phi).real, 0.0, None).reshape(k_count, d)
+    counts = np.stack([rng.multinomial(int(shots_per_setting), b / b.sum()) for b in born]).reshape(-1)
+    return Problem(num_qubits, np.ascontiguousarray(povm.real), np.ascontiguousarray(povm.imag),
+                   counts.astype(np.int32), truth, int(num_chains), int(num_steps), float(beta0), int(chain_seed),
+                   name)
+
+
+def random_basis_problem(num_qubits: int, num_settings: int, seed: int = 1100, num_chains: int = 256,
+                         num_steps: int = 200, shots_per_setting: int = 1000, beta0: float = 0.05) -> Problem:
+    """Measurements in ``num_settings`` Haar-random bases of the whole register (entries not
+    exact in bf16: the FP32 form), Ginibre truth of rank 2 mixed with I/D at weight 0.05."""
+    d = 1 << num_qubits
+    rng = np.random.default_rng(seed)
+    truth = depolarise(ginibre_state(d, min(2, d), rng), 0.05)
+    bases = np.stack([_haar_unitary(d, rng) for _ in range(num_settings)])
+    return basis_problem(num_qubits, bases, truth, shots_per_setting, num_chains, num_steps, beta0, seed + 1000,
+                         seed + 2000, name=f"random_bases_{num_qubits}q")
+
+
+def dyadic_basis_problem(num_qubits: int, seed: int = 1200, num_chains: int = 256, num_steps: int = 200,
+                         shots_per_setting: int = 1000, beta0: float = 0.05) -> Problem:
+    """Entangled (non-Pauli) measurements whose packed projectors are exact in bf16: every
+    setting is a Kronecker product of the two-qubit bases above over qubit pairs (0,1), (2,3),
+    ..., times the Z or X basis on a last odd qubit -- 3^(Q/2) settings for even Q.  Ginibre
+    truth of rank 2 mixed with I/D at weight 0.05."""
+    if num_qubits < 2:
+        raise ValueError("dyadic entangled bases need at least two qubits")
+    d = 1 << num_qubits
+    rng = np.random.default_rng(seed)
+    truth = depolarise(ginibre_state(d, min(2, d), rng), 0.05)
+    factors = [list(_TWO_QUBIT_BASES)] * (num_qubits // 2)
+    if num_qubits % 2:
+        factors.append([np.eye(2, dtype=np.complex128), np.array([[_B, _B], [_B, -_B]], dtype=np.complex128)])
+    bases = [np.ones((1, 1), dtype=np.complex128)]
+    for opts in factors:
+        bases = [np.kron(b, f) for b in bases for f in opts]
+    return basis_problem(num_qubits, np.stack(bases), truth, shots_per_setting, num_chains, num_steps, beta0,
+                         seed + 1000, seed + 2000, name=f"dyadic_bases_{num_qubits}q", dyadic=True)
 
 
 def latent_batch(num: int, num_qubits: int, seed: int, scale: float = 1.0) -> np.ndarray:
