@@ -23,3 +23,24 @@ def pack_rho(rho):
     out = np.where(upper, rho.real, 0.0) + np.where(upper.T, rho.imag, 0.0) + \
         np.diagonal(rho.real, axis1=-2, axis2=-1)[..., None] * np.eye(D)
     return out.reshape(*rho.shape[:-2], D * D)
+
+
+def near_tie_band(acc_gpu, acc_ref, ll_prop_gpu, ll_prop_ref):
+    """Band within which an accept decision may legitimately differ from the oracle's: twice
+    the largest |log L(y') GPU - oracle| measured in the same run (the current and the
+    proposed state each carry one error), over every chain-step up to and including a
+    chain's first differing decision (until then both sides hold identical states), finite
+    entries only.  Arrays are [chains, steps]."""
+    acc_gpu = np.asarray(acc_gpu)
+    acc_ref = np.asarray(acc_ref)
+    R, S = acc_ref.shape
+    first = np.full(R, S)
+    for r in range(R):
+        bad = np.nonzero(acc_gpu[r] != acc_ref[r])[0]
+        if bad.size:
+            first[r] = bad[0] + 1
+    mask = np.arange(S)[None, :] < first[:, None]
+    a = np.asarray(ll_prop_gpu, dtype=np.float64)
+    b = np.asarray(ll_prop_ref, dtype=np.float64)
+    ok = mask & np.isfinite(a) & np.isfinite(b)
+    return 2.0 * np.abs(a[ok] - b[ok]).max() + 1e-9

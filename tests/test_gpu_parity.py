@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from paper_2501_17334_gb300 import workload as W
-from tests._helpers import unpack_rho
+from tests._helpers import near_tie_band, unpack_rho
 
 pytestmark = pytest.mark.gpu
 
@@ -139,15 +139,19 @@ def test_first_200_decisions(qst, oracle_mod, cuda_ok, prec, q, R, beta0):
     s.close()
     ref = oracle_mod.run(prob, num_steps=200, trace_steps=200, want_final=True)
     margin = ref["trace_log_alpha"] - (ref["trace_logl_prop"] - ref["trace_logl_cur"])
-    compared, mism = _compare_decisions(acc_gpu.T, ref["trace_accept"], margin, tol=5e-2)
-    assert mism <= max(2, R // 50), f"{mism} chains hit near-tie mismatches"
-    assert compared >= 0.9 * R * 200
     # log L of the proposals agree where trajectories still coincide: relative error of
     # the FP32 assembly, largest for proposals deep in the tails (p_kl -> 0 for counted
     # outcomes, which are rejected anyway)
     same = np.all(acc_gpu.T == ref["trace_accept"], axis=1)
     d = np.abs(ll_prop_gpu.T[same] - ref["trace_logl_prop"][same])
     fin = np.isfinite(ref["trace_logl_prop"][same])
+    # a decision may differ only at a near tie: where |log alpha - Delta log L| is within
+    # twice the log L error measured in this run (the current and the proposed state each
+    # carry one)
+    tol = near_tie_band(acc_gpu.T, ref["trace_accept"], ll_prop_gpu.T, ref["trace_logl_prop"])
+    compared, mism = _compare_decisions(acc_gpu.T, ref["trace_accept"], margin, tol=tol)
+    assert mism <= max(2, R // 50), f"{mism} chains hit near-tie mismatches"
+    assert compared >= 0.9 * R * 200
     rel = d[fin] / np.abs(ref["trace_logl_prop"][same][fin])
     assert np.median(rel) < 1e-7
     assert rel.max() < 1e-4
