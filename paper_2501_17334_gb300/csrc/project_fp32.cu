@@ -3,7 +3,11 @@
 //
 // p = A . P with A = packed vec_h(rho) rows [rows][d_pad] and P the packed projector
 // matrix [d_pad][KD_pad].  A CTA owns 128 chains and sweeps a group of 128-column
-// tiles; each thread keeps an 8 x 8 register tile.  The epilogue evaluates the
+// tiles; each thread keeps an 8 x 8 register tile.  The K sum runs in chunks of 32 terms:
+// after each chunk the tile is added into a second-level sum (a thread-private array in
+// shared memory) and restarted, so no FP32 chain is longer than 32 terms -- a 256-term chain
+// rounds at the scale of its running sum 256 times, which at four qubits is most of the FP32
+// form's log L error.  The epilogue evaluates the
 // likelihood in deviance form, every setting k renormalised by its own sum S_k = sum_l q_kl,
 //     log L = C0 - N log t + sum_k [ sum_{c_kl > 0} c_kl log(q_kl invf_kl) - P_k log(S_k / t) ],
 // invf_kl = P_k / c_kl (q = vec_h(rho) . P, t the exact trace of the stored rho), which equals
@@ -19,6 +23,9 @@ namespace qst {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 16, kThreads = 256;
+constexpr int kChunkSteps = 2;   // K steps of BK per chunk of the sum (32 terms)
+// dynamic shared memory: the A and B stages, the column weights and the second-level sums
+constexpr size_t kSmemBytes = sizeof(float) * (2 * BK * BM + 2 * BK * BN + 2 * BN + 64 * kThreads);
 
 struct ProjectArgs {
     const float *A;      // [rows][d_pad]
@@ -36,9 +43,11 @@ struct ProjectArgs {
 };
 
 __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
-    __shared__ __align__(16) float As[2][BK][BM];
-    __shared__ __align__(16) float Bs[2][BK][BN];
-    __shared__ float cnt_s[BN], invf_s[BN];
+    extern __shared__ __align__(16) float dyn[];
+    float (*As)[BK][BM] = reinterpret_cast<float (*)[BK][BM]>(dyn);
+    float (*Bs)[BK][BN] = reinterpret_cast<float (*)[BK][BN]>(dyn + 2 * BK * BM);
+    float *cnt_s = dyn + 2 * BK * BM + 2 * BK * BN, *invf_s = cnt_s + BN;
+    float *tot = invf_s + BN;   // [64][kThreads]: element e of this thread's tile at e * kThreads + tid
 
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
@@ -124,7 +133,25 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
             if (ks + 1 < k_steps) {
                 store_shared(buf ^ 1);
             }
+            // end of a 32-term chunk (not the last one): fold the tile into the second-level sum
+            if (ks % kChunkSteps == kChunkSteps - 1 && ks + 1 < k_steps) {
+                const bool first = ks == kChunkSteps - 1;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        float *t = tot + (i * 8 + jj) * kThreads + tid;
+                        *t = first ? acc[i][jj] : *t + acc[i][jj];
+                        acc[i][jj] = 0.0f;
+                    }
+            }
             __syncthreads();
+        }
+        if (k_steps > kChunkSteps) {   // the last chunk joins the earlier ones
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) acc[i][jj] = tot[(i * 8 + jj) * kThreads + tid] + acc[i][jj];
         }
 
         // epilogue: deviance terms of this tile, and the renormalisation of its settings.  The
@@ -230,7 +257,17 @@ cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t ro
     const int groups = p.ngroups;
     a.tiles_per_group = (nt + groups - 1) / groups;
     dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)groups);
-    project_fp32_kernel<<<grid, kThreads, 0, s>>>(a);
+    // more than 48 KB of dynamic shared memory: opted into once per device
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && !((attr_set >> dev) & 1ull)) {
+        e = cudaFuncSetAttribute(project_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set |= 1ull << dev;
+    }
+    project_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(a);
     return cudaGetLastError();
 }
 

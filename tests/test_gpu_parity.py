@@ -176,7 +176,7 @@ def test_four_qubit_posterior_fidelity_within_monte_carlo_error(qst, oracle_mod,
     groups = ref["chain_pool"].reshape(32, R // 32, 16, 16).sum(axis=1)      # [32][D][D] sums
     total = groups.sum(axis=0)
     loo = (total[None] - groups) / ((R - R // 32) * S)                      # leave-one-group-out means
-    se = np.sqrt((32 - 1) / 32 * ((loo - loo.mean(axis=0)) ** 2).sum(axis=0))
+    se = np.sqrt((32 - 1) / 32 * (np.abs(loo - loo.mean(axis=0)) ** 2).sum(axis=0))   # |.|^2: complex entries
     assert np.all(np.abs(rho - ref["mean"]) <= 3 * se + 1e-9)
     f_loo = np.array([oracle_mod.fidelity(m, prob.truth) for m in loo])
     se_f = np.sqrt((32 - 1) / 32 * ((f_loo - f_loo.mean()) ** 2).sum())
