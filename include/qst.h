@@ -115,10 +115,16 @@ typedef struct {
     int32_t use_graph;      /* 1 (default): qst_run_chains replays one step captured as a CUDA graph
                                (the step counter lives on the device); 0: plain launches. Kernel
                                timing (qst_set_profiling) always uses plain launches */
-    int32_t autotune;       /* 1 (default): qst_create times the projection of every problem with
+    int32_t autotune;       /* 1 (default): qst_create times, for every problem, the projection with
                                each candidate number of column groups (the split of its N tiles
-                               over CTAs) and keeps the fastest; 0: a fixed rule */
+                               over CTAs) and, at 1-4 qubits with fewer chains than fill the GPU
+                               twice, the proposal kernel with 128-, 64- and 32-thread CTAs, and
+                               keeps the fastest of each (reported by qst_diagnostics); 0: fixed
+                               rules */
     int32_t prior;          /* qst_prior: QST_PRIOR_BURES (0, the default) or QST_PRIOR_HS */
+    int32_t propose_threads;/* 0 (default): the proposal kernel's CTA size at 1-4 qubits is 128 threads,
+                               or the autotuner's pick; 32, 64 or 128: that size, untimed (the chains
+                               are the same bits for every size) */
 } qst_sampler_cfg;
 
 /* Diagnostics of one problem (Sec. IV). */
@@ -136,6 +142,8 @@ typedef struct {
     double n_eff;            /* N R / tau_mean (Sec. IV) */
     uint32_t device_status;  /* raw status bits */
     uint32_t column_groups;  /* column groups of the projection schedule in use (autotuned or fixed) */
+    uint32_t propose_chains_per_cta;  /* chains per CTA of the proposal kernel (autotuned at 1-4 qubits) */
+    uint32_t accept_chains_per_cta;   /* chains per CTA of the accept kernel (one pooled-sum slot each) */
 } qst_diag;
 
 typedef struct qst_handle qst_handle;
@@ -156,7 +164,7 @@ const char *qst_status_string(qst_status status);
 const char *qst_last_error(void);
 /* Fills cfg with the paper's settings: beta0 0.1, M_A 500, window [0.2, 0.6], factor 1.1,
  * beta_max 1, T 1, no burn-in, 256 diagnostic chains, capacity 1024, l_max 200, FP32,
- * two Gram-Schmidt passes. */
+ * qr_passes 3 (one Gram-Schmidt pass and the refinement), graphs and the autotuner on. */
 void qst_default_config(qst_sampler_cfg *cfg);
 
 /* ---- lifecycle ---------------------------------------------------------------------- */

@@ -140,6 +140,9 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
         return fail(QST_ERR_INVALID_ARG, "unknown prior %d", cfg->prior);
     if (cfg->use_graph != 0 && cfg->use_graph != 1) return fail(QST_ERR_INVALID_ARG, "use_graph must be 0 or 1");
     if (cfg->autotune != 0 && cfg->autotune != 1) return fail(QST_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (cfg->propose_threads != 0 && cfg->propose_threads != 32 && cfg->propose_threads != 64 &&
+        cfg->propose_threads != 128)
+        return fail(QST_ERR_INVALID_ARG, "propose_threads must be 0, 32, 64 or 128");
     return QST_OK;
 }
 
@@ -395,6 +398,11 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         hp.part_slots = v.ngroups;
         for (int g : hp.group_choices) hp.part_slots = std::max(hp.part_slots, g);
         v.qr_passes = cfg->prior == QST_PRIOR_HS ? 0 : cfg->qr_passes;   // 0: no QR, W = G
+        // a forced proposal CTA size (only the default QR and the Hilbert-Schmidt prior have the
+        // smaller sizes; it must hold at least one chain)
+        if (cfg->propose_threads != 0 && v.D <= 16 && (v.qr_passes == 0 || v.qr_passes == 3) &&
+            cfg->propose_threads >= v.D)
+            v.propose_threads = cfg->propose_threads;
         v.accept_cpc = accept_chains_per_cta(v.R, v.d);
         v.n_slots = (int)((v.R + v.accept_cpc - 1) / v.accept_cpc);
         v.n_diag = (int)std::min<int64_t>(cfg->diag_chains, v.R);
@@ -634,6 +642,7 @@ void qst_default_config(qst_sampler_cfg *cfg) {
     cfg->qr_passes = 3;
     cfg->use_graph = 1;
     cfg->autotune = 1;
+    cfg->propose_threads = 0;
 }
 
 qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_problems, const qst_sampler_cfg *cfg,
@@ -680,6 +689,60 @@ qst_status autotune_groups(qst_handle *h) {
             }
         }
         hp.v.ngroups = best;
+        if (st != QST_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+// Times the proposal kernel of every problem of 1-4 qubits with 128-, 64- and 32-thread CTAs
+// (16, 8, 4 ... chains per CTA at four qubits) and keeps the fastest.  A problem whose
+// 128-thread grid already fills every SM twice keeps 128 untimed.  The proposal writes only
+// the proposal buffers, which hold nothing the chains need between steps, so the timing
+// launches (step 1, one warm-up and three timed) change no chain state.
+qst_status autotune_propose(qst_handle *h) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms <= 0)
+        sms = 148;
+    cudaEvent_t e0, e1;
+    QST_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    QST_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    qst_status st = QST_OK;
+    for (auto &hp : h->plan.probs) {
+        ProblemView &v = hp.v;
+        if (v.D > 16 || (v.qr_passes != 0 && v.qr_passes != 3) || h->cfg.propose_threads != 0) continue;
+        const int64_t blocks128 = (v.R + 128 / v.D - 1) / (128 / v.D);
+        if (blocks128 >= 2 * 5 * (int64_t)sms) continue;
+        int best = 128;
+        float best_ms = 0.0f;
+        for (int threads : {128, 64, 32}) {
+            if (threads < v.D) continue;
+            v.propose_threads = threads;
+            auto run = [&] {
+                return launch(h, QST_KERNEL_PROPOSE, "autotune propose", [&] {
+                    return launch_propose(v, MODE_STEP, 1u, nullptr, nullptr, 0, is_tc(h), nullptr, h->d_status,
+                                          h->stream);
+                });
+            };
+            st = run();
+            if (st != QST_OK) break;
+            if (cudaEventRecord(e0, h->stream) != cudaSuccess) { st = fail(QST_ERR_CUDA, "autotune: event"); break; }
+            for (int r = 0; r < 3 && st == QST_OK; ++r) st = run();
+            if (st != QST_OK) break;
+            float ms = 0.0f;
+            if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = fail(QST_ERR_CUDA, "autotune: timing");
+                break;
+            }
+            if (best_ms == 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best = threads;
+            }
+        }
+        v.propose_threads = best;
         if (st != QST_OK) break;
     }
     cudaEventDestroy(e0);
@@ -778,6 +841,7 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
     }
     if (cfg->autotune) {
         st = autotune_groups(h.get());
+        if (st == QST_OK) st = autotune_propose(h.get());
         if (st != QST_OK) return st;
     }
     *out = h.release();
@@ -985,6 +1049,8 @@ qst_status qst_diagnostics(qst_handle *h, int32_t problem, qst_diag *out, double
     cudaMemcpy(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost);
     out->device_status = status;
     out->column_groups = (uint32_t)(is_tc(h) ? hp->v.ngroups / 4 : hp->v.ngroups);
+    out->propose_chains_per_cta = (uint32_t)(v.D <= 16 ? v.propose_threads / v.D : (v.D == 32 ? 4 : 1));
+    out->accept_chains_per_cta = (uint32_t)v.accept_cpc;
     if (st != QST_OK) return st;
     double bmin = 1e300, bmax = -1e300, bsum = 0.0;
     int64_t acc_sum = 0, nonfinite = 0;

@@ -51,10 +51,10 @@ constexpr int kThreads = 128;
 //           triangular solve reads; area B then holds H's original columns during the
 //           refinement's products.  At D = 16 the Q planes are unpadded there (area A stays at
 //           W's 576 floats), which keeps five CTAs on an SM.
-template <int D, int PASSES = 2>
+template <int D, int PASSES = 2, int THREADS = kThreads>
 struct Shape {
     static constexpr int d = D * D;
-    static constexpr int chains_per_block = kThreads / D;
+    static constexpr int chains_per_block = THREADS / D;
     static constexpr int row_stride = D + 2;                    // float2 per row of W (padded)
     static constexpr int qcol = (PASSES == 3 && D == 16) ? D : D + 4;   // floats per column of a Q plane
     static constexpr int pk_stride = D + 1;                     // floats per row of the staged rho
@@ -243,9 +243,12 @@ struct ProposeArgs {
     Philox::RoundKeys rk;        // the generator's round keys for `seed`
 };
 
-template <int D, int PASSES>
-__global__ void __launch_bounds__(kThreads, 5) propose_kernel(ProposeArgs a) {
-    using S = Shape<D, PASSES>;
+// THREADS: the CTA size (chains per CTA = THREADS / D); 128 by default, 64 or 32 when the
+// autotuner finds that a small problem covers more SMs that way.  The register budget per
+// thread is the same for every size (five 128-thread CTAs' worth per SM).
+template <int D, int PASSES, int THREADS = kThreads>
+__global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kernel(ProposeArgs a) {
+    using S = Shape<D, PASSES, THREADS>;
     constexpr int d = S::d;
     constexpr int nx = 4 * d;
     constexpr int RS = S::row_stride;
@@ -1524,6 +1527,26 @@ cudaError_t launch_propose_d32(const ProposeArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int D, int PASSES, int THREADS>
+cudaError_t launch_propose_small(const ProposeArgs &a, int64_t rows, cudaStream_t s) {
+    using S = Shape<D, PASSES, THREADS>;
+    const size_t smem = sizeof(float) * S::smem_floats * S::chains_per_block;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(propose_kernel<D, PASSES, THREADS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(propose_kernel<D, PASSES, THREADS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t blocks = (rows + S::chains_per_block - 1) / S::chains_per_block;
+    if (blocks == 0) return cudaSuccess;
+    propose_kernel<D, PASSES, THREADS><<<(unsigned)blocks, THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int D, int PASSES>
 cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, const StepState *step_dev,
                               const float *x_eval, int64_t rows, bool want_split, float *rho_norm_out, cudaStream_t s) {
@@ -1557,22 +1580,13 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
         if (a.split_tf) return cudaErrorNotSupported;   // the TF32 forms stop at D = 16
         return launch_propose_d32<WIDE_PASSES>(a, s);
     } else {
-        using S = Shape<D, PASSES>;
-        const size_t smem = sizeof(float) * S::smem_floats * S::chains_per_block;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e =
-                cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(propose_kernel<D, PASSES>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
+        // the CTA sizes the autotuner may pick are built for the default QR (3) and the
+        // Hilbert-Schmidt prior (0); other settings run 128-thread CTAs
+        if constexpr (PASSES == 0 || PASSES == 3) {
+            if (p.propose_threads == 32) return launch_propose_small<D, PASSES, 32>(a, rows, s);
+            if (p.propose_threads == 64) return launch_propose_small<D, PASSES, 64>(a, rows, s);
         }
-        const int64_t blocks = (rows + S::chains_per_block - 1) / S::chains_per_block;
-        if (blocks == 0) return cudaSuccess;
-        propose_kernel<D, PASSES><<<(unsigned)blocks, kThreads, smem, s>>>(a);
-        return cudaGetLastError();
+        return launch_propose_small<D, PASSES, kThreads>(a, rows, s);
     }
 }
 

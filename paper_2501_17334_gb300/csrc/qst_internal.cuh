@@ -171,7 +171,9 @@ struct ProblemView {
     double *trace_logl;          // [trace_steps][R]
     int trace_steps;
     int ngroups;                 // column groups of the projection (partial sums per group)
-    int qr_passes;               // 1 or 2 modified Gram-Schmidt passes; 0: no QR (Hilbert-Schmidt prior, W = G)
+    int qr_passes;               // 1 or 2 modified Gram-Schmidt passes, 3: one pass and the refinement; 0: no QR
+                                 // (Hilbert-Schmidt prior, W = G)
+    int propose_threads = 128;   // CTA size of the proposal kernel at D <= 16 (32, 64 or 128; autotuned)
 };
 
 struct SamplerParams {

@@ -47,7 +47,7 @@ class SamplerCfg(ctypes.Structure):
                 ("thin", ctypes.c_int32), ("burn_in", ctypes.c_int32), ("diag_chains", ctypes.c_int32),
                 ("traj_capacity", ctypes.c_int32), ("acf_lmax", ctypes.c_int32), ("trace_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("qr_passes", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("prior", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("prior", ctypes.c_int32), ("propose_threads", ctypes.c_int32)]
 
 
 class Diag(ctypes.Structure):
@@ -55,7 +55,8 @@ class Diag(ctypes.Structure):
                 ("accept_rate", ctypes.c_double), ("beta_min", ctypes.c_double), ("beta_mean", ctypes.c_double),
                 ("beta_max", ctypes.c_double), ("num_nonfinite", ctypes.c_int64), ("diag_chains", ctypes.c_int32),
                 ("acf_lmax", ctypes.c_int32), ("tau_mean", ctypes.c_double), ("tau_max", ctypes.c_double),
-                ("n_eff", ctypes.c_double), ("device_status", ctypes.c_uint32), ("column_groups", ctypes.c_uint32)]
+                ("n_eff", ctypes.c_double), ("device_status", ctypes.c_uint32), ("column_groups", ctypes.c_uint32),
+                ("propose_chains_per_cta", ctypes.c_uint32), ("accept_chains_per_cta", ctypes.c_uint32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}

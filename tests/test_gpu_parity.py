@@ -277,19 +277,30 @@ def test_graph_replay_matches_plain_launches(qst, cuda_ok, prec):
 
 @pytest.mark.parametrize("prec", PRECISIONS)
 def test_autotuned_schedule_gives_the_same_chains(qst, cuda_ok, prec):
-    """The autotuner only changes how the projection's N tiles are split over CTAs: the
-    partial sums are the same numbers associated differently in FP64, so the chains agree."""
-    prob = W.config_problem(2, num_chains=700, num_steps=30)
-    tuned = _sampler(qst, prob, prec, diag_chains=0, autotune=1)
-    fixed = _sampler(qst, prob, prec, diag_chains=0, autotune=0)
-    tuned.run_chains(30)
-    fixed.run_chains(30)
-    a, b = tuned.get_state(), fixed.get_state()
-    assert np.array_equal(a["accepts"], b["accepts"])
-    assert np.allclose(a["logl"], b["logl"], rtol=1e-12, atol=0)
-    assert tuned.diagnostics()["column_groups"] >= 1 and fixed.diagnostics()["column_groups"] >= 1
-    tuned.close()
-    fixed.close()
+    """The autotuner changes how the projection's N tiles are split over CTAs (the partial
+    sums are the same numbers associated differently in FP64) and how many chains share a
+    proposal CTA (the same per-chain arithmetic), so the chains agree: the latent states bit
+    for bit, log L to FP64 association.  Every proposal CTA size is forced once."""
+    for q, R in [(2, 700), (4, 300)]:
+        prob = W.config_problem(q, num_chains=R, num_steps=30)
+        tuned = _sampler(qst, prob, prec, diag_chains=0, autotune=1)
+        runs = [tuned] + [_sampler(qst, prob, prec, diag_chains=0, autotune=0, propose_threads=t)
+                          for t in (128, 64, 32)]
+        for s in runs:
+            s.run_chains(30)
+        a = tuned.get_state()
+        dg = tuned.diagnostics()
+        assert dg["column_groups"] >= 1
+        assert dg["propose_chains_per_cta"] in (128 >> q, 64 >> q, 32 >> q)
+        assert dg["accept_chains_per_cta"] >= 8
+        for s, t in zip(runs[1:], (128, 64, 32)):
+            b = s.get_state()
+            assert s.diagnostics()["propose_chains_per_cta"] == t >> q
+            assert np.array_equal(a["y"], b["y"]), (q, t)
+            assert np.array_equal(a["accepts"], b["accepts"])
+            assert np.allclose(a["logl"], b["logl"], rtol=1e-12, atol=0)
+        for s in runs:
+            s.close()
 
 
 def test_chain_offset_partition_is_exact(qst, cuda_ok):
