@@ -43,12 +43,12 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "788fb450d44d69a82b7b449dc9222407116b644f164f8f337849f60c51ec0273",
-                "chains": 32768, "bytes": 134.882304e6 + 162.290432e6},
+                "sha256": "e19de5ac7014bedd20814c9765501f1ba6de374f58ea2b0e3816c8c525f57798",
+                "chains": 32768, "bytes": 135.156992e6 + 161.061376e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "0f046db29f097b38ad8e2df865cad9b5f22ad35179d1616de5154f68f2e5df19",
-                "chains": 32768, "bytes": 51.399680e6 + 3.840000e6},
+                "sha256": "b5f8838cb1b252b8b3a4d31a7aa63fcda6bf8673262bf99e7a2d4c9b69f4d108",
+                "chains": 32768, "bytes": 51.399936e6 + 20.48e6},
 }
 
 def _sha256(path):
@@ -270,6 +270,7 @@ def other_configs(qst, W, oracle):
     ms_mixed = time_handle(qst, batch, qst.PREC_BF16X3, 20, 3)
     ms_plain = time_handle(qst, batch, qst.PREC_FP32, 3, 1)
     ms_pauli = time_handle(qst, batch, qst.PREC_PAULI, 20, 3)
+    ms_auto = time_handle(qst, batch, qst.PREC_AUTO, 20, 3)   # per problem the faster form (timed at creation)
     # six qubits (D = 64, 46656 projectors): the structured Pauli form is the one that covers it
     p6 = W.six_qubit_problem(num_chains=4096, num_steps=20)
     ms6, s6 = time_handle(qst, p6, qst.PREC_PAULI, 10, 3, keep=True)
@@ -282,7 +283,8 @@ def other_configs(qst, W, oracle):
         "qubits_hist": [sum(p.num_qubits == q for p in batch) for q in range(1, 6)],
         "ms_per_step_bf16x3": ms_mixed, "chain_steps_per_s_bf16x3": chains / (ms_mixed / 1000.0),
         "ms_per_step_fp32": ms_plain, "chain_steps_per_s_fp32": chains / (ms_plain / 1000.0),
-        "ms_per_step_pauli": ms_pauli, "chain_steps_per_s_pauli": chains / (ms_pauli / 1000.0)}
+        "ms_per_step_pauli": ms_pauli, "chain_steps_per_s_pauli": chains / (ms_pauli / 1000.0),
+        "ms_per_step_auto": ms_auto, "chain_steps_per_s_auto": chains / (ms_auto / 1000.0)}
     return out
 
 

@@ -58,12 +58,17 @@ typedef enum {
                             a comparison form, not an accurate one */
     QST_PREC_TF32X2 = 3, /* tcgen05 kind::tf32: rho = hi + lo, both TF32 (22 significant bits),
                             hi and lo products in two accumulators; 1..3 qubits */
-    QST_PREC_PAULI = 4   /* structured FP32 form for the Pauli POVMs only (NULL POVM arrays or
+    QST_PREC_PAULI = 4,  /* structured FP32 form for the Pauli POVMs only (NULL POVM arrays or
                             arrays equal to qst_pauli_povms): no projector matrix; the 6^Q
                             probabilities come from rho by one split per qubit, each a few FP32
                             adds of the parent block's entries (about 3.5 * 6^Q adds per chain
                             against 2 * 24^Q FLOPs dense), every setting renormalised by its own
                             sum; 1..6 qubits (6 only with NULL POVM arrays) */
+    QST_PREC_AUTO = 5    /* per problem, the faster of the forms that apply to it: BF16X3 where its
+                            packed projectors are exact in bf16 (1..5 qubits), PAULI where its POVMs
+                            are the Pauli set (1..6 qubits), FP32 if neither; qst_create times the
+                            candidates (with autotune; else PAULI from five qubits on, BF16X3 below)
+                            and qst_diagnostics reports the form in use */
 } qst_precision;
 
 /* Prior of rho, i.e. the map from the latent Gaussian vector x to rho (Algorithm 1 is the
@@ -144,6 +149,7 @@ typedef struct {
     uint32_t column_groups;  /* column groups of the projection schedule in use (autotuned or fixed) */
     uint32_t propose_chains_per_cta;  /* chains per CTA of the proposal kernel (autotuned at 1-4 qubits) */
     uint32_t accept_chains_per_cta;   /* chains per CTA of the accept kernel (one pooled-sum slot each) */
+    int32_t projection_form;          /* qst_precision of the projection in use (QST_PREC_AUTO picks one) */
 } qst_diag;
 
 typedef struct qst_handle qst_handle;

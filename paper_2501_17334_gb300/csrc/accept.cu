@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) accept_kernel(AcceptArgs a) {
             if (a.mode == MODE_INIT) {
                 acc = 1;
                 p.logl_cur[c] = logl_prop;
-                p.cur[c] ^= 1;
+                p.cur[c] = 1;   // the initial proposal always lands in slot 1
             } else {
                 // accept test: alpha ~ U(0,1), accept iff log alpha < log L(y') - log L(y)
                 const uint32_t chain_id = (uint32_t)(p.chain_offset + c);

@@ -101,6 +101,11 @@ struct HostProblem {
     int Q = 0, K = 0, KDmax = 0;
     int part_slots = 0;               // partial sums per chain the workspace holds (largest schedule)
     std::vector<int> group_choices;   // candidate ngroups values for the autotuner
+    // QST_PREC_AUTO: the forms this problem's projection can take, and the tensor-core form's
+    // column-group rule and candidates (kept while the structured Pauli form is in use)
+    bool can_tc = false, can_pauli = false;
+    int tc_groups_rule = 0;
+    std::vector<int> tc_group_choices;
     double beta0 = 0.0;
     Layout off{};
     std::vector<float> P32;
@@ -133,7 +138,7 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
     if (cfg->diag_chains < 0 || cfg->traj_capacity < 0 || cfg->acf_lmax < 0 || cfg->trace_steps < 0)
         return fail(QST_ERR_INVALID_ARG, "diagnostic sizes must be >= 0");
     if (cfg->precision != QST_PREC_FP32 && cfg->precision != QST_PREC_BF16X3 && cfg->precision != QST_PREC_TF32 &&
-        cfg->precision != QST_PREC_TF32X2 && cfg->precision != QST_PREC_PAULI)
+        cfg->precision != QST_PREC_TF32X2 && cfg->precision != QST_PREC_PAULI && cfg->precision != QST_PREC_AUTO)
         return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
     if (cfg->qr_passes < 1 || cfg->qr_passes > 3) return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1, 2 or 3");
     if (cfg->prior != QST_PRIOR_BURES && cfg->prior != QST_PRIOR_HS)
@@ -154,7 +159,19 @@ void pauli_povms(int Q, std::vector<double> &re, std::vector<double> &im);
 
 // Qubits the forms cover: 1..5, and 6 for the structured Pauli form with the built-in POVMs
 // (NULL arrays: as dense [K*D][D][D] arrays they would take 3 GB).
-int max_qubits(const qst_sampler_cfg *cfg, bool builtin) { return cfg->precision == QST_PREC_PAULI && builtin ? 6 : 5; }
+int max_qubits(const qst_sampler_cfg *cfg, bool builtin) {
+    return (cfg->precision == QST_PREC_PAULI || cfg->precision == QST_PREC_AUTO) && builtin ? 6 : 5;
+}
+
+// The POVM arrays of d are the built-in Pauli set (to 1e-12).
+bool povms_are_pauli(const qst_problem_desc &d) {
+    if (d.num_povms != (int32_t)std::lround(std::pow(3.0, d.num_qubits))) return false;
+    std::vector<double> pre, pim;
+    pauli_povms(d.num_qubits, pre, pim);
+    for (size_t e = 0; e < pre.size(); ++e)
+        if (std::fabs(d.povm_re[e] - pre[e]) > 1e-12 || std::fabs(d.povm_im[e] - pim[e]) > 1e-12) return false;
+    return true;
+}
 
 qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sampler_cfg *cfg) {
     const bool builtin = !d.povm_re && !d.povm_im;   // only the Pauli form keeps them unmaterialised
@@ -180,7 +197,8 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
     for (int m = 0; m < KD; ++m)
         if (d.counts[m] < 0) return fail(QST_ERR_INVALID_ARG, "problem %d: negative count at %d", idx, m);
     if (builtin) {   // the built-in Pauli set (make_plan checked num_povms = 3^Q)
-        if (cfg->precision != QST_PREC_PAULI) return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
+        if (cfg->precision != QST_PREC_PAULI && cfg->precision != QST_PREC_AUTO)
+            return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
         return QST_OK;
     }
     // Hermitian elements, completeness per setting
@@ -261,15 +279,19 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
     std::vector<qst_problem_desc> probs_v(probs_in, probs_in + n);
     std::vector<std::vector<double>> pauli_store;
     pauli_store.reserve(2 * (size_t)n);
+    std::vector<char> builtin_in(n, 0);
+    const bool autof = cfg->precision == QST_PREC_AUTO;
     for (int i = 0; i < n; ++i) {
         qst_problem_desc &d = probs_v[i];
         if (d.povm_re || d.povm_im) continue;
+        builtin_in[i] = 1;
         if (d.num_qubits < 1 || d.num_qubits > max_qubits(cfg, true))
             return fail(QST_ERR_INVALID_ARG, "problem %d: num_qubits %d outside 1..%d", i, d.num_qubits,
                         max_qubits(cfg, true));
         if (d.num_povms != (int32_t)std::lround(std::pow(3.0, d.num_qubits)))
             return fail(QST_ERR_INVALID_ARG, "problem %d: the built-in Pauli POVMs need num_povms = 3^Q", i);
         if (cfg->precision == QST_PREC_PAULI) continue;   // never reads the arrays
+        if (autof && d.num_qubits > 5) continue;         // only the structured form goes that far
         pauli_store.emplace_back();
         pauli_store.emplace_back();
         std::vector<double> &re = pauli_store[pauli_store.size() - 2], &im = pauli_store.back();
@@ -304,9 +326,15 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         v.chain_offset = d.chain_offset;
         v.seed = d.seed;
         hp.beta0 = d.beta0 > 0.0 ? d.beta0 : cfg->beta0;
-        const int kind = tc_kind_of(cfg->precision);
-        const bool tc = kind != TC_NONE;
-        const bool pauli = cfg->precision == QST_PREC_PAULI;
+        int kind = tc_kind_of(cfg->precision);
+        bool pauli = cfg->precision == QST_PREC_PAULI;
+        if (autof) {   // the forms that apply; the choice between them comes after the packing
+            hp.can_pauli = builtin_in[i] || povms_are_pauli(d);
+            hp.can_tc = d.povm_re != nullptr && tc_supported(TC_BF16X3, v.D);
+            kind = hp.can_tc ? TC_BF16X3 : TC_NONE;
+            pauli = false;
+        }
+        bool tc = kind != TC_NONE;
         v.tc_kind = kind;
         v.pauli = pauli ? 1 : 0;
         if (tc) {
@@ -319,12 +347,22 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         hp.KDmax = std::max(v.KD_pad, v.KD_tc);
         // packed projectors
         std::vector<double> P;
-        if (!pauli) {   // the structured form never reads a projector matrix
+        if (!pauli && d.povm_re) {   // the structured form never reads a projector matrix
             P.resize((size_t)v.d * v.KD);
             pack_projectors(v.D, v.KD, d.povm_re, d.povm_im, P.data(), v.KD);
             hp.P32.assign((size_t)v.d_pad * v.KD_pad, 0.0f);
             for (int r = 0; r < v.d; ++r)
                 for (int m = 0; m < v.KD; ++m) hp.P32[(size_t)r * v.KD_pad + m] = (float)P[(size_t)r * v.KD + m];
+        }
+        if (kind == TC_BF16X3 && autof) {   // AUTO: the tensor-core form only where P is exact in bf16
+            for (size_t e = 0; e < P.size() && hp.can_tc; ++e) hp.can_tc = bf16_exact(P[e]);
+            if (!hp.can_tc) {
+                kind = TC_NONE;
+                tc = false;
+                v.tc_kind = TC_NONE;
+                v.KD_tc = 0;
+                hp.KDmax = v.KD_pad;
+            }
         }
         if (kind == TC_BF16X3) {
             hp.Pbf.assign((size_t)v.KD_tc * v.d_pad, __float2bfloat16_rn(0.0f));
@@ -372,23 +410,31 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         }
         v.C0 = C0;
         v.Ntot = Ntot;
-        if (pauli) {
+        if (pauli || hp.can_pauli) {
             pauli_tree_order(hp.Q, hp.pauli_perm);
             pauli_weights(hp.Q, hp.pauli_perm, hp.cnt.data(), hp.invf.data(), hp.pauli_wq, hp.pauli_wc);
         }
+        if (autof) {   // the rule without timing: the structured form from five qubits on or without P
+            pauli = hp.can_pauli && (v.D >= 32 || !hp.can_tc);
+            v.pauli = pauli ? 1 : 0;
+        }
         // column groups: a fixed rule, and the candidates the autotuner may time instead
+        if (tc) {
+            hp.tc_groups_rule = tc_ngroups(v, v.R);
+            const int ntiles = v.KD_tc / tc_column_tile(v.D, v.KD);
+            if (v.D == 32) {
+                hp.tc_group_choices = {hp.tc_groups_rule};
+            } else {
+                for (int g = 1; g < ntiles; g *= 2) hp.tc_group_choices.push_back(4 * g);
+                hp.tc_group_choices.push_back(4 * ntiles);
+            }
+        }
         if (pauli) {
             v.ngroups = 1;
             hp.group_choices = {1};
         } else if (tc) {
-            v.ngroups = tc_ngroups(v, v.R);
-            const int ntiles = v.KD_tc / tc_column_tile(v.D, v.KD);
-            if (v.D == 32) {
-                hp.group_choices = {v.ngroups};
-            } else {
-                for (int g = 1; g < ntiles; g *= 2) hp.group_choices.push_back(4 * g);
-                hp.group_choices.push_back(4 * ntiles);
-            }
+            v.ngroups = hp.tc_groups_rule;
+            hp.group_choices = hp.tc_group_choices;
         } else {
             v.ngroups = fp32_ngroups(v, v.R);
             const int nt = v.KD_pad / 128;
@@ -397,6 +443,7 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         }
         hp.part_slots = v.ngroups;
         for (int g : hp.group_choices) hp.part_slots = std::max(hp.part_slots, g);
+        for (int g : hp.tc_group_choices) hp.part_slots = std::max(hp.part_slots, g);
         v.qr_passes = cfg->prior == QST_PRIOR_HS ? 0 : cfg->qr_passes;   // 0: no QR, W = G
         // a forced proposal CTA size (only the default QR and the Hilbert-Schmidt prior have the
         // smaller sizes; it must hold at least one chain)
@@ -545,9 +592,10 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     v.invf = reinterpret_cast<const float *>(b + L.invf);
     v.ptot = reinterpret_cast<const float *>(b + L.ptot);
     v.colw = reinterpret_cast<const float4 *>(b + L.colw);
-    v.pauli_wq = v.pauli ? reinterpret_cast<const float4 *>(b + L.pauli_wq) : nullptr;
-    v.pauli_wc = v.pauli ? reinterpret_cast<const float2 *>(b + L.pauli_wc) : nullptr;
-    v.pauli_perm = v.pauli ? reinterpret_cast<const int32_t *>(b + L.pauli_perm) : nullptr;
+    const bool pauli_buffers = !hp.pauli_wq.empty();
+    v.pauli_wq = pauli_buffers ? reinterpret_cast<const float4 *>(b + L.pauli_wq) : nullptr;
+    v.pauli_wc = pauli_buffers ? reinterpret_cast<const float2 *>(b + L.pauli_wc) : nullptr;
+    v.pauli_perm = pauli_buffers ? reinterpret_cast<const int32_t *>(b + L.pauli_perm) : nullptr;
     v.y = reinterpret_cast<float *>(b + L.y);
     v.cur = reinterpret_cast<uint8_t *>(b + L.cur);
     v.rho_cur = reinterpret_cast<float *>(b + L.rho_cur);
@@ -567,7 +615,8 @@ qst_status bind_problem(qst_handle *h, HostProblem &hp) {
     return QST_OK;
 }
 
-bool is_tc(const qst_handle *h) { return tc_kind_of(h->cfg.precision) != TC_NONE; }
+// the problem's projection runs on the tensor cores (and so needs the split operand)
+bool uses_tc(const ProblemView &v) { return v.tc_kind != TC_NONE && !v.pauli; }
 
 // proposal -> projection -> (accept) for one problem
 qst_status enqueue_projection(qst_handle *h, HostProblem &hp, int64_t rows, float *p_out) {
@@ -577,7 +626,7 @@ qst_status enqueue_projection(qst_handle *h, HostProblem &hp, int64_t rows, floa
             return launch_project_pauli(v, v.rho_prop, rows, v.logl_part, p_out, h->stream);
         });
     }
-    if (is_tc(h)) {
+    if (v.tc_kind != TC_NONE) {
         return launch(h, QST_KERNEL_PROJECT, "projection (tcgen05)", [&] {
             return launch_project_tc(hp.tc, v, rows, v.logl_part, p_out, h->d_status, h->stream);
         });
@@ -590,7 +639,7 @@ qst_status enqueue_projection(qst_handle *h, HostProblem &hp, int64_t rows, floa
 qst_status enqueue_init(qst_handle *h, HostProblem &hp) {
     ProblemView &v = hp.v;
     qst_status st = launch(h, QST_KERNEL_PROPOSE, "propose (init)", [&] {
-        return launch_propose(v, MODE_INIT, 0u, nullptr, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
+        return launch_propose(v, MODE_INIT, 0u, nullptr, nullptr, 0, uses_tc(v), nullptr, h->d_status, h->stream);
     });
     if (st != QST_OK) return st;
     st = enqueue_projection(h, hp, v.R, nullptr);
@@ -657,6 +706,52 @@ qst_status qst_workspace_size(const qst_problem_desc *problems, int32_t num_prob
 
 namespace {
 
+// QST_PREC_AUTO: for every problem whose projection can run both on the tensor cores and in
+// the structured Pauli form, times both (each on its rule's column groups, one warm-up launch
+// and three timed ones, on a fresh step-1 proposal that carries the tensor cores' split
+// operand) and keeps the faster.  A problem whose form changes is initialised again, so that
+// the cached log L of its current state comes from the form it will run.
+qst_status autotune_form(qst_handle *h) {
+    if (h->cfg.precision != QST_PREC_AUTO) return QST_OK;
+    cudaEvent_t e0, e1;
+    QST_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    QST_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    qst_status st = QST_OK;
+    for (auto &hp : h->plan.probs) {
+        ProblemView &v = hp.v;
+        if (!(hp.can_tc && hp.can_pauli)) continue;
+        const int first = v.pauli;
+        v.pauli = 0;
+        st = launch(h, QST_KERNEL_PROPOSE, "autotune form (proposal)", [&] {
+            return launch_propose(v, MODE_STEP, 1u, nullptr, nullptr, 0, true, nullptr, h->d_status, h->stream);
+        });
+        float ms[2] = {0.0f, 0.0f};
+        for (int f = 0; f < 2 && st == QST_OK; ++f) {
+            v.pauli = f;   // 0: tensor cores, 1: structured Pauli
+            v.ngroups = f ? 1 : hp.tc_groups_rule;
+            st = enqueue_projection(h, hp, v.R, nullptr);
+            if (st != QST_OK) break;
+            if (cudaEventRecord(e0, h->stream) != cudaSuccess) { st = fail(QST_ERR_CUDA, "autotune: event"); break; }
+            for (int r = 0; r < 3 && st == QST_OK; ++r) st = enqueue_projection(h, hp, v.R, nullptr);
+            if (st != QST_OK) break;
+            if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms[f], e0, e1) != cudaSuccess)
+                st = fail(QST_ERR_CUDA, "autotune: timing");
+        }
+        if (st != QST_OK) break;
+        v.pauli = ms[1] < ms[0] ? 1 : 0;
+        v.ngroups = v.pauli ? 1 : hp.tc_groups_rule;
+        hp.group_choices = v.pauli ? std::vector<int>{1} : hp.tc_group_choices;
+        if (v.pauli != first) {
+            st = enqueue_init(h, hp);
+            if (st != QST_OK) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 // Times the projection of every problem with each candidate column-group count (one warm-up
 // launch, then three timed ones on the handle's stream, on the proposal buffers that hold
 // rho(y0) after initialisation) and keeps the fastest.  Only the schedule changes: every
@@ -722,7 +817,7 @@ qst_status autotune_propose(qst_handle *h) {
             v.propose_threads = threads;
             auto run = [&] {
                 return launch(h, QST_KERNEL_PROPOSE, "autotune propose", [&] {
-                    return launch_propose(v, MODE_STEP, 1u, nullptr, nullptr, 0, is_tc(h), nullptr, h->d_status,
+                    return launch_propose(v, MODE_STEP, 1u, nullptr, nullptr, 0, uses_tc(v), nullptr, h->d_status,
                                           h->stream);
                 });
             };
@@ -790,7 +885,7 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
         const Layout &L = hp.off;
         QST_CUDA(cudaMemcpyAsync(h->ws + L.P32, hp.P32.data(), sizeof(float) * hp.P32.size(), cudaMemcpyHostToDevice,
                                  h->stream), "upload P");
-        if (v.pauli) {
+        if (!hp.pauli_wq.empty()) {
             QST_CUDA(cudaMemcpyAsync(h->ws + L.pauli_wq, hp.pauli_wq.data(), sizeof(float4) * hp.pauli_wq.size(),
                                      cudaMemcpyHostToDevice, h->stream), "upload deviance weights");
             QST_CUDA(cudaMemcpyAsync(h->ws + L.pauli_wc, hp.pauli_wc.data(), sizeof(float2) * hp.pauli_wc.size(),
@@ -829,7 +924,7 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
                  "upload proposal coefficients");
         // pageable copies above are staged synchronously; keep the host vectors alive until then
         QST_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
-        if (is_tc(h.get())) {
+        if (v.tc_kind != TC_NONE) {
             cudaError_t e = tc_plan_create(v, v.rho_split, v.R, &hp.tc);
             if (e != cudaSuccess) return cuda_fail(e, "tensor-core plan");
         }
@@ -840,7 +935,8 @@ qst_status qst_create(const qst_problem_desc *problems, int32_t num_problems, co
         std::vector<float>().swap(hp.Ptf);
     }
     if (cfg->autotune) {
-        st = autotune_groups(h.get());
+        st = autotune_form(h.get());
+        if (st == QST_OK) st = autotune_groups(h.get());
         if (st == QST_OK) st = autotune_propose(h.get());
         if (st != QST_OK) return st;
     }
@@ -857,7 +953,7 @@ namespace {
 qst_status enqueue_problem(qst_handle *h, HostProblem &hp) {
     ProblemView &v = hp.v;
     qst_status st = launch(h, QST_KERNEL_PROPOSE, "propose", [&] {
-        return launch_propose(v, MODE_STEP, 0u, h->d_step, nullptr, 0, is_tc(h), nullptr, h->d_status, h->stream);
+        return launch_propose(v, MODE_STEP, 0u, h->d_step, nullptr, 0, uses_tc(v), nullptr, h->d_status, h->stream);
     });
     if (st != QST_OK) return st;
     st = enqueue_projection(h, hp, v.R, nullptr);
@@ -1048,7 +1144,11 @@ qst_status qst_diagnostics(qst_handle *h, int32_t problem, qst_diag *out, double
     uint32_t status = 0;
     cudaMemcpy(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost);
     out->device_status = status;
-    out->column_groups = (uint32_t)(is_tc(h) ? hp->v.ngroups / 4 : hp->v.ngroups);
+    out->column_groups = (uint32_t)(uses_tc(hp->v) ? hp->v.ngroups / 4 : hp->v.ngroups);
+    out->projection_form = v.pauli ? QST_PREC_PAULI : uses_tc(v) ? h->cfg.precision == QST_PREC_AUTO
+                                                                        ? (int32_t)QST_PREC_BF16X3
+                                                                        : h->cfg.precision
+                                                 : (int32_t)QST_PREC_FP32;
     out->propose_chains_per_cta = (uint32_t)(v.D <= 16 ? v.propose_threads / v.D : (v.D == 32 ? 4 : 1));
     out->accept_chains_per_cta = (uint32_t)v.accept_cpc;
     if (st != QST_OK) return st;
@@ -1222,7 +1322,7 @@ qst_status qst_evaluate(qst_handle *h, int32_t problem, const float *x, int64_t 
     if (n == 0) return QST_OK;
     if (!x) return fail(QST_ERR_INVALID_ARG, "x is NULL");
     st = launch(h, QST_KERNEL_PROPOSE, "propose (eval)", [&] {
-        return launch_propose(v, MODE_EVAL, 0u, nullptr, x, n, is_tc(h), rho, h->d_status, h->stream);
+        return launch_propose(v, MODE_EVAL, 0u, nullptr, x, n, uses_tc(v), rho, h->d_status, h->stream);
     });
     if (st != QST_OK) return st;
     st = enqueue_projection(h, *hp, n, p);

@@ -146,8 +146,8 @@ __device__ __forceinline__ void split_level(const float *in, float *out, int par
 // 2 q of X+- and Y+- (the 1/2 sits in their weights), (e00, e11) are q of Z+-.
 template <bool P_OUT>
 __device__ __forceinline__ void last_split(float e00, float e01, float e10, float e11, const PauliArgs &a, int j0,
-                                           int stride, int blk, float2 &dev, int &xmin, float (&sh)[3],
-                                           float (&sl)[3], float *p_row, int o0, float inv_t) {
+                                           int stride, int blk, float2 &dev, float2 &comp, int &xmin,
+                                           float (&sh)[3], float (&sl)[3], float *p_row, int o0, float inv_t) {
     float4 wq[3];   // the three pairs' weights, requested before the arithmetic that needs them
     float2 wc[3];
 #pragma unroll
@@ -164,7 +164,7 @@ __device__ __forceinline__ void last_split(float e00, float e01, float e10, floa
         const float2 cnt = wc[j];
         const float2 x = fma2(q2[j], make_float2(w.x, w.y), make_float2(w.z, w.w));
         xmin = min(xmin, min(__float_as_int(x.x), __float_as_int(x.y)));
-        dev = fma2(cnt, log_poly2(x), dev);
+        kahan_fma2(dev, comp, cnt, log_poly2(x));   // compensated: far from the posterior the terms are O(c)
         // the setting sum of this pair's q (2 q for X, Y): high parts on the grid, exactly
         const float2 C = splat2(j < 2 ? 24.0f : 12.0f);
         const float2 hq = sub2(add2(q2[j], C), C), lq = sub2(q2[j], hq);
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
     constexpr int D = S::D, d = S::d, TPC = S::TPC, CPB = S::CPB, NB = S::NB;
     constexpr int NS = S::NS;
     extern __shared__ __align__(16) float smem[];
-    __shared__ float part[S::threads];
+    __shared__ float part[S::threads], part_lo[S::threads];
     __shared__ float4 tinfo[CPB];                                   // (t_hi, t_lo, 1 / t_hi) per chain
     __shared__ float2 spart_s[(Q >= 3 && !S::alias_spart) ? CPB * NS * S::slot_stride : 1];   // setting sums per block
     const int g = threadIdx.x / TPC, lt = threadIdx.x - g * TPC;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
         __syncthreads();
     }
 
-    float2 dev = splat2(0.0f);
+    float2 dev = splat2(0.0f), comp = splat2(0.0f);   // deviance sum (dev - comp)
     int xmin = 0x7fffffff;   // smallest bit pattern of a log argument (sign included)
     float inv_t = 0.0f;
     float *p_row = nullptr;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
     for (int j = 0; j < 3; ++j) sh[j] = sl[j] = 0.0f;
     if constexpr (Q == 1) {
         const float4 m = *reinterpret_cast<const float4 *>(bufA);   // [[a, Re b], [Im b*, e]]
-        last_split<P_OUT>(m.x, m.y, m.z, m.w, a, 0, 1, 0, dev, xmin, sh, sl, p_row, 0, inv_t);
+        last_split<P_OUT>(m.x, m.y, m.z, m.w, a, 0, 1, 0, dev, comp, xmin, sh, sl, p_row, 0, inv_t);
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             extra += renorm(sh[j], sl[j], j < 2 ? 0.5f : 1.0f, j);
@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
             // sums of settings (s, j) are complete for this block
 #pragma unroll
             for (int c1 = 0; c1 < 6; ++c1) {
-                last_split<P_OUT>(e00[c1], e01[c1], e10[c1], e11[c1], a, 3 * c1, NB, blk, dev, xmin, sh, sl, p_row,
-                                  36 * blk + 6 * c1, inv_t);
+                last_split<P_OUT>(e00[c1], e01[c1], e10[c1], e11[c1], a, 3 * c1, NB, blk, dev, comp, xmin, sh, sl,
+                                  p_row, 36 * blk + 6 * c1, inv_t);
                 if (c1 & 1) {
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
@@ -328,26 +328,31 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
             extra += renorm(vh, vl, slot % 3 < 2 ? 0.5f : 1.0f, k);
         }
     }
-    // a counted outcome with q <= 0 (or below the normal range): log L = -inf
-    const float acc = (xmin < 0x00800000) ? -INFINITY : (dev.x + dev.y) + extra;
+    // this thread's sum as an unevaluated pair (hi, lo): the two halves of the compensated sum
+    // added exactly, the compensations and the small renormalisation terms in lo; a counted
+    // outcome with q <= 0 (or below the normal range) makes log L = -inf
+    float acc_hi, acc_lo;
+    two_sum(dev.x, dev.y, acc_hi, acc_lo);
+    acc_lo += extra - (comp.x + comp.y);
+    if (xmin < 0x00800000) acc_hi = -INFINITY;
 
-    // the chain's threads' FP32 sums, added in thread order as an unevaluated FP32 pair (hi, lo)
-    // by one thread per chain; the CTA's chains sit in its first threads, so the FP64 result
-    // (scarce FP64 instructions, each costing its warp the same however many lanes are active)
-    // takes a few warp instructions per CTA
+    // the chain's threads' pairs, added in thread order (two-sum of the high parts) by one thread
+    // per chain; the CTA's chains sit in its first threads, so the FP64 result (scarce FP64
+    // instructions, each costing its warp the same however many lanes are active) takes a few
+    // warp instructions per CTA
     if constexpr (TPC == 1) {
-        if (active) a.out[c] = (double)acc;
+        if (active) a.out[c] = (double)acc_hi + (double)acc_lo;
     } else {
-        part[threadIdx.x] = acc;
+        part[threadIdx.x] = acc_hi;
+        part_lo[threadIdx.x] = acc_lo;
         __syncthreads();
         if (threadIdx.x < CPB) {
             const int64_t cc = (int64_t)blockIdx.x * CPB + threadIdx.x;
             float hi = 0.0f, lo = 0.0f;
-            for (int t = 0; t < TPC; ++t) {   // two-sum: hi + lo = the exact running sum, up to lo's rounding
-                const float x = part[threadIdx.x * TPC + t];
-                const float sum = hi + x, bp = sum - hi;
-                lo += (hi - (sum - bp)) + (x - bp);
-                hi = sum;
+            for (int t = 0; t < TPC; ++t) {
+                float e;
+                two_sum(hi, part[threadIdx.x * TPC + t], hi, e);
+                lo += e + part_lo[threadIdx.x * TPC + t];
             }
             if (cc < a.rows) a.out[cc] = (double)hi + (double)lo;
         }

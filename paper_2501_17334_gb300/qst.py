@@ -23,6 +23,7 @@ PREC_BF16X3 = 1
 PREC_TF32 = 2
 PREC_TF32X2 = 3
 PREC_PAULI = 4   # structured FP32 form, Pauli POVMs only
+PREC_AUTO = 5    # per problem the faster of the forms that apply (timed at creation)
 PRIOR_BURES = 0  # Algorithm 1
 PRIOR_HS = 1     # Hilbert-Schmidt: rho = G G^dag / Tr
 KERNEL_PROPOSE, KERNEL_PROJECT, KERNEL_ACCEPT, KERNEL_DIAG = range(4)
@@ -56,7 +57,8 @@ class Diag(ctypes.Structure):
                 ("beta_max", ctypes.c_double), ("num_nonfinite", ctypes.c_int64), ("diag_chains", ctypes.c_int32),
                 ("acf_lmax", ctypes.c_int32), ("tau_mean", ctypes.c_double), ("tau_max", ctypes.c_double),
                 ("n_eff", ctypes.c_double), ("device_status", ctypes.c_uint32), ("column_groups", ctypes.c_uint32),
-                ("propose_chains_per_cta", ctypes.c_uint32), ("accept_chains_per_cta", ctypes.c_uint32)]
+                ("propose_chains_per_cta", ctypes.c_uint32), ("accept_chains_per_cta", ctypes.c_uint32),
+                ("projection_form", ctypes.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
