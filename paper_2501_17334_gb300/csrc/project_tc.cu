@@ -126,14 +126,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-// One bounded try: the thread is suspended until the phase completes or about 1 ms has passed
-// (the time hint), so waiting warps do not take issue slots from the working ones.
+// One bounded try: the thread may be suspended until the phase completes or a system-dependent
+// time limit passes.  (A suspend-time hint of 1 ms, tried first, woke the waiting warps later:
+// the tensor-core kernel took 4% longer.)
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(parity), "r"(1000000u)
+        : "r"(bar), "r"(parity)
         : "memory");
     return done != 0;
 }
@@ -373,8 +374,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(smem_u32(&bar_b_empty[s]), 1);
         }
         mbar_init(smem_u32(&bar_acc_full), 1);
-        mbar_init(smem_u32(&bar_acc_empty), 4 * TC_EPI_PER_QUAD * 32);
-        for (int s = 0; s < 2; ++s) mbar_init(smem_u32(&bar_alo_full[s]), 4 * TC_EPI_PER_QUAD * 32);
+        mbar_init(smem_u32(&bar_acc_empty), 4 * TC_EPI_PER_QUAD);   // one arrival per epilogue warp
+        for (int s = 0; s < 2; ++s) mbar_init(smem_u32(&bar_alo_full[s]), 4 * TC_EPI_PER_QUAD);
         mbar_init(smem_u32(&bar_mma_done), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -550,7 +551,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         };
         auto alo_done = [&](uint32_t b) {
             tc_fence_before();
-            mbar_arrive(smem_u32(&bar_alo_full[b]));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_alo_full[b]));
         };
         if (T::lo_in_tmem && blockIdx.x < a.units) {
             for (int piece = 0; piece < NP; ++piece) alo_store(0u, piece, alo_fetch(blockIdx.x, piece));
@@ -595,7 +597,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     float vr[32];
                     tmem_ld32_pair(lane_base, lane_base + TC_REST_COL, v, vr);
                     tc_fence_before();
-                    mbar_arrive(smem_u32(&bar_acc_empty));   // both slices are in registers
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty));   // the warp's slices are in registers
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) {
                         const float2 q = add2(make_float2(v[i], v[i + 1]), make_float2(vr[i], vr[i + 1]));
@@ -605,7 +608,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 } else {
                     tmem_ld32(lane_base, v);
                     tc_fence_before();
-                    mbar_arrive(smem_u32(&bar_acc_empty));   // the slice is in registers
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty));   // the warp's slice is in registers
                 }
                 bool tile_neg_inf = false;
                 if (n0 < a.KD) {   // (columns past KD: the last tile's MMA did not write them)
@@ -721,7 +725,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
         mbar_init(smem_u32(&bar_acc_full), 1);
-        mbar_init(smem_u32(&bar_acc_empty), 4 * TC_EPI_PER_QUAD * 32);
+        mbar_init(smem_u32(&bar_acc_empty), 4 * TC_EPI_PER_QUAD);   // one arrival per epilogue warp
         mbar_init(smem_u32(&bar_mma_done), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -851,7 +855,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             tc_fence_before();
-            mbar_arrive(smem_u32(&bar_acc_empty));   // both accumulators' slices are in registers
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty));   // the warp's slices are in registers
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int n0 = t * TCW_N + col0 + 32 * half;   // one setting of 32 outcomes

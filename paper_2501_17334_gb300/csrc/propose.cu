@@ -36,6 +36,10 @@ namespace qst {
 namespace {
 
 constexpr int kThreads = 128;
+// the refinement of U (PASSES = 3): at most this many first-order passes, another one while the
+// chain's largest |Y| entry exceeds kRefineTol (the residual of a pass is about |Y|^2)
+constexpr int kRefinePasses = 3;
+constexpr float kRefineTol = 0x1p-14f;
 
 // Shared memory per chain (floats), laid out so every access is free of bank conflicts:
 //   area A: the real and imaginary planes of H's columns as they are orthogonalised (column
@@ -51,6 +55,7 @@ constexpr int kThreads = 128;
 //           triangular solve reads; area B then holds H's original columns during the
 //           refinement's products.  At D = 16 the Q planes are unpadded there (area A stays at
 //           W's 576 floats), which keeps five CTAs on an SM.
+
 template <int D, int PASSES = 2, int THREADS = kThreads>
 struct Shape {
     static constexpr int d = D * D;
@@ -65,14 +70,16 @@ struct Shape {
     static constexpr int smem_floats = (raw + 31) / 32 * 32 + 16;
 };
 
-// Box-Muller with the fast hardware log and sine/cosine: the angle is reduced to
-// 2 pi (v - 1/2) in (-pi, pi), where the intrinsics are accurate to ~2^-21 absolute, and
-// cos/sin(2 pi v) = -cos/-sin(2 pi (v - 1/2)).  v - 1/2 is exact.  The normals agree with
-// the FP64 Box-Muller of the same uniforms to about 1e-6 relative.
+// Box-Muller with the fast hardware log, reciprocal square root and sine/cosine: the angle is
+// reduced to 2 pi (v - 1/2) in (-pi, pi), where the intrinsics are accurate to ~2^-21
+// absolute, and cos/sin(2 pi v) = -cos/-sin(2 pi (v - 1/2)).  v - 1/2 is exact.  The radius
+// sqrt(t), t = -2 ln u >= 2^-23, is t rsqrt(t) (a few ulps).  The normals agree with the FP64
+// Box-Muller of the same uniforms to about 1e-6 relative.
 __device__ __forceinline__ void gaussian_pair_fast(uint32_t wu, uint32_t wv, float &z0, float &z1) {
     const float u = Philox::uniform(wu);
     const float v = Philox::uniform(wv);
-    const float radius = sqrtf(-2.0f * __logf(u));
+    const float t = -2.0f * __logf(u);
+    const float radius = t * rsqrtf(t);
     float s, c;
     __sincosf(6.283185307179586f * (v - 0.5f), &s, &c);
     z0 = -radius * c;
@@ -449,7 +456,12 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
         // So X^dag (called Y below) has: strictly lower part from the triangular system
         // lower(Y R) = lower(M), upper part N - conj(lower part)^T, real diagonal (N_jj - 1) / 2,
         // imaginary diagonal from the real diagonal of R; and U = Q1 V^-1 = Q1 (I - Y^dag) to
-        // first order (second order: (cond(H) 2^-24)^2, below FP32 rounding for cond(H) < 10^3).
+        // first order.  The step leaves about |Y|^2 (|Y| ~ cond(H) 2^-24): below FP32 rounding
+        // while every |Y| entry is below 2^-14 (cond(H) up to ~10^3).  A chain above that repeats
+        // the step from the refined U, its H and the same R; each pass squares the residual, and
+        // three passes cover cond(H) up to ~10^6.  (The posterior's chains reach cond(H) ~10^5:
+        // one chain in 1024 at configuration 4 after 2000 steps, which a single pass left 6e-3
+        // from the oracle's log L.)
         // The lower part of M and N - I are tiny differences of O(1) products, so they are formed
         // without rounding error: lane j forms row j (c < j: M_jc = q_j^dag h_c; c > j: N_jc =
         // q_j^dag q_c) with error-free products (sum_products_exact), its own q_j in (hr, hi) and
@@ -461,6 +473,26 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
         // (hre) and imaginary (him) planes, so that the lanes' writes of a step, a lane's reads
         // of its row and the reads of a column all hit distinct banks.
         auto cidx = [](int r, int cc) { return cc * D + (r ^ cc); };
+        // One pass.  `again`: a pass after the first (H's column and this lane's vector are read
+        // back first); `apply`: write the refined U (a further pass runs for the whole warp when
+        // any of its chains needs it, and the others discard theirs, so a chain's bits never
+        // depend on its neighbours).  Returns the chain's largest |Y| entry.
+        auto refine_pass = [&](bool again, bool apply) -> float {
+        if (again) {   // H's column j into area B again (it held C), U's column j as the vector
+#pragma unroll
+            for (int i = 0; i < D; i += (D >= 4 ? 4 : 1)) {
+                if constexpr (D >= 4) {
+                    *reinterpret_cast<float4 *>(hre + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 2 * d + j * D + i);
+                    *reinterpret_cast<float4 *>(him + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 3 * d + j * D + i);
+                } else {
+                    hre[j * D + i] = gsrc[2 * d + j * D + i];
+                    him[j * D + i] = gsrc[3 * d + j * D + i];
+                }
+            }
+            load_column2<D>(qre + j * QC, hr);
+            load_column2<D>(qim + j * QC, hi);
+            __syncwarp();
+        }
 #pragma unroll 1
         for (int cc = 0; cc < D; ++cc) {
             const bool lower = cc < j;   // M_jc = q_j^dag h_c; at c = j (and above) N_jc = q_j^dag q_c
@@ -518,6 +550,12 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
 #pragma unroll
         for (int c = 0; c < D; ++c)
             if (c == j) y[c] = ydiag;
+        // the chain's largest |Y| entry decides whether another pass follows
+        float ymax = 0.0f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) ymax = fmaxf(ymax, fmaxf(fabsf(y[c].x), fabsf(y[c].y)));
+#pragma unroll
+        for (int off = D / 2; off >= 1; off /= 2) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, off, D));
         // U = Q1 - Q1 Y^dag: column j is q_j - sum_k q_k conj(Y[j][k]); the correction is summed
         // on its own (it is small) and subtracted once.  Rows go in two halves: a half is
         // overwritten only after every lane has read that half of every column.
@@ -541,15 +579,26 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
                 }
             }
             __syncwarp();   // every lane has read this half of every q_k
+            if (apply) {
 #pragma unroll
-            for (int p = 0; p < HP; ++p) {
-                const int row = 2 * (half * HP + p);
-                float2 *ur = reinterpret_cast<float2 *>(qre + j * QC + row);
-                float2 *ui = reinterpret_cast<float2 *>(qim + j * QC + row);
-                *ur = sub2(*ur, cr[p]);
-                *ui = sub2(*ui, ci[p]);
+                for (int p = 0; p < HP; ++p) {
+                    const int row = 2 * (half * HP + p);
+                    float2 *ur = reinterpret_cast<float2 *>(qre + j * QC + row);
+                    float2 *ui = reinterpret_cast<float2 *>(qim + j * QC + row);
+                    *ur = sub2(*ur, cr[p]);
+                    *ui = sub2(*ui, ci[p]);
+                }
             }
             __syncwarp();
+        }
+        return ymax;
+        };
+        float ymax = refine_pass(false, true);
+#pragma unroll 1
+        for (int pass = 1; pass < kRefinePasses && __any_sync(0xffffffffu, ymax > kRefineTol); ++pass) {
+            const bool need = ymax > kRefineTol;
+            const float next = refine_pass(true, need);
+            ymax = need ? next : ymax;
         }
     }
 

@@ -76,9 +76,11 @@ struct Philox {
         return ctr;
     }
 
-    // Open-interval uniform from the top 23 bits: (2 m + 1) 2^-24, exact in float.
+    // Open-interval uniform from the top 23 bits m: (2 m + 1) 2^-24, exact in float.  Formed
+    // by bit operations: 1 + m 2^-23 is the float with m as its mantissa, and subtracting
+    // 1 - 2^-24 (a float) leaves (2 m + 1) 2^-24, representable, so the subtraction is exact.
     __device__ __forceinline__ static float uniform(uint32_t word) {
-        return __fmaf_rn((float)(word >> 9), 0x1p-23f, 0x1p-24f);
+        return __int_as_float(0x3f800000u | (word >> 9)) - 0x1.fffffep-1f;
     }
 
     // Box-Muller on one uniform pair: (sqrt(-2 ln u) cos 2 pi v, sqrt(-2 ln u) sin 2 pi v).

@@ -48,3 +48,34 @@ def test_small_sweep_writes_consistent_rows(qst, cuda_ok, tmp_path):
     with open(tmp_path / "tau.csv") as f:
         taus = [float(r["tau_mean"]) for r in csv.DictReader(f)]
     assert all(np.isfinite(t) for t in taus)
+
+
+def test_sweep_points_recomputed_by_the_oracle(qst, oracle_mod, cuda_ok, tmp_path):
+    """eps_F^2 (Eq. fro) and 1 - F (Eq. fid) of a small sweep, Q = 1, T in {1, 2}, R in {1, 8},
+    against the same quantities of the oracle's chains on the same data, seed and chain ids.
+
+    Every accept decision of those chains lies at least 1e-5 from its threshold in the oracle's
+    own trace (asserted below), far outside the GPU's log L error at one qubit, so the two chain
+    sets agree step for step and their pooled means differ only by FP32 rounding of rho."""
+    from paper_2501_17334_gb300 import experiment as E
+    keep, chains, thins = 256, (1, 8), (1, 2)
+    rows = E.sweep([1], [0, 1], list(chains), keep, str(tmp_path))
+    prob = E.paper_problem(1, max(chains))
+    means = {}
+    for t in thins:
+        r = oracle_mod.run(prob, num_chains=max(chains), num_steps=keep * t, thin=t, trace_steps=keep * t,
+                           want_chain_pool=True)
+        margin = np.abs(r["trace_log_alpha"] - (r["trace_logl_prop"] - r["trace_logl_cur"]))
+        assert np.nanmin(margin[np.isfinite(margin)]) > 1e-5
+        assert r["num_pooled"] == keep * max(chains)
+        means[(t, max(chains))] = r["mean"]
+        means[(t, 1)] = r["chain_pool"][0] / keep
+    ref = means[(max(thins), max(chains))]
+    frob = {(t, rr): e for q, t, rr, _, e in rows["frob"]}
+    fid = {(t, rr): f for q, t, rr, _, f in rows["fidelity"]}
+    for key, m in means.items():
+        eps = E.frobenius_sq(m, ref)
+        one_minus_f = 1.0 - E.fidelity(ref, m)
+        assert abs(frob[key] - eps) <= 1e-6 * np.sqrt(eps) + 1e-12, (key, frob[key], eps)
+        assert abs(fid[key] - one_minus_f) <= 1e-6, (key, fid[key], one_minus_f)
+    assert frob[(1, 1)] > frob[(1, 8)] > 0.0   # one chain is further from the reference pool than eight

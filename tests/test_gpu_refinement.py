@@ -1,0 +1,68 @@
+"""The refinement of U (Algorithm 1's QR beyond FP32) on ill-conditioned H.
+
+One first-order pass leaves U about (cond(H) 2^-24)^2 from the exact factor: invisible below
+cond(H) ~ 10^3, but the posterior's chains do reach cond(H) ~ 10^5 (one chain in 1024 at
+configuration 4 after 2000 steps), where one pass left rho ~1e-5 and log L ~6e-3 from the FP64
+oracle.  The kernel repeats the pass for such chains.  Here latent rows get an H with a
+prescribed condition number (Haar unitaries around log-spaced singular values) and the
+standard-normal G; rho and p must meet the parity bars of well-conditioned rows
+(test_gpu_parity.py) on every row.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_17334_gb300 import workload as W
+
+from tests._helpers import unpack_rho
+
+pytestmark = pytest.mark.gpu
+
+
+def _haar(rng, n):
+    z = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def _rows(q, kappas, per, seed):
+    """Latent rows (float32, the layout of Algorithm 1: G then H, each column-major real then
+    imaginary) whose H has condition number kappa."""
+    D = 1 << q
+    d = D * D
+    rng = np.random.default_rng(seed)
+    out = []
+    for kappa in kappas:
+        for _ in range(per):
+            s = np.sqrt(D) * np.logspace(0.0, -np.log10(kappa), D)
+            H = _haar(rng, D) @ np.diag(s) @ _haar(rng, D)
+            x = np.empty(4 * d)
+            x[:2 * d] = rng.standard_normal(2 * d)
+            x[2 * d:3 * d] = H.real.T.reshape(-1)   # column-major: element (i, j) at j D + i
+            x[3 * d:] = H.imag.T.reshape(-1)
+            out.append(x)
+    return np.array(out, dtype=np.float32)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("q", [3, 4])
+def test_ill_conditioned_h_meets_the_parity_bars(qst, oracle_mod, cuda_ok, prec, q):
+    import torch
+    D = 1 << q
+    kappas = [1e2, 3e4, 1e5, 3e5]
+    x32 = _rows(q, kappas, 16, seed=40 + q)
+    H = (x32[:, 2 * D * D:3 * D * D] + 1j * x32[:, 3 * D * D:]).astype(np.complex128).reshape(-1, D, D)
+    cond = np.linalg.cond(np.transpose(H, (0, 2, 1)))
+    assert cond.min() > 50 and cond.max() > 1e5   # the float32 rows keep their conditioning
+    prob = W.config_problem(q, num_chains=1024, num_steps=1)
+    p = {"bf16x3": qst.PREC_BF16X3, "fp32": qst.PREC_FP32}[prec]
+    s = qst.Sampler(prob, precision=p, diag_chains=0)
+    rho_p, p_gpu, ll_gpu = s.evaluate(torch.from_numpy(x32).cuda())
+    torch.cuda.synchronize()
+    rho_gpu = unpack_rho(rho_p.cpu().numpy(), D)
+    p_gpu = p_gpu.cpu().numpy().astype(np.float64)
+    s.close()
+    rho_ref, p_ref, _ = oracle_mod.evaluate(prob, x32.astype(np.float64))
+    err_rho = np.abs(rho_gpu - rho_ref).max(axis=(1, 2))
+    err_p = np.abs(p_gpu - p_ref).max(axis=1)
+    assert err_rho.max() < 2e-6, (err_rho.max(), cond[np.argmax(err_rho)])
+    assert err_p.max() < 1e-6, (err_p.max(), cond[np.argmax(err_p)])
