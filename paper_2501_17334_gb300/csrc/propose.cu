@@ -39,7 +39,7 @@ constexpr int kThreads = 128;
 // the refinement of U (PASSES = 3): at most this many first-order passes, another one while the
 // chain's largest |Y| entry exceeds kRefineTol (the residual of a pass is about |Y|^2)
 constexpr int kRefinePasses = 3;
-constexpr float kRefineTol = 0x1p-14f;
+constexpr float kRefineTol = 0x1p-13f;
 
 // Shared memory per chain (floats), laid out so every access is free of bank conflicts:
 //   area A: the real and imaginary planes of H's columns as they are orthogonalised (column
@@ -249,6 +249,148 @@ struct ProposeArgs {
     int d_pad;
     Philox::RoundKeys rk;        // the generator's round keys for `seed`
 };
+
+// One first-order pass of the refinement of U (step 2b of the D <= 16 kernel below, where the
+// method is described).  `again`: a pass after the first, which reads H's column j back from y'
+// into area B (it held C) and U's column j as this lane's vector; `apply`: write the refined U
+// (a further pass runs for the whole warp when any of its chains needs it, and the others
+// discard theirs, so a chain's bits never depend on its neighbours).  Returns the chain's
+// largest |Y| entry.
+template <int D, int QC>
+__device__ __forceinline__ float refine_pass(float2 (&hr)[D / 2], float2 (&hi)[D / 2], float *qre, float *qim,
+                                             float *hre, float *him, const float2 *rpk, const float *gsrc, int j,
+                                             bool again, bool apply) {
+    constexpr int d = D * D;
+    auto cidx = [](int r, int cc) { return cc * D + (r ^ cc); };
+    if (again) {   // H's column j into area B again (it held C), U's column j as the vector
+#pragma unroll
+        for (int i = 0; i < D; i += (D >= 4 ? 4 : 1)) {
+            if constexpr (D >= 4) {
+                *reinterpret_cast<float4 *>(hre + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 2 * d + j * D + i);
+                *reinterpret_cast<float4 *>(him + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 3 * d + j * D + i);
+            } else {
+                hre[j * D + i] = gsrc[2 * d + j * D + i];
+                him[j * D + i] = gsrc[3 * d + j * D + i];
+            }
+        }
+        load_column2<D>(qre + j * QC, hr);
+        load_column2<D>(qim + j * QC, hi);
+        __syncwarp();
+    }
+#pragma unroll 1
+    for (int cc = 0; cc < D; ++cc) {
+        const bool lower = cc < j;   // M_jc = q_j^dag h_c; at c = j (and above) N_jc = q_j^dag q_c
+        const float *pre = lower ? hre + cc * D : qre + cc * QC;
+        const float *pim = lower ? him + cc * D : qim + cc * QC;
+        // every partial sum of M stays below 2^6 (|h| < 64), of N below 2^1
+        const float2 res = sum_products_exact<D>(hr, hi, pre, pim, lower ? 192.0f : 6.0f, cc == j ? 1.0f : 0.0f);
+        __syncwarp();   // every lane is done with column c of H
+        hre[cidx(j, cc)] = res.x;
+        him[cidx(j, cc)] = res.y;
+    }
+    // M_jj, the one entry of the row not formed above: its column of H now holds C, so h_j is
+    // read again from the proposal's own y' (or the evaluated row; for an inactive lane the
+    // first chain's row, in bounds, whose result is not used)
+    const float2 mjj = sum_products_exact<D>(hr, hi, gsrc + 2 * d + j * D, gsrc + 3 * d + j * D, 192.0f, 0.0f);
+    __syncwarp();
+    // Y, row j, in registers: y[c] = Y[j][c].  Forward substitution, right-looking: after
+    // Y[j][c0] = (M_jc0 - ...) / R_c0c0 every later entry of the row takes its share
+    // -Y[j][c0] R[c0][c] at once, so each R entry is read once for all lanes; entries at
+    // c >= j stay zero (the lane's row has no such unknowns) until the upper part below.
+    float2 y[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+        y[c] = (c < j) ? make_float2(hre[cidx(j, c)], him[cidx(j, c)]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c0 = 0; c0 < D - 1; ++c0) {
+        const float inv_r = rpk[c0 * (c0 + 1) / 2 + c0].y;
+        y[c0] = make_float2(y[c0].x * inv_r, y[c0].y * inv_r);
+#pragma unroll
+        for (int c = c0 + 1; c < D - 1; ++c) {
+            const float2 r = rpk[c * (c + 1) / 2 + c0];   // R[c0][c]
+            y[c].x -= y[c0].x * r.x - y[c0].y * r.y;
+            y[c].y -= y[c0].x * r.y + y[c0].y * r.x;
+        }
+    }
+    // diagonal: Re Y_jj = (N_jj - 1) / 2; Im Y_jj makes R_jj real
+    float ydi = mjj.y;
+#pragma unroll
+    for (int k = 0; k < D - 1; ++k) {
+        const float2 r = rpk[j * (j + 1) / 2 + (k < j ? k : 0)];   // R[k][j] (k < j)
+        if (k < j) ydi -= y[k].x * r.y + y[k].y * r.x;
+    }
+    const float2 ydiag = make_float2(0.5f * hre[cidx(j, j)], ydi * rpk[j * (j + 1) / 2 + j].y);
+    // upper part: Y[j][c] = N_jc - conj(Y[c][j]), c > j, through area B
+#pragma unroll
+    for (int c = 0; c < D - 1; ++c)
+        if (c < j) {
+            hre[cidx(j, c)] = y[c].x;
+            him[cidx(j, c)] = y[c].y;
+        }
+    __syncwarp();   // every lane's lower row is in place
+#pragma unroll
+    for (int c = 1; c < D; ++c)
+        if (c > j) y[c] = make_float2(hre[cidx(j, c)] - hre[cidx(c, j)], him[cidx(j, c)] + him[cidx(c, j)]);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+        if (c == j) y[c] = ydiag;
+    // the chain's largest |Y| entry decides whether another pass follows
+    float ymax = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) ymax = fmaxf(ymax, fmaxf(fabsf(y[c].x), fabsf(y[c].y)));
+#pragma unroll
+    for (int off = D / 2; off >= 1; off /= 2) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, off, D));
+    // U = Q1 - Q1 Y^dag: column j is q_j - sum_k q_k conj(Y[j][k]); the correction is summed
+    // on its own (it is small) and subtracted once.  Rows go in two halves: a half is
+    // overwritten only after every lane has read that half of every column.
+    constexpr int HP = (D >= 4) ? D / 4 : 1;   // row pairs per half
+#pragma unroll
+    for (int half = 0; half < (D >= 4 ? 2 : 1); ++half) {
+        float2 cr[HP], ci[HP];
+#pragma unroll
+        for (int p = 0; p < HP; ++p) cr[p] = ci[p] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float2 yx = make_float2(y[k].x, y[k].x), yy = make_float2(y[k].y, y[k].y);
+            const float2 myy = make_float2(-y[k].y, -y[k].y);   // conj(y) = (y.x, -y.y)
+#pragma unroll
+            for (int p = 0; p < HP; ++p) {   // (vr + i vi)(y.x - i y.y)
+                const int row = 2 * (half * HP + p);
+                const float2 vr = *reinterpret_cast<const float2 *>(qre + k * QC + row);
+                const float2 vi = *reinterpret_cast<const float2 *>(qim + k * QC + row);
+                cr[p] = __ffma2_rn(vr, yx, __ffma2_rn(vi, yy, cr[p]));
+                ci[p] = __ffma2_rn(vi, yx, __ffma2_rn(vr, myy, ci[p]));
+            }
+        }
+        __syncwarp();   // every lane has read this half of every q_k
+        if (apply) {
+#pragma unroll
+            for (int p = 0; p < HP; ++p) {
+                const int row = 2 * (half * HP + p);
+                float2 *ur = reinterpret_cast<float2 *>(qre + j * QC + row);
+                float2 *ui = reinterpret_cast<float2 *>(qim + j * QC + row);
+                *ur = sub2(*ur, cr[p]);
+                *ui = sub2(*ui, ci[p]);
+            }
+        }
+        __syncwarp();
+    }
+    return ymax;
+}
+
+// The passes after the first, for the few chains whose first pass left |Y| above kRefineTol: out
+// of line, so that the common path keeps its registers.
+template <int D, int QC>
+__device__ __noinline__ void refine_more(float *qre, float *qim, float *hre, float *him, const float2 *rpk,
+                                         const float *gsrc, int j, float ymax) {
+    float2 hr[D / 2], hi[D / 2];
+#pragma unroll 1
+    for (int pass = 1; pass < kRefinePasses && __any_sync(0xffffffffu, ymax > kRefineTol); ++pass) {
+        const bool need = ymax > kRefineTol;
+        const float next = refine_pass<D, QC>(hr, hi, qre, qim, hre, him, rpk, gsrc, j, true, need);
+        ymax = need ? next : ymax;
+    }
+}
 
 // THREADS: the CTA size (chains per CTA = THREADS / D); 128 by default, 64 or 32 when the
 // autotuner finds that a small problem covers more SMs that way.  The register budget per
@@ -472,134 +614,8 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
         // take the D lanes' results of that step -- element (r, c) at c D + (r ^ c) of the real
         // (hre) and imaginary (him) planes, so that the lanes' writes of a step, a lane's reads
         // of its row and the reads of a column all hit distinct banks.
-        auto cidx = [](int r, int cc) { return cc * D + (r ^ cc); };
-        // One pass.  `again`: a pass after the first (H's column and this lane's vector are read
-        // back first); `apply`: write the refined U (a further pass runs for the whole warp when
-        // any of its chains needs it, and the others discard theirs, so a chain's bits never
-        // depend on its neighbours).  Returns the chain's largest |Y| entry.
-        auto refine_pass = [&](bool again, bool apply) -> float {
-        if (again) {   // H's column j into area B again (it held C), U's column j as the vector
-#pragma unroll
-            for (int i = 0; i < D; i += (D >= 4 ? 4 : 1)) {
-                if constexpr (D >= 4) {
-                    *reinterpret_cast<float4 *>(hre + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 2 * d + j * D + i);
-                    *reinterpret_cast<float4 *>(him + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 3 * d + j * D + i);
-                } else {
-                    hre[j * D + i] = gsrc[2 * d + j * D + i];
-                    him[j * D + i] = gsrc[3 * d + j * D + i];
-                }
-            }
-            load_column2<D>(qre + j * QC, hr);
-            load_column2<D>(qim + j * QC, hi);
-            __syncwarp();
-        }
-#pragma unroll 1
-        for (int cc = 0; cc < D; ++cc) {
-            const bool lower = cc < j;   // M_jc = q_j^dag h_c; at c = j (and above) N_jc = q_j^dag q_c
-            const float *pre = lower ? hre + cc * D : qre + cc * QC;
-            const float *pim = lower ? him + cc * D : qim + cc * QC;
-            // every partial sum of M stays below 2^6 (|h| < 64), of N below 2^1
-            const float2 res = sum_products_exact<D>(hr, hi, pre, pim, lower ? 192.0f : 6.0f, cc == j ? 1.0f : 0.0f);
-            __syncwarp();   // every lane is done with column c of H
-            hre[cidx(j, cc)] = res.x;
-            him[cidx(j, cc)] = res.y;
-        }
-        // M_jj, the one entry of the row not formed above: its column of H now holds C, so h_j is
-        // read again from the proposal's own y' (or the evaluated row; for an inactive lane the
-        // first chain's row, in bounds, whose result is not used)
-        const float2 mjj = sum_products_exact<D>(hr, hi, gsrc + 2 * d + j * D, gsrc + 3 * d + j * D, 192.0f, 0.0f);
-        __syncwarp();
-        // Y, row j, in registers: y[c] = Y[j][c].  Forward substitution, right-looking: after
-        // Y[j][c0] = (M_jc0 - ...) / R_c0c0 every later entry of the row takes its share
-        // -Y[j][c0] R[c0][c] at once, so each R entry is read once for all lanes; entries at
-        // c >= j stay zero (the lane's row has no such unknowns) until the upper part below.
-        float2 y[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            y[c] = (c < j) ? make_float2(hre[cidx(j, c)], him[cidx(j, c)]) : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c0 = 0; c0 < D - 1; ++c0) {
-            const float inv_r = rpk[c0 * (c0 + 1) / 2 + c0].y;
-            y[c0] = make_float2(y[c0].x * inv_r, y[c0].y * inv_r);
-#pragma unroll
-            for (int c = c0 + 1; c < D - 1; ++c) {
-                const float2 r = rpk[c * (c + 1) / 2 + c0];   // R[c0][c]
-                y[c].x -= y[c0].x * r.x - y[c0].y * r.y;
-                y[c].y -= y[c0].x * r.y + y[c0].y * r.x;
-            }
-        }
-        // diagonal: Re Y_jj = (N_jj - 1) / 2; Im Y_jj makes R_jj real
-        float ydi = mjj.y;
-#pragma unroll
-        for (int k = 0; k < D - 1; ++k) {
-            const float2 r = rpk[j * (j + 1) / 2 + (k < j ? k : 0)];   // R[k][j] (k < j)
-            if (k < j) ydi -= y[k].x * r.y + y[k].y * r.x;
-        }
-        const float2 ydiag = make_float2(0.5f * hre[cidx(j, j)], ydi * rpk[j * (j + 1) / 2 + j].y);
-        // upper part: Y[j][c] = N_jc - conj(Y[c][j]), c > j, through area B
-#pragma unroll
-        for (int c = 0; c < D - 1; ++c)
-            if (c < j) {
-                hre[cidx(j, c)] = y[c].x;
-                him[cidx(j, c)] = y[c].y;
-            }
-        __syncwarp();   // every lane's lower row is in place
-#pragma unroll
-        for (int c = 1; c < D; ++c)
-            if (c > j) y[c] = make_float2(hre[cidx(j, c)] - hre[cidx(c, j)], him[cidx(j, c)] + him[cidx(c, j)]);
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            if (c == j) y[c] = ydiag;
-        // the chain's largest |Y| entry decides whether another pass follows
-        float ymax = 0.0f;
-#pragma unroll
-        for (int c = 0; c < D; ++c) ymax = fmaxf(ymax, fmaxf(fabsf(y[c].x), fabsf(y[c].y)));
-#pragma unroll
-        for (int off = D / 2; off >= 1; off /= 2) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, off, D));
-        // U = Q1 - Q1 Y^dag: column j is q_j - sum_k q_k conj(Y[j][k]); the correction is summed
-        // on its own (it is small) and subtracted once.  Rows go in two halves: a half is
-        // overwritten only after every lane has read that half of every column.
-        constexpr int HP = (D >= 4) ? D / 4 : 1;   // row pairs per half
-#pragma unroll
-        for (int half = 0; half < (D >= 4 ? 2 : 1); ++half) {
-            float2 cr[HP], ci[HP];
-#pragma unroll
-            for (int p = 0; p < HP; ++p) cr[p] = ci[p] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const float2 yx = make_float2(y[k].x, y[k].x), yy = make_float2(y[k].y, y[k].y);
-                const float2 myy = make_float2(-y[k].y, -y[k].y);   // conj(y) = (y.x, -y.y)
-#pragma unroll
-                for (int p = 0; p < HP; ++p) {   // (vr + i vi)(y.x - i y.y)
-                    const int row = 2 * (half * HP + p);
-                    const float2 vr = *reinterpret_cast<const float2 *>(qre + k * QC + row);
-                    const float2 vi = *reinterpret_cast<const float2 *>(qim + k * QC + row);
-                    cr[p] = __ffma2_rn(vr, yx, __ffma2_rn(vi, yy, cr[p]));
-                    ci[p] = __ffma2_rn(vi, yx, __ffma2_rn(vr, myy, ci[p]));
-                }
-            }
-            __syncwarp();   // every lane has read this half of every q_k
-            if (apply) {
-#pragma unroll
-                for (int p = 0; p < HP; ++p) {
-                    const int row = 2 * (half * HP + p);
-                    float2 *ur = reinterpret_cast<float2 *>(qre + j * QC + row);
-                    float2 *ui = reinterpret_cast<float2 *>(qim + j * QC + row);
-                    *ur = sub2(*ur, cr[p]);
-                    *ui = sub2(*ui, ci[p]);
-                }
-            }
-            __syncwarp();
-        }
-        return ymax;
-        };
-        float ymax = refine_pass(false, true);
-#pragma unroll 1
-        for (int pass = 1; pass < kRefinePasses && __any_sync(0xffffffffu, ymax > kRefineTol); ++pass) {
-            const bool need = ymax > kRefineTol;
-            const float next = refine_pass(true, need);
-            ymax = need ? next : ymax;
-        }
+        const float ymax = refine_pass<D, QC>(hr, hi, qre, qim, hre, him, rpk, gsrc, j, false, true);
+        if (__any_sync(0xffffffffu, ymax > kRefineTol)) refine_more<D, QC>(qre, qim, hre, him, rpk, gsrc, j, ymax);
     }
 
     if constexpr (PASSES == 2) {
