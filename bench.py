@@ -43,12 +43,12 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "e19de5ac7014bedd20814c9765501f1ba6de374f58ea2b0e3816c8c525f57798",
-                "chains": 32768, "bytes": 135.156992e6 + 161.061376e6},
+                "sha256": "dcd7ab273995ed275f853d911b206237830f7a4c935e7eaf1565d44b56370086",
+                "chains": 32768, "bytes": 135.304448e6 + 165.147904e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "b5f8838cb1b252b8b3a4d31a7aa63fcda6bf8673262bf99e7a2d4c9b69f4d108",
-                "chains": 32768, "bytes": 51.399936e6 + 20.48e6},
+                "sha256": "9e172b66122b4210bf72c44527272c171153650ff89b379e6116f16647fdd32c",
+                "chains": 32768, "bytes": 51.39968e6 + 4.352e6},
 }
 
 def _sha256(path):
