@@ -41,6 +41,18 @@ constexpr int kThreads = 128;
 constexpr int kRefinePasses = 3;
 constexpr float kRefineTol = 0x1p-13f;
 
+// The refinement keeps Q's and H's columns unpadded at D = 16 (16 floats each, so that five CTAs
+// fit on an SM), where the 16 lanes of a chain reaching block b of their own columns would hit
+// 8 of the 32 banks.  So block b (4 floats) of Q's column c is stored at b ^ ((c >> 1) & 3), and
+// of H's column c at b ^ ((c >> 1) & 3) ^ 2: a chain's lanes then cover all 32 banks, and the Q
+// and H columns of one index, which the refinement's products read side by side, never share
+// banks.  Within a block the order is kept, so every value and every result is unchanged.
+// (QC == D only for that layout; every other one is padded and unswizzled.)
+template <int D, int QC>
+__device__ __forceinline__ int qsw(int c) { return (QC == D && D == 16) ? ((c >> 1) & 3) : 0; }
+template <int D, int QC>
+__device__ __forceinline__ int hsw(int c) { return (QC == D && D == 16) ? (((c >> 1) & 3) ^ 2) : 0; }
+
 // Shared memory per chain (floats), laid out so every access is free of bank conflicts:
 //   area A: the real and imaginary planes of H's columns as they are orthogonalised (column
 //           stride D + 4, so that 128-bit accesses of eight consecutive lanes' columns hit
@@ -88,11 +100,11 @@ __device__ __forceinline__ void gaussian_pair_fast(uint32_t wu, uint32_t wv, flo
 
 // a D-float column into / from registers, 128-bit at a time where D allows
 template <int D>
-__device__ __forceinline__ void load_column(const float *src, float (&v)[D]) {
+__device__ __forceinline__ void load_column(const float *src, float (&v)[D], int s = 0) {
     if constexpr (D >= 4) {
 #pragma unroll
         for (int i = 0; i < D; i += 4) {
-            const float4 t = *reinterpret_cast<const float4 *>(src + i);
+            const float4 t = *reinterpret_cast<const float4 *>(src + 4 * ((i / 4) ^ s));
             v[i] = t.x;
             v[i + 1] = t.y;
             v[i + 2] = t.z;
@@ -115,13 +127,15 @@ __device__ __forceinline__ void store_column(float *dst, const float (&v)[D]) {
     }
 }
 
-// a D-float column as D/2 pairs of consecutive entries (for the packed f32x2 arithmetic)
+// a D-float column as D/2 pairs of consecutive entries (for the packed f32x2 arithmetic).  `s`:
+// the column's 4-float blocks are stored in the order b ^ s (the swizzle of the unpadded
+// 16-float columns of the refinement, kSwizzle below; 0 elsewhere)
 template <int D>
-__device__ __forceinline__ void load_column2(const float *src, float2 (&v)[D / 2]) {
+__device__ __forceinline__ void load_column2(const float *src, float2 (&v)[D / 2], int s = 0) {
     if constexpr (D >= 4) {
 #pragma unroll
         for (int p = 0; p < D / 2; p += 2) {
-            const float4 t = *reinterpret_cast<const float4 *>(src + 2 * p);
+            const float4 t = *reinterpret_cast<const float4 *>(src + 4 * ((p / 2) ^ s));
             v[p] = make_float2(t.x, t.y);
             v[p + 1] = make_float2(t.z, t.w);
         }
@@ -130,11 +144,11 @@ __device__ __forceinline__ void load_column2(const float *src, float2 (&v)[D / 2
     }
 }
 template <int D>
-__device__ __forceinline__ void store_column2(float *dst, const float2 (&v)[D / 2]) {
+__device__ __forceinline__ void store_column2(float *dst, const float2 (&v)[D / 2], int s = 0) {
     if constexpr (D >= 4) {
 #pragma unroll
         for (int p = 0; p < D / 2; p += 2)
-            *reinterpret_cast<float4 *>(dst + 2 * p) = make_float4(v[p].x, v[p].y, v[p + 1].x, v[p + 1].y);
+            *reinterpret_cast<float4 *>(dst + 4 * ((p / 2) ^ s)) = make_float4(v[p].x, v[p].y, v[p + 1].x, v[p + 1].y);
     } else {
         *reinterpret_cast<float2 *>(dst) = v[0];
     }
@@ -188,7 +202,8 @@ __device__ __forceinline__ void group_sum_exact(float v, float &hi, float &lo) {
 // exact); its error is about 2^(e-45) per product.
 template <int D>
 __device__ __forceinline__ float2 sum_products_exact(const float2 (&qr)[D / 2], const float2 (&qi)[D / 2],
-                                                     const float *pre, const float *pim, float offset, float sub) {
+                                                     const float *pre, const float *pim, float offset, float sub,
+                                                     int s = 0) {
     // four accumulators: qr pr + qi pi (real part), qr pi and qi pr (imaginary part, subtracted
     // at the end); each a grid sum s1 and an error sum s2
     float2 a1 = make_float2(offset, offset), b1 = a1, c1 = a1;
@@ -203,8 +218,8 @@ __device__ __forceinline__ float2 sum_products_exact(const float2 (&qr)[D / 2], 
     for (int p0 = 0; p0 < D / 2; p0 += (D >= 4 ? 2 : 1)) {
         float2 pr[2], pi[2];
         if constexpr (D >= 4) {
-            const float4 r4 = *reinterpret_cast<const float4 *>(pre + 2 * p0);
-            const float4 i4 = *reinterpret_cast<const float4 *>(pim + 2 * p0);
+            const float4 r4 = *reinterpret_cast<const float4 *>(pre + 4 * ((p0 / 2) ^ s));   // (block swizzle s)
+            const float4 i4 = *reinterpret_cast<const float4 *>(pim + 4 * ((p0 / 2) ^ s));
             pr[0] = make_float2(r4.x, r4.y);
             pr[1] = make_float2(r4.z, r4.w);
             pi[0] = make_float2(i4.x, i4.y);
@@ -266,15 +281,16 @@ __device__ __forceinline__ float refine_pass(float2 (&hr)[D / 2], float2 (&hi)[D
 #pragma unroll
         for (int i = 0; i < D; i += (D >= 4 ? 4 : 1)) {
             if constexpr (D >= 4) {
-                *reinterpret_cast<float4 *>(hre + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 2 * d + j * D + i);
-                *reinterpret_cast<float4 *>(him + j * D + i) = *reinterpret_cast<const float4 *>(gsrc + 3 * d + j * D + i);
+                const int o = j * D + 4 * ((i / 4) ^ hsw<D, QC>(j));
+                *reinterpret_cast<float4 *>(hre + o) = *reinterpret_cast<const float4 *>(gsrc + 2 * d + j * D + i);
+                *reinterpret_cast<float4 *>(him + o) = *reinterpret_cast<const float4 *>(gsrc + 3 * d + j * D + i);
             } else {
                 hre[j * D + i] = gsrc[2 * d + j * D + i];
                 him[j * D + i] = gsrc[3 * d + j * D + i];
             }
         }
-        load_column2<D>(qre + j * QC, hr);
-        load_column2<D>(qim + j * QC, hi);
+        load_column2<D>(qre + j * QC, hr, qsw<D, QC>(j));
+        load_column2<D>(qim + j * QC, hi, qsw<D, QC>(j));
         __syncwarp();
     }
 #pragma unroll 1
@@ -283,7 +299,8 @@ __device__ __forceinline__ float refine_pass(float2 (&hr)[D / 2], float2 (&hi)[D
         const float *pre = lower ? hre + cc * D : qre + cc * QC;
         const float *pim = lower ? him + cc * D : qim + cc * QC;
         // every partial sum of M stays below 2^6 (|h| < 64), of N below 2^1
-        const float2 res = sum_products_exact<D>(hr, hi, pre, pim, lower ? 192.0f : 6.0f, cc == j ? 1.0f : 0.0f);
+        const float2 res = sum_products_exact<D>(hr, hi, pre, pim, lower ? 192.0f : 6.0f, cc == j ? 1.0f : 0.0f,
+                                                 lower ? hsw<D, QC>(cc) : qsw<D, QC>(cc));
         __syncwarp();   // every lane is done with column c of H
         hre[cidx(j, cc)] = res.x;
         him[cidx(j, cc)] = res.y;
@@ -356,21 +373,36 @@ __device__ __forceinline__ float refine_pass(float2 (&hr)[D / 2], float2 (&hi)[D
 #pragma unroll
             for (int p = 0; p < HP; ++p) {   // (vr + i vi)(y.x - i y.y)
                 const int row = 2 * (half * HP + p);
-                const float2 vr = *reinterpret_cast<const float2 *>(qre + k * QC + row);
-                const float2 vi = *reinterpret_cast<const float2 *>(qim + k * QC + row);
+                const int o = k * QC + 4 * ((row >> 2) ^ qsw<D, QC>(k)) + (row & 3);
+                const float2 vr = *reinterpret_cast<const float2 *>(qre + o);
+                const float2 vi = *reinterpret_cast<const float2 *>(qim + o);
                 cr[p] = __ffma2_rn(vr, yx, __ffma2_rn(vi, yy, cr[p]));
                 ci[p] = __ffma2_rn(vi, yx, __ffma2_rn(vr, myy, ci[p]));
             }
         }
         __syncwarp();   // every lane has read this half of every q_k
         if (apply) {
+            if constexpr (HP % 2 == 0) {   // two row pairs, one 4-float block, at a time
 #pragma unroll
-            for (int p = 0; p < HP; ++p) {
-                const int row = 2 * (half * HP + p);
-                float2 *ur = reinterpret_cast<float2 *>(qre + j * QC + row);
-                float2 *ui = reinterpret_cast<float2 *>(qim + j * QC + row);
-                *ur = sub2(*ur, cr[p]);
-                *ui = sub2(*ui, ci[p]);
+                for (int p = 0; p < HP; p += 2) {
+                    const int row = 2 * (half * HP + p);
+                    float4 *ur = reinterpret_cast<float4 *>(qre + j * QC + 4 * ((row >> 2) ^ qsw<D, QC>(j)));
+                    float4 *ui = reinterpret_cast<float4 *>(qim + j * QC + 4 * ((row >> 2) ^ qsw<D, QC>(j)));
+                    const float4 u0 = *ur, u1 = *ui;
+                    const float2 a0 = sub2(make_float2(u0.x, u0.y), cr[p]), a1 = sub2(make_float2(u0.z, u0.w), cr[p + 1]);
+                    const float2 b0 = sub2(make_float2(u1.x, u1.y), ci[p]), b1 = sub2(make_float2(u1.z, u1.w), ci[p + 1]);
+                    *ur = make_float4(a0.x, a0.y, a1.x, a1.y);
+                    *ui = make_float4(b0.x, b0.y, b1.x, b1.y);
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < HP; ++p) {
+                    const int row = 2 * (half * HP + p);
+                    float2 *ur = reinterpret_cast<float2 *>(qre + j * QC + row);
+                    float2 *ui = reinterpret_cast<float2 *>(qim + j * QC + row);
+                    *ur = sub2(*ur, cr[p]);
+                    *ui = sub2(*ui, ci[p]);
+                }
             }
         }
         __syncwarp();
@@ -509,8 +541,8 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
     }
 
     if constexpr (PASSES == 3) {   // H's original columns, for the refinement after the sweep
-        store_column2<D>(hre + j * D, hr);
-        store_column2<D>(him + j * D, hi);
+        store_column2<D>(hre + j * D, hr, hsw<D, QC>(j));
+        store_column2<D>(him + j * D, hi, hsw<D, QC>(j));
     }
 
     // ---- 2a. modified Gram-Schmidt on the columns of H (Algorithm 1) ---------------------------
@@ -527,13 +559,13 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
 #pragma unroll 1
     for (int k = 0; k < D; ++k) {
         if (j == k) {   // column k is final: publish it
-            store_column2<D>(qre + k * QC, hr);
-            store_column2<D>(qim + k * QC, hi);
+            store_column2<D>(qre + k * QC, hr, qsw<D, QC>(k));
+            store_column2<D>(qim + k * QC, hi, qsw<D, QC>(k));
         }
         __syncwarp();
         float2 vr[D / 2], vi[D / 2];
-        load_column2<D>(qre + k * QC, vr);
-        load_column2<D>(qim + k * QC, vi);
+        load_column2<D>(qre + k * QC, vr, qsw<D, QC>(k));
+        load_column2<D>(qim + k * QC, vi, qsw<D, QC>(k));
         // r = v^dag h = sum (vr hr + vi hi) + i sum (vr hi - vi hr)
         float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
 #pragma unroll
@@ -583,8 +615,8 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
             hi[p] = __fmul2_rn(hi[p], sc);
         }
         __syncwarp();
-        store_column2<D>(qre + j * QC, hr);
-        store_column2<D>(qim + j * QC, hi);
+        store_column2<D>(qre + j * QC, hr, qsw<D, QC>(j));
+        store_column2<D>(qim + j * QC, hi, qsw<D, QC>(j));
         __syncwarp();
     }
     }   // PASSES > 0
@@ -734,8 +766,8 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
             }
 #pragma unroll 4
             for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {
-                const float2 ur2 = *reinterpret_cast<const float2 *>(qre + k * QC + 4 * bi + 2 * hb);
-                const float2 ui2 = *reinterpret_cast<const float2 *>(qim + k * QC + 4 * bi + 2 * hb);
+                const float2 ur2 = *reinterpret_cast<const float2 *>(qre + k * QC + 4 * (bi ^ qsw<D, QC>(k)) + 2 * hb);
+                const float2 ui2 = *reinterpret_cast<const float2 *>(qim + k * QC + 4 * (bi ^ qsw<D, QC>(k)) + 2 * hb);
                 const float4 g4r = *reinterpret_cast<const float4 *>(gsr + k * D + 4 * bj);
                 const float4 g4i = *reinterpret_cast<const float4 *>(gsi + k * D + 4 * bj);
                 const float2 gr2[2] = {make_float2(g4r.x, g4r.y), make_float2(g4r.z, g4r.w)};
@@ -792,8 +824,8 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
     #pragma unroll
         for (int k = 0; k < (PASSES > 0 ? D : 0); ++k) {
             float ur[D], ui[D];
-            load_column<D>(qre + k * QC, ur);
-            load_column<D>(qim + k * QC, ui);
+            load_column<D>(qre + k * QC, ur, qsw<D, QC>(k));
+            load_column<D>(qim + k * QC, ui, qsw<D, QC>(k));
     #pragma unroll
             for (int i = 0; i < D; ++i) {
                 wr[i] = __fmaf_rn(ur[i], gr[k], __fmaf_rn(-ui[i], gi[k], wr[i]));
