@@ -80,7 +80,10 @@ __device__ __forceinline__ float2 log_poly2(float2 x) {
     const int k0 = (ix0 - 0x3f3504f3) >> 23, k1 = (ix1 - 0x3f3504f3) >> 23;
     const float2 m = make_float2(__int_as_float(ix0 - (k0 << 23)), __int_as_float(ix1 - (k1 << 23)));
     const float2 f = add2(m, splat2(-1.0f));
-    const float2 kf = make_float2((float)k0, (float)k1);
+    // k as a float without a conversion instruction: adding k to the bits of 1.5 2^23 gives the
+    // float 1.5 2^23 + k (|k| < 2^22), and subtracting 1.5 2^23 leaves k exactly
+    const float2 kf = sub2(make_float2(__int_as_float(0x4b400000 + k0), __int_as_float(0x4b400000 + k1)),
+                           splat2(12582912.0f));
     float2 q = splat2(-0.08064694682313636f);
     q = fma2(q, f, splat2(0.1291790293475221f));
     q = fma2(q, f, splat2(-0.13072555472249744f));

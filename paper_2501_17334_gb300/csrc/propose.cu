@@ -370,14 +370,31 @@ __device__ __forceinline__ float refine_pass(float2 (&hr)[D / 2], float2 (&hi)[D
         for (int k = 0; k < D; ++k) {
             const float2 yx = make_float2(y[k].x, y[k].x), yy = make_float2(y[k].y, y[k].y);
             const float2 myy = make_float2(-y[k].y, -y[k].y);   // conj(y) = (y.x, -y.y)
+            if constexpr (HP % 2 == 0) {   // column k's rows read a 4-float block (two pairs) at a time
 #pragma unroll
-            for (int p = 0; p < HP; ++p) {   // (vr + i vi)(y.x - i y.y)
-                const int row = 2 * (half * HP + p);
-                const int o = k * QC + 4 * ((row >> 2) ^ qsw<D, QC>(k)) + (row & 3);
-                const float2 vr = *reinterpret_cast<const float2 *>(qre + o);
-                const float2 vi = *reinterpret_cast<const float2 *>(qim + o);
-                cr[p] = __ffma2_rn(vr, yx, __ffma2_rn(vi, yy, cr[p]));
-                ci[p] = __ffma2_rn(vi, yx, __ffma2_rn(vr, myy, ci[p]));
+                for (int p = 0; p < HP; p += 2) {   // (vr + i vi)(y.x - i y.y)
+                    const int row = 2 * (half * HP + p);
+                    const int o = k * QC + 4 * ((row >> 2) ^ qsw<D, QC>(k));
+                    const float4 r4 = *reinterpret_cast<const float4 *>(qre + o);
+                    const float4 i4 = *reinterpret_cast<const float4 *>(qim + o);
+                    const float2 vr[2] = {make_float2(r4.x, r4.y), make_float2(r4.z, r4.w)};
+                    const float2 vi[2] = {make_float2(i4.x, i4.y), make_float2(i4.z, i4.w)};
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        cr[p + u] = __ffma2_rn(vr[u], yx, __ffma2_rn(vi[u], yy, cr[p + u]));
+                        ci[p + u] = __ffma2_rn(vi[u], yx, __ffma2_rn(vr[u], myy, ci[p + u]));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < HP; ++p) {   // (vr + i vi)(y.x - i y.y)
+                    const int row = 2 * (half * HP + p);
+                    const int o = k * QC + 4 * ((row >> 2) ^ qsw<D, QC>(k)) + (row & 3);
+                    const float2 vr = *reinterpret_cast<const float2 *>(qre + o);
+                    const float2 vi = *reinterpret_cast<const float2 *>(qim + o);
+                    cr[p] = __ffma2_rn(vr, yx, __ffma2_rn(vi, yy, cr[p]));
+                    ci[p] = __ffma2_rn(vi, yx, __ffma2_rn(vr, myy, ci[p]));
+                }
             }
         }
         __syncwarp();   // every lane has read this half of every q_k
