@@ -43,7 +43,7 @@ class OracleCfg(ctypes.Structure):
         ("acc_lo", ctypes.c_double), ("acc_hi", ctypes.c_double), ("adapt_factor", ctypes.c_double),
         ("beta_max", ctypes.c_double), ("thin", ctypes.c_int32), ("burn_in", ctypes.c_int32),
         ("trace_steps", ctypes.c_int32), ("traj_chains", ctypes.c_int32), ("traj_capacity", ctypes.c_int32),
-        ("prior", ctypes.c_int32),
+        ("prior", ctypes.c_int32), ("likelihood", ctypes.c_int32), ("mu", ctypes.c_void_p),
     ]
 
 
@@ -72,8 +72,10 @@ def lib():
         L.oracle_probabilities_split.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P]
         L.oracle_loglik.argtypes = [ctypes.c_int, P, P]
         L.oracle_loglik.restype = ctypes.c_double
-        L.oracle_evaluate_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int64, P, P,
-                                            P, P, P]
+        L.oracle_loglik_poisson.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
+        L.oracle_loglik_poisson.restype = ctypes.c_double
+        L.oracle_evaluate_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, P,
+                                            ctypes.c_int64, P, P, P, P, P]
         L.oracle_run.argtypes = [ctypes.POINTER(OracleCfg), ctypes.POINTER(OracleOut)]
         L.oracle_run.restype = ctypes.c_int
         L.oracle_num_threads.restype = ctypes.c_int
@@ -128,6 +130,16 @@ def qr_unitary(H: np.ndarray):
 
 
 PRIOR_BURES, PRIOR_HS = 0, 1   # Algorithm 1; Hilbert-Schmidt (rho = G G^dag / Tr)
+LIK_MULTINOMIAL, LIK_POISSON = 0, 1   # Eq. likelihood; Poisson counts of mean mu_k p_kl
+
+
+def _likelihood(problem):
+    """(likelihood, mu as a contiguous FP64 array or None) of a problem (multinomial by default)."""
+    lik = int(getattr(problem, "likelihood", LIK_MULTINOMIAL))
+    mu = getattr(problem, "trials", None)
+    if lik == LIK_POISSON and mu is None:
+        raise ValueError("a Poisson problem needs its expected trials per setting")
+    return lik, _c(mu, np.float64)
 
 
 def evaluate(problem, x: np.ndarray, want_rho=True, want_p=True, prior=PRIOR_BURES):
@@ -141,8 +153,9 @@ def evaluate(problem, x: np.ndarray, want_rho=True, want_p=True, prior=PRIOR_BUR
     ll = np.zeros(n)
     pr = _c(problem.povm_re, np.float64); pi = _c(problem.povm_im, np.float64)
     cnt = _c(problem.counts, np.int32)
-    lib().oracle_evaluate_batch(D, int(prior), KD, _ptr(pr), _ptr(pi), _ptr(cnt), n, _ptr(x), _ptr(rr), _ptr(ri), _ptr(p),
-                                _ptr(ll))
+    lik, mu = _likelihood(problem)
+    lib().oracle_evaluate_batch(D, int(prior), lik, _ptr(mu), KD, _ptr(pr), _ptr(pi), _ptr(cnt), n, _ptr(x), _ptr(rr),
+                                _ptr(ri), _ptr(p), _ptr(ll))
     rho = (rr + 1j * ri) if want_rho else None
     return rho, p, ll
 
@@ -159,6 +172,13 @@ def probabilities(problem, rho: np.ndarray) -> np.ndarray:
 def loglik(counts: np.ndarray, p: np.ndarray) -> float:
     c = _c(counts, np.int32); pp = _c(p, np.float64)
     return lib().oracle_loglik(len(c), _ptr(c), _ptr(pp))
+
+
+def loglik_poisson(counts: np.ndarray, p: np.ndarray, mu: np.ndarray) -> float:
+    """Poisson log-likelihood of counts of mean mu_k p_kl (D = len(counts) / len(mu) outcomes
+    per setting), without - log c!."""
+    c = _c(counts, np.int32); pp = _c(p, np.float64); m = _c(mu, np.float64)
+    return lib().oracle_loglik_poisson(len(c) // len(m), len(c), _ptr(c), _ptr(m), _ptr(pp))
 
 
 # --------------------------------------------------------------------------- the sampler
@@ -192,6 +212,10 @@ def run(problem, num_chains=None, num_steps=None, chain_begin=0, trace_steps=0, 
                     adapt_factor=float(opts["adapt_factor"]), beta_max=float(opts["beta_max"]),
                     thin=int(opts["thin"]), burn_in=int(opts["burn_in"]), trace_steps=int(trace_steps),
                     traj_chains=int(traj_chains), traj_capacity=int(traj_capacity), prior=int(prior))
+    lik, mu = _likelihood(problem)
+    keep.append(mu)
+    cfg.likelihood = lik
+    cfg.mu = None if mu is None else mu.ctypes.data
     res = {}
 
     def buf(name, shape, dtype):

@@ -21,6 +21,10 @@
  *                     POVM arrays, Lambda_kl is the Pauli projector of setting k and outcome l,
  *                     each entry the product of the qubits' eigenprojector entries.
  *   loglik            log L = sum_kl c_kl log p_kl (Eq. likelihood).
+ *   loglik_poisson    a non-multinomial likelihood (Sec. III: other likelihoods change only
+ *                     the likelihood step of Algorithm 2): independent Poisson counts of mean
+ *                     mu_k p_kl, mu_k the expected trials of setting k, whose elements need
+ *                     not sum to the identity (lossy detectors).
  *   oracle_run        Algorithm 2 for chains [chain_begin, chain_begin+num_chains)
  *                     with step-size adaptation and thinning, pooled as in
  *                     Eq. BME2 / Step 6.
@@ -306,15 +310,40 @@ double oracle_loglik(int KD, const int32_t *counts, const double *p)
     return s;
 }
 
+/* Poisson counts c_kl of mean mu_k p_kl (k = m / D the setting of element m):
+ * log L = sum_kl [c_kl log(mu_k p_kl) - mu_k p_kl], without the data-only - log c_kl! (the
+ * multinomial form above leaves out its coefficient likewise).  A counted outcome with
+ * p <= 0 gives -inf; an outcome never observed contributes - mu_k p_kl only. */
+double oracle_loglik_poisson(int D, int KD, const int32_t *counts, const double *mu, const double *p)
+{
+    double s = 0.0;
+    for (int m = 0; m < KD; ++m) {
+        const double lambda = mu[m / D] * p[m];
+        if (counts[m] > 0) {
+            if (!(p[m] > 0.0)) return -INFINITY;
+            s += (double)counts[m] * log(lambda);
+        }
+        s -= lambda;
+    }
+    return s;
+}
+
+/* the likelihood of a problem: 0 multinomial (Eq. likelihood), 1 Poisson (mu required) */
+static double loglik_model(int D, int KD, int likelihood, const int32_t *counts, const double *mu, const double *p)
+{
+    return likelihood == 1 ? oracle_loglik_poisson(D, KD, counts, mu, p) : oracle_loglik(KD, counts, p);
+}
+
 /* rho(x) followed by its log-likelihood, for one latent vector. */
-double oracle_loglik_of_x(int D, int prior, int KD, const double *povm_re, const double *povm_im, const int32_t *counts,
-                          const double *x, double *rho_re, double *rho_im, double *p_out)
+double oracle_loglik_of_x(int D, int prior, int likelihood, const double *mu, int KD, const double *povm_re,
+                          const double *povm_im, const int32_t *counts, const double *x, double *rho_re,
+                          double *rho_im, double *p_out)
 {
     cplx *rho = malloc(sizeof(cplx) * D * D);
     double *p = malloc(sizeof(double) * KD);
     rho_of_x(D, prior, x, rho);
     oracle_probabilities(D, KD, povm_re, povm_im, rho, p);
-    double ll = oracle_loglik(KD, counts, p);
+    double ll = loglik_model(D, KD, likelihood, counts, mu, p);
     if (rho_re)
         for (int e = 0; e < D * D; ++e) { rho_re[e] = creal(rho[e]); rho_im[e] = cimag(rho[e]); }
     if (p_out) memcpy(p_out, p, sizeof(double) * KD);
@@ -324,14 +353,14 @@ double oracle_loglik_of_x(int D, int prior, int KD, const double *povm_re, const
 }
 
 /* Batched helper: rows of x [n][4D^2] -> rho, p, logL (each output optional). */
-void oracle_evaluate_batch(int D, int prior, int KD, const double *povm_re, const double *povm_im,
-                           const int32_t *counts, int64_t n, const double *x, double *rho_re, double *rho_im,
-                           double *p, double *logl)
+void oracle_evaluate_batch(int D, int prior, int likelihood, const double *mu, int KD, const double *povm_re,
+                           const double *povm_im, const int32_t *counts, int64_t n, const double *x, double *rho_re,
+                           double *rho_im, double *p, double *logl)
 {
     const int64_t nx = 4 * (int64_t)D * D, d2 = (int64_t)D * D;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < n; ++i) {
-        double ll = oracle_loglik_of_x(D, prior, KD, povm_re, povm_im, counts, x + i * nx,
+        double ll = oracle_loglik_of_x(D, prior, likelihood, mu, KD, povm_re, povm_im, counts, x + i * nx,
                                        rho_re ? rho_re + i * d2 : NULL, rho_im ? rho_im + i * d2 : NULL,
                                        p ? p + i * KD : NULL);
         if (logl) logl[i] = ll;
@@ -362,6 +391,8 @@ typedef struct {
     int32_t traj_chains;     /* store the pooled trajectory of the first traj_chains chains */
     int32_t traj_capacity;   /* ... up to this many kept samples each */
     int32_t prior;           /* 0 Bures (Algorithm 1), 1 Hilbert-Schmidt */
+    int32_t likelihood;      /* 0 multinomial (Eq. likelihood), 1 Poisson */
+    const double *mu;        /* [KD / D] expected trials per setting (Poisson) */
 } oracle_cfg;
 
 typedef struct {
@@ -398,7 +429,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
     oracle_normals(cfg->seed, 0u, chain, TAG_INIT, nx, y);
     rho_of_x(D, cfg->prior, y, rho);
     oracle_probabilities(D, KD, cfg->povm_re, cfg->povm_im, rho, p);
-    double logl = oracle_loglik(KD, cfg->counts, p);
+    double logl = loglik_model(D, KD, cfg->likelihood, cfg->counts, cfg->mu, p);
 
     for (int64_t j = 1; j <= cfg->num_steps; ++j) {
         /* proposal: eta ~ N(0, I), y' = sqrt(1 - beta^2) y + beta eta */
@@ -408,7 +439,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
         /* likelihood: rho(y') and L(y'); rho(y^{j-1}) and L(y^{j-1}) are kept from the last accept */
         rho_of_x(D, cfg->prior, yp, rhop);
         oracle_probabilities(D, KD, cfg->povm_re, cfg->povm_im, rhop, p);
-        double loglp = oracle_loglik(KD, cfg->counts, p);
+        double loglp = loglik_model(D, KD, cfg->likelihood, cfg->counts, cfg->mu, p);
         /* accept test: alpha ~ U(0,1); accept iff log alpha < log L(y') - log L(y) */
         double log_alpha = log(oracle_alpha(cfg->seed, (uint32_t)j, chain));
         int accept = log_alpha < loglp - logl;
@@ -463,6 +494,7 @@ static void run_one_chain(const oracle_cfg *cfg, int64_t r, const oracle_out *ou
 int oracle_run(const oracle_cfg *cfg, const oracle_out *out)
 {
     if (cfg->D < 1 || cfg->KD < 1 || cfg->num_chains < 0 || cfg->thin < 1) return 1;
+    if (cfg->likelihood == 1 && !cfg->mu) return 1;
     const int d2 = cfg->D * cfg->D;
     const int64_t R = cfg->num_chains;
     double *pr = calloc((size_t)(R > 0 ? R : 1) * d2, sizeof(double));

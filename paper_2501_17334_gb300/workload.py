@@ -145,6 +145,8 @@ class Problem:
     beta0: float
     seed: int
     name: str = ""
+    likelihood: int = 0                  # 0 multinomial (Eq. likelihood), 1 Poisson
+    trials: Optional[np.ndarray] = None  # [K] expected trials mu_k per setting (Poisson)
 
     @property
     def dim(self) -> int:
@@ -328,3 +330,28 @@ def latent_batch(num: int, num_qubits: int, seed: int, scale: float = 1.0) -> np
     d = 1 << num_qubits
     rng = np.random.default_rng(seed)
     return scale * rng.standard_normal((num, 4 * d * d))
+
+
+# ---- a non-multinomial likelihood: Poisson counts through lossy detectors ----------------------
+
+def lossy_pauli_problem(num_qubits: int, num_chains: int = 256, num_steps: int = 200, trials: float = 1000.0,
+                        seed: int = 1300, beta0: float = 0.05) -> Problem:
+    """Pauli settings measured through detectors of efficiency eta_kl in {8/16, ..., 16/16}: the
+    elements are Lambda'_kl = eta_kl Lambda_kl, whose sum over a setting falls short of the
+    identity, and the counts are independent Poisson variables of mean mu_k Tr(Lambda'_kl rho),
+    mu_k = `trials` (the expected number of trials of every setting).  The efficiencies keep
+    every packed entry exact in bf16, so the tensor-core forms apply.  Truth: a rank-2 Ginibre
+    state mixed 0.05 with I / D."""
+    rng = np.random.default_rng(seed)
+    D = 1 << num_qubits
+    truth = 0.95 * ginibre_state(D, 2, rng) + 0.05 * np.eye(D) / D
+    re, im = pauli_povms(num_qubits)
+    eta = rng.integers(8, 17, size=re.shape[0]).astype(np.float64) / 16.0
+    re = re * eta[:, None, None]
+    im = im * eta[:, None, None]
+    p = np.einsum("mab,ba->m", re + 1j * im, truth).real
+    K = re.shape[0] // D
+    mu = np.full(K, float(trials))
+    counts = rng.poisson(np.repeat(mu, D) * np.clip(p, 0.0, None)).astype(np.int32)
+    return Problem(num_qubits, re, im, counts, truth, int(num_chains), int(num_steps), float(beta0),
+                   int(rng.integers(1 << 31)), f"lossy_pauli_q{num_qubits}", likelihood=1, trials=mu)
