@@ -80,6 +80,22 @@ typedef enum {
                             is skipped (H's entries are still drawn and carried, unused) */
 } qst_prior;
 
+/* The likelihood of a problem's counts.  The method changes only its likelihood step for another
+ * one (Sec. III); the Poisson form covers counts whose number of trials per setting is known but
+ * whose detected outcomes do not exhaust the trials (lossy detectors: the elements of a setting
+ * then sum to less than the identity). */
+typedef enum {
+    QST_LIKELIHOOD_MULTINOMIAL = 0, /* Eq. likelihood: log L = sum_kl c_kl log p_kl; every setting's
+                                       elements must sum to the identity */
+    QST_LIKELIHOOD_POISSON = 1      /* independent Poisson counts of mean mu_k p_kl:
+                                       log L = sum_kl [c_kl log(mu_k p_kl) - mu_k p_kl] (the data-only
+                                       - log c_kl! left out); mu_k = trials[k] > 0, exact in FP32 (an
+                                       integer below 2^24, for instance).  A setting's
+                                       elements must be Hermitian with diagonals in [0, 1] summing to at
+                                       most 1 (the checks a sub-normalised POVM passes; the caller
+                                       supplies positive semidefinite elements summing to at most I) */
+} qst_likelihood;
+
 /* One tomography problem (Sec. III Steps 1-4).  All pointers are host memory,
  * read during qst_create only. */
 typedef struct {
@@ -94,6 +110,8 @@ typedef struct {
     int64_t chain_offset;   /* global id of chain 0 (disjoint ranges shard one run) */
     uint64_t seed;          /* Philox4x32-10 key */
     double beta0;           /* this problem's initial beta (Algorithm 2, initialisation); 0 = the config's beta0 */
+    int32_t likelihood;     /* qst_likelihood: QST_LIKELIHOOD_MULTINOMIAL (0, the default) or _POISSON */
+    const double *trials;   /* [K] expected trials mu_k per setting (QST_LIKELIHOOD_POISSON; NULL otherwise) */
 } qst_problem_desc;
 
 /* Sampler settings (Algorithm 2 and Sec. IV); qst_default_config fills the paper's values. */

@@ -196,6 +196,15 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
     const int D = 1 << d.num_qubits, KD = d.num_povms * D;
     for (int m = 0; m < KD; ++m)
         if (d.counts[m] < 0) return fail(QST_ERR_INVALID_ARG, "problem %d: negative count at %d", idx, m);
+    if (d.likelihood != QST_LIKELIHOOD_MULTINOMIAL && d.likelihood != QST_LIKELIHOOD_POISSON)
+        return fail(QST_ERR_INVALID_ARG, "problem %d: unknown likelihood %d", idx, d.likelihood);
+    const bool poisson = d.likelihood == QST_LIKELIHOOD_POISSON;
+    if (poisson) {
+        if (!d.trials) return fail(QST_ERR_INVALID_ARG, "problem %d: the Poisson likelihood needs trials", idx);
+        for (int k = 0; k < d.num_povms; ++k)
+            if (!(d.trials[k] > 0.0) || !std::isfinite(d.trials[k]) || (double)(float)d.trials[k] != d.trials[k])
+                return fail(QST_ERR_INVALID_ARG, "problem %d: trials[%d] must be > 0 and exact in FP32", idx, k);
+    }
     if (builtin) {   // the built-in Pauli set (make_plan checked num_povms = 3^Q)
         if (cfg->precision != QST_PREC_PAULI && cfg->precision != QST_PREC_AUTO)
             return fail(QST_ERR_INVALID_ARG, "problem %d: NULL input", idx);
@@ -219,9 +228,16 @@ qst_status validate_problem(const qst_problem_desc &d, int idx, const qst_sample
                 for (int l = 0; l < D; ++l) {
                     sr += d.povm_re[((size_t)(k * D + l) * D + i) * D + j];
                     si += d.povm_im[((size_t)(k * D + l) * D + i) * D + j];
+                    if (poisson && i == j && d.povm_re[((size_t)(k * D + l) * D + i) * D + j] < -1e-12)
+                        return fail(QST_ERR_INVALID_ARG, "problem %d: element %d has a negative diagonal entry",
+                                    idx, k * D + l);
                 }
-                if (std::fabs(sr - (i == j ? 1.0 : 0.0)) > 1e-12 || std::fabs(si) > 1e-12)
+                if (poisson) {   // a sub-normalised setting: diagonal of the sum within [0, 1]
+                    if (i == j && sr > 1.0 + 1e-12)
+                        return fail(QST_ERR_INVALID_ARG, "problem %d: setting %d sums above the identity", idx, k);
+                } else if (std::fabs(sr - (i == j ? 1.0 : 0.0)) > 1e-12 || std::fabs(si) > 1e-12) {
                     return fail(QST_ERR_INVALID_ARG, "problem %d: setting %d does not sum to the identity", idx, k);
+                }
             }
     if (cfg->precision == QST_PREC_PAULI) {   // the structured form assumes the Pauli POVMs
         if (d.num_povms != (int32_t)std::lround(std::pow(3.0, d.num_qubits)))
@@ -388,7 +404,12 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
                     hp.Ptf[(size_t)m * v.d_pad + r] = (float)x;
                 }
         }
-        // deviance weights: log L = C0 + sum_{c>0} c log(p * invf), invf = P_k / c (as float)
+        // deviance weights: log L = C0 + sum_{c>0} c log(p * invf), invf = P_k / c (as float); for
+        // the Poisson likelihood invf = mu_k / c, the per-setting weight is mu_k, and C0 adds
+        // sum_{c>0} c log mu_k - sum_k mu_k (the projection kernels give each setting
+        // -mu_k (S_k / t - 1) in place of -P_k log(S_k / t))
+        const bool poisson = d.likelihood == QST_LIKELIHOOD_POISSON;
+        v.poisson = poisson ? 1 : 0;
         hp.cnt.assign(hp.KDmax, 0.0f);
         hp.invf.assign(hp.KDmax, 1.0f);
         hp.ptot.assign(hp.KDmax / v.D, 0.0f);
@@ -396,15 +417,18 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         for (int k = 0; k < d.num_povms; ++k) {
             int64_t Pk = 0;
             for (int l = 0; l < v.D; ++l) Pk += d.counts[k * v.D + l];
-            hp.ptot[k] = (float)Pk;
+            const double wk = poisson ? d.trials[k] : (double)Pk;
+            hp.ptot[k] = (float)wk;
+            if (poisson) C0 -= wk;
             for (int l = 0; l < v.D; ++l) {
                 const int m = k * v.D + l;
                 const int c = d.counts[m];
                 if (c == 0) continue;
-                const float invf = (float)((double)Pk / (double)c);
+                const float invf = (float)(wk / (double)c);
                 hp.cnt[m] = (float)c;
                 hp.invf[m] = invf;
                 C0 -= (double)c * std::log((double)invf);
+                if (poisson) C0 += (double)c * std::log(wk);
                 Ntot += (double)c;
             }
         }

@@ -72,6 +72,35 @@ __device__ __forceinline__ void add_setting(float &hi, float &lo, float2 sum, fl
     lo += (e2 + e) - ((comp.x + comp.y) + sub);
 }
 
+// A setting's term in the Poisson likelihood beyond its deviance sum, mu (S - t) / t, from the
+// exact pairs S = s_hi + s_lo (the setting's computed sum of q) and t = t_hi + t_lo (the exact
+// trace, |t - 1| a few ulps): returned as h + l, h = mu (s_hi - t_hi) rounded and l the rest
+// (the product's rounding error, the small parts, and the division by t to first order), so
+// that the term keeps FP32 accuracy relative to mu even where S - t is of the order of t (a
+// setting whose elements do not exhaust the trials).  mu is exact in FP32.
+__device__ __forceinline__ void poisson_setting(float mu, float s_hi, float s_lo, float t_hi, float t_lo, float &h,
+                                                float &l) {
+    float dh, de;
+    two_sum(s_hi, -t_hi, dh, de);             // s_hi - t_hi exactly
+    const float dl = de + (s_lo - t_lo);      // with the small parts
+    h = mu * dh;
+    const float e = (t_hi - 1.0f) + t_lo;     // t - 1 (t_hi - 1 is exact)
+    l = (__fmaf_rn(mu, dh, -h) + mu * dl) - h * e;
+}
+
+// add_setting for a subtracted term given as a pair (sub_h + sub_l): the large part goes
+// through the exact two-sums with the deviance sum and the running hi
+__device__ __forceinline__ void add_setting_pair(float &hi, float &lo, float2 sum, float2 comp, float sub_h, float sub_l) {
+    float s, e;
+    two_sum(sum.x, sum.y, s, e);
+    float dd, e1;
+    two_sum(s, -sub_h, dd, e1);
+    float h, e2;
+    two_sum(hi, dd, h, e2);
+    hi = h;
+    lo += ((e2 + e1) + e) - ((comp.x + comp.y) + sub_l);
+}
+
 // qst_log_poly (log_poly.h) on two arguments at once, operation for operation, so each
 // result has the same bits as the scalar function; arguments must be positive normal finite
 // (the caller checks that separately).

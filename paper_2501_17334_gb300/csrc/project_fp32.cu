@@ -18,6 +18,7 @@
 // 16 threads sharing a chain, and one FP64 partial per (column group, chain) is written.  The
 // constant and trace terms are added by the accept kernel.
 #include "qst_internal.cuh"
+#include "f32x2.cuh"
 
 namespace qst {
 namespace {
@@ -40,6 +41,7 @@ struct ProjectArgs {
     int d_pad, KD, KD_pad;
     int D;               // outcomes per setting (a setting's columns are consecutive)
     int tiles_per_group;
+    int poisson;         // 1: each setting adds -mu_k (S_k / t - 1) (Poisson) instead of -P_k log(S_k / t)
 };
 
 __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
@@ -198,8 +200,37 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
                         sl += __shfl_xor_sync(0xffffffffu, sl, off);
                     }
                 }
-                // one thread per setting adds -P_k log(S_k / t)
-                if (per >= 1 && (tx & (per - 1)) == 0 && n0 + col0 < a.KD) {
+                if (a.poisson) {
+                    // Poisson: -mu_k (S_k / t - 1) per setting, its large part into the compensated
+                    // sum; at D = 2 a thread's four columns are two whole settings
+                    auto add_poisson = [&](float mu, float s_hi, float s_lo) {
+                        float ph, pl;
+                        poisson_setting(mu, s_hi, s_lo, trace_hi[i], trace_lo[i], ph, pl);
+                        const float y = -ph - rowcomp[i];
+                        const float tt = rowsum[i] + y;
+                        rowcomp[i] = (tt - rowsum[i]) - y;
+                        rowsum[i] = tt;
+                        rowsmall[i] -= pl;
+                    };
+                    if (per >= 1) {
+                        if ((tx & (per - 1)) == 0 && n0 + col0 < a.KD) add_poisson(a.ptot[(n0 + col0) / a.D], sh, sl);
+                    } else {
+#pragma unroll
+                        for (int s2 = 0; s2 < 2; ++s2) {
+                            if (n0 + col0 + 2 * s2 >= a.KD) continue;
+                            float s_hi = 0.0f, s_lo = 0.0f;
+#pragma unroll
+                            for (int u = 2 * s2; u < 2 * s2 + 2; ++u) {
+                                const float pv = acc[i][4 * h + u];
+                                const float hq = (pv + 12.0f) - 12.0f;
+                                s_hi += hq;
+                                s_lo += pv - hq;
+                            }
+                            add_poisson(a.ptot[(n0 + col0 + 2 * s2) / 2], s_hi, s_lo);
+                        }
+                    }
+                } else if (per >= 1 && (tx & (per - 1)) == 0 && n0 + col0 < a.KD) {
+                    // one thread per setting adds -P_k log(S_k / t)
                     const float pk = a.ptot[(n0 + col0) / a.D];
                     const float rel = ((sh - trace_hi[i]) + (sl - trace_lo[i])) / trace_hi[i];
                     const float l1p = fabsf(rel) < 0x1p-10f
@@ -253,6 +284,7 @@ cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t ro
     a.d_pad = p.d_pad;
     a.KD = p.KD;
     a.KD_pad = p.KD_pad;
+    a.poisson = p.poisson;
     const int nt = p.KD_pad / BN;
     const int groups = p.ngroups;
     a.tiles_per_group = (nt + groups - 1) / groups;

@@ -94,6 +94,8 @@ struct PauliArgs {
     const double *trace;     // [rows] exact trace of the stored rho (P_OUT only)
     int64_t rows;
     int d_pad, KD;
+    int poisson;             // 1: each setting adds -mu_k (S_k / t - 1) (Poisson; S_k / t - 1 is a few ulps
+                             // here, the Pauli settings being complete) instead of -P_k log(S_k / t)
 };
 
 // The six children of one split at an entry: s = A + C, x = B + B^dag, y = i(B - B^dag) there.
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
     auto renorm = [&](float sh, float sl, float unit, int k) {
         const float rel = ((unit * sh - ti.x) + (unit * sl - ti.y)) * ti.z;
         // log1p(rel): |rel| is a few ulps, where three terms are exact to 2^-40
+        if (a.poisson) return -__ldg(a.ptot + k) * rel;
         const float l1p = fabsf(rel) < 0x1p-10f ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
                                                 : log1pf(rel);
         return -__ldg(a.ptot + k) * l1p;
@@ -434,6 +437,7 @@ cudaError_t launch_project_pauli(const ProblemView &p, const float *A, int64_t r
     a.rows = rows;
     a.d_pad = p.d_pad;
     a.KD = p.KD;
+    a.poisson = p.poisson;
     switch (p.D) {
         case 2: return launch_q<1>(a, s);
         case 4: return launch_q<2>(a, s);

@@ -106,6 +106,7 @@ struct TcArgs {
     int ntiles;            // KD_tc / 128
     int tiles_per_group;
     int ngroups;
+    int poisson;           // 1: each setting adds -mu_k (S_k / t - 1) (Poisson) instead of -P_k log(S_k / t)
 };
 
 // ---- PTX wrappers ---------------------------------------------------------------------------
@@ -643,14 +644,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 kahan_fma2(dev, comp, c, log_poly2(x));
                             }
                             const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;   // (s_hi exact)
-                            // log(S_k / t), S_k - t formed from the exact pairs (Sterbenz: s_hi - t_hi exact)
-                            const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
-                            // log1p(rel): |rel| is a few ulps, where three terms are exact to 2^-40
-                            const float l1p = fabsf(rel) < 0x1p-10f
-                                                  ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
-                                                  : log1pf(rel);
-                            // the setting's term goes straight into the unit's pair
-                            add_setting(tot_hi, tot_lo, dev, comp, pk * l1p);
+                            if (a.poisson) {
+                                float ph, pl;
+                                poisson_setting(pk, s_hi, s_lo, t_hi, t_lo, ph, pl);
+                                add_setting_pair(tot_hi, tot_lo, dev, comp, ph, pl);
+                            } else {
+                                // log(S_k / t), S_k - t formed from the exact pairs (Sterbenz: s_hi - t_hi exact)
+                                const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
+                                // log1p(rel): |rel| is a few ulps, where three terms are exact to 2^-40
+                                const float l1p = fabsf(rel) < 0x1p-10f
+                                                      ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
+                                                      : log1pf(rel);
+                                // the setting's term goes straight into the unit's pair
+                                add_setting(tot_hi, tot_lo, dev, comp, pk * l1p);
+                            }
                         }
                     }
                     // a counted outcome with q <= 0 (or below the normal range): log L = -inf
@@ -878,11 +885,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         kahan_fma2(dev, comp, c, log_poly2(x));
                     }
                     const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;
-                    const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
-                    const float l1p = fabsf(rel) < 0x1p-10f
-                                          ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
-                                          : log1pf(rel);
-                    add_setting(tile_hi, tile_lo, dev, comp, pk * l1p);
+                    if (a.poisson) {
+                        float ph, pl;
+                        poisson_setting(pk, s_hi, s_lo, t_hi, t_lo, ph, pl);
+                        add_setting_pair(tile_hi, tile_lo, dev, comp, ph, pl);
+                    } else {
+                        const float rel = ((s_hi - t_hi) + (s_lo - t_lo)) * inv_t;
+                        const float l1p = fabsf(rel) < 0x1p-10f
+                                              ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
+                                              : log1pf(rel);
+                        add_setting(tile_hi, tile_lo, dev, comp, pk * l1p);
+                    }
                 }
                 if (a.p_out && valid) {
 #pragma unroll
@@ -1077,6 +1090,7 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     a.KD = p.KD;
     a.n_katoms = plan->n_katoms;
     a.ntiles = plan->ntiles;
+    a.poisson = p.poisson;
     const int groups = p.ngroups / 4;   // the epilogue writes four column-slice partials per group
     a.ngroups = groups;
     a.tiles_per_group = (plan->ntiles + groups - 1) / groups;

@@ -133,16 +133,19 @@ struct ProblemView {
     int64_t R;
     int64_t chain_offset;
     uint64_t seed;
-    double C0;     // -sum_{c>0} c log(invf): constant of the deviance form (see the projection kernels)
+    double C0;     // constant of the deviance form: -sum_{c>0} c log(invf), and for the Poisson
+                   // likelihood + sum_{c>0} c log(mu_k) - sum_k mu_k (see the projection kernels)
     double Ntot;   // sum of all counts: weight of log t (trace of the stored rho) in log L
+    int poisson;   // 0: the multinomial likelihood (Eq. likelihood); 1: Poisson counts of mean mu_k p_kl
 
     // packed projector operands and per-column likelihood weights
     const float *P32;            // [d_pad][KD_pad]  (row = packed rho index, contiguous columns)
     const void *Ptc;             // [KD_tc][d_pad]   tensor-core B operand (row = projector, contiguous packed
                                  //                  index): bf16, or FP32 holding TF32 values
     const float *cnt;            // [max(KD_pad, KD_tc)] counts as float, 0 on padding
-    const float *invf;           // [max(KD_pad, KD_tc)] P_k / c_kl (1 where c_kl = 0)
-    const float *ptot;           // [max(KD_pad, KD_tc) / D] shots P_k of each setting (0 on padding)
+    const float *invf;           // [max(KD_pad, KD_tc)] P_k / c_kl, Poisson: mu_k / c_kl (1 where c_kl = 0)
+    const float *ptot;           // [max(KD_pad, KD_tc) / D] shots P_k of each setting, Poisson: its expected
+                                 //                  trials mu_k (0 on padding)
     const float4 *colw;          // [max(KD_pad, KD_tc) / 2] per column pair (invf, invf, add, add), tensor epilogue
     int pauli;                   // the structured Pauli form of the projection (project_pauli.cu)
     const float4 *pauli_wq;      // [KD / 2] deviance weights per output pair in the structured form's order

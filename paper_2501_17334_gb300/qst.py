@@ -26,6 +26,8 @@ PREC_PAULI = 4   # structured FP32 form, Pauli POVMs only
 PREC_AUTO = 5    # per problem the faster of the forms that apply (timed at creation)
 PRIOR_BURES = 0  # Algorithm 1
 PRIOR_HS = 1     # Hilbert-Schmidt: rho = G G^dag / Tr
+LIKELIHOOD_MULTINOMIAL = 0  # Eq. likelihood
+LIKELIHOOD_POISSON = 1      # Poisson counts of mean mu_k p_kl (Problem.trials = mu)
 KERNEL_PROPOSE, KERNEL_PROJECT, KERNEL_ACCEPT, KERNEL_DIAG = range(4)
 KERNEL_NAMES = {KERNEL_PROPOSE: "propose", KERNEL_PROJECT: "project", KERNEL_ACCEPT: "accept", KERNEL_DIAG: "diag"}
 
@@ -39,7 +41,8 @@ class QstError(RuntimeError):
 class ProblemDesc(ctypes.Structure):
     _fields_ = [("num_qubits", ctypes.c_int32), ("num_povms", ctypes.c_int32), ("counts", ctypes.c_void_p),
                 ("povm_re", ctypes.c_void_p), ("povm_im", ctypes.c_void_p), ("num_chains", ctypes.c_int64),
-                ("chain_offset", ctypes.c_int64), ("seed", ctypes.c_uint64), ("beta0", ctypes.c_double)]
+                ("chain_offset", ctypes.c_int64), ("seed", ctypes.c_uint64), ("beta0", ctypes.c_double),
+                ("likelihood", ctypes.c_int32), ("trials", ctypes.c_void_p)]
 
 
 class SamplerCfg(ctypes.Structure):
@@ -181,6 +184,14 @@ class _Descs:
             d.chain_offset = 0 if chain_offsets is None else int(chain_offsets[i])
             d.seed = p.seed
             d.beta0 = float(getattr(p, "beta0", 0.0) or 0.0)
+            d.likelihood = int(getattr(p, "likelihood", LIKELIHOOD_MULTINOMIAL))
+            trials = getattr(p, "trials", None)
+            if trials is None:
+                d.trials = None
+            else:
+                t = np.ascontiguousarray(trials, dtype=np.float64)
+                self.arrays.append(t)
+                d.trials = t.ctypes.data
 
 
 def workspace_size(problems: Sequence, cfg: SamplerCfg, chain_offsets=None) -> int:

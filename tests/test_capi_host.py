@@ -78,6 +78,35 @@ def test_validation_rejects_bad_inputs(qst):
     assert "identity" in qst.load().qst_last_error().decode() or True
 
 
+def test_poisson_likelihood_validation(qst):
+    """QST_LIKELIHOOD_POISSON: settings may fall short of the identity (lossy detectors), but
+    not exceed it; every setting needs trials exact in FP32; an incomplete setting is refused
+    under the multinomial likelihood."""
+    import copy
+    ok = qst.default_config()
+    prob = W.lossy_pauli_problem(2, num_chains=64, num_steps=10)
+    assert qst.workspace_size([prob], ok) > 0
+    assert qst.workspace_size([prob], qst.default_config(precision=qst.PREC_BF16X3)) > 0
+    multinomial = copy.copy(prob)
+    multinomial.likelihood = 0
+    assert _status(lambda: qst.workspace_size([multinomial], ok)) == 1
+    no_trials = copy.copy(prob)
+    no_trials.trials = None
+    assert _status(lambda: qst.workspace_size([no_trials], ok)) == 1
+    for bad_mu in (0.0, -5.0, np.nan, 1000.1):   # 1000.1 is not exact in FP32
+        wrong = copy.copy(prob)
+        wrong.trials = prob.trials.copy()
+        wrong.trials[1] = bad_mu
+        assert _status(lambda: qst.workspace_size([wrong], ok)) == 1
+    above = copy.copy(prob)
+    above.povm_re = prob.povm_re * 2.0   # every setting sums to eta / 2 * 2 > 1 somewhere
+    above.povm_im = prob.povm_im * 2.0
+    assert _status(lambda: qst.workspace_size([above], ok)) == 1
+    unknown = copy.copy(prob)
+    unknown.likelihood = 7
+    assert _status(lambda: qst.workspace_size([unknown], ok)) == 1
+
+
 def test_five_qubits_are_accepted_and_six_refused(qst):
     prob = W.five_qubit_problem(num_chains=8, num_steps=1)
     assert qst.workspace_size([prob], qst.default_config()) > 0
