@@ -43,12 +43,12 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "dcd7ab273995ed275f853d911b206237830f7a4c935e7eaf1565d44b56370086",
-                "chains": 32768, "bytes": 135.304448e6 + 165.147904e6},
+                "sha256": "b520335b656e6ce98cee64073549f8aae8b168852ff5a5d1926bb6563ffa76bf",
+                "chains": 32768, "bytes": 135.300864e6 + 166.508032e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
-                "sha256": "9e172b66122b4210bf72c44527272c171153650ff89b379e6116f16647fdd32c",
-                "chains": 32768, "bytes": 51.39968e6 + 4.352e6},
+                "sha256": "37119239961d9995f5809f45982402867e875058dcd74658ffb9b5d6b4a08518",
+                "chains": 32768, "bytes": 51.399424e6 + 25.088e6},
 }
 
 def _sha256(path):

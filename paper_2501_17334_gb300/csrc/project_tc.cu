@@ -305,7 +305,9 @@ __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&r)[NC])
 // Padded K (d_pad) of the packed rho for D: D^2 rounded up to 64.
 __host__ __device__ constexpr int tc_dpad(int D) { return (D * D + 63) / 64 * 64; }
 
-template <int D, int KIND>
+// POISSON: the Poisson likelihood's setting term (a compile-time choice, so that the
+// multinomial instantiation carries none of its code)
+template <int D, int KIND, bool POISSON>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     project_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
     using T = TcOps<KIND>;
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 kahan_fma2(dev, comp, c, log_poly2(x));
                             }
                             const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;   // (s_hi exact)
-                            if (a.poisson) {
+                            if constexpr (POISSON) {
                                 float ph, pl;
                                 poisson_setting(pk, s_hi, s_lo, t_hi, t_lo, ph, pl);
                                 add_setting_pair(tot_hi, tot_lo, dev, comp, ph, pl);
@@ -708,6 +710,7 @@ constexpr int TCW_STAGES = 2;
 constexpr int TCW_STAGE_BYTES = 3 * TC_ATOM_BYTES + TCW_N * TC_KATOM * 2;   // 80 KB
 constexpr int TCW_EPI_COLS = TCW_N / TC_EPI_PER_QUAD;                        // 64
 
+template <bool POISSON>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     project_tc_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
     constexpr int D = 32;
@@ -885,7 +888,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         kahan_fma2(dev, comp, c, log_poly2(x));
                     }
                     const float s_hi = sh.x + sh.y, s_lo = sl.x + sl.y;
-                    if (a.poisson) {
+                    if constexpr (POISSON) {
                         float ph, pl;
                         poisson_setting(pk, s_hi, s_lo, t_hi, t_lo, ph, pl);
                         add_setting_pair(tile_hi, tile_lo, dev, comp, ph, pl);
@@ -981,16 +984,33 @@ struct TcPlan {
 };
 
 namespace {
-template <int D, int KIND>
-cudaError_t launch_tc_dk(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
+template <int D, int KIND, bool POISSON>
+cudaError_t launch_tc_dkp(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
-        cudaError_t e =
-            cudaFuncSetAttribute(project_tc_kernel<D, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(project_tc_kernel<D, KIND, POISSON>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    project_tc_kernel<D, KIND><<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
+    project_tc_kernel<D, KIND, POISSON><<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
+    return cudaGetLastError();
+}
+template <int D, int KIND>
+cudaError_t launch_tc_dk(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
+    return a.poisson ? launch_tc_dkp<D, KIND, true>(plan, a, grid, smem, s)
+                     : launch_tc_dkp<D, KIND, false>(plan, a, grid, smem, s);
+}
+template <bool POISSON>
+cudaError_t launch_tc_wide(const TcPlan *plan, const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(project_tc_wide_kernel<POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    project_tc_wide_kernel<POISSON><<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
     return cudaGetLastError();
 }
 template <int D>
@@ -1108,14 +1128,7 @@ cudaError_t launch_project_tc(const TcPlan *plan, const ProblemView &p, int64_t 
     dim3 grid((unsigned)std::min<int64_t>(a.units, num_sms));
     if (p.D == 32) {   // units: (chain tile, N tile) pairs
         const size_t smem = 1024 + (size_t)TCW_STAGES * TCW_STAGE_BYTES;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(project_tc_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        project_tc_wide_kernel<<<grid, TC_THREADS, smem, s>>>(plan->a, plan->b, a);
-        return cudaGetLastError();
+        return a.poisson ? launch_tc_wide<true>(plan, a, grid, smem, s) : launch_tc_wide<false>(plan, a, grid, smem, s);
     }
     const size_t smem = tc_smem_bytes(plan->kind, plan->n_katoms, plan->ntiles * TC_N, p.D);
     switch (p.D) {
