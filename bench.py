@@ -353,7 +353,7 @@ def run_reference(args):
 
 
 def run_profile_case(args):
-    """A short run of the headline form (or, with --qubits 6, the six-qubit problem) for ncu
+    """A short run of the headline form (or, with --qubits 5 or 6, the five- or six-qubit problem) for ncu
     captures (no timing)."""
     import torch
     from paper_2501_17334_gb300 import qst, workload as W
@@ -361,8 +361,12 @@ def run_profile_case(args):
     prec = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "pauli": qst.PREC_PAULI}[args.form]
     # the fixed column-group rule (no autotuner timing pass): a profiler distorts the timings
     # the autotuner compares, and with it the captured kernel's schedule
-    prob = W.six_qubit_problem(num_chains=args.chains) if args.qubits == 6 else \
-        W.config_problem(CONFIG_INDEX, num_chains=args.chains)
+    if args.qubits == 6:
+        prob = W.six_qubit_problem(num_chains=args.chains)
+    elif args.qubits == 5:
+        prob = W.five_qubit_problem(num_chains=args.chains)
+    else:
+        prob = W.config_problem(CONFIG_INDEX, num_chains=args.chains)
     s = qst.Sampler(prob, precision=prec, diag_chains=0, autotune=0)
     s.run_chains(args.steps)
     s.synchronize()
@@ -380,7 +384,7 @@ def main():
     ap.add_argument("--chains", type=int, default=CHAINS)
     ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp32", "pauli"])
     ap.add_argument("--profile-case", action="store_true")
-    ap.add_argument("--qubits", type=int, default=4, choices=[4, 6], help="profile case: the 4-qubit "
+    ap.add_argument("--qubits", type=int, default=4, choices=[4, 5, 6], help="profile case: the 4-qubit "
                     "workload or the six-qubit problem (structured Pauli form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
