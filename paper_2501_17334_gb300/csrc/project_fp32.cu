@@ -44,6 +44,9 @@ struct ProjectArgs {
     int poisson;         // 1: each setting adds -mu_k (S_k / t - 1) (Poisson) instead of -P_k log(S_k / t)
 };
 
+// POISSON: the Poisson likelihood's setting term (a compile-time choice, so that the multinomial
+// instantiation carries none of its code)
+template <bool POISSON>
 __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
     extern __shared__ __align__(16) float dyn[];
     float (*As)[BK][BM] = reinterpret_cast<float (*)[BK][BM]>(dyn);
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
                         sl += __shfl_xor_sync(0xffffffffu, sl, off);
                     }
                 }
-                if (a.poisson) {
+                if constexpr (POISSON) {
                     // Poisson: -mu_k (S_k / t - 1) per setting, its large part into the compensated
                     // sum; at D = 2 a thread's four columns are two whole settings
                     auto add_poisson = [&](float mu, float s_hi, float s_lo) {
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
                             add_poisson(a.ptot[(n0 + col0 + 2 * s2) / 2], s_hi, s_lo);
                         }
                     }
-                } else if (per >= 1 && (tx & (per - 1)) == 0 && n0 + col0 < a.KD) {
+                } else if (per >= 1 && (tx & (per - 1)) == 0 && n0 + col0 < a.KD) {   // (multinomial)
                     // one thread per setting adds -P_k log(S_k / t)
                     const float pk = a.ptot[(n0 + col0) / a.D];
                     const float rel = ((sh - trace_hi[i]) + (sl - trace_lo[i])) / trace_hi[i];
@@ -266,6 +269,25 @@ int fp32_ngroups(const ProblemView &p, int64_t rows) {
     return g > nt ? nt : g;
 }
 
+namespace {
+template <bool POISSON>
+cudaError_t launch_fp32(const ProjectArgs &a, dim3 grid, cudaStream_t s) {
+    // more than 48 KB of dynamic shared memory: opted into once per device
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && !((attr_set >> dev) & 1ull)) {
+        e = cudaFuncSetAttribute(project_fp32_kernel<POISSON>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set |= 1ull << dev;
+    }
+    project_fp32_kernel<POISSON><<<grid, kThreads, kSmemBytes, s>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t rows, double *out_part, float *p_out,
                                 cudaStream_t s) {
     if (rows <= 0) return cudaSuccess;
@@ -289,18 +311,7 @@ cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t ro
     const int groups = p.ngroups;
     a.tiles_per_group = (nt + groups - 1) / groups;
     dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)groups);
-    // more than 48 KB of dynamic shared memory: opted into once per device
-    static unsigned long long attr_set = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 64 && !((attr_set >> dev) & 1ull)) {
-        e = cudaFuncSetAttribute(project_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr_set |= 1ull << dev;
-    }
-    project_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(a);
-    return cudaGetLastError();
+    return a.poisson ? launch_fp32<true>(a, grid, s) : launch_fp32<false>(a, grid, s);
 }
 
 }  // namespace qst

@@ -182,7 +182,7 @@ __device__ __forceinline__ void last_split(float e00, float e01, float e10, floa
     }
 }
 
-template <int Q, bool P_OUT>
+template <int Q, bool P_OUT, bool POISSON>
 __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_ctas) project_pauli_kernel(PauliArgs a) {
     using S = PauliShape<Q>;
     constexpr int D = S::D, d = S::d, TPC = S::TPC, CPB = S::CPB, NB = S::NB;
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
     auto renorm = [&](float sh, float sl, float unit, int k) {
         const float rel = ((unit * sh - ti.x) + (unit * sl - ti.y)) * ti.z;
         // log1p(rel): |rel| is a few ulps, where three terms are exact to 2^-40
-        if (a.poisson) return -__ldg(a.ptot + k) * rel;
+        if constexpr (POISSON) return -__ldg(a.ptot + k) * rel;   // (a compile-time choice)
         const float l1p = fabsf(rel) < 0x1p-10f ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
                                                 : log1pf(rel);
         return -__ldg(a.ptot + k) * l1p;
@@ -362,20 +362,25 @@ __global__ void __launch_bounds__(PauliShape<Q>::threads, PauliShape<Q>::min_cta
     }
 }
 
-template <int Q, bool P_OUT>
-cudaError_t launch_qp(const PauliArgs &a, cudaStream_t s) {
+template <int Q, bool P_OUT, bool POISSON>
+cudaError_t launch_qpp(const PauliArgs &a, cudaStream_t s) {
     using S = PauliShape<Q>;
     const size_t smem = sizeof(float) * (size_t)S::floats * S::CPB;
     static bool attr_set = false;
     if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(project_pauli_kernel<Q, P_OUT>,
+        const cudaError_t e = cudaFuncSetAttribute(project_pauli_kernel<Q, P_OUT, POISSON>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t blocks = (a.rows + S::CPB - 1) / S::CPB;
-    project_pauli_kernel<Q, P_OUT><<<(unsigned)blocks, S::threads, smem, s>>>(a);
+    project_pauli_kernel<Q, P_OUT, POISSON><<<(unsigned)blocks, S::threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int Q, bool P_OUT>
+cudaError_t launch_qp(const PauliArgs &a, cudaStream_t s) {
+    return a.poisson ? launch_qpp<Q, P_OUT, true>(a, s) : launch_qpp<Q, P_OUT, false>(a, s);
 }
 
 template <int Q>
