@@ -130,3 +130,30 @@ def test_poisson_pooled_mean_matches_oracle(qst, oracle_mod, cuda_ok, prec):
     assert np.all(np.abs(rho - ref["mean"]) <= 3 * se + 1e-9), np.abs(rho - ref["mean"]).max()
     # the truth is recovered far better than by the prior mean I / D
     assert np.linalg.norm(rho - prob.truth) < 0.6 * np.linalg.norm(np.eye(4) / 4 - prob.truth)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_poisson_five_qubits(qst, oracle_mod, cuda_ok, prec):
+    """D = 32 (the streamed tensor-core kernel and the FP32 form's split settings): rho, p and
+    log L of 64 latent rows through lossy detectors against the oracle."""
+    import torch
+    q, n = 5, 64
+    prob = W.lossy_pauli_problem(q, num_chains=256)
+    s = qst.Sampler(prob, precision=_prec(qst, prec), diag_chains=0)
+    x32 = W.latent_batch(n, q, seed=205).astype(np.float32)
+    rho_p, p_gpu, ll_gpu = s.evaluate(torch.from_numpy(x32).cuda())
+    torch.cuda.synchronize()
+    s.close()
+    p_gpu = p_gpu.cpu().numpy().astype(np.float64)
+    ll_gpu = ll_gpu.cpu().numpy()
+    _, p_ref, ll_ref = oracle_mod.evaluate(prob, x32.astype(np.float64), want_rho=False)
+    ok = _cond(x32.astype(np.float64), 32) <= 1e3
+    assert ok.mean() > 0.9
+    assert np.abs(p_gpu - p_ref).max(axis=1)[ok].max() < 1e-6
+    c = prob.counts.astype(np.float64)
+    mu = np.repeat(prob.trials, 32)
+    for i in range(n):
+        own = oracle_mod.loglik_poisson(prob.counts, p_gpu[i], prob.trials)
+        bound = np.sum(c) * 6 * 2.0 ** -24 + np.sum(mu * np.abs(p_gpu[i])) * 4 * 2.0 ** -24
+        assert abs(ll_gpu[i] - own) < bound, (i, ll_gpu[i], own, bound)
+    assert np.nanmax((np.abs(ll_gpu - ll_ref) / np.abs(ll_ref))[ok]) < 1e-5
