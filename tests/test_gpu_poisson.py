@@ -157,3 +157,51 @@ def test_poisson_five_qubits(qst, oracle_mod, cuda_ok, prec):
         bound = np.sum(c) * 6 * 2.0 ** -24 + np.sum(mu * np.abs(p_gpu[i])) * 4 * 2.0 ** -24
         assert abs(ll_gpu[i] - own) < bound, (i, ll_gpu[i], own, bound)
     assert np.nanmax((np.abs(ll_gpu - ll_ref) / np.abs(ll_ref))[ok]) < 1e-5
+
+
+def test_poisson_with_the_other_features(qst, oracle_mod, cuda_ok):
+    """The Poisson likelihood beside the rest of the sampler: under QST_PREC_AUTO in a batch with
+    multinomial problems (every problem's chains equal, bit for bit, a handle of it alone in the
+    form chosen for it); under the Hilbert-Schmidt prior (the oracle's log L of the same latent
+    rows); and across a checkpoint (a restored run continues bit-exactly)."""
+    import torch
+    lossy = W.lossy_pauli_problem(3, num_chains=300, num_steps=30)
+    batch = [W.config_problem(2, num_chains=256, num_steps=30), lossy,
+             W.lossy_pauli_problem(2, num_chains=200, num_steps=30, seed=1301)]
+    s = qst.Sampler(batch, precision=qst.PREC_AUTO, diag_chains=0)
+    s.run_chains(30)
+    forms = [s.diagnostics(i)["projection_form"] for i in range(len(batch))]
+    for i, p in enumerate(batch):
+        ref = qst.Sampler(p, precision=forms[i], diag_chains=0, autotune=0)
+        ref.run_chains(30)
+        a, b = s.get_state(i), ref.get_state()
+        ref.close()
+        assert np.array_equal(a["y"], b["y"]), (i, forms[i])
+        assert np.array_equal(a["accepts"], b["accepts"])
+    s.close()
+    # the Hilbert-Schmidt prior
+    hs = qst.Sampler(lossy, precision=qst.PREC_BF16X3, diag_chains=0, prior=qst.PRIOR_HS)
+    x32 = W.latent_batch(256, 3, seed=77).astype(np.float32)
+    _, _, ll = hs.evaluate(torch.from_numpy(x32).cuda(), want_rho=False, want_p=False)
+    torch.cuda.synchronize()
+    hs.close()
+    _, _, ll_ref = oracle_mod.evaluate(lossy, x32.astype(np.float64), want_rho=False, want_p=False,
+                                       prior=oracle_mod.PRIOR_HS)
+    assert np.nanmax(np.abs(ll.cpu().numpy() - ll_ref) / np.abs(ll_ref)) < 1e-5
+    # checkpoint and restore
+    kw = dict(precision=qst.PREC_FP32, diag_chains=0, adapt_interval=10)
+    straight = qst.Sampler(lossy, **kw)
+    straight.run_chains(30)
+    first = qst.Sampler(lossy, **kw)
+    first.run_chains(12)
+    ck = first.checkpoint()
+    first.close()
+    second = qst.Sampler(lossy, **kw)
+    second.restore(ck)
+    second.run_chains(18)
+    a, b = straight.get_state(), second.get_state()
+    for k in ("y", "logl", "beta", "accepts"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(straight.posterior_mean()[0], second.posterior_mean()[0])
+    straight.close()
+    second.close()
