@@ -226,11 +226,11 @@ def time_form(qst, prob, precision, steps, warmup, world, chain_offset):
     return s, ms, launches, kernel_ms, ms_profiled
 
 
-def time_handle(qst, probs, precision, steps, warmup, keep=False):
+def time_handle(qst, probs, precision, steps, warmup, keep=False, **cfg):
     """ms per step of one handle over `probs` (device-timed, steps after warmup); with `keep`
     the sampler is returned too, still open."""
     import torch
-    s = qst.Sampler(probs, precision=precision, diag_chains=0)
+    s = qst.Sampler(probs, precision=precision, diag_chains=0, **cfg)
     s.run_chains(warmup)
     stream = torch.cuda.current_stream()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -247,9 +247,9 @@ def time_handle(qst, probs, precision, steps, warmup, keep=False):
 
 
 def other_configs(qst, W, oracle):
-    """The other workloads, measured briefly (one handle each; chain state resident).  At
-    configuration 3 every form of the projection runs, each with its log L error against the
-    oracle on 1024 of its chains' current states."""
+    """The other workloads, measured briefly (one handle each; chain state resident), each with
+    its log L error against the oracle on up to 1024 of its chains' current states (at
+    configuration 3 for every form of the projection; at configuration 5 by qubit count)."""
     out = {}
     precs = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "tf32": qst.PREC_TF32, "tf32x2": qst.PREC_TF32X2,
              "pauli": qst.PREC_PAULI}
@@ -259,8 +259,8 @@ def other_configs(qst, W, oracle):
         ms, s = time_handle(qst, prob, precs[form], steps, 5, keep=True)
         out[f"config{c}_{form}"] = {"chains": prob.num_chains, "qubits": prob.num_qubits, "ms_per_step": ms,
                                     "chain_steps_per_s": prob.num_chains / (ms / 1000.0), "steps": steps}
-        if c == 3:
-            out[f"config{c}_{form}"]["logl_err"] = logl_error(qst, oracle, s, prob)
+        # the log L error against the oracle, stated per workload (every form at configuration 3)
+        out[f"config{c}_{form}"]["logl_err"] = logl_error(qst, oracle, s, prob)
         s.close()
     # configuration 5: 64 problems of 1..5 qubits with uneven chain counts in one handle (one
     # launch per kernel and problem per step, replayed as a CUDA graph), mixed form; the plain
@@ -270,7 +270,16 @@ def other_configs(qst, W, oracle):
     ms_mixed = time_handle(qst, batch, qst.PREC_BF16X3, 20, 3)
     ms_plain = time_handle(qst, batch, qst.PREC_FP32, 3, 1)
     ms_pauli = time_handle(qst, batch, qst.PREC_PAULI, 20, 3)
-    ms_auto = time_handle(qst, batch, qst.PREC_AUTO, 20, 3)   # per problem the faster form (timed at creation)
+    # per problem the faster form (timed at creation); the log L error on the chains' states
+    # after 1000 steps, with five qubits on the first-order QR (the default) and refined (qr_passes 4)
+    ms_auto, s5 = time_handle(qst, batch, qst.PREC_AUTO, 20, 3, keep=True)
+    s5.run_chains(1000 - 23)
+    err5 = logl_error_batch(qst, oracle, s5, batch, 32, 1000)
+    s5.close()
+    ms_auto4, s5 = time_handle(qst, batch, qst.PREC_AUTO, 20, 3, keep=True, qr_passes=4)
+    s5.run_chains(1000 - 23)
+    err5_4 = logl_error_batch(qst, oracle, s5, batch, 32, 1000)
+    s5.close()
     # six qubits (D = 64, 46656 projectors): the structured Pauli form is the one that covers it
     p6 = W.six_qubit_problem(num_chains=4096, num_steps=20)
     ms6, s6 = time_handle(qst, p6, qst.PREC_PAULI, 10, 3, keep=True)
@@ -284,22 +293,47 @@ def other_configs(qst, W, oracle):
         "ms_per_step_bf16x3": ms_mixed, "chain_steps_per_s_bf16x3": chains / (ms_mixed / 1000.0),
         "ms_per_step_fp32": ms_plain, "chain_steps_per_s_fp32": chains / (ms_plain / 1000.0),
         "ms_per_step_pauli": ms_pauli, "chain_steps_per_s_pauli": chains / (ms_pauli / 1000.0),
-        "ms_per_step_auto": ms_auto, "chain_steps_per_s_auto": chains / (ms_auto / 1000.0)}
+        "ms_per_step_auto": ms_auto, "chain_steps_per_s_auto": chains / (ms_auto / 1000.0),
+        "logl_err_auto": err5,
+        "ms_per_step_auto_qr4": ms_auto4, "chain_steps_per_s_auto_qr4": chains / (ms_auto4 / 1000.0),
+        "logl_err_auto_qr4": err5_4}
     return out
+
+
+def logl_diffs(qst, oracle, s, prob, nsample=1024, problem=0):
+    """|log L_gpu - log L_oracle| on the current states of up to nsample chains of one problem
+    of the handle (identical y)."""
+    import torch
+    st = s.get_state(problem)
+    nsample = min(nsample, prob.num_chains)
+    idx = np.linspace(0, prob.num_chains - 1, nsample).astype(np.int64)
+    y = st["y"][idx]
+    _, _, ll = s.evaluate(torch.from_numpy(y).cuda(), problem=problem, want_rho=False, want_p=False)
+    torch.cuda.synchronize()
+    _, _, ll_ref = oracle.evaluate(prob, y.astype(np.float64), want_rho=False, want_p=False)
+    return np.abs(ll.cpu().numpy() - ll_ref)
+
+
+def _err_summary(d, sample):
+    return {"max_abs": float(np.max(d)), "median_abs": float(np.median(d)),
+            "frac_le_1e-3": float(np.mean(d <= 1e-3)), "sample": sample}
 
 
 def logl_error(qst, oracle, s, prob, nsample=1024):
     """|log L_gpu - log L_oracle| on the current states of nsample chains (identical y)."""
-    import torch
-    st = s.get_state()
-    idx = np.linspace(0, prob.num_chains - 1, nsample).astype(np.int64)
-    y = st["y"][idx]
-    _, _, ll = s.evaluate(torch.from_numpy(y).cuda(), want_rho=False, want_p=False)
-    torch.cuda.synchronize()
-    _, _, ll_ref = oracle.evaluate(prob, y.astype(np.float64), want_rho=False, want_p=False)
-    d = np.abs(ll.cpu().numpy() - ll_ref)
-    return {"max_abs": float(np.max(d)), "median_abs": float(np.median(d)),
-            "frac_le_1e-3": float(np.mean(d <= 1e-3)), "sample": f"{nsample} chains' current states"}
+    d = logl_diffs(qst, oracle, s, prob, nsample)
+    return _err_summary(d, f"{d.size} chains' current states")
+
+
+def logl_error_batch(qst, oracle, s, probs, per_problem, steps):
+    """The same over a batch handle: per_problem chains of every problem, summarised by qubit
+    count."""
+    by_q = {}
+    for i, p in enumerate(probs):
+        by_q.setdefault(p.num_qubits, []).append(logl_diffs(qst, oracle, s, p, per_problem, problem=i))
+    return {f"{q}_qubits": _err_summary(np.concatenate(v), f"{per_problem} chains of each of {len(v)} problems, "
+                                                            f"current states after {steps} steps")
+            for q, v in sorted(by_q.items())}
 
 
 def cpu_baseline(oracle, prob, seconds_target=15.0):

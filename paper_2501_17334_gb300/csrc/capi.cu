@@ -140,7 +140,7 @@ qst_status validate_cfg(const qst_sampler_cfg *cfg) {
     if (cfg->precision != QST_PREC_FP32 && cfg->precision != QST_PREC_BF16X3 && cfg->precision != QST_PREC_TF32 &&
         cfg->precision != QST_PREC_TF32X2 && cfg->precision != QST_PREC_PAULI && cfg->precision != QST_PREC_AUTO)
         return fail(QST_ERR_INVALID_ARG, "unknown precision %d", cfg->precision);
-    if (cfg->qr_passes < 1 || cfg->qr_passes > 3) return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1, 2 or 3");
+    if (cfg->qr_passes < 1 || cfg->qr_passes > 4) return fail(QST_ERR_INVALID_ARG, "qr_passes must be 1, 2, 3 or 4");
     if (cfg->prior != QST_PRIOR_BURES && cfg->prior != QST_PRIOR_HS)
         return fail(QST_ERR_INVALID_ARG, "unknown prior %d", cfg->prior);
     if (cfg->use_graph != 0 && cfg->use_graph != 1) return fail(QST_ERR_INVALID_ARG, "use_graph must be 0 or 1");
@@ -468,7 +468,10 @@ qst_status make_plan(const qst_problem_desc *probs_in, int32_t n, const qst_samp
         hp.part_slots = v.ngroups;
         for (int g : hp.group_choices) hp.part_slots = std::max(hp.part_slots, g);
         for (int g : hp.tc_group_choices) hp.part_slots = std::max(hp.part_slots, g);
-        v.qr_passes = cfg->prior == QST_PRIOR_HS ? 0 : cfg->qr_passes;   // 0: no QR, W = G
+        // the passes this problem's proposal kernel runs: 0, no QR (W = G); the refinement (3) at
+        // D <= 16, and at D = 32 only when 4 is asked for; D = 64 has the first-order form (2)
+        v.qr_passes = cfg->prior == QST_PRIOR_HS ? 0 : cfg->qr_passes;
+        if (v.qr_passes >= 3) v.qr_passes = (v.D <= 16 || (v.D == 32 && v.qr_passes == 4)) ? 3 : 2;
         // a forced proposal CTA size (only the default QR and the Hilbert-Schmidt prior have the
         // smaller sizes; it must hold at least one chain)
         if (cfg->propose_threads != 0 && v.D <= 16 && (v.qr_passes == 0 || v.qr_passes == 3) &&

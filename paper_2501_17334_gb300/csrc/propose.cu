@@ -951,22 +951,28 @@ __global__ void __launch_bounds__(THREADS, 5 * kThreads / THREADS) propose_kerne
 // ---- five qubits (D = 32): one warp per chain ----------------------------------------------
 // The same algorithm with the same lane ownership (lane j: column j, then row j), but at D = 32 a
 // lane cannot also hold the operand it is multiplied with, so that operand is streamed from
-// shared memory four complex entries (two 128-bit loads) at a time.
-struct Wide {
+// shared memory four complex entries (two 128-bit loads) at a time.  With PASSES = 3 the
+// refinement of U runs as in the D <= 16 kernel (refine_pass); its copy of H and the packed R take
+// 4.2 KB more per chain, so that form runs two chains per CTA (THREADS = 64): five CTAs, ten
+// warps, on an SM.
+template <int PASSES = 2, int THREADS = kThreads>
+struct WideShape {
     static constexpr int D = 32;
     static constexpr int d = D * D;
-    static constexpr int chains_per_block = kThreads / D;   // 4
+    static constexpr int chains_per_block = THREADS / D;
     static constexpr int qcol = D + 4;                      // floats per column of a Q plane
     static constexpr int pk_stride = D + 1;
     static constexpr int area_a = 2 * D * qcol;             // Q planes, then W as two planes of stride qcol
-    static constexpr int area_b = 2 * D * D;                // F planes, then the staged rho (>= D pk_stride)
-    static constexpr int smem_floats = (area_a + area_b + 31) / 32 * 32 + 16;
+    static constexpr int area_b = 2 * D * D;                // F planes (PASSES = 3: H's columns), then the staged rho
+    static constexpr int area_r = (PASSES == 3) ? D * (D + 1) : 0;   // PASSES = 3: packed R
+    static constexpr int smem_floats = (area_a + area_b + area_r + 31) / 32 * 32 + 16;
 };
+using Wide = WideShape<>;
 static_assert(Wide::area_b >= Wide::D * Wide::pk_stride, "areas");
 
-template <int PASSES>
-__global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a) {
-    using S = Wide;
+template <int PASSES, int THREADS = kThreads>
+__global__ void __launch_bounds__(THREADS, 3 * kThreads / THREADS) propose_kernel_d32(ProposeArgs a) {
+    using S = WideShape<PASSES, THREADS>;
     constexpr int D = S::D, d = S::d, nx = 4 * d, QC = S::qcol, PK = S::pk_stride;
     extern __shared__ __align__(16) float smem[];
     const int j = threadIdx.x % D;
@@ -979,6 +985,8 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
     float *wre = sm, *wim = sm + D * QC;                 // W planes (row stride QC), replace Q
     float *fre = sm + S::area_a, *fim = fre + D * D;     // F column-major (stride D), re / im planes
     float *packed = sm + S::area_a;                      // staged rho (row stride PK), replaces F
+    float *hre = sm + S::area_a, *him = hre + D * D;     // PASSES = 3: H's columns (stride D), in area B
+    float2 *rpk = reinterpret_cast<float2 *>(sm + S::area_a + S::area_b);   // PASSES = 3: packed R
 
     // ---- 1. latent proposal (as in the D <= 16 kernel: lane j owns column j of each part) ------
     float coef_y = 1.0f, coef_eta = 0.0f;
@@ -1027,6 +1035,10 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
                 hi[2 * q + 1] = make_float2(yn.z, yn.w);
             }
         }
+    }
+    if constexpr (PASSES == 3) {   // H's original columns, for the refinement after the sweep
+        store_column2<D>(hre + j * D, hr);
+        store_column2<D>(him + j * D, hi);
     }
 
     // ---- 2a. modified Gram-Schmidt, the published column streamed in chunks --------------------
@@ -1084,6 +1096,10 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
                 fim[k * D + j] = -ri * sc;
             }
         }
+        if constexpr (PASSES == 3) {   // R for the refinement's solve, as in the D <= 16 kernel
+            if (j > k) rpk[j * (j + 1) / 2 + k] = make_float2(rr * rs, ri * rs);
+            if (j == k) rpk[k * (k + 1) / 2 + k] = make_float2(nk * rs, rs);
+        }
     }
     if constexpr (PASSES > 0) {   // normalise the own column and publish it
         const float2 sc = make_float2(inv_own, inv_own);
@@ -1096,6 +1112,14 @@ __global__ void __launch_bounds__(kThreads, 3) propose_kernel_d32(ProposeArgs a)
         store_column2<D>(qre + j * QC, hr);
         store_column2<D>(qim + j * QC, hi);
         __syncwarp();
+    }
+
+    if constexpr (PASSES == 3) {
+        // ---- 2b. refinement of Q1 to the QR factor of H beyond FP32 (the D <= 16 kernel's step 2b:
+        // error-free M and N rows per lane, the triangular solve, U = Q1 - Q1 Y^dag, repeated while
+        // the chain's largest |Y| entry exceeds kRefineTol) ----------------------------------------
+        const float ymax = refine_pass<D, QC>(hr, hi, qre, qim, hre, him, rpk, gsrc, j, false, true);
+        if (__any_sync(0xffffffffu, ymax > kRefineTol)) refine_more<D, QC>(qre, qim, hre, him, rpk, gsrc, j, ymax);
     }
 
     if constexpr (PASSES == 2) {
@@ -1624,20 +1648,22 @@ cudaError_t launch_propose_d64(const ProposeArgs &a, cudaStream_t s) {
 
 template <int PASSES>
 cudaError_t launch_propose_d32(const ProposeArgs &a, cudaStream_t s) {
-    using S = Wide;
+    constexpr int THREADS = (PASSES == 3) ? 64 : kThreads;   // two chains per CTA with the refinement
+    using S = WideShape<PASSES, THREADS>;
     const size_t smem = sizeof(float) * S::smem_floats * S::chains_per_block;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(propose_kernel_d32<PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(propose_kernel_d32<PASSES, THREADS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(propose_kernel_d32<PASSES>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(propose_kernel_d32<PASSES, THREADS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t blocks = (a.rows + S::chains_per_block - 1) / S::chains_per_block;
     if (blocks == 0) return cudaSuccess;
-    propose_kernel_d32<PASSES><<<(unsigned)blocks, kThreads, smem, s>>>(a);
+    propose_kernel_d32<PASSES, THREADS><<<(unsigned)blocks, THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1685,14 +1711,14 @@ cudaError_t launch_propose_pd(const ProblemView &p, int mode, uint32_t step, con
     a.step_dev = step_dev;
     a.mode = mode;
     a.d_pad = p.d_pad;
-    // the five- and six-qubit kernels have no refinement: they take the FP32 re-orthogonalisation
+    // the six-qubit kernel has no refinement: it takes the FP32 re-orthogonalisation
     constexpr int WIDE_PASSES = PASSES == 3 ? 2 : PASSES;
     if constexpr (D == 64) {
         if (a.split_out || a.split_tf) return cudaErrorNotSupported;   // no tensor-core form at D = 64
         return launch_propose_d64<WIDE_PASSES>(a, s);
     } else if constexpr (D == 32) {
         if (a.split_tf) return cudaErrorNotSupported;   // the TF32 forms stop at D = 16
-        return launch_propose_d32<WIDE_PASSES>(a, s);
+        return launch_propose_d32<PASSES>(a, s);
     } else {
         // the CTA sizes the autotuner may pick are built for the default QR (3) and the
         // Hilbert-Schmidt prior (0); other settings run 128-thread CTAs

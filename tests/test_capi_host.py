@@ -59,6 +59,9 @@ def test_validation_rejects_bad_inputs(qst):
     assert _status(lambda: qst.workspace_size([prob], qst.default_config(beta0=0.0))) == 1
     assert _status(lambda: qst.workspace_size([prob], qst.default_config(beta0=1.5))) == 1
     assert _status(lambda: qst.workspace_size([prob], qst.default_config(precision=9))) == 1
+    assert _status(lambda: qst.workspace_size([prob], qst.default_config(qr_passes=0))) == 1
+    assert _status(lambda: qst.workspace_size([prob], qst.default_config(qr_passes=5))) == 1
+    assert qst.workspace_size([prob], qst.default_config(qr_passes=4)) > 0   # five qubits refined too
     bad = W.config_problem(2, num_chains=64, num_steps=10)
     bad.counts = bad.counts.copy()
     bad.counts[3] = -1

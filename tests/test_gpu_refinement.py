@@ -43,8 +43,7 @@ def _rows(q, kappas, per, seed):
     return np.array(out, dtype=np.float32)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
-@pytest.mark.parametrize("q", [3, 4])
+@pytest.mark.parametrize("prec,q", [("bf16x3", 3), ("fp32", 3), ("bf16x3", 4), ("fp32", 4), ("bf16x3", 5), ("fp32", 5)])
 def test_ill_conditioned_h_meets_the_parity_bars(qst, oracle_mod, cuda_ok, prec, q):
     import torch
     D = 1 << q
@@ -53,9 +52,10 @@ def test_ill_conditioned_h_meets_the_parity_bars(qst, oracle_mod, cuda_ok, prec,
     H = (x32[:, 2 * D * D:3 * D * D] + 1j * x32[:, 3 * D * D:]).astype(np.complex128).reshape(-1, D, D)
     cond = np.linalg.cond(np.transpose(H, (0, 2, 1)))
     assert cond.min() > 50 and cond.max() > 1e5   # the float32 rows keep their conditioning
-    prob = W.config_problem(q, num_chains=1024, num_steps=1)
+    prob = W.config_problem(q, num_chains=1024, num_steps=1) if q < 5 else W.five_qubit_problem(num_chains=256)
     p = {"bf16x3": qst.PREC_BF16X3, "fp32": qst.PREC_FP32}[prec]
-    s = qst.Sampler(prob, precision=p, diag_chains=0)
+    # five qubits are refined when qr_passes 4 asks for it (the default, 3, refines D <= 16)
+    s = qst.Sampler(prob, precision=p, diag_chains=0, qr_passes=4 if q == 5 else 3)
     rho_p, p_gpu, ll_gpu = s.evaluate(torch.from_numpy(x32).cuda())
     torch.cuda.synchronize()
     rho_gpu = unpack_rho(rho_p.cpu().numpy(), D)
@@ -66,3 +66,22 @@ def test_ill_conditioned_h_meets_the_parity_bars(qst, oracle_mod, cuda_ok, prec,
     err_p = np.abs(p_gpu - p_ref).max(axis=1)
     assert err_rho.max() < 2e-6, (err_rho.max(), cond[np.argmax(err_rho)])
     assert err_p.max() < 1e-6, (err_p.max(), cond[np.argmax(err_p)])
+
+
+def test_five_qubits_default_form_is_unrefined(qst, oracle_mod, cuda_ok):
+    """The default (qr_passes 3) leaves five qubits on the first-order form: on H with cond(H)
+    up to 3e5 its rho misses the bar that qr_passes 4 meets (which shows that 4 reaches the
+    refined kernel and 3 does not)."""
+    import torch
+    D = 32
+    x32 = _rows(5, [1e2, 3e4, 1e5, 3e5], 16, seed=45)
+    prob = W.five_qubit_problem(num_chains=256)
+    rho_ref, _, _ = oracle_mod.evaluate(prob, x32.astype(np.float64), want_p=False)
+    err = {}
+    for passes in (3, 4):
+        s = qst.Sampler(prob, precision=qst.PREC_FP32, diag_chains=0, qr_passes=passes)
+        rho_p, _, _ = s.evaluate(torch.from_numpy(x32).cuda(), want_p=False)
+        torch.cuda.synchronize()
+        s.close()
+        err[passes] = np.abs(unpack_rho(rho_p.cpu().numpy(), D) - rho_ref).max()
+    assert err[4] < 2e-6 < err[3], err
