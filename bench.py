@@ -401,12 +401,12 @@ def run_profile_case(args):
         prob = W.five_qubit_problem(num_chains=args.chains)
     else:
         prob = W.config_problem(CONFIG_INDEX, num_chains=args.chains)
-    s = qst.Sampler(prob, precision=prec, diag_chains=0, autotune=0)
+    s = qst.Sampler(prob, precision=prec, diag_chains=0, autotune=0, qr_passes=args.qr_passes)
     s.run_chains(args.steps)
     s.synchronize()
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": True, "chains": args.chains, "steps": args.steps, "form": args.form,
-                      "qubits": prob.num_qubits}))
+                      "qubits": prob.num_qubits, "qr_passes": args.qr_passes}))
 
 
 def main():
@@ -420,6 +420,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true")
     ap.add_argument("--qubits", type=int, default=4, choices=[4, 5, 6], help="profile case: the 4-qubit "
                     "workload or the six-qubit problem (structured Pauli form)")
+    ap.add_argument("--qr-passes", type=int, default=3, choices=[2, 3, 4],
+                    help="profile case: the QR setting (4: five qubits refined too)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-pauli", action="store_true", help="skip the structured Pauli form")

@@ -135,7 +135,7 @@ typedef struct {
                                to the exact QR factor from Q1^dag H and Q1^dag Q1 formed without
                                rounding error (U within ~2^-24 of the exact factor).  Five and six
                                qubits take 2 when 3 is asked for; 4, as 3 and five qubits refined
-                               too (their proposal kernel then takes about 2.6 times as long; six
+                               too (their proposal kernel then takes about 2.3 times as long; six
                                qubits still take 2) */
     int32_t use_graph;      /* 1 (default): qst_run_chains replays one step captured as a CUDA graph
                                (the step counter lives on the device); 0: plain launches. Kernel

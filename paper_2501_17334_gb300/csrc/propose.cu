@@ -265,6 +265,102 @@ struct ProposeArgs {
     Philox::RoundKeys rk;        // the generator's round keys for `seed`
 };
 
+// The rest of a refinement pass at D >= 32 (the solve, Y's upper part and diagonal, U = Q1 -
+// Q1 Y^dag), with rolled loops and Y's row j kept in place in area B: unrolled over registers, as
+// refine_pass does for D <= 16, the pass is several thousand straight-line instructions at D = 32
+// and the warps stall on instruction fetch.  The arithmetic of each entry is refine_pass's.  Lane j
+// writes only row j of area B: its lower part (read by the other lanes for their upper parts only
+// after the barrier below), then its diagonal and upper part, which no other lane reads.
+template <int D, int QC>
+__device__ __noinline__ float refine_tail_rolled(float *qre, float *qim, float *hre, float *him, const float2 *rpk,
+                                                 int j, float2 mjj, bool apply) {
+    auto cidx = [](int r, int cc) { return cc * D + (r ^ cc); };
+    // forward substitution on row j: entries c < j only (the row has no unknowns beyond)
+#pragma unroll 1
+    for (int c0 = 0; c0 < j; ++c0) {
+        const float inv_r = rpk[c0 * (c0 + 1) / 2 + c0].y;
+        const int o0 = cidx(j, c0);
+        const float ar = hre[o0] * inv_r, ai = him[o0] * inv_r;
+        hre[o0] = ar;
+        him[o0] = ai;
+#pragma unroll 2
+        for (int c = c0 + 1; c < j; ++c) {
+            const float2 r = rpk[c * (c + 1) / 2 + c0];   // R[c0][c]
+            const int o = cidx(j, c);
+            hre[o] -= ar * r.x - ai * r.y;
+            him[o] -= ar * r.y + ai * r.x;
+        }
+    }
+    // diagonal: Re Y_jj = (N_jj - 1) / 2; Im Y_jj makes R_jj real
+    float ydi = mjj.y;
+    float ymax = 0.0f;
+#pragma unroll 1
+    for (int k = 0; k < j; ++k) {
+        const float2 r = rpk[j * (j + 1) / 2 + k];   // R[k][j]
+        const float yr = hre[cidx(j, k)], yi = him[cidx(j, k)];
+        ydi -= yr * r.y + yi * r.x;
+        ymax = fmaxf(ymax, fmaxf(fabsf(yr), fabsf(yi)));
+    }
+    const float2 ydiag = make_float2(0.5f * hre[cidx(j, j)], ydi * rpk[j * (j + 1) / 2 + j].y);
+    __syncwarp();   // every lane's lower row is in place
+    // upper part: Y[j][c] = N_jc - conj(Y[c][j]), c > j, over N_jc
+#pragma unroll 1
+    for (int c = j + 1; c < D; ++c) {
+        const float yr = hre[cidx(j, c)] - hre[cidx(c, j)], yi = him[cidx(j, c)] + him[cidx(c, j)];
+        hre[cidx(j, c)] = yr;
+        him[cidx(j, c)] = yi;
+        ymax = fmaxf(ymax, fmaxf(fabsf(yr), fabsf(yi)));
+    }
+    hre[cidx(j, j)] = ydiag.x;
+    him[cidx(j, j)] = ydiag.y;
+    ymax = fmaxf(ymax, fmaxf(fabsf(ydiag.x), fabsf(ydiag.y)));
+#pragma unroll
+    for (int off = D / 2; off >= 1; off /= 2) ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, off, D));
+    // U = Q1 - Q1 Y^dag: column j is q_j - sum_k q_k conj(Y[j][k]), in two halves of rows as in
+    // refine_pass
+    constexpr int HP = D / 4;   // row pairs per half
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        float2 cr[HP], ci[HP];
+#pragma unroll
+        for (int p = 0; p < HP; ++p) cr[p] = ci[p] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int k = 0; k < D; ++k) {
+            const float ykr = hre[cidx(j, k)], yki = him[cidx(j, k)];
+            const float2 yx = make_float2(ykr, ykr), yy = make_float2(yki, yki), myy = make_float2(-yki, -yki);
+#pragma unroll
+            for (int p = 0; p < HP; p += 2) {   // (vr + i vi)(y.x - i y.y), a 4-float block of rows at a time
+                const int o = k * QC + 2 * (half * HP + p);
+                const float4 r4 = *reinterpret_cast<const float4 *>(qre + o);
+                const float4 i4 = *reinterpret_cast<const float4 *>(qim + o);
+                const float2 vr[2] = {make_float2(r4.x, r4.y), make_float2(r4.z, r4.w)};
+                const float2 vi[2] = {make_float2(i4.x, i4.y), make_float2(i4.z, i4.w)};
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    cr[p + u] = __ffma2_rn(vr[u], yx, __ffma2_rn(vi[u], yy, cr[p + u]));
+                    ci[p + u] = __ffma2_rn(vi[u], yx, __ffma2_rn(vr[u], myy, ci[p + u]));
+                }
+            }
+        }
+        __syncwarp();   // every lane has read this half of every q_k
+        if (apply) {
+#pragma unroll
+            for (int p = 0; p < HP; p += 2) {
+                const int o = j * QC + 2 * (half * HP + p);
+                float4 *ur = reinterpret_cast<float4 *>(qre + o);
+                float4 *ui = reinterpret_cast<float4 *>(qim + o);
+                const float4 u0 = *ur, u1 = *ui;
+                const float2 a0 = sub2(make_float2(u0.x, u0.y), cr[p]), a1 = sub2(make_float2(u0.z, u0.w), cr[p + 1]);
+                const float2 b0 = sub2(make_float2(u1.x, u1.y), ci[p]), b1 = sub2(make_float2(u1.z, u1.w), ci[p + 1]);
+                *ur = make_float4(a0.x, a0.y, a1.x, a1.y);
+                *ui = make_float4(b0.x, b0.y, b1.x, b1.y);
+            }
+        }
+        __syncwarp();
+    }
+    return ymax;
+}
+
 // One first-order pass of the refinement of U (step 2b of the D <= 16 kernel below, where the
 // method is described).  `again`: a pass after the first, which reads H's column j back from y'
 // into area B (it held C) and U's column j as this lane's vector; `apply`: write the refined U
@@ -310,6 +406,7 @@ __device__ __forceinline__ float refine_pass(float2 (&hr)[D / 2], float2 (&hi)[D
     // first chain's row, in bounds, whose result is not used)
     const float2 mjj = sum_products_exact<D>(hr, hi, gsrc + 2 * d + j * D, gsrc + 3 * d + j * D, 192.0f, 0.0f);
     __syncwarp();
+    if constexpr (D >= 32) return refine_tail_rolled<D, QC>(qre, qim, hre, him, rpk, j, mjj, apply);
     // Y, row j, in registers: y[c] = Y[j][c].  Forward substitution, right-looking: after
     // Y[j][c0] = (M_jc0 - ...) / R_c0c0 every later entry of the row takes its share
     // -Y[j][c0] R[c0][c] at once, so each R entry is read once for all lanes; entries at
