@@ -303,13 +303,16 @@ __device__ __noinline__ float refine_tail_rolled(float *qre, float *qim, float *
     }
     const float2 ydiag = make_float2(0.5f * hre[cidx(j, j)], ydi * rpk[j * (j + 1) / 2 + j].y);
     __syncwarp();   // every lane's lower row is in place
-    // upper part: Y[j][c] = N_jc - conj(Y[c][j]), c > j, over N_jc
-#pragma unroll 1
-    for (int c = j + 1; c < D; ++c) {
-        const float yr = hre[cidx(j, c)] - hre[cidx(c, j)], yi = him[cidx(j, c)] + him[cidx(c, j)];
-        hre[cidx(j, c)] = yr;
-        him[cidx(j, c)] = yi;
-        ymax = fmaxf(ymax, fmaxf(fabsf(yr), fabsf(yi)));
+    // upper part: Y[j][c] = N_jc - conj(Y[c][j]), c > j, over N_jc; every lane walks the same c
+    // (its entries (j, c) and (c, j) then lie in distinct banks across the lanes)
+#pragma unroll 2
+    for (int c = 1; c < D; ++c) {
+        if (c > j) {
+            const float yr = hre[cidx(j, c)] - hre[cidx(c, j)], yi = him[cidx(j, c)] + him[cidx(c, j)];
+            hre[cidx(j, c)] = yr;
+            him[cidx(j, c)] = yi;
+            ymax = fmaxf(ymax, fmaxf(fabsf(yr), fabsf(yi)));
+        }
     }
     hre[cidx(j, j)] = ydiag.x;
     him[cidx(j, j)] = ydiag.y;
