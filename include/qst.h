@@ -170,6 +170,8 @@ typedef struct {
     uint32_t propose_chains_per_cta;  /* chains per CTA of the proposal kernel (autotuned at 1-4 qubits) */
     uint32_t accept_chains_per_cta;   /* chains per CTA of the accept kernel (one pooled-sum slot each) */
     int32_t projection_form;          /* qst_precision of the projection in use (QST_PREC_AUTO picks one) */
+    int32_t qr_passes;                /* the QR form this problem's proposal runs (qst_sampler_cfg.qr_passes
+                                         resolved for its size: 3 = refined, 2 = first-order, 0 = none) */
 } qst_diag;
 
 typedef struct qst_handle qst_handle;

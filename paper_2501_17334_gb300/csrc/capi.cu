@@ -1176,7 +1176,9 @@ qst_status qst_diagnostics(qst_handle *h, int32_t problem, qst_diag *out, double
                                                                         ? (int32_t)QST_PREC_BF16X3
                                                                         : h->cfg.precision
                                                  : (int32_t)QST_PREC_FP32;
-    out->propose_chains_per_cta = (uint32_t)(v.D <= 16 ? v.propose_threads / v.D : (v.D == 32 ? 4 : 1));
+    out->propose_chains_per_cta =
+        (uint32_t)(v.D <= 16 ? v.propose_threads / v.D : (v.D == 32 ? (v.qr_passes == 3 ? 2 : 4) : 1));
+    out->qr_passes = v.qr_passes;
     out->accept_chains_per_cta = (uint32_t)v.accept_cpc;
     if (st != QST_OK) return st;
     double bmin = 1e300, bmax = -1e300, bsum = 0.0;

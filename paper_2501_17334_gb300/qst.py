@@ -61,7 +61,7 @@ class Diag(ctypes.Structure):
                 ("acf_lmax", ctypes.c_int32), ("tau_mean", ctypes.c_double), ("tau_max", ctypes.c_double),
                 ("n_eff", ctypes.c_double), ("device_status", ctypes.c_uint32), ("column_groups", ctypes.c_uint32),
                 ("propose_chains_per_cta", ctypes.c_uint32), ("accept_chains_per_cta", ctypes.c_uint32),
-                ("projection_form", ctypes.c_int32)]
+                ("projection_form", ctypes.c_int32), ("qr_passes", ctypes.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}

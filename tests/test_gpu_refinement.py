@@ -82,6 +82,9 @@ def test_five_qubits_default_form_is_unrefined(qst, oracle_mod, cuda_ok):
         s = qst.Sampler(prob, precision=qst.PREC_FP32, diag_chains=0, qr_passes=passes)
         rho_p, _, _ = s.evaluate(torch.from_numpy(x32).cuda(), want_p=False)
         torch.cuda.synchronize()
+        dg = s.diagnostics()
+        # the form the problem runs, and the refined form's two-chain CTAs
+        assert (dg["qr_passes"], dg["propose_chains_per_cta"]) == ((2, 4) if passes == 3 else (3, 2)), dg
         s.close()
         err[passes] = np.abs(unpack_rho(rho_p.cpu().numpy(), D) - rho_ref).max()
     assert err[4] < 2e-6 < err[3], err
