@@ -261,6 +261,8 @@ def other_configs(qst, W, oracle):
                                     "chain_steps_per_s": prob.num_chains / (ms / 1000.0), "steps": steps}
         # the log L error against the oracle, stated per workload (every form at configuration 3)
         out[f"config{c}_{form}"]["logl_err"] = logl_error(qst, oracle, s, prob)
+        if form == "fp32":   # the oracle's own throughput on a bounded sample of the same workload
+            out[f"config{c}_{form}"]["oracle"] = cpu_baseline(oracle, prob, 3.0, label=f"config {c}", max_steps=2000)
         s.close()
     # configuration 5: 64 problems of 1..5 qubits with uneven chain counts in one handle (one
     # launch per kernel and problem per step, replayed as a CUDA graph), mixed form; the plain
@@ -336,7 +338,7 @@ def logl_error_batch(qst, oracle, s, probs, per_problem, steps):
             for q, v in sorted(by_q.items())}
 
 
-def cpu_baseline(oracle, prob, seconds_target=15.0):
+def cpu_baseline(oracle, prob, seconds_target=15.0, label="config 4", max_steps=50):
     """The FP64 oracle (as it stands) on a bounded sample of the workload."""
     nthreads = oracle.num_threads()
     chains = max(16, 16 * nthreads)
@@ -346,12 +348,12 @@ def cpu_baseline(oracle, prob, seconds_target=15.0):
     t1 = time.perf_counter()
     oracle.run(prob, num_chains=chains, num_steps=1)
     per_step = max(time.perf_counter() - t1 - init, 1e-6)
-    steps = int(max(1, min(50, (seconds_target - init) / per_step)))
+    steps = int(max(1, min(max_steps, (seconds_target - init) / per_step)))
     t2 = time.perf_counter()
     oracle.run(prob, num_chains=chains, num_steps=steps)
     total = time.perf_counter() - t2 - init
     return {"value": chains * steps / total, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"config 4 problem, {chains} chains x {steps} steps (FP64 C oracle, OpenMP over chains); "
+            "sample": f"{label} problem, {chains} chains x {steps} steps (FP64 C oracle, OpenMP over chains); "
                       f"the y0 initialisation time is subtracted"}
 
 
