@@ -1287,12 +1287,18 @@ __global__ void __launch_bounds__(THREADS, 3 * kThreads / THREADS) propose_kerne
     float2 wr[D / 2], wi[D / 2];
 #pragma unroll
     for (int p = 0; p < D / 2; ++p) wr[p] = wi[p] = make_float2(0.f, 0.f);
+    // G[k0..k0+3, j] from y' (L2), requested one group ahead of its use
+    float4 g4r_next = make_float4(0.f, 0.f, 0.f, 0.f), g4i_next = g4r_next;
+    if (active && PASSES > 0) {
+        g4r_next = *reinterpret_cast<const float4 *>(gsrc + j * D);
+        g4i_next = *reinterpret_cast<const float4 *>(gsrc + d + j * D);
+    }
 #pragma unroll 1
     for (int k0 = 0; k0 < (PASSES > 0 ? D : 0); k0 += 4) {
-        float4 g4r = make_float4(0.f, 0.f, 0.f, 0.f), g4i = g4r;
-        if (active) {
-            g4r = *reinterpret_cast<const float4 *>(gsrc + j * D + k0);
-            g4i = *reinterpret_cast<const float4 *>(gsrc + d + j * D + k0);
+        const float4 g4r = g4r_next, g4i = g4i_next;
+        if (active && k0 + 4 < D) {
+            g4r_next = *reinterpret_cast<const float4 *>(gsrc + j * D + k0 + 4);
+            g4i_next = *reinterpret_cast<const float4 *>(gsrc + d + j * D + k0 + 4);
         }
         const float gkr[4] = {g4r.x, g4r.y, g4r.z, g4r.w}, gki[4] = {g4i.x, g4i.y, g4i.z, g4i.w};
 #pragma unroll
