@@ -43,8 +43,8 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "b520335b656e6ce98cee64073549f8aae8b168852ff5a5d1926bb6563ffa76bf",
-                "chains": 32768, "bytes": 135.300864e6 + 166.508032e6},
+                "sha256": "91779384943d5883e94c834b00e40ae668d5f307a5cb90e31d57b16a711cbc6c",
+                "chains": 32768, "bytes": 135.3408e6 + 167.00928e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
                 "sha256": "37119239961d9995f5809f45982402867e875058dcd74658ffb9b5d6b4a08518",
