@@ -258,6 +258,77 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
     }
 }
 
+// ---- small problems (D <= 4, at most 32 settings, KD <= 128): one thread per (chain, setting) --
+// The tiled kernel above is several thousand unrolled instructions; for a one- or two-qubit
+// problem its few warps run them once per step from a cold instruction cache (about 40 us per
+// launch at configurations 1 and 2, most of it stalled on instruction fetch).  Here a thread
+// forms its setting's D values q_kl = sum_i A_ri P_i,(kD+l) as one FMA chain over i (d <= 16
+// terms), their deviance terms (compensated, as above), the setting's exact sum S_k and its
+// renormalisation term, and the KP threads of a chain (KP >= K, a power of two, so that a chain's
+// threads share a warp) add their partials in FP64 by shuffles: one partial per chain, the
+// single column group this size has.  P (d x KD floats) is staged in shared memory.
+template <int D, bool POISSON>
+__global__ void __launch_bounds__(256) project_fp32_small_kernel(ProjectArgs a, int K, int KP) {
+    constexpr int d = D * D;
+    extern __shared__ __align__(16) float ps[];
+    const int KD = a.KD;
+    for (int e = threadIdx.x; e < d * KD; e += blockDim.x) ps[e] = a.P[(int64_t)(e / KD) * a.KD_pad + (e % KD)];
+    __syncthreads();
+    const int k = threadIdx.x % KP;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / KP) + threadIdx.x / KP;
+    double v = 0.0;
+    if (row < a.rows && k < K) {
+        float ar[d];
+#pragma unroll
+        for (int i = 0; i < d; i += 4) {
+            const float4 t4 = *reinterpret_cast<const float4 *>(a.A + row * a.d_pad + i);
+            ar[i] = t4.x;
+            ar[i + 1] = t4.y;
+            ar[i + 2] = t4.z;
+            ar[i + 3] = t4.w;
+        }
+        const double t = a.trace[row];
+        const float t_hi = (float)t, t_lo = (float)(t - (double)t_hi);
+        const float inv_tr = a.p_out ? (float)(1.0 / t) : 0.0f;
+        float sum = 0.0f, comp = 0.0f, small = 0.0f, sh = 0.0f, sl = 0.0f;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const int col = k * D + l;
+            float q = 0.0f;
+#pragma unroll
+            for (int i = 0; i < d; ++i) q = __fmaf_rn(ar[i], ps[i * KD + col], q);
+            const float cv = a.cnt[col];
+            if (cv > 0.0f) {   // Kahan: sum - comp
+                const float y = __fmaf_rn(cv, deviance_log(q * a.invf[col]), -comp);
+                const float tt = sum + y;
+                comp = (tt - sum) - y;
+                sum = tt;
+            }
+            const float hq = (q + 12.0f) - 12.0f;   // S_k as an exact pair, as above
+            sh += hq;
+            sl += q - hq;
+            if (a.p_out) a.p_out[row * KD + col] = q * inv_tr;
+        }
+        if constexpr (POISSON) {   // -mu_k (S_k / t - 1)
+            float ph, pl;
+            poisson_setting(a.ptot[k], sh, sl, t_hi, t_lo, ph, pl);
+            const float y = -ph - comp;
+            const float tt = sum + y;
+            comp = (tt - sum) - y;
+            sum = tt;
+            small -= pl;
+        } else {   // -P_k log(S_k / t)
+            const float rel = ((sh - t_hi) + (sl - t_lo)) / t_hi;
+            const float l1p = fabsf(rel) < 0x1p-10f ? rel * __fmaf_rn(rel, __fmaf_rn(rel, 0.33333334f, -0.5f), 1.0f)
+                                                    : log1pf(rel);
+            small -= a.ptot[k] * l1p;
+        }
+        v = ((double)sum - (double)comp) + (double)small;
+    }
+    for (int off = 1; off < KP; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (k == 0 && row < a.rows) a.out[row] = v;
+}
+
 }  // namespace
 
 int fp32_ngroups(const ProblemView &p, int64_t rows) {
@@ -307,6 +378,21 @@ cudaError_t launch_project_fp32(const ProblemView &p, const float *A, int64_t ro
     a.KD = p.KD;
     a.KD_pad = p.KD_pad;
     a.poisson = p.poisson;
+    const int K = p.KD / p.D;
+    if (p.D <= 4 && p.KD <= 128 && K <= 32 && p.ngroups == 1) {   // one column group: the small kernel
+        int KP = 1;
+        while (KP < K) KP <<= 1;
+        const unsigned blocks = (unsigned)((rows + (256 / KP) - 1) / (256 / KP));
+        const size_t smem = sizeof(float) * (size_t)p.D * p.D * p.KD;
+        if (p.D == 2) {
+            if (a.poisson) project_fp32_small_kernel<2, true><<<blocks, 256, smem, s>>>(a, K, KP);
+            else project_fp32_small_kernel<2, false><<<blocks, 256, smem, s>>>(a, K, KP);
+        } else {
+            if (a.poisson) project_fp32_small_kernel<4, true><<<blocks, 256, smem, s>>>(a, K, KP);
+            else project_fp32_small_kernel<4, false><<<blocks, 256, smem, s>>>(a, K, KP);
+        }
+        return cudaGetLastError();
+    }
     const int nt = p.KD_pad / BN;
     const int groups = p.ngroups;
     a.tiles_per_group = (nt + groups - 1) / groups;
