@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) project_fp32_kernel(ProjectArgs a) {
 // ---- small problems (D <= 4, at most 32 settings, KD <= 128): one thread per (chain, setting) --
 // The tiled kernel above is several thousand unrolled instructions; for a one- or two-qubit
 // problem its few warps run them once per step from a cold instruction cache (about 40 us per
-// launch at configurations 1 and 2, most of it stalled on instruction fetch).  Here a thread
+// launch for 64 one-qubit or 4096 two-qubit chains, most of it stalled on instruction fetch).  Here a thread
 // forms its setting's D values q_kl = sum_i A_ri P_i,(kD+l) as one FMA chain over i (d <= 16
 // terms), their deviance terms (compensated, as above), the setting's exact sum S_k and its
 // renormalisation term, and the KP threads of a chain (KP >= K, a power of two, so that a chain's

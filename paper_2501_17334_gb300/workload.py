@@ -224,7 +224,7 @@ def six_qubit_problem(num_chains: int = 64, num_steps: int = 50, seed: int = 100
 
 def heterogeneous_batch(num_problems: int = 64, seed: int = 1005, max_qubits: int = 5,
                         chain_scale: float = 1.0) -> List[Problem]:
-    """Batch of independent problems of uneven size (configuration 5).
+    """Batch of independent problems of uneven size (64 problems of 1-5 qubits by default).
 
     Qubits uniform in 1..max_qubits, shots per basis uniform in 500..4000, Ginibre truth of
     rank uniform in 1..D, chain counts log-uniform in [256, 32768] (times ``chain_scale``).
