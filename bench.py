@@ -248,8 +248,8 @@ def time_handle(qst, probs, precision, steps, warmup, keep=False, **cfg):
 
 def other_configs(qst, W, oracle):
     """The other workloads, measured briefly (one handle each; chain state resident), each with
-    its log L error against the oracle on up to 1024 of its chains' current states (at
-    configuration 3 for every form of the projection; at configuration 5 by qubit count)."""
+    its log L error against the oracle on up to 1024 of its chains' current states (for every
+    form of the projection at three qubits; by qubit count for the batch of 64 problems)."""
     out = {}
     precs = {"fp32": qst.PREC_FP32, "bf16x3": qst.PREC_BF16X3, "tf32": qst.PREC_TF32, "tf32x2": qst.PREC_TF32X2,
              "pauli": qst.PREC_PAULI}
@@ -259,12 +259,12 @@ def other_configs(qst, W, oracle):
         ms, s = time_handle(qst, prob, precs[form], steps, 5, keep=True)
         out[f"config{c}_{form}"] = {"chains": prob.num_chains, "qubits": prob.num_qubits, "ms_per_step": ms,
                                     "chain_steps_per_s": prob.num_chains / (ms / 1000.0), "steps": steps}
-        # the log L error against the oracle, stated per workload (every form at configuration 3)
+        # the log L error against the oracle, stated per workload (every form at three qubits)
         out[f"config{c}_{form}"]["logl_err"] = logl_error(qst, oracle, s, prob)
         if form == "fp32":   # the oracle's own throughput on a bounded sample of the same workload
             out[f"config{c}_{form}"]["oracle"] = cpu_baseline(oracle, prob, 3.0, label=f"config {c}", max_steps=2000)
         s.close()
-    # configuration 5: 64 problems of 1..5 qubits with uneven chain counts in one handle (one
+    # 64 problems of 1..5 qubits with uneven chain counts in one handle (one
     # launch per kernel and problem per step, replayed as a CUDA graph), mixed form; the plain
     # FP32 form on the same batch for comparison (few steps: its 5-qubit projections are slow)
     batch = W.heterogeneous_batch(64)
