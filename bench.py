@@ -43,8 +43,8 @@ WORKLOAD = ("config 4: 4-qubit Pauli QST (D=16, 81 bases x 16 outcomes = 1296 pr
 NCU_TRAFFIC = {
     # profiles/propose_kernel_config4.md
     "propose": {"source": "paper_2501_17334_gb300/csrc/propose.cu",
-                "sha256": "91779384943d5883e94c834b00e40ae668d5f307a5cb90e31d57b16a711cbc6c",
-                "chains": 32768, "bytes": 135.3408e6 + 167.00928e6},
+                "sha256": "8c10ac52736ae4c95d48aa85a8f92c4c6980c58d0d6d7839ae7fbc33d7af46a4",
+                "chains": 32768, "bytes": 135.274752e6 + 166.74688e6},
     # profiles/project_tc_kernel_config4.md
     "project": {"source": "paper_2501_17334_gb300/csrc/project_tc.cu",
                 "sha256": "37119239961d9995f5809f45982402867e875058dcd74658ffb9b5d6b4a08518",
