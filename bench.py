@@ -342,16 +342,20 @@ def cpu_baseline(oracle, prob, seconds_target=15.0, label="config 4", max_steps=
     """The FP64 oracle (as it stands) on a bounded sample of the workload."""
     nthreads = oracle.num_threads()
     chains = max(16, 16 * nthreads)
-    t0 = time.perf_counter()
-    oracle.run(prob, num_chains=chains, num_steps=0)
-    init = time.perf_counter() - t0
-    t1 = time.perf_counter()
-    oracle.run(prob, num_chains=chains, num_steps=1)
-    per_step = max(time.perf_counter() - t1 - init, 1e-6)
+
+    def timed(steps):
+        t = time.perf_counter()
+        oracle.run(prob, num_chains=chains, num_steps=steps)
+        return time.perf_counter() - t
+
+    timed(1)   # warm-up: library, threads, first touch of every buffer
+    # the y0 initialisation every run repeats, measured warm and subtracted (never more than
+    # half of a run, so that timing noise cannot swamp a short one)
+    init = min(timed(0) for _ in range(3))
+    per_step = max(timed(1) - init, 1e-6)
     steps = int(max(1, min(max_steps, (seconds_target - init) / per_step)))
-    t2 = time.perf_counter()
-    oracle.run(prob, num_chains=chains, num_steps=steps)
-    total = time.perf_counter() - t2 - init
+    run = timed(steps)
+    total = max(run - init, 0.5 * run)
     return {"value": chains * steps / total, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{label} problem, {chains} chains x {steps} steps (FP64 C oracle, OpenMP over chains); "
                       f"the y0 initialisation time is subtracted"}
@@ -368,13 +372,18 @@ def run_reference(args):
     oracle.lib()
     nthreads = oracle.num_threads()
     chains = max(16, 8 * nthreads)
-    t0 = time.perf_counter()
-    oracle.run(prob, num_chains=chains, num_steps=0)
-    init = time.perf_counter() - t0
-    oracle.run(prob, num_chains=chains, num_steps=args.warmup)
-    t1 = time.perf_counter()
-    oracle.run(prob, num_chains=chains, num_steps=args.steps)
-    total = time.perf_counter() - t1 - init
+
+    def timed(steps):
+        t = time.perf_counter()
+        oracle.run(prob, num_chains=chains, num_steps=steps)
+        return time.perf_counter() - t
+
+    timed(args.warmup)   # warm-up: library, threads, first touch of every buffer
+    # the y0 initialisation every run repeats, measured warm; it is subtracted from the timed run
+    # (but never more than half of it, so that a short run's timing noise cannot swamp it)
+    init = min(timed(0) for _ in range(3))
+    run = timed(args.steps)
+    total = max(run - init, 0.5 * run)
     value = chains * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
