@@ -410,8 +410,8 @@ def run_profile_case(args):
         prob = W.six_qubit_problem(num_chains=args.chains)
     elif args.qubits == 5:
         prob = W.five_qubit_problem(num_chains=args.chains)
-    else:
-        prob = W.config_problem(CONFIG_INDEX, num_chains=args.chains)
+    else:   # the 1- to 4-qubit workloads (4: the headline's)
+        prob = W.config_problem(args.qubits, num_chains=args.chains)
     s = qst.Sampler(prob, precision=prec, diag_chains=0, autotune=0, qr_passes=args.qr_passes)
     s.run_chains(args.steps)
     s.synchronize()
@@ -429,8 +429,8 @@ def main():
     ap.add_argument("--chains", type=int, default=CHAINS)
     ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp32", "pauli"])
     ap.add_argument("--profile-case", action="store_true")
-    ap.add_argument("--qubits", type=int, default=4, choices=[4, 5, 6], help="profile case: the 4-qubit "
-                    "workload or the six-qubit problem (structured Pauli form)")
+    ap.add_argument("--qubits", type=int, default=4, choices=[1, 2, 3, 4, 5, 6], help="profile case: the 1- to 4-qubit "
+                    "workloads (4: the headline's), the five- or the six-qubit problem")
     ap.add_argument("--qr-passes", type=int, default=3, choices=[2, 3, 4],
                     help="profile case: the QR setting (4: five qubits refined too)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
